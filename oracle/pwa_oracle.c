@@ -1,0 +1,424 @@
+/*
+ * FP64 CPU oracle for the partial wave analysis likelihood.
+ *
+ * TEST INFRASTRUCTURE, not part of the library: only the tests, the smoke
+ * check and the CPU-baseline leg of the benchmark load it. It shares no code,
+ * header or table with the CUDA path. Every function is a plain, slow,
+ * literal statement of the paper's definitions in double precision with
+ * Neumaier-compensated sums, so that it can be checked against the paper by
+ * eye:
+ *
+ *   Eq. 1   I(Omega) = | sum_alpha V_alpha A_alpha(Omega) |^2
+ *   Eq. 3   -ln L = - sum_i ln( sum_{alpha,alpha'} V_alpha V*_alpha' A_alpha(i) A*_alpha'(i) )
+ *                   + sum_{alpha,alpha'} V_alpha V*_alpha' (1/N_gen) sum_{j in Acc} A_alpha(j) A*_alpha'(j)
+ *   Sec. 2 (after Eq. 3): with masses and widths fixed, the MC bracket and
+ *           the per-event products A_alpha A*_alpha' can be precomputed
+ *           (the "table form").
+ *
+ * Conventions (one reading of Eq. 3, fixed here):
+ *   M[a][b] = (1/N_gen) sum_j conj(A_a(j)) A_b(j), so that the normalisation
+ *   term equals V^H M V = (1/N_gen) sum_j |S_j|^2 with S_j = sum_a V_a A_a(j).
+ *   This is the paper's double sum in Eq. 3 written with the conjugate on the
+ *   other index pair; both give the same real number because the double sum
+ *   is a Hermitian form.
+ *   The gradient is the Wirtinger derivative g_a = dNLL/dV*_a
+ *     = - sum_i conj(A_a(i)) S_i / I_i + (M V)_a.
+ *   An intensity that is not positive and finite makes the evaluation
+ *   undefined: the call reports status 1, NLL = +inf and a zero gradient.
+ *
+ * Layouts: complex numbers are interleaved (re, im) doubles.
+ *   Amplitudes: event-major A[(i*N + a)*2 + {0,1}].
+ *   Table: event-major T[i*N*N + p] with p = a for the real diagonal
+ *   |A_a|^2, then for each pair a < b in row-major order the two reals
+ *   Re(A_a conj A_b), Im(A_a conj A_b).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ---- Neumaier summation ---------------------------------------------- */
+typedef struct { double s, c; } nsum;
+
+static void nadd(nsum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x))
+        a->c += (a->s - t) + x;
+    else
+        a->c += (x - t) + a->s;
+    a->s = t;
+}
+
+static double nval(const nsum *a) { return a->s + a->c; }
+
+/* complex helpers on interleaved doubles */
+static void cmul(double ar, double ai, double br, double bi, double *r, double *i)
+{
+    *r = ar * br - ai * bi;
+    *i = ar * bi + ai * br;
+}
+
+/* ---- Eq. 1: coherent intensity per event ------------------------------ */
+/* I[i] = |sum_a V_a A_a(i)|^2 for one parameter set V. */
+void oracle_intensity(const double *A, int64_t n, int N, const double *V, double *I)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        nsum sr = {0, 0}, si = {0, 0};
+        for (int a = 0; a < N; ++a) {
+            double pr, pi;
+            cmul(V[2 * a], V[2 * a + 1], A[(i * N + a) * 2], A[(i * N + a) * 2 + 1], &pr, &pi);
+            nadd(&sr, pr);
+            nadd(&si, pi);
+        }
+        double r = nval(&sr), im = nval(&si);
+        I[i] = r * r + im * im;
+    }
+}
+
+/* ---- Normalisation matrix (Eq. 3, inner bracket of the second term) --- */
+/* M[a][b] = (1/n_gen) sum_{j < n_acc} conj(A_a(j)) A_b(j), all N x N entries. */
+int oracle_norm_matrix(const double *A, int64_t n_acc, int N, double n_gen, double *M)
+{
+    if (N <= 0 || n_acc < 0 || !(n_gen > 0))
+        return -1;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            nsum re = {0, 0}, im = {0, 0};
+            for (int64_t j = 0; j < n_acc; ++j) {
+                double xr = A[(j * N + a) * 2], xi = -A[(j * N + a) * 2 + 1];
+                double yr = A[(j * N + b) * 2], yi = A[(j * N + b) * 2 + 1];
+                double pr, pi;
+                cmul(xr, xi, yr, yi, &pr, &pi);
+                nadd(&re, pr);
+                nadd(&im, pi);
+            }
+            M[(a * N + b) * 2] = nval(&re) / n_gen;
+            M[(a * N + b) * 2 + 1] = nval(&im) / n_gen;
+        }
+    return 0;
+}
+
+/* Normalisation term V^H M V (real part; the imaginary part of a Hermitian
+ * form vanishes) and the vector M V. */
+void oracle_norm_term(const double *M, int N, const double *V, double *nv, double *MV)
+{
+    nsum q = {0, 0};
+    for (int a = 0; a < N; ++a) {
+        nsum r = {0, 0}, im = {0, 0};
+        for (int b = 0; b < N; ++b) {
+            double pr, pi;
+            cmul(M[(a * N + b) * 2], M[(a * N + b) * 2 + 1], V[2 * b], V[2 * b + 1], &pr, &pi);
+            nadd(&r, pr);
+            nadd(&im, pi);
+        }
+        double mr = nval(&r), mi = nval(&im);
+        if (MV) {
+            MV[2 * a] = mr;
+            MV[2 * a + 1] = mi;
+        }
+        /* conj(V_a) * (M V)_a, real part */
+        nadd(&q, V[2 * a] * mr + V[2 * a + 1] * mi);
+    }
+    *nv = nval(&q);
+}
+
+/* ---- Eq. 3, amplitude form -------------------------------------------- */
+/* For each of K parameter sets V[k][N]: nll[k] and, if grad != NULL,
+ * grad[k][N] (complex) = dNLL/dV*. Returns the number of parameter sets
+ * whose evaluation hit a non-positive or non-finite intensity. */
+int oracle_nll_amp(const double *A, int64_t n, int N, const double *M,
+                   const double *V, int K, double *nll, double *grad)
+{
+    int bad_sets = 0;
+    nsum *gr = (nsum *)malloc(sizeof(nsum) * 2 * (size_t)N);
+    double *mv = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    for (int k = 0; k < K; ++k) {
+        const double *v = V + (size_t)k * 2 * N;
+        nsum lnsum = {0, 0};
+        int bad = 0;
+        memset(gr, 0, sizeof(nsum) * 2 * (size_t)N);
+        for (int64_t i = 0; i < n && !bad; ++i) {
+            nsum sr = {0, 0}, si = {0, 0};
+            for (int a = 0; a < N; ++a) {
+                double pr, pi;
+                cmul(v[2 * a], v[2 * a + 1], A[(i * N + a) * 2], A[(i * N + a) * 2 + 1], &pr, &pi);
+                nadd(&sr, pr);
+                nadd(&si, pi);
+            }
+            double s_r = nval(&sr), s_i = nval(&si);
+            double I = s_r * s_r + s_i * s_i;
+            if (!(I > 0) || !isfinite(I)) {
+                bad = 1;
+                break;
+            }
+            nadd(&lnsum, log(I));
+            if (grad) {
+                /* conj(A_a) * S / I */
+                double rr = s_r / I, ri = s_i / I;
+                for (int a = 0; a < N; ++a) {
+                    double xr = A[(i * N + a) * 2], xi = -A[(i * N + a) * 2 + 1];
+                    double pr, pi;
+                    cmul(xr, xi, rr, ri, &pr, &pi);
+                    nadd(&gr[2 * a], pr);
+                    nadd(&gr[2 * a + 1], pi);
+                }
+            }
+        }
+        double nv;
+        oracle_norm_term(M, N, v, &nv, mv);
+        if (bad) {
+            ++bad_sets;
+            nll[k] = INFINITY;
+            if (grad)
+                memset(grad + (size_t)k * 2 * N, 0, sizeof(double) * 2 * (size_t)N);
+            continue;
+        }
+        nll[k] = -nval(&lnsum) + nv;
+        if (grad)
+            for (int c = 0; c < 2 * N; ++c)
+                grad[(size_t)k * 2 * N + c] = -nval(&gr[c]) + mv[c];
+    }
+    free(gr);
+    free(mv);
+    return bad_sets;
+}
+
+/* ---- Precomputed per-event table (Sec. 2, after Eq. 3) ---------------- */
+int oracle_table(const double *A, int64_t n, int N, double *T)
+{
+    const int64_t P = (int64_t)N * N;
+    for (int64_t i = 0; i < n; ++i) {
+        double *t = T + i * P;
+        for (int a = 0; a < N; ++a) {
+            double ar = A[(i * N + a) * 2], ai = A[(i * N + a) * 2 + 1];
+            t[a] = ar * ar + ai * ai;
+        }
+        int p = N;
+        for (int a = 0; a < N; ++a)
+            for (int b = a + 1; b < N; ++b) {
+                double pr, pi;
+                cmul(A[(i * N + a) * 2], A[(i * N + a) * 2 + 1],
+                     A[(i * N + b) * 2], -A[(i * N + b) * 2 + 1], &pr, &pi);
+                t[p++] = pr;
+                t[p++] = pi;
+            }
+    }
+    return 0;
+}
+
+/* Element [a][b] of the Hermitian per-event matrix T_ab = A_a conj(A_b),
+ * read back from the stored upper triangle. */
+static void table_entry(const double *t, int N, int a, int b, double *re, double *im)
+{
+    if (a == b) {
+        *re = t[a];
+        *im = 0;
+        return;
+    }
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    /* position of pair (lo, hi) among the row-major pairs lo < hi */
+    int idx = lo * N - lo * (lo + 1) / 2 + (hi - lo - 1);
+    double r = t[N + 2 * idx], i = t[N + 2 * idx + 1];
+    *re = r;
+    *im = (a < b) ? i : -i;
+}
+
+/* Eq. 3 evaluated on the table: I_i = sum_{a,b} V_a conj(V_b) T_i[a][b],
+ * g_a = - sum_i (1/I_i) sum_b V_b T_i[b][a] + (M V)_a. */
+int oracle_nll_table(const double *T, int64_t n, int N, const double *M,
+                     const double *V, int K, double *nll, double *grad)
+{
+    const int64_t P = (int64_t)N * N;
+    int bad_sets = 0;
+    nsum *gr = (nsum *)malloc(sizeof(nsum) * 2 * (size_t)N);
+    double *mv = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    for (int k = 0; k < K; ++k) {
+        const double *v = V + (size_t)k * 2 * N;
+        nsum lnsum = {0, 0};
+        int bad = 0;
+        memset(gr, 0, sizeof(nsum) * 2 * (size_t)N);
+        for (int64_t i = 0; i < n && !bad; ++i) {
+            const double *t = T + i * P;
+            nsum Is = {0, 0};
+            for (int a = 0; a < N; ++a)
+                for (int b = 0; b < N; ++b) {
+                    double tr, ti, pr, pi, qr, qi;
+                    table_entry(t, N, a, b, &tr, &ti);
+                    cmul(v[2 * a], v[2 * a + 1], v[2 * b], -v[2 * b + 1], &pr, &pi);
+                    cmul(pr, pi, tr, ti, &qr, &qi);
+                    nadd(&Is, qr);
+                }
+            double I = nval(&Is);
+            if (!(I > 0) || !isfinite(I)) {
+                bad = 1;
+                break;
+            }
+            nadd(&lnsum, log(I));
+            if (grad)
+                for (int a = 0; a < N; ++a)
+                    for (int b = 0; b < N; ++b) {
+                        double tr, ti, pr, pi;
+                        table_entry(t, N, b, a, &tr, &ti);
+                        cmul(v[2 * b], v[2 * b + 1], tr, ti, &pr, &pi);
+                        nadd(&gr[2 * a], pr / I);
+                        nadd(&gr[2 * a + 1], pi / I);
+                    }
+        }
+        double nv;
+        oracle_norm_term(M, N, v, &nv, mv);
+        if (bad) {
+            ++bad_sets;
+            nll[k] = INFINITY;
+            if (grad)
+                memset(grad + (size_t)k * 2 * N, 0, sizeof(double) * 2 * (size_t)N);
+            continue;
+        }
+        nll[k] = -nval(&lnsum) + nv;
+        if (grad)
+            for (int c = 0; c < 2 * N; ++c)
+                grad[(size_t)k * 2 * N + c] = -nval(&gr[c]) + mv[c];
+    }
+    free(gr);
+    free(mv);
+    return bad_sets;
+}
+
+/* ---- Free resonance parameters ----------------------------------------- */
+/* When masses and widths are fit parameters the precompute of Sec. 2 no
+ * longer holds: the amplitudes of the free waves are re-evaluated from the
+ * event's mass and the MC term is summed directly each call.
+ *
+ * Waves 0..R-1 are free: A_r(i) = BW(m_i; mass_r, width_r) * Y_r(i) with
+ * BW(m; M, G) = 1 / (M^2 - m^2 - i M G). Waves R..N-1 are fixed:
+ * A_{R+f}(i) = Afix[i][f]. Y is [n][R] complex, Afix is [n][N-R] complex.
+ *
+ * NLL(V, mass, width) = - sum_i ln I_i + (1/n_gen) sum_{j in MC} I_j.
+ * Outputs: nll, gV[N] complex (dNLL/dV*), gM[R], gW[R] (real derivatives). */
+static void bw_and_derivs(double m, double M, double G, double *bw, double *dM, double *dG)
+{
+    /* BW = 1/(M^2 - m^2 - i M G);  dBW/dM = -(2M - i G) BW^2;  dBW/dG = i M BW^2 */
+    double dr = M * M - m * m, di = -M * G;
+    double den = dr * dr + di * di;
+    double br = dr / den, bi = -di / den;
+    double b2r, b2i;
+    cmul(br, bi, br, bi, &b2r, &b2i);
+    bw[0] = br;
+    bw[1] = bi;
+    double pr, pi;
+    cmul(-2.0 * M, G, b2r, b2i, &pr, &pi);
+    dM[0] = pr;
+    dM[1] = pi;
+    cmul(0.0, M, b2r, b2i, &pr, &pi);
+    dG[0] = pr;
+    dG[1] = pi;
+}
+
+static void res_amp(int64_t i, int N, int R, const double *m, const double *Y, const double *Afix,
+                    const double *mass, const double *width, double *A, double *dAM, double *dAG)
+{
+    for (int r = 0; r < R; ++r) {
+        double bw[2], dM[2], dG[2];
+        bw_and_derivs(m[i], mass[r], width[r], bw, dM, dG);
+        double yr = Y[(i * R + r) * 2], yi = Y[(i * R + r) * 2 + 1];
+        cmul(bw[0], bw[1], yr, yi, &A[2 * r], &A[2 * r + 1]);
+        cmul(dM[0], dM[1], yr, yi, &dAM[2 * r], &dAM[2 * r + 1]);
+        cmul(dG[0], dG[1], yr, yi, &dAG[2 * r], &dAG[2 * r + 1]);
+    }
+    for (int f = 0; f < N - R; ++f) {
+        A[2 * (R + f)] = Afix[(i * (N - R) + f) * 2];
+        A[2 * (R + f) + 1] = Afix[(i * (N - R) + f) * 2 + 1];
+    }
+}
+
+/* One pass over a sample: accumulates sum ln I (if lnsum), or sum I (if isum),
+ * and the derivative sums. weight multiplies each event's contribution to the
+ * gradients: -1/I_i for data, +1/n_gen for MC. */
+static int res_pass(int64_t n, int N, int R, const double *m, const double *Y, const double *Afix,
+                    const double *mass, const double *width, const double *V, int data,
+                    nsum *acc, nsum *gV, nsum *gM, nsum *gW)
+{
+    double *A = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    double *dAM = (double *)malloc(sizeof(double) * 2 * (size_t)(R > 0 ? R : 1));
+    double *dAG = (double *)malloc(sizeof(double) * 2 * (size_t)(R > 0 ? R : 1));
+    int bad = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        res_amp(i, N, R, m, Y, Afix, mass, width, A, dAM, dAG);
+        nsum sr = {0, 0}, si = {0, 0};
+        for (int a = 0; a < N; ++a) {
+            double pr, pi;
+            cmul(V[2 * a], V[2 * a + 1], A[2 * a], A[2 * a + 1], &pr, &pi);
+            nadd(&sr, pr);
+            nadd(&si, pi);
+        }
+        double s_r = nval(&sr), s_i = nval(&si);
+        double I = s_r * s_r + s_i * s_i;
+        double w;
+        if (data) {
+            if (!(I > 0) || !isfinite(I)) {
+                bad = 1;
+                break;
+            }
+            nadd(acc, log(I));
+            w = -1.0 / I;
+        } else {
+            nadd(acc, I);
+            w = 1.0;
+        }
+        /* dI/dV*_a = conj(A_a) S ; dI/dp = 2 Re(conj(S) V_r dA_r/dp) */
+        for (int a = 0; a < N; ++a) {
+            double pr, pi;
+            cmul(A[2 * a], -A[2 * a + 1], s_r, s_i, &pr, &pi);
+            nadd(&gV[2 * a], w * pr);
+            nadd(&gV[2 * a + 1], w * pi);
+        }
+        for (int r = 0; r < R; ++r) {
+            double vr, vi, pr, pi;
+            cmul(V[2 * r], V[2 * r + 1], dAM[2 * r], dAM[2 * r + 1], &vr, &vi);
+            cmul(s_r, -s_i, vr, vi, &pr, &pi);
+            nadd(&gM[r], w * 2.0 * pr);
+            cmul(V[2 * r], V[2 * r + 1], dAG[2 * r], dAG[2 * r + 1], &vr, &vi);
+            cmul(s_r, -s_i, vr, vi, &pr, &pi);
+            nadd(&gW[r], w * 2.0 * pr);
+        }
+    }
+    free(A);
+    free(dAM);
+    free(dAG);
+    return bad;
+}
+
+int oracle_nll_res(int N, int R,
+                   const double *m_d, const double *Y_d, const double *Afix_d, int64_t n_d,
+                   const double *m_mc, const double *Y_mc, const double *Afix_mc, int64_t n_mc,
+                   double n_gen, const double *V, const double *mass, const double *width,
+                   double *nll, double *gV, double *gM, double *gW)
+{
+    if (R < 0 || R > N || !(n_gen > 0))
+        return -1;
+    nsum *gVd = (nsum *)calloc(2 * (size_t)N, sizeof(nsum));
+    nsum *gVm = (nsum *)calloc(2 * (size_t)N, sizeof(nsum));
+    nsum *gMd = (nsum *)calloc((size_t)R + 1, sizeof(nsum));
+    nsum *gMm = (nsum *)calloc((size_t)R + 1, sizeof(nsum));
+    nsum *gWd = (nsum *)calloc((size_t)R + 1, sizeof(nsum));
+    nsum *gWm = (nsum *)calloc((size_t)R + 1, sizeof(nsum));
+    nsum lnsum = {0, 0}, isum = {0, 0};
+    int bad = res_pass(n_d, N, R, m_d, Y_d, Afix_d, mass, width, V, 1, &lnsum, gVd, gMd, gWd);
+    res_pass(n_mc, N, R, m_mc, Y_mc, Afix_mc, mass, width, V, 0, &isum, gVm, gMm, gWm);
+    if (bad) {
+        *nll = INFINITY;
+        memset(gV, 0, sizeof(double) * 2 * (size_t)N);
+        memset(gM, 0, sizeof(double) * (size_t)R);
+        memset(gW, 0, sizeof(double) * (size_t)R);
+    } else {
+        *nll = -nval(&lnsum) + nval(&isum) / n_gen;
+        for (int c = 0; c < 2 * N; ++c)
+            gV[c] = nval(&gVd[c]) + nval(&gVm[c]) / n_gen;
+        for (int r = 0; r < R; ++r) {
+            gM[r] = nval(&gMd[r]) + nval(&gMm[r]) / n_gen;
+            gW[r] = nval(&gWd[r]) + nval(&gWm[r]) / n_gen;
+        }
+    }
+    free(gVd); free(gVm); free(gMd); free(gMm); free(gWd); free(gWm);
+    return bad;
+}

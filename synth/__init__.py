@@ -1,0 +1,246 @@
+"""Seeded synthetic inputs for the partial wave analysis likelihood.
+
+This module only draws events and evaluates the physics amplitude model
+(Breit-Wigner line shape x spherical harmonic) that both the oracle and the
+CUDA path consume. It holds none of the likelihood's arithmetic: it never
+forms a coherent sum over waves, an intensity, a logarithm or a normalisation
+integral.
+
+Phase space follows the radiative decay J/psi -> gamma X, X -> K+ K- used as
+the example of Sec. 2: each event is (m_KK, cos theta, phi) with m_KK uniform
+in [0.98, 3.0] GeV, cos theta uniform in [-1, 1] and phi uniform in [0, 2 pi).
+The detector efficiency is eps = 0.6 + 0.3 cos theta; accepted Monte Carlo is
+drawn by keeping a uniformly generated candidate with probability eps, and the
+number of candidates drawn is N_MC^Gen (Sec. 2, the text after Eq. 2).
+
+Amplitudes: A_alpha(Omega) = BW(m; M_alpha, Gamma_alpha) * Y_{l_alpha}^{m_alpha}
+(cos theta, phi) with the fixed-width Breit-Wigner 1 / (M^2 - m^2 - i M Gamma)
+and orthonormal spherical harmonics carrying the Condon-Shortley phase.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+M_LO, M_HI = 0.98, 3.0
+EFF_MAX = 0.9
+
+SEED_DATA = 1108
+SEED_MC = 5673
+SEED_VTRUE = 42
+SEED_STARTS = 7
+
+
+@dataclass(frozen=True)
+class Wave:
+    mass: float
+    width: float
+    l: int
+    m: int
+
+
+def efficiency(costh):
+    """Detector efficiency eps(Omega) = 0.6 + 0.3 cos theta (always in [0.3, 0.9])."""
+    return 0.6 + 0.3 * np.asarray(costh)
+
+
+def waves_small():
+    """Four waves: (M, Gamma) = (1.5, 0.1), (1.7, 0.15), (2.0, 0.2), (2.3, 0.25) GeV,
+    (l, m) = (0,0), (2,0), (2,1), (4,0)."""
+    return [Wave(1.5, 0.10, 0, 0), Wave(1.7, 0.15, 2, 0),
+            Wave(2.0, 0.20, 2, 1), Wave(2.3, 0.25, 4, 0)]
+
+
+def waves_linear(n, m_lo=1.0, m_hi=2.9, w_lo=0.05, w_hi=0.4):
+    """n waves with masses and widths linearly spaced over the given ranges,
+    l = (0, 2, 4)[alpha mod 3] and m = 0 for l = 0, else floor(alpha/3) mod (l+1)."""
+    if n == 1:
+        return [Wave(m_lo, w_lo, 0, 0)]
+    out = []
+    for a in range(n):
+        l = (0, 2, 4)[a % 3]
+        mm = 0 if l == 0 else (a // 3) % (l + 1)
+        t = a / (n - 1)
+        out.append(Wave(m_lo + (m_hi - m_lo) * t, w_lo + (w_hi - w_lo) * t, l, mm))
+    return out
+
+
+def breit_wigner(m, mass, width):
+    """Fixed-width Breit-Wigner 1 / (M^2 - m^2 - i M Gamma), complex128."""
+    m = np.asarray(m, dtype=np.float64)
+    return 1.0 / (mass * mass - m * m - 1j * mass * width)
+
+
+def _assoc_legendre(l, mm, x):
+    """P_l^m(x) for m >= 0 including the Condon-Shortley phase (-1)^m,
+    by the standard upward recurrence in l."""
+    x = np.asarray(x, dtype=np.float64)
+    s = np.sqrt(np.maximum(0.0, 1.0 - x * x))
+    pmm = np.ones_like(x)
+    fact = 1.0
+    for _ in range(mm):
+        pmm = -pmm * fact * s
+        fact += 2.0
+    if l == mm:
+        return pmm
+    pm1 = x * (2 * mm + 1) * pmm
+    if l == mm + 1:
+        return pm1
+    p2, p1 = pmm, pm1
+    for ll in range(mm + 2, l + 1):
+        p = ((2 * ll - 1) * x * p1 - (ll + mm - 1) * p2) / (ll - mm)
+        p2, p1 = p1, p
+    return p1
+
+
+def ylm(l, mm, costh, phi):
+    """Orthonormal spherical harmonic Y_l^m(theta, phi), Condon-Shortley phase."""
+    if mm < 0:
+        return (-1) ** (-mm) * np.conj(ylm(l, -mm, costh, phi))
+    norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - mm) / math.factorial(l + mm))
+    return norm * _assoc_legendre(l, mm, costh) * np.exp(1j * mm * np.asarray(phi, dtype=np.float64))
+
+
+def phase_space(n, rng):
+    """n events uniform in (m_KK, cos theta, phi)."""
+    m = rng.uniform(M_LO, M_HI, n)
+    c = rng.uniform(-1.0, 1.0, n)
+    p = rng.uniform(0.0, 2.0 * math.pi, n)
+    return {"m": m, "costh": c, "phi": p}
+
+
+def _concat(parts, n):
+    return {k: np.concatenate([p[k] for p in parts])[:n] for k in parts[0]}
+
+
+def mc_sample(n_acc, seed=SEED_MC, batch=1 << 20):
+    """Accepted Monte Carlo: uniform candidates kept with probability eps.
+    Returns (events, n_gen) where n_gen counts every candidate drawn up to and
+    including the n_acc-th accepted one."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    parts, got, n_gen = [], 0, 0
+    while got < n_acc:
+        ev = phase_space(batch, rng)
+        keep = rng.uniform(0.0, 1.0, batch) < efficiency(ev["costh"])
+        idx = np.nonzero(keep)[0]
+        need = n_acc - got
+        if len(idx) >= need:
+            n_gen += int(idx[need - 1]) + 1
+            idx = idx[:need]
+        else:
+            n_gen += batch
+        parts.append({k: v[idx] for k, v in ev.items()})
+        got += len(idx)
+    return _concat(parts, n_acc), n_gen
+
+
+def data_sample_mixture(n, waves, V, seed=SEED_DATA, batch=1 << 20):
+    """Data-like events concentrated on the resonances without evaluating the
+    likelihood's intensity: pick wave alpha with probability proportional to
+    |V_alpha|^2, draw m_KK from a Cauchy of location M_alpha and half-width
+    Gamma_alpha/2 truncated to [0.98, 3.0] GeV, cos theta from the efficiency
+    shape (accept with eps/0.9) and phi uniform."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    w = np.abs(np.asarray(V)) ** 2
+    w = w / w.sum()
+    M = np.array([wv.mass for wv in waves])
+    G = np.array([wv.width for wv in waves])
+    parts, got = [], 0
+    while got < n:
+        a = rng.choice(len(waves), size=batch, p=w)
+        lo = np.arctan((M_LO - M[a]) / (G[a] / 2)) / math.pi + 0.5
+        hi = np.arctan((M_HI - M[a]) / (G[a] / 2)) / math.pi + 0.5
+        u = lo + (hi - lo) * rng.uniform(0.0, 1.0, batch)
+        m = M[a] + (G[a] / 2) * np.tan(math.pi * (u - 0.5))
+        m = np.clip(m, M_LO, M_HI)
+        c = rng.uniform(-1.0, 1.0, batch)
+        keep = rng.uniform(0.0, 1.0, batch) < efficiency(c) / EFF_MAX
+        p = rng.uniform(0.0, 2.0 * math.pi, batch)
+        parts.append({"m": m[keep], "costh": c[keep], "phi": p[keep]})
+        got += int(keep.sum())
+    return _concat(parts, n)
+
+
+def accept_reject(n, density, envelope, seed, batch=1 << 16):
+    """Events drawn from a caller-supplied density over phase space by
+    accept-reject against a constant envelope. `density(events)` returns
+    non-negative weights; every weight must stay below `envelope` (a weight
+    above it raises, since the sample would then be biased)."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    parts, got = [], 0
+    while got < n:
+        ev = phase_space(batch, rng)
+        d = np.asarray(density(ev), dtype=np.float64)
+        if np.any(d > envelope):
+            raise ValueError("accept-reject envelope violated: max %g > %g" % (d.max(), envelope))
+        keep = rng.uniform(0.0, envelope, batch) < d
+        parts.append({k: v[keep] for k, v in ev.items()})
+        got += int(keep.sum())
+    return _concat(parts, n)
+
+
+def amplitudes(events, waves, dtype=np.complex64, chunk=1 << 20):
+    """Event-major amplitude matrix A[i, alpha] = BW_alpha(m_i) Y_alpha(Omega_i),
+    evaluated in float64 and rounded once to `dtype`."""
+    n = len(events["m"])
+    out = np.empty((n, len(waves)), dtype=dtype)
+    for s in range(0, n, chunk):
+        e = slice(s, min(n, s + chunk))
+        m, c, p = events["m"][e], events["costh"][e], events["phi"][e]
+        for a, wv in enumerate(waves):
+            out[e, a] = breit_wigner(m, wv.mass, wv.width) * ylm(wv.l, wv.m, c, p)
+    return out
+
+
+def angular(events, waves, dtype=np.complex64):
+    """Angular factors Y_alpha(Omega_i) alone, [n, len(waves)]."""
+    n = len(events["m"])
+    out = np.empty((n, len(waves)), dtype=dtype)
+    for a, wv in enumerate(waves):
+        out[:, a] = ylm(wv.l, wv.m, events["costh"], events["phi"])
+    return out
+
+
+def random_V(n_waves, seed=SEED_VTRUE, k=None):
+    """Production amplitudes with Re and Im drawn N(0, 1): shape [n_waves] or [k, n_waves]."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    shape = (n_waves,) if k is None else (k, n_waves)
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+@dataclass
+class Workload:
+    name: str
+    waves: list
+    A_data: np.ndarray   # [n_data, N] complex64, event-major
+    A_mc: np.ndarray     # [n_mc_acc, N] complex64, event-major
+    n_gen: int
+    V_true: np.ndarray   # [N] complex128
+
+
+def mixture_workload(name, waves, n_data, n_mc_acc, seed_data=SEED_DATA, seed_mc=SEED_MC,
+                     seed_v=SEED_VTRUE, dtype=np.complex64):
+    """A sample of the given sizes: data-like events from `data_sample_mixture`
+    with V_true ~ N(0,1) and accepted MC from `mc_sample`."""
+    V = random_V(len(waves), seed_v)
+    ev_d = data_sample_mixture(n_data, waves, V, seed_data)
+    ev_m, n_gen = mc_sample(n_mc_acc, seed_mc)
+    return Workload(name, waves, amplitudes(ev_d, waves, dtype), amplitudes(ev_m, waves, dtype),
+                    n_gen, V)
+
+
+def paper_scale(n_data=1_000_000, n_mc_acc=5_000_000, n_waves=20, **kw):
+    """The paper-scale single fit: 20 waves, 1M data events, 5M accepted MC."""
+    return mixture_workload("pwa_1M_events_20_waves", waves_linear(n_waves), n_data, n_mc_acc, **kw)
+
+
+def multistart_scale(n_data=4_000_000, n_mc_acc=10_000_000, n_waves=32, **kw):
+    """The batched multistart sample: 32 waves, 4M data events, 10M accepted MC."""
+    return mixture_workload("pwa_4M_events_32_waves", waves_linear(n_waves), n_data, n_mc_acc, **kw)
+
+
+def start_points(n_waves, k, seed=SEED_STARTS):
+    """K starting parameter sets, Re/Im ~ N(0,1): [k, n_waves] complex128."""
+    return random_V(n_waves, seed, k)

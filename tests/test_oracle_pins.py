@@ -1,0 +1,350 @@
+"""Pins of the FP64 oracle to things other than itself.
+
+Each test checks the oracle against what Eq. 1-3 and the mathematics fix:
+brute force on tiny inputs, closed forms, invariants, finite differences and
+truth recovery from accept-reject toys. A plausible slip in the oracle (a
+dropped conjugate, a transposed M, a sign, the N_gen vs N_acc divisor, a
+missing term of the table form) fails at least one of them.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate, optimize
+
+import oracle
+import synth
+from oracle import brute
+
+
+def small_sample(n_data=30, n_mc=40, n_waves=4, seed=3):
+    waves = synth.waves_small()[:n_waves]
+    rng = np.random.Generator(np.random.Philox(seed))
+    ev = synth.phase_space(n_data, rng)
+    ev_mc = synth.phase_space(n_mc, rng)
+    A = synth.amplitudes(ev, waves, np.complex128)
+    A_mc = synth.amplitudes(ev_mc, waves, np.complex128)
+    V = synth.random_V(n_waves, seed + 1)
+    return A, A_mc, V
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ---- P1: brute force ------------------------------------------------------
+
+@pytest.mark.parametrize("n_waves", [1, 2, 4])
+def test_brute_force_nll_and_norm(n_waves):
+    A, A_mc, V = small_sample(n_waves=n_waves)
+    n_gen = 57.0
+    M = oracle.norm_matrix(A_mc, n_gen)
+    Mb = np.array(brute.norm_matrix(A_mc.tolist(), n_gen, n_waves))
+    assert rel(M, Mb) < 1e-13
+    nll, g, bad = oracle.nll_amp(A, M, V)
+    assert bad == 0
+    nb = brute.nll(A.tolist(), A_mc.tolist(), n_gen, list(V))
+    assert abs(nll - nb) <= 1e-12 * abs(nb)
+    gb = np.array(brute.grad_closed(A.tolist(), A_mc.tolist(), n_gen, list(V)))
+    assert rel(g, gb) < 1e-12
+
+
+def test_brute_force_gradient_by_differences():
+    """The Wirtinger gradient against central differences of the literal
+    double sum of Eq. 3."""
+    A, A_mc, V = small_sample(n_waves=3, n_data=12, n_mc=15)
+    n_gen = 20.0
+    M = oracle.norm_matrix(A_mc, n_gen)
+    _, g, _ = oracle.nll_amp(A, M, V)
+    gfd = np.array(brute.wirtinger_grad(A.tolist(), A_mc.tolist(), n_gen, list(V)))
+    assert rel(g, gfd) < 1e-6
+
+
+# ---- P2 and the degenerate cases of C8 ---------------------------------------
+
+def test_intensity_nonnegative_and_zero_V():
+    A, A_mc, V = small_sample()
+    I = oracle.intensity(A, V)
+    assert np.all(I >= 0)
+    M = oracle.norm_matrix(A_mc, 50.0)
+    nll, g, bad = oracle.nll_amp(A, M, np.zeros_like(V))
+    assert bad == 1 and math.isinf(nll) and np.all(g == 0)
+
+
+def test_single_wave_closed_form():
+    """N = 1: -ln L = -sum ln(|V|^2 |A_i|^2) + |V|^2 (1/N_gen) sum |A_j|^2."""
+    A, A_mc, V = small_sample(n_waves=1)
+    n_gen = 77.0
+    M = oracle.norm_matrix(A_mc, n_gen)
+    nll, g, _ = oracle.nll_amp(A, M, V)
+    v2 = abs(V[0]) ** 2
+    want = -np.sum(np.log(v2 * np.abs(A[:, 0]) ** 2)) + v2 * np.sum(np.abs(A_mc[:, 0]) ** 2) / n_gen
+    assert abs(nll - want) < 1e-12 * abs(want)
+    # dNLL/dV* = -N_d / conj(V) + V * M
+    gw = -len(A) / np.conj(V[0]) + V[0] * M[0, 0]
+    assert abs(g[0] - gw) < 1e-12 * abs(len(A) / V[0])
+
+
+# ---- P3: table form equals amplitude form -------------------------------------
+
+@pytest.mark.parametrize("n_waves", [1, 3, 4])
+def test_table_equals_amplitude(n_waves):
+    A, A_mc, V = small_sample(n_data=200, n_waves=n_waves)
+    M = oracle.norm_matrix(A_mc, 80.0)
+    T = oracle.table(A)
+    assert T.shape == (200, n_waves * n_waves)
+    # diagonal entries are |A_a|^2
+    assert rel(T[:, :n_waves], np.abs(A) ** 2) < 1e-15
+    na, ga, _ = oracle.nll_amp(A, M, V)
+    nt, gt, _ = oracle.nll_table(T, M, V)
+    assert abs(na - nt) < 1e-12 * abs(na)
+    assert rel(gt, ga) < 1e-12
+
+
+# ---- P4: V^H M V = (1/N_gen) sum_j I_j --------------------------------------
+
+def test_norm_term_matches_direct_mc_sum():
+    waves = synth.waves_small()
+    ev, n_gen = synth.mc_sample(3000, seed=11)
+    A_mc = synth.amplitudes(ev, waves, np.complex128)
+    V = synth.random_V(4, 5)
+    M = oracle.norm_matrix(A_mc, n_gen)
+    # M is Hermitian with genuinely complex off-diagonals, so a transposed
+    # convention would change V^H M V
+    assert np.allclose(M, M.conj().T, rtol=0, atol=1e-15 * np.abs(M).max())
+    assert np.abs(M.imag).max() > 1e-3 * np.abs(M).max()
+    nv, mv = oracle.norm_term(M, V)
+    direct = np.sum(oracle.intensity(A_mc, V)) / n_gen
+    assert abs(nv - direct) < 1e-12 * direct
+    nv_t = np.real(np.conj(V) @ M.T @ V)
+    assert abs(nv_t - direct) > 1e-6 * direct
+
+
+# ---- P5: global phase --------------------------------------------------------
+
+def test_global_phase_invariance():
+    A, A_mc, V = small_sample(n_data=300)
+    M = oracle.norm_matrix(A_mc, 60.0)
+    n0, g0, _ = oracle.nll_amp(A, M, V)
+    for phi in (0.3, 2.0, -2.9):
+        n1, g1, _ = oracle.nll_amp(A, M, V * np.exp(1j * phi))
+        assert abs(n1 - n0) < 1e-12 * abs(n0)
+        assert rel(g1, g0 * np.exp(1j * phi)) < 1e-12
+
+
+# ---- P6: Euler identity and the scale profile (Eq. 2 vs Eq. 3) --------------
+
+def test_euler_identity_and_scale_profile():
+    A, A_mc, V = small_sample(n_data=400, n_mc=500)
+    n_gen = 700.0
+    M = oracle.norm_matrix(A_mc, n_gen)
+    nll, g, _ = oracle.nll_amp(A, M, V)
+    nv, _ = oracle.norm_term(M, V)
+    vg = np.vdot(V, g)                      # sum_a conj(V_a) g_a
+    assert abs(vg.real - (nv - len(A))) < 1e-10 * len(A)
+    assert abs(vg.imag) < 1e-10 * len(A)
+    # min over a real scale s of NLL(s V) = -sum ln I(V) + N ln N(V) - N ln N + N
+    Nd = len(A)
+    f = lambda s: oracle.nll_amp(A, M, s * V, grad=False)[0]
+    s0 = math.sqrt(Nd / nv)
+    res = optimize.minimize_scalar(f, bracket=(0.3 * s0, 1.1 * s0, 3.0 * s0), tol=1e-12)
+    lnI = np.log(oracle.intensity(A, V)).sum()
+    want = -lnI + Nd * math.log(nv) - Nd * math.log(Nd) + Nd
+    assert abs(res.fun - want) < 1e-9 * abs(want)
+    assert abs(res.x ** 2 - Nd / nv) < 1e-5
+
+
+# ---- P8: closed-form normalisation for orthonormal toys ------------------------
+
+def _cos_coupling(la, ma, lb, mb):
+    """int cos(theta) conj(Y_la^ma) Y_lb^mb dOmega."""
+    if ma != mb:
+        return 0.0
+    m = ma
+    if lb == la + 1:
+        l = la
+    elif lb == la - 1:
+        l = lb
+    else:
+        return 0.0
+    return math.sqrt(((l + 1) ** 2 - m * m) / ((2 * l + 1) * (2 * l + 3)))
+
+
+def _mc_closed_form_check(waves, amp_fn, n_acc, closed):
+    ev, n_gen = synth.mc_sample(n_acc, seed=99)
+    A = amp_fn(ev)
+    M = oracle.norm_matrix(A, n_gen)
+    # five standard deviations of the MC estimate: sqrt(sum_j |conj(A_a) A_b|^2) / N_gen
+    A2 = np.abs(A) ** 2
+    tol = 5 * np.sqrt(A2.T @ A2) / n_gen
+    assert np.all(np.abs(M - closed) <= tol), (np.abs(M - closed) / tol).max()
+    return M
+
+
+def test_norm_closed_form_spherical_harmonics():
+    """A_a = Y_a only: M = [0.6 delta + 0.3 C] / (4 pi), C the cos(theta)
+    coupling of neighbouring l at equal m."""
+    lm = [(0, 0), (1, 0), (1, 1), (2, 1), (2, 0), (3, 0)]
+    waves = [synth.Wave(1.0, 1.0, l, m) for l, m in lm]
+    closed = np.array([[0.6 * (a == b) + 0.3 * _cos_coupling(*lm[a], *lm[b])
+                        for b in range(len(lm))] for a in range(len(lm))]) / (4 * math.pi)
+    M = _mc_closed_form_check(waves, lambda ev: synth.angular(ev, waves, np.complex128),
+                              400_000, closed)
+    # the coupling term is present (it is ~0.3/(4 pi)/sqrt(3) for (0,0)-(1,0))
+    assert abs(M[0, 1] - closed[0, 1]) < 0.1 * abs(closed[0, 1])
+
+
+def test_norm_closed_form_breit_wigner():
+    """A_a = BW_a(m) Y_a: M_ab = <conj(BW_a) BW_b>_m * <eps conj(Y_a) Y_b>_Omega.
+    The imaginary part of the mass integral fixes which index carries the
+    conjugate."""
+    waves = [synth.Wave(1.3, 0.2, 0, 0), synth.Wave(1.5, 0.3, 1, 0), synth.Wave(2.2, 0.4, 2, 0)]
+    lm = [(w.l, w.m) for w in waves]
+    dm = synth.M_HI - synth.M_LO
+
+    def mass_int(a, b):
+        f = lambda m: np.conj(synth.breit_wigner(m, waves[a].mass, waves[a].width)) * \
+            synth.breit_wigner(m, waves[b].mass, waves[b].width)
+        re = integrate.quad(lambda m: f(m).real, synth.M_LO, synth.M_HI, limit=400)[0]
+        im = integrate.quad(lambda m: f(m).imag, synth.M_LO, synth.M_HI, limit=400)[0]
+        return (re + 1j * im) / dm
+
+    closed = np.array([[mass_int(a, b) * (0.6 * (a == b) + 0.3 * _cos_coupling(*lm[a], *lm[b]))
+                        / (4 * math.pi) for b in range(3)] for a in range(3)])
+    assert abs(closed[0, 1].imag) > 0.2 * abs(closed[0, 1])
+    _mc_closed_form_check(waves, lambda ev: synth.amplitudes(ev, waves, np.complex128),
+                          400_000, closed)
+
+
+# ---- P9: finite differences ----------------------------------------------------
+
+def test_gradient_central_differences():
+    A, A_mc, V = small_sample(n_data=500, n_mc=600)
+    M = oracle.norm_matrix(A_mc, 900.0)
+    _, g, _ = oracle.nll_amp(A, M, V)
+    gdata = g - oracle.norm_term(M, V)[1]
+    h = 1e-4
+    gfd = np.empty_like(g)
+    for a in range(len(V)):
+        d = []
+        for step in (h, 1j * h):
+            vp, vm = V.copy(), V.copy()
+            vp[a] += step
+            vm[a] -= step
+            d.append((oracle.nll_amp(A, M, vp, False)[0] - oracle.nll_amp(A, M, vm, False)[0]) / (2 * h))
+        gfd[a] = complex(d[0], d[1]) / 2
+    assert np.max(np.abs(gfd - g)) < 1e-6 * np.linalg.norm(gdata)
+
+
+def _res_sample(R=2, F=2, n=300, n_mc=400, seed=8):
+    waves = synth.waves_linear(R + F, 1.2, 2.4, 0.1, 0.3)
+    rng = np.random.Generator(np.random.Philox(seed))
+    ev, ev_mc = synth.phase_space(n, rng), synth.phase_space(n_mc, rng)
+    Y = synth.angular(ev, waves[:R], np.complex128)
+    Ym = synth.angular(ev_mc, waves[:R], np.complex128)
+    Af = synth.amplitudes(ev, waves[R:], np.complex128)
+    Afm = synth.amplitudes(ev_mc, waves[R:], np.complex128)
+    mass = np.array([w.mass for w in waves[:R]])
+    width = np.array([w.width for w in waves[:R]])
+    V = synth.random_V(R + F, seed)
+    return waves, ev, ev_mc, Y, Ym, Af, Afm, mass, width, V
+
+
+def test_free_resonance_matches_fixed_form_and_differences():
+    waves, ev, ev_mc, Y, Ym, Af, Afm, mass, width, V = _res_sample()
+    n_gen = 650.0
+    args = (ev["m"], Y, Af, ev_mc["m"], Ym, Afm, n_gen)
+    nll, gV, gM, gW, bad = oracle.nll_res(*args, V, mass, width)
+    assert bad == 0
+    # at the same masses and widths it is the fixed-parameter NLL
+    A = synth.amplitudes(ev, waves, np.complex128)
+    A_mc = synth.amplitudes(ev_mc, waves, np.complex128)
+    M = oracle.norm_matrix(A_mc, n_gen)
+    n2, g2, _ = oracle.nll_amp(A, M, V)
+    assert abs(nll - n2) < 1e-11 * abs(n2)
+    assert rel(gV, g2) < 1e-10
+    # dNLL/dmass, dNLL/dwidth by central differences (P12: BW derivatives)
+    h = 1e-6
+    for r in range(len(mass)):
+        for par, gpar in ((mass, gM), (width, gW)):
+            p1, p2 = par.copy(), par.copy()
+            p1[r] += h
+            p2[r] -= h
+            if par is mass:
+                fp = oracle.nll_res(*args, V, p1, width)[0]
+                fm = oracle.nll_res(*args, V, p2, width)[0]
+            else:
+                fp = oracle.nll_res(*args, V, mass, p1)[0]
+                fm = oracle.nll_res(*args, V, mass, p2)[0]
+            fd = (fp - fm) / (2 * h)
+            assert abs(fd - gpar[r]) < 1e-5 * max(1.0, abs(gpar[r])), (r, fd, gpar[r])
+
+
+# ---- P10 / P7: truth recovery from an accept-reject toy ----------------------
+
+def _phase_fix(V):
+    return V * np.exp(-1j * np.angle(V[0]))
+
+
+def _fit(A, M, V0):
+    N = len(V0)
+
+    def f(x):
+        V = x[:N] + 1j * x[N:]
+        nll, g, bad = oracle.nll_amp(A, M, V)
+        if bad:
+            return 1e300, np.zeros(2 * N)
+        return nll, np.concatenate([2 * g.real, 2 * g.imag])
+
+    x0 = np.concatenate([V0.real, V0.imag])
+    r = optimize.minimize(f, x0, jac=True, method="L-BFGS-B",
+                          options={"maxiter": 2000, "ftol": 1e-15, "gtol": 1e-8})
+    return r.x[:N] + 1j * r.x[N:], r
+
+
+@pytest.mark.slow
+def test_truth_recovery_accept_reject():
+    """Data drawn from eps * I with the small 4-wave model; the fit returns
+    V_true within its statistical errors and N(V_hat) = N_data."""
+    waves = synth.waves_small()
+    V_true = synth.random_V(4, synth.SEED_VTRUE)
+    ymax = [math.sqrt((2 * w.l + 1) / (4 * math.pi)) for w in waves]
+    bwmax = [1.0 / (w.mass * w.width) for w in waves]
+    envelope = synth.EFF_MAX * sum(abs(v) * b * y for v, b, y in zip(V_true, bwmax, ymax)) ** 2
+
+    def density(ev):
+        A = synth.amplitudes(ev, waves, np.complex128)
+        return synth.efficiency(ev["costh"]) * oracle.intensity(A, V_true)
+
+    n_data = 10_000
+    ev = synth.accept_reject(n_data, density, envelope, seed=synth.SEED_DATA)
+    A = synth.amplitudes(ev, waves, np.complex128)
+    ev_mc, n_gen = synth.mc_sample(30_000, seed=synth.SEED_MC)   # about 50k generated
+    A_mc = synth.amplitudes(ev_mc, waves, np.complex128)
+    M = oracle.norm_matrix(A_mc, n_gen)
+    # the truth up to the overall scale, which the extended likelihood fixes
+    V0 = V_true * math.sqrt(n_data / oracle.norm_term(M, V_true)[0])
+    Vh, res = _fit(A, M, V0 * (1 + 0.2j))
+    nv, _ = oracle.norm_term(M, Vh)
+    assert abs(nv - n_data) < 1e-3 * n_data                       # P7
+    assert res.fun <= oracle.nll_amp(A, M, V0, False)[0] + 1e-9
+    # pulls from the inverse Hessian of the phase-fixed real parameters
+    Vf, Tf = _phase_fix(Vh), _phase_fix(V0)
+    N = 4
+    x = np.concatenate([Vf.real, Vf.imag[1:]])
+
+    def grad_x(xx):
+        V = xx[:N] + 1j * np.concatenate([[0.0], xx[N:]])
+        _, g, _ = oracle.nll_amp(A, M, V)
+        return np.concatenate([2 * g.real, 2 * g.imag[1:]])
+
+    H = np.empty((2 * N - 1, 2 * N - 1))
+    for k in range(2 * N - 1):
+        e = np.zeros(2 * N - 1)
+        e[k] = 1e-5
+        H[:, k] = (grad_x(x + e) - grad_x(x - e)) / 2e-5
+    cov = np.linalg.inv(0.5 * (H + H.T))
+    t = np.concatenate([Tf.real, Tf.imag[1:]])
+    pulls = (x - t) / np.sqrt(np.diag(cov))
+    assert np.all(np.abs(pulls) < 5), pulls
