@@ -1,0 +1,150 @@
+/*
+ * pwa.h -- C ABI of the GB300 partial wave analysis likelihood library.
+ *
+ * The library evaluates the extended negative log-likelihood of Eq. 3 of
+ * Berger, "Partial wave analysis at BES III harnessing the power of GPUs":
+ *
+ *   NLL(V) = - sum_{i in data} ln I(Omega_i) + V^H M V,
+ *   I(Omega) = | sum_alpha V_alpha A_alpha(Omega) |^2                  (Eq. 1)
+ *   M[a][b]  = (1/N_MC^Gen) sum_{j in accepted MC} conj(A_a(j)) A_b(j)
+ *
+ * and its Wirtinger gradient g_a = dNLL/dV*_a
+ *   = - sum_i conj(A_a(i)) S_i / I_i + (M V)_a,  S_i = sum_b V_b A_b(i).
+ * The real-parameter gradient is dNLL/dRe V_a = 2 Re g_a and
+ * dNLL/dIm V_a = 2 Im g_a.
+ *
+ * As in Sec. 2 (after Eq. 3), amplitudes are fixed once loaded and the MC
+ * bracket M is built once; per call only the parameters go in and the
+ * likelihood and gradient come out (Sec. 5: transfers are restricted to the
+ * fit parameters and the results).
+ *
+ * Conventions shared by every call:
+ *  - Complex numbers are interleaved (re, im) pairs.
+ *  - Amplitudes are event-major: element (i, a) of an [n][n_waves] array.
+ *  - V for K parameter sets is [K][n_waves] complex128 (double pairs).
+ *  - Every function returns a status code (PWA_OK = 0 or a negative error);
+ *    pwa_last_error() gives a human-readable message for the last failure on
+ *    that context. No function aborts, traps or throws across the ABI.
+ *  - A context is bound to one device and one CUDA stream and must not be
+ *    used from two host threads at once.
+ */
+#ifndef PWA_H
+#define PWA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PWA_OK 0
+#define PWA_EINVAL -1   /* bad argument (null pointer, size, K out of range) */
+#define PWA_ENOMEM -2   /* a device or pinned allocation failed */
+#define PWA_ECUDA -3    /* a CUDA runtime/driver call failed */
+#define PWA_ESTATE -4   /* call out of order (e.g. pwa_nll before pwa_build_norm) */
+#define PWA_EDOMAIN -5  /* some data intensity I_i was <= 0 or not finite for a
+                           parameter set: that set's nll is +inf and its gradient 0 */
+#define PWA_ETIMEOUT -6 /* a device-side bounded wait gave up; results invalid */
+#define PWA_ENOTSUP -7  /* configuration not supported by this build */
+
+/* ---- forms of the data term (Sec. 2, after Eq. 3) ----------------------- */
+#define PWA_FORM_AMP 1   /* direct: S_i = sum_a V_a A_a(i), I_i = |S_i|^2 */
+#define PWA_FORM_TABLE 2 /* precomputed per-event table A_a A*_b (upper triangle) */
+
+/* ---- amplitude element types ------------------------------------------- */
+#define PWA_C64 1  /* float pairs: used as given */
+#define PWA_C128 2 /* double pairs: rounded to nearest float on load */
+
+typedef struct pwa_ctx pwa_ctx;
+
+typedef struct pwa_config {
+    int n_waves;   /* number of partial waves N, 1 <= N <= 48 */
+    int forms;     /* bitmask of PWA_FORM_* stores built by pwa_load_events;
+                      0 means PWA_FORM_AMP */
+    int precision; /* reserved for the batched tensor-core path; 0 */
+    int max_k;     /* largest K accepted by the evaluation calls (>= 1) */
+    void *stream;  /* cudaStream_t to run on; NULL = a stream the context owns */
+} pwa_config;
+
+/* Create a context on CUDA device `device`. On success *out owns all device
+ * memory the library allocates for it; release it with pwa_destroy.
+ * Errors: PWA_EINVAL (null out/cfg, n_waves or max_k out of range),
+ * PWA_ECUDA (device not usable), PWA_ENOMEM. */
+int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg);
+
+/* Free everything the context owns. Null is accepted. */
+int pwa_destroy(pwa_ctx *ctx);
+
+/* Load the data sample and the accepted MC sample (Eq. 2/3 and the text after
+ * Eq. 2: the normalisation integral is a sum over the N_MC^Acc accepted events
+ * divided by the number generated, N_MC^Gen).
+ *   data_amp: [n_data][n_waves] complex, host or device pointer (detected)
+ *   mc_amp:   [n_mc_acc][n_waves] complex, host or device pointer
+ *   n_mc_gen: number of generated MC events, n_mc_gen >= n_mc_acc
+ *   amp_dtype: PWA_C64 or PWA_C128 (C128 is rounded to float on the device)
+ * The library copies the amplitudes into its own structure-of-arrays store
+ * (one float plane per real and imaginary part of each wave, events
+ * contiguous), and builds the per-event table if PWA_FORM_TABLE was
+ * requested; the caller keeps ownership of its buffers. Loading again
+ * replaces the sample and invalidates the normalisation matrix.
+ * Errors: PWA_EINVAL (n_data < 1, n_mc_acc < 1, n_mc_gen < n_mc_acc, null
+ * pointers, bad dtype), PWA_ENOMEM, PWA_ECUDA. */
+int pwa_load_events(pwa_ctx *ctx, const void *data_amp, int64_t n_data,
+                    const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
+                    int amp_dtype);
+
+/* Build the MC normalisation matrix M (the inner bracket of the second term
+ * of Eq. 3), once per loaded sample. If M_out is not NULL it receives M as
+ * [n_waves][n_waves] complex128, row-major, M_out[a][b] as defined above.
+ * Errors: PWA_ESTATE (no events loaded), PWA_ECUDA. */
+int pwa_build_norm(pwa_ctx *ctx, double *M_out);
+
+/* Select which store evaluates the data term: PWA_FORM_AMP (default) or
+ * PWA_FORM_TABLE. Both give the same NLL up to rounding.
+ * Errors: PWA_EINVAL (unknown form), PWA_ESTATE (store not built). */
+int pwa_set_form(pwa_ctx *ctx, int form);
+
+/* Negative log-likelihood of Eq. 3 for K parameter sets.
+ *   V:   host [K][n_waves] complex128
+ *   nll: host [K]
+ * Returns PWA_EDOMAIN if any set had a non-positive intensity (its nll is
+ * +inf; the others are valid). Errors: PWA_EINVAL (K < 1 or K > max_k, null
+ * pointers), PWA_ESTATE (before pwa_build_norm), PWA_ECUDA, PWA_ETIMEOUT. */
+int pwa_nll(pwa_ctx *ctx, const double *V, int K, double *nll);
+
+/* NLL and its Wirtinger gradient dNLL/dV* for K parameter sets.
+ *   grad: host [K][n_waves] complex128
+ * Otherwise as pwa_nll; a set with PWA_EDOMAIN gets a zero gradient. */
+int pwa_nll_grad(pwa_ctx *ctx, const double *V, int K, double *nll, double *grad);
+
+/* Stream-ordered variant with device pointers: d_V [K][n_waves] complex128,
+ * d_nll [K], d_grad [K][n_waves] complex128 (d_grad may be NULL for the NLL
+ * alone). Returns after enqueueing. Device-side status (domain, timeout)
+ * accumulates in the context until pwa_sync. */
+int pwa_nll_grad_async(pwa_ctx *ctx, const double *d_V, int K, double *d_nll, double *d_grad);
+
+/* Wait for the context's stream and return the status accumulated by the
+ * asynchronous calls since the previous pwa_sync (PWA_OK, PWA_EDOMAIN or
+ * PWA_ETIMEOUT), then clear it. */
+int pwa_sync(pwa_ctx *ctx);
+
+/* Message describing the last error on ctx ("" if none); valid until the
+ * next call on ctx. A NULL ctx gives the message of the last failed
+ * pwa_create on this thread. */
+const char *pwa_last_error(const pwa_ctx *ctx);
+
+/* Host-only size query: bytes of the per-event table for n_events events of
+ * n_waves waves (n_waves^2 floats per event: n_waves real diagonal entries
+ * and n_waves(n_waves-1)/2 complex off-diagonal ones; Sec. 2 sizes the table
+ * as about 1.5 GB per million events at 20 waves). Errors: PWA_EINVAL. */
+int pwa_table_bytes(int n_waves, int64_t n_events, int64_t *bytes);
+
+/* Library version as an integer MAJOR*10000 + MINOR*100 + PATCH. */
+int pwa_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PWA_H */

@@ -86,6 +86,19 @@ def norm_matrix(A_mc, n_gen):
     return M
 
 
+def norm_matrix_blas(A_mc, n_gen, chunk=1 << 20):
+    """The same M as norm_matrix, with the sum over events done by a library
+    complex128 matrix product (conj(A)^T A) in chunks; for samples where the
+    plain loops take minutes. Pinned against norm_matrix in the tests."""
+    A = np.asarray(A_mc)
+    N = A.shape[1]
+    M = np.zeros((N, N), dtype=np.complex128)
+    for s in range(0, A.shape[0], chunk):
+        a = A[s:s + chunk].astype(np.complex128)
+        M += a.conj().T @ a
+    return M / float(n_gen)
+
+
 def norm_term(M, V):
     """(V^H M V, M V)."""
     M, V = _c128(M), _c128(V)

@@ -1,0 +1,72 @@
+"""GB300-native partial wave analysis likelihood (Berger, arXiv:1108.5673).
+
+The hot path, the extended negative log-likelihood of Eq. 3 and its gradient
+with respect to the production amplitudes V, runs in hand-written CUDA
+kernels for sm_103a behind the C ABI of include/pwa.h. This package is the
+thin Python binding of that ABI (`_abi`, same function names) plus a small
+object wrapper; PyTorch is only used by callers for device memory and
+streams.
+
+The compiled library is built by `paper_1108_5673_gb300.build.build()`.
+"""
+from ._abi import (PWA_C64, PWA_C128, PWA_EDOMAIN, PWA_FORM_AMP, PWA_FORM_TABLE, PWA_OK,
+                   PwaError)
+
+__all__ = ["Likelihood", "PwaError", "PWA_FORM_AMP", "PWA_FORM_TABLE", "PWA_OK", "PWA_EDOMAIN",
+           "PWA_C64", "PWA_C128"]
+
+
+class Likelihood:
+    """One library context: a loaded sample, its normalisation matrix, and
+    evaluations of NLL(V) and dNLL/dV* (Wirtinger) for K parameter sets."""
+
+    def __init__(self, n_waves, device=0, forms=PWA_FORM_AMP, max_k=1, stream=None):
+        from . import _abi
+        self._abi = _abi
+        self.n_waves = n_waves
+        self.max_k = max_k
+        self.ctx = _abi.pwa_create(device, n_waves, forms, 0, max_k, stream)
+        self.last_status = PWA_OK
+
+    def load_events(self, data_amp, mc_amp, n_mc_gen):
+        self._abi.pwa_load_events(self.ctx, data_amp, mc_amp, n_mc_gen)
+        return self
+
+    def build_norm(self):
+        """Build M on the device; returns a host copy ([N, N] complex128)."""
+        return self._abi.pwa_build_norm(self.ctx, self.n_waves)
+
+    def set_form(self, form):
+        self._abi.pwa_set_form(self.ctx, form)
+
+    def nll(self, V):
+        nll, self.last_status = self._abi.pwa_nll(self.ctx, V)
+        return nll
+
+    def nll_grad(self, V):
+        nll, g, self.last_status = self._abi.pwa_nll_grad(self.ctx, V)
+        return nll, g
+
+    def nll_grad_async(self, d_V, d_nll, d_grad=None):
+        self._abi.pwa_nll_grad_async(self.ctx, d_V, d_V.shape[0], d_nll, d_grad)
+
+    def sync(self):
+        self.last_status = self._abi.pwa_sync(self.ctx)
+        return self.last_status
+
+    def close(self):
+        if self.ctx is not None:
+            self._abi.pwa_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,198 @@
+"""ctypes binding of libpwa (include/pwa.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the likelihood; all computation runs in the library's CUDA
+kernels. Arrays may be numpy arrays (host memory) or CUDA tensors of any
+library exposing `data_ptr()` and `is_cuda` (device memory).
+
+Importing this module loads the compiled library and fails loudly if it is
+missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libpwa.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "pwa.h")
+
+PWA_OK = 0
+PWA_EINVAL = -1
+PWA_ENOMEM = -2
+PWA_ECUDA = -3
+PWA_ESTATE = -4
+PWA_EDOMAIN = -5
+PWA_ETIMEOUT = -6
+PWA_ENOTSUP = -7
+PWA_FORM_AMP = 1
+PWA_FORM_TABLE = 2
+PWA_C64 = 1
+PWA_C128 = 2
+
+ERROR_NAMES = {PWA_EINVAL: "PWA_EINVAL", PWA_ENOMEM: "PWA_ENOMEM", PWA_ECUDA: "PWA_ECUDA",
+               PWA_ESTATE: "PWA_ESTATE", PWA_EDOMAIN: "PWA_EDOMAIN",
+               PWA_ETIMEOUT: "PWA_ETIMEOUT", PWA_ENOTSUP: "PWA_ENOTSUP"}
+
+
+class PwaError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (ERROR_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+class pwa_config(ctypes.Structure):
+    _fields_ = [("n_waves", ctypes.c_int), ("forms", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_k", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path=LIB_PATH):
+    """Load libpwa.so (built by paper_1108_5673_gb300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError("libpwa.so not found at %s: run paper_1108_5673_gb300.build.build() "
+                          "(nvcc, sm_103a); there is no CPU fallback" % path)
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "pwa_create": ([ctypes.POINTER(ctypes.c_void_p), I, ctypes.POINTER(pwa_config)], I),
+        "pwa_destroy": ([P], I),
+        "pwa_load_events": ([P, P, I64, P, I64, D, I], I),
+        "pwa_build_norm": ([P, P], I),
+        "pwa_set_form": ([P, I], I),
+        "pwa_nll": ([P, P, I, P], I),
+        "pwa_nll_grad": ([P, P, I, P, P], I),
+        "pwa_nll_grad_async": ([P, P, I, P, P], I),
+        "pwa_sync": ([P], I),
+        "pwa_last_error": ([P], ctypes.c_char_p),
+        "pwa_table_bytes": ([I, I64, ctypes.POINTER(ctypes.c_int64)], I),
+        "pwa_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def header_symbols(header=HEADER):
+    """Names of the functions declared in include/pwa.h."""
+    text = open(header).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(pwa_\w+)\s*\(", text, re.M)))
+
+
+def _ptr(x, dtype=None):
+    """(pointer, keepalive) for a numpy array or a CUDA tensor."""
+    if x is None:
+        return None, None
+    if hasattr(x, "data_ptr") and getattr(x, "is_cuda", False):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return ctypes.c_void_p(x.data_ptr()), x
+    a = np.ascontiguousarray(x, dtype=dtype) if dtype is not None else np.ascontiguousarray(x)
+    return a.ctypes.data_as(ctypes.c_void_p), a
+
+
+def _check(ctx, rc, allow=()):
+    if rc != PWA_OK and rc not in allow:
+        msg = load().pwa_last_error(ctx)
+        raise PwaError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def pwa_version():
+    return load().pwa_version()
+
+
+def pwa_table_bytes(n_waves, n_events):
+    out = ctypes.c_int64()
+    _check(None, load().pwa_table_bytes(n_waves, n_events, ctypes.byref(out)))
+    return out.value
+
+
+def pwa_create(device, n_waves, forms=PWA_FORM_AMP, precision=0, max_k=1, stream=None):
+    cfg = pwa_config(n_waves, forms, precision, max_k,
+                     ctypes.c_void_p(stream) if stream else None)
+    h = ctypes.c_void_p()
+    _check(None, load().pwa_create(ctypes.byref(h), device, ctypes.byref(cfg)))
+    return h
+
+
+def pwa_destroy(ctx):
+    return load().pwa_destroy(ctx)
+
+
+def pwa_load_events(ctx, data_amp, mc_amp, n_mc_gen):
+    """data_amp / mc_amp: [n, n_waves] complex64 or complex128 (numpy or CUDA tensor)."""
+    def kind(x):
+        dt = str(getattr(x, "dtype", ""))
+        if "complex64" in dt:
+            return PWA_C64
+        if "complex128" in dt:
+            return PWA_C128
+        raise ValueError("amplitudes must be complex64 or complex128, got %s" % dt)
+    kd, km = kind(data_amp), kind(mc_amp)
+    if kd != km:
+        raise ValueError("data and MC amplitudes must share one dtype")
+    pd, kd_ = _ptr(data_amp)
+    pm, km_ = _ptr(mc_amp)
+    return _check(ctx, load().pwa_load_events(ctx, pd, int(data_amp.shape[0]), pm,
+                                              int(mc_amp.shape[0]), float(n_mc_gen), kd))
+
+
+def pwa_build_norm(ctx, n_waves):
+    M = np.empty((n_waves, n_waves), dtype=np.complex128)
+    _check(ctx, load().pwa_build_norm(ctx, M.ctypes.data_as(ctypes.c_void_p)))
+    return M
+
+
+def pwa_set_form(ctx, form):
+    return _check(ctx, load().pwa_set_form(ctx, form))
+
+
+def pwa_nll(ctx, V):
+    """V: [K, n_waves] complex128 (host). Returns (nll [K], status)."""
+    V = np.ascontiguousarray(np.atleast_2d(V), dtype=np.complex128)
+    nll = np.empty(V.shape[0])
+    rc = _check(ctx, load().pwa_nll(ctx, V.ctypes.data_as(ctypes.c_void_p), V.shape[0],
+                                    nll.ctypes.data_as(ctypes.c_void_p)), allow=(PWA_EDOMAIN,))
+    return nll, rc
+
+
+def pwa_nll_grad(ctx, V):
+    """V: [K, n_waves] complex128 (host). Returns (nll [K], grad [K, n_waves], status)."""
+    V = np.ascontiguousarray(np.atleast_2d(V), dtype=np.complex128)
+    nll = np.empty(V.shape[0])
+    g = np.empty_like(V)
+    rc = _check(ctx, load().pwa_nll_grad(ctx, V.ctypes.data_as(ctypes.c_void_p), V.shape[0],
+                                         nll.ctypes.data_as(ctypes.c_void_p),
+                                         g.ctypes.data_as(ctypes.c_void_p)),
+                allow=(PWA_EDOMAIN,))
+    return nll, g, rc
+
+
+def pwa_nll_grad_async(ctx, d_V, K, d_nll, d_grad=None):
+    """Device pointers (CUDA tensors): d_V [K, n_waves] complex128, d_nll [K]
+    float64, d_grad [K, n_waves] complex128 or None."""
+    pv, _a = _ptr(d_V)
+    pn, _b = _ptr(d_nll)
+    pg, _c = _ptr(d_grad)
+    return _check(ctx, load().pwa_nll_grad_async(ctx, pv, K, pn, pg))
+
+
+def pwa_sync(ctx):
+    return _check(ctx, load().pwa_sync(ctx), allow=(PWA_EDOMAIN,))
+
+
+def pwa_last_error(ctx):
+    m = load().pwa_last_error(ctx)
+    return m.decode() if m else ""

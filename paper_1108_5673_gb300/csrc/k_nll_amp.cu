@@ -1,0 +1,429 @@
+// Fused data-term kernel, direct amplitude form (Eq. 1 and the first sum of
+// Eq. 3), followed in the same launch by the deterministic FP64 final sum
+// and the normalisation term (Sec. 4: single precision per event, double
+// precision final sum).
+//
+// Per event i (one thread handles EPT adjacent events of a tile):
+//   S_i = sum_a Vhi_a A_a(i)            FP32, two partial accumulators
+//   I_i = |S_i|^2                        FP32
+//   ln I_i = e_i ln 2 + ln f_i           f_i in [2^-1/2, 2^1/2], e_i summed exactly
+//   r_i = S_i / I_i,  g_a += conj(A_a(i)) r_i
+// Vhi is V rounded to float. The remainder dV = V - Vhi is applied to the
+// NLL to first order in the final sum: NLL(V) = NLL(Vhi) + 2 Re(g_data^H dV)
+// (the second-order term is ~N_data * 2^-48 and far below FP32 rounding).
+//
+// Data movement: a persistent grid (one CTA per SM) streams tiles of TE
+// events x 2N planes from the structure-of-arrays store into a ring of
+// shared-memory stages with TMA (cp.async.bulk.tensor.2d); one producer
+// thread issues the copies, CW consumer warps compute. Every wait is bounded
+// (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
+//
+// Cross-block reduction: each CTA writes 2N+2 doubles of partial sums; the
+// last CTA to finish (atomic ticket) adds them in block order, so the result
+// is bitwise reproducible from run to run.
+#include "pwa_internal.cuh"
+
+namespace pwa {
+
+namespace {
+
+constexpr double kLn2 = 0.69314718055994530942;
+
+template <int N>
+struct AmpCfg {
+    static constexpr int CW = 4;                       // consumer warps
+    static constexpr int EPT = (N <= 24) ? 2 : 1;      // events per thread per tile
+    static constexpr int TE = CW * 32 * EPT;           // events per tile
+    static constexpr int ROWS = 2 * N;
+    static constexpr uint32_t STAGE_BYTES = ROWS * TE * 4;
+    static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+    static constexpr bool AREG = (N <= 24);            // keep A in registers between passes
+    static constexpr int THREADS = (CW + 1) * 32;
+    static constexpr int NC = 2 * N + 2;               // partial components
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
+};
+
+template <int EPT>
+__device__ __forceinline__ void lds_ept(const float *p, float (&x)[EPT])
+{
+    if constexpr (EPT == 2) {
+        float2 v = *reinterpret_cast<const float2 *>(p);
+        x[0] = v.x;
+        x[1] = v.y;
+    } else {
+        x[0] = *p;
+    }
+}
+
+template <int N, bool GRAD>
+__global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
+    nll_amp_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs a, const int n_tiles,
+                   int *work_flags)
+{
+    using C = AmpCfg<N>;
+    constexpr int TE = C::TE, EPT = C::EPT, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
+    constexpr int NC = C::NC;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float *tiles = reinterpret_cast<float *>(smem_raw);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
+    uint64_t *empty = full + STAGES;
+
+    __shared__ float2 Vs[N];
+    __shared__ double red[CW][NC];
+    __shared__ double fin[NC];
+    __shared__ double mv_s[2 * N];
+    __shared__ int s_flags;
+    __shared__ int s_last;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        fence_barrier_init();
+        s_flags = 0;
+    }
+    // Rows of padded waves (n_waves < N) are never written by TMA: zero them
+    // once so that they contribute nothing (their V is zero as well).
+    const uint32_t stage_tx = 2u * (uint32_t)a.n_waves * TE * 4u;
+    for (int s = 0; s < STAGES; ++s)
+        for (int i = 2 * a.n_waves * TE + threadIdx.x; i < ROWS * TE; i += blockDim.x)
+            tiles[(size_t)s * ROWS * TE + i] = 0.f;
+    if (threadIdx.x < N) {
+        const int w = threadIdx.x;
+        Vs[w] = (w < a.n_waves) ? make_float2(__double2float_rn(a.V[2 * w]),
+                                              __double2float_rn(a.V[2 * w + 1]))
+                                : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+
+    int flags = 0;
+    double lacc = 0.0;
+    long long eacc = 0;
+    float g[GRAD ? 2 * N : 1];
+#pragma unroll
+    for (int c = 0; c < (GRAD ? 2 * N : 1); ++c)
+        g[c] = 0.f;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- producer: one thread issues the TMA copies ----------------
+            int j = 0;
+            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+                const int s = j % STAGES;
+                const uint32_t u = j / STAGES;
+                if (j >= STAGES && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
+                    flags |= FLAG_TIMEOUT;
+                    break;
+                }
+                mbar_arrive_expect_tx(&full[s], stage_tx);
+                tma_load_2d(tiles + (size_t)s * ROWS * TE, &map, tile * TE, 0, &full[s]);
+            }
+            // no copy may still be landing in shared memory when the CTA exits
+            for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q)
+                if (!mbar_wait(&full[q % STAGES], (q / STAGES) & 1))
+                    flags |= FLAG_TIMEOUT;
+        }
+    } else {
+        // ---- consumers ----------------------------------------------------
+        const int ct = threadIdx.x - 32;
+        float vr[N], vi[N];
+#pragma unroll
+        for (int w = 0; w < N; ++w) {
+            vr[w] = Vs[w].x;
+            vi[w] = Vs[w].y;
+        }
+        int bad = 0;
+        int j = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+            const int s = j % STAGES;
+            const uint32_t u = j / STAGES;
+            if (!mbar_wait(&full[s], u & 1)) {
+                flags |= FLAG_TIMEOUT;
+                break;
+            }
+            const float *T = tiles + (size_t)s * ROWS * TE + ct * EPT;
+            const int64_t ev0 = (int64_t)tile * TE + ct * EPT;
+
+            float sr0[EPT], si0[EPT], sr1[EPT], si1[EPT];
+            float ar[C::AREG ? N : 1][EPT], ai[C::AREG ? N : 1][EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e)
+                sr0[e] = si0[e] = sr1[e] = si1[e] = 0.f;
+#pragma unroll
+            for (int w = 0; w < N; ++w) {
+                float xr[EPT], xi[EPT];
+                lds_ept<EPT>(T + (2 * w) * TE, xr);
+                lds_ept<EPT>(T + (2 * w + 1) * TE, xi);
+#pragma unroll
+                for (int e = 0; e < EPT; ++e) {
+                    if constexpr (C::AREG) {
+                        ar[w][e] = xr[e];
+                        ai[w][e] = xi[e];
+                    }
+                    if (w & 1) {
+                        sr1[e] = fmaf(vr[w], xr[e], sr1[e]);
+                        sr1[e] = fmaf(-vi[w], xi[e], sr1[e]);
+                        si1[e] = fmaf(vr[w], xi[e], si1[e]);
+                        si1[e] = fmaf(vi[w], xr[e], si1[e]);
+                    } else {
+                        sr0[e] = fmaf(vr[w], xr[e], sr0[e]);
+                        sr0[e] = fmaf(-vi[w], xi[e], sr0[e]);
+                        si0[e] = fmaf(vr[w], xi[e], si0[e]);
+                        si0[e] = fmaf(vi[w], xr[e], si0[e]);
+                    }
+                }
+            }
+            float rr[EPT], ri[EPT];
+#pragma unroll
+            for (int e = 0; e < EPT; ++e) {
+                const float Sr = sr0[e] + sr1[e], Si = si0[e] + si1[e];
+                const float I = fmaf(Sr, Sr, Si * Si);
+                const bool in = (ev0 + e) < a.n_events;
+                const bool ok = (I > 0.f) && (I < INFINITY);
+                rr[e] = 0.f;
+                ri[e] = 0.f;
+                if (in) {
+                    if (ok) {
+                        int ex;
+                        const float f = split_exponent(I, ex);
+                        lacc += (double)logf(f);
+                        eacc += ex;
+                        const float rI = __frcp_rn(I);
+                        rr[e] = Sr * rI;
+                        ri[e] = Si * rI;
+                    } else {
+                        bad = 1;
+                    }
+                }
+            }
+            if constexpr (GRAD) {
+#pragma unroll
+                for (int w = 0; w < N; ++w) {
+                    float xr[EPT], xi[EPT];
+                    if constexpr (C::AREG) {
+#pragma unroll
+                        for (int e = 0; e < EPT; ++e) {
+                            xr[e] = ar[w][e];
+                            xi[e] = ai[w][e];
+                        }
+                    } else {
+                        lds_ept<EPT>(T + (2 * w) * TE, xr);
+                        lds_ept<EPT>(T + (2 * w + 1) * TE, xi);
+                    }
+#pragma unroll
+                    for (int e = 0; e < EPT; ++e) {
+                        // conj(A) * r = (xr rr + xi ri) + i (xr ri - xi rr)
+                        g[2 * w] = fmaf(xr[e], rr[e], fmaf(xi[e], ri[e], g[2 * w]));
+                        g[2 * w + 1] = fmaf(xr[e], ri[e], fmaf(-xi[e], rr[e], g[2 * w + 1]));
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0)
+                mbar_arrive(&empty[s]);
+        }
+        if (bad)
+            flags |= FLAG_DOMAIN;
+
+        // ---- per-warp reduction of this thread's sums -------------------
+        const double l_w = warp_sum(lacc);
+        const double e_w = warp_sum((double)eacc);
+        const int cw = warp - 1;
+        if (lane == 0) {
+            red[cw][0] = l_w;
+            red[cw][1] = e_w;
+        }
+        if constexpr (GRAD) {
+#pragma unroll
+            for (int c = 0; c < 2 * N; ++c) {
+                const double v = warp_sum((double)g[c]);
+                if (lane == 0)
+                    red[cw][2 + c] = v;
+            }
+        } else {
+            if (lane == 0)
+                for (int c = 0; c < 2 * N; ++c)
+                    red[cw][2 + c] = 0.0;
+        }
+    }
+    if (flags)
+        atomicOr(&s_flags, flags);
+    __syncthreads();
+
+    // ---- block partial, fixed order over warps -------------------------
+    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < CW; ++w)
+            v += red[w][c];
+        a.partials[(size_t)blockIdx.x * NC + c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_flags)
+            atomicOr(work_flags, s_flags);
+        __threadfence();
+        const unsigned t = atomicAdd(a.ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last)
+        return;
+
+    // ---- last CTA: deterministic final sum + normalisation term ---------
+    __threadfence();
+    const int nwarps = blockDim.x >> 5;
+    for (int c = warp; c < NC; c += nwarps) {
+        double v = 0.0;
+        for (int b = lane; b < (int)gridDim.x; b += 32)
+            v += __ldcg(&a.partials[(size_t)b * NC + c]);
+        v = warp_sum(v);
+        if (lane == 0)
+            fin[c] = v;
+    }
+    // (M V)_a in FP64, one thread per wave
+    const int Nw = a.n_waves;
+    for (int w = threadIdx.x; w < Nw; w += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int b = 0; b < Nw; ++b) {
+            const double mr = a.M[2 * (w * Nw + b)], mi = a.M[2 * (w * Nw + b) + 1];
+            const double vr = a.V[2 * b], vi = a.V[2 * b + 1];
+            re = fma(mr, vr, fma(-mi, vi, re));
+            im = fma(mr, vi, fma(mi, vr, im));
+        }
+        mv_s[2 * w] = re;
+        mv_s[2 * w + 1] = im;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int wf = __ldcg(work_flags);
+        double nv = 0.0, corr = 0.0;
+        for (int w = 0; w < Nw; ++w) {
+            const double vr = a.V[2 * w], vi = a.V[2 * w + 1];
+            nv += vr * mv_s[2 * w] + vi * mv_s[2 * w + 1];
+            if (GRAD) {
+                const double dvr = vr - (double)__double2float_rn(vr);
+                const double dvi = vi - (double)__double2float_rn(vi);
+                corr += -fin[2 + 2 * w] * dvr - fin[3 + 2 * w] * dvi;
+            }
+        }
+        const double data = -(fin[0] + fin[1] * kLn2) + 2.0 * corr;
+        double nll = data + nv;
+        if (wf & FLAG_DOMAIN)
+            nll = INFINITY;
+        if (wf & FLAG_TIMEOUT)
+            nll = NAN;
+        a.nll[0] = nll;
+        if (a.grad) {
+            for (int c = 0; c < 2 * Nw; ++c)
+                a.grad[c] = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) ? 0.0 : (-fin[2 + c] + mv_s[c]);
+        }
+        if (wf)
+            atomicOr(a.status, wf);
+        if (a.done)
+            atomicAdd(a.done, 1);
+        *work_flags = 0;
+        *a.ticket = 0u;
+        __threadfence();
+    }
+}
+
+// Without the gradient the first-order correction needs g_data, which the
+// NLL-only kernel does not form; it therefore evaluates with the gradient
+// sums enabled but discards them (the extra FMAs hide under the HBM time).
+
+template <int N>
+cudaError_t configure_n()
+{
+    return cudaFuncSetAttribute(nll_amp_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)AmpCfg<N>::SMEM);
+}
+
+template <int N>
+cudaError_t launch_n(const CUtensorMap *map, const EvalArgs &a, int grid, int n_tiles,
+                     int *work_flags, cudaStream_t s)
+{
+    using C = AmpCfg<N>;
+    nll_amp_kernel<N, true><<<grid, C::THREADS, C::SMEM, s>>>(*map, a, n_tiles, work_flags);
+    return cudaGetLastError();
+}
+
+int pad_waves(int n)
+{
+    static const int pads[] = {4, 8, 12, 16, 20, 24, 32, 40, 48};
+    for (int p : pads)
+        if (n <= p)
+            return p;
+    return -1;
+}
+
+}  // namespace
+
+int amp_box_events(int n_waves)
+{
+    switch (pad_waves(n_waves)) {
+    case 4: return AmpCfg<4>::TE;
+    case 8: return AmpCfg<8>::TE;
+    case 12: return AmpCfg<12>::TE;
+    case 16: return AmpCfg<16>::TE;
+    case 20: return AmpCfg<20>::TE;
+    case 24: return AmpCfg<24>::TE;
+    case 32: return AmpCfg<32>::TE;
+    case 40: return AmpCfg<40>::TE;
+    case 48: return AmpCfg<48>::TE;
+    }
+    return -1;
+}
+
+int amp_box_rows(int n_waves) { return 2 * n_waves; }
+
+cudaError_t amp_configure()
+{
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {configure_n<4>(), configure_n<8>(), configure_n<12>(), configure_n<16>(),
+                          configure_n<20>(), configure_n<24>(), configure_n<32>(), configure_n<40>(),
+                          configure_n<48>()})
+        if (r != cudaSuccess)
+            e = r;
+    return e;
+}
+
+int amp_grid(int n_waves, int num_sms)
+{
+    (void)n_waves;
+    return num_sms;
+}
+
+size_t amp_partials_doubles(int n_waves, int num_sms)
+{
+    return (size_t)amp_grid(n_waves, num_sms) * (2 * kMaxWaves + 2) + 64;
+}
+
+// The work-flag word lives just past the partials in the same scratch
+// buffer (EvalArgs::partials), so one allocation serves both.
+cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
+                           int num_sms, cudaStream_t s)
+{
+    const int grid = amp_grid(amp.n_waves, num_sms);
+    const int te = amp_box_events(amp.n_waves);
+    if (te <= 0)
+        return cudaErrorInvalidValue;
+    const int n_tiles = (int)((amp.n + te - 1) / te);
+    int *work_flags = reinterpret_cast<int *>(a.partials + (size_t)grid * (2 * kMaxWaves + 2));
+    switch (pad_waves(amp.n_waves)) {
+    case 4: return launch_n<4>(map, a, grid, n_tiles, work_flags, s);
+    case 8: return launch_n<8>(map, a, grid, n_tiles, work_flags, s);
+    case 12: return launch_n<12>(map, a, grid, n_tiles, work_flags, s);
+    case 16: return launch_n<16>(map, a, grid, n_tiles, work_flags, s);
+    case 20: return launch_n<20>(map, a, grid, n_tiles, work_flags, s);
+    case 24: return launch_n<24>(map, a, grid, n_tiles, work_flags, s);
+    case 32: return launch_n<32>(map, a, grid, n_tiles, work_flags, s);
+    case 40: return launch_n<40>(map, a, grid, n_tiles, work_flags, s);
+    case 48: return launch_n<48>(map, a, grid, n_tiles, work_flags, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace pwa

@@ -1,0 +1,93 @@
+// Loading the sample into the device store (Sec. 2: amplitudes are computed
+// once per event and kept; Sec. 5, Table 1: "Start-up" and "Lookup table
+// creation").
+//
+//  pack:  event-major interleaved complex [n][N] (float or double pairs) ->
+//         structure-of-arrays planes, plane 2a = Re A_a, plane 2a+1 = Im A_a,
+//         events contiguous. Doubles are rounded to nearest float.
+//  table: planes -> per-event Hermitian table of Sec. 2, coefficient-major
+//         t[p][i]: p < N holds |A_a|^2, then for each pair a < b in
+//         row-major order two planes Re(A_a conj A_b), Im(A_a conj A_b).
+#include "pwa_internal.cuh"
+
+namespace pwa {
+
+namespace {
+
+constexpr int kPackEvents = 64;
+
+template <typename T2>
+__global__ void pack_kernel(const T2 *__restrict__ src, int64_t n, int N, float *__restrict__ planes,
+                            int64_t pitch)
+{
+    extern __shared__ float sm[];  // [2N][kPackEvents + 1]
+    constexpr int LD = kPackEvents + 1;
+    const int64_t e0 = (int64_t)blockIdx.x * kPackEvents;
+    const int cnt = (int)((n - e0) < kPackEvents ? (n - e0) : kPackEvents);
+    const T2 *in = src + e0 * N;
+    for (int idx = threadIdx.x; idx < cnt * N; idx += blockDim.x) {
+        const int e = idx / N, w = idx - e * N;
+        const T2 v = in[idx];
+        sm[(2 * w) * LD + e] = (float)v.x;   // round-to-nearest for doubles
+        sm[(2 * w + 1) * LD + e] = (float)v.y;
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 2 * N * kPackEvents; idx += blockDim.x) {
+        const int r = idx / kPackEvents, e = idx - r * kPackEvents;
+        if (e < cnt)
+            planes[r * pitch + e0 + e] = sm[r * LD + e];
+    }
+}
+
+__global__ void table_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n, int N,
+                             float *__restrict__ table, int64_t tpitch)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    float ar[kMaxWaves], ai[kMaxWaves];
+    for (int w = 0; w < N; ++w) {
+        ar[w] = planes[(2 * w) * pitch + i];
+        ai[w] = planes[(2 * w + 1) * pitch + i];
+    }
+    for (int w = 0; w < N; ++w)
+        table[w * tpitch + i] = fmaf(ar[w], ar[w], ai[w] * ai[w]);
+    int p = N;
+    for (int x = 0; x < N; ++x)
+        for (int y = x + 1; y < N; ++y) {
+            // A_x conj(A_y) = (ar_x ar_y + ai_x ai_y) + i (ai_x ar_y - ar_x ai_y)
+            table[(int64_t)p * tpitch + i] = fmaf(ar[x], ar[y], ai[x] * ai[y]);
+            table[(int64_t)(p + 1) * tpitch + i] = fmaf(ai[x], ar[y], -(ar[x] * ai[y]));
+            p += 2;
+        }
+}
+
+}  // namespace
+
+cudaError_t launch_pack(const void *src, int dtype, int64_t n, int n_waves, float *planes,
+                        int64_t pitch, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    const int64_t blocks = (n + kPackEvents - 1) / kPackEvents;
+    const size_t smem = (size_t)2 * n_waves * (kPackEvents + 1) * sizeof(float);
+    if (dtype == PWA_C64)
+        pack_kernel<float2><<<(unsigned)blocks, 256, smem, s>>>(
+            static_cast<const float2 *>(src), n, n_waves, planes, pitch);
+    else
+        pack_kernel<double2><<<(unsigned)blocks, 256, smem, s>>>(
+            static_cast<const double2 *>(src), n, n_waves, planes, pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_build(const Planes &amp, float *table, int64_t table_pitch, cudaStream_t s)
+{
+    if (amp.n <= 0)
+        return cudaSuccess;
+    const int64_t blocks = (amp.n + 127) / 128;
+    table_kernel<<<(unsigned)blocks, 128, 0, s>>>(amp.ptr, amp.pitch, amp.n, amp.n_waves, table,
+                                                   table_pitch);
+    return cudaGetLastError();
+}
+
+}  // namespace pwa

@@ -1,0 +1,543 @@
+// C ABI of libpwa: context, device store, and the per-call path of the
+// likelihood (declared and documented in include/pwa.h).
+//
+// Per call only the parameters cross to the device and only the likelihood
+// and gradient come back (Sec. 5): V is staged in pinned memory, copied in
+// one transfer together with a zeroed status word, the fused kernel runs,
+// and one transfer brings back [nll | grad | status].
+#include <cudaTypedefs.h>
+
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+
+#include "pwa_internal.cuh"
+
+using namespace pwa;
+
+struct pwa_ctx {
+    int device = 0;
+    pwa_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    int N = 0;
+    int form = PWA_FORM_AMP;
+
+    // sample
+    int64_t n_data = 0, n_mc = 0;
+    double n_gen = 0;
+    Planes data{}, mc{};
+    float *table = nullptr;
+    int64_t table_pitch = 0;
+    CUtensorMap data_map;
+    bool loaded = false, has_norm = false;
+    double *M = nullptr;  // [N][N] complex
+
+    // per-call buffers
+    double *d_io = nullptr;  // [nll K | grad 2NK | status,done | V 2NK]
+    double *h_io = nullptr;  // pinned mirror
+    double *d_work = nullptr;  // partials + work flag, then ticket and async status
+    unsigned *ticket = nullptr;
+    int *async_status = nullptr;
+
+    char err[512] = {0};
+};
+
+namespace {
+
+thread_local char g_create_err[512];
+
+int fail(pwa_ctx *ctx, int code, const char *fmt, ...)
+{
+    char *buf = ctx ? ctx->err : g_create_err;
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, 512, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+// Host-side fault injection for tests of the error paths: PWA_FAULT=alloc:N
+// makes the N-th device allocation of the process fail (no GPU state is
+// touched by the failure itself).
+std::atomic<long> g_alloc_count{0};
+
+bool injected_alloc_failure()
+{
+    static long target = [] {
+        const char *f = getenv("PWA_FAULT");
+        if (f && strncmp(f, "alloc:", 6) == 0)
+            return atol(f + 6);
+        return 0L;
+    }();
+    const long n = ++g_alloc_count;
+    return target > 0 && n == target;
+}
+
+int dev_alloc(pwa_ctx *ctx, void **p, size_t bytes, const char *what)
+{
+    *p = nullptr;
+    if (injected_alloc_failure())
+        return fail(ctx, PWA_ENOMEM, "injected allocation failure (%s, %zu bytes)", what, bytes);
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(ctx, PWA_ENOMEM, "cudaMalloc(%s, %zu bytes): %s", what, bytes,
+                    cudaGetErrorString(e));
+    }
+    return PWA_OK;
+}
+
+template <typename T>
+void dev_free(T *&p)
+{
+    if (p)
+        cudaFree(p);
+    p = nullptr;
+}
+
+#define CK(ctx, call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            cudaGetLastError();                                                            \
+            return fail(ctx, PWA_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+        }                                                                                  \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev)
+    {
+        cudaGetDevice(&prev);
+        if (prev != dev)
+            cudaSetDevice(dev);
+        else
+            prev = -1;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0)
+            cudaSetDevice(prev);
+    }
+};
+
+bool is_device_pointer(const void *p)
+{
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+size_t io_doubles(int N, int max_k) { return (size_t)max_k * (1 + 4 * (size_t)N) + 1; }
+
+void free_sample(pwa_ctx *c)
+{
+    dev_free(c->data.ptr);
+    dev_free(c->mc.ptr);
+    dev_free(c->table);
+    c->loaded = c->has_norm = false;
+}
+
+// Copy one sample into planes [2N][pitch]: device sources are packed
+// directly; host sources go through a bounded device staging buffer.
+int load_planes(pwa_ctx *c, const void *src, int64_t n, int dtype, Planes *out)
+{
+    const int N = c->N;
+    out->n = n;
+    out->n_waves = N;
+    out->pitch = round_up(n, 256);
+    int rc = dev_alloc(c, (void **)&out->ptr, (size_t)2 * N * out->pitch * sizeof(float), "planes");
+    if (rc)
+        return rc;
+    CK(c, cudaMemsetAsync(out->ptr, 0, (size_t)2 * N * out->pitch * sizeof(float), c->stream));
+    const size_t esz = (dtype == PWA_C64 ? 8 : 16) * (size_t)N;
+    if (is_device_pointer(src)) {
+        CK(c, launch_pack(src, dtype, n, N, out->ptr, out->pitch, c->stream));
+        return PWA_OK;
+    }
+    const int64_t chunk = (int64_t)((64u << 20) / esz) > 0 ? (int64_t)((64u << 20) / esz) : 1;
+    void *staging = nullptr;
+    rc = dev_alloc(c, &staging, (size_t)std::min<int64_t>(chunk, n) * esz, "staging");
+    if (rc)
+        return rc;
+    for (int64_t s = 0; s < n; s += chunk) {
+        const int64_t m = std::min(chunk, n - s);
+        cudaError_t e = cudaMemcpyAsync(staging, static_cast<const char *>(src) + s * esz, m * esz,
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = launch_pack(staging, dtype, m, N, out->ptr + s, out->pitch, c->stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(staging);
+            cudaGetLastError();
+            return fail(c, PWA_ECUDA, "loading amplitudes: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaFree(staging);
+    if (e != cudaSuccess)
+        return fail(c, PWA_ECUDA, "loading amplitudes: %s", cudaGetErrorString(e));
+    return PWA_OK;
+}
+
+int status_from_flags(pwa_ctx *c, int flags)
+{
+    if (flags & FLAG_TIMEOUT)
+        return fail(c, PWA_ETIMEOUT, "a device-side wait timed out; results are invalid");
+    if (flags & FLAG_DOMAIN)
+        return fail(c, PWA_EDOMAIN, "an intensity was not positive and finite (nll = +inf)");
+    return PWA_OK;
+}
+
+int check_eval_args(pwa_ctx *c, const void *V, int K, const void *nll)
+{
+    if (!V || !nll)
+        return fail(c, PWA_EINVAL, "null V or nll");
+    if (K < 1 || K > c->cfg.max_k)
+        return fail(c, PWA_EINVAL, "K=%d outside [1, max_k=%d]", K, c->cfg.max_k);
+    if (!c->loaded || !c->has_norm)
+        return fail(c, PWA_ESTATE, "pwa_load_events and pwa_build_norm must come first");
+    return PWA_OK;
+}
+
+// Enqueue the evaluation of K parameter sets (device pointers).
+int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgrad, int *status,
+                 int *done)
+{
+    const int N = c->N;
+    for (int k = 0; k < K; ++k) {
+        EvalArgs a{};
+        a.n_waves = N;
+        a.n_events = c->n_data;
+        a.V = dV + (size_t)2 * N * k;
+        a.M = c->M;
+        a.partials = c->d_work;
+        a.ticket = c->ticket;
+        a.status = status;
+        a.done = done;
+        a.nll = dnll + k;
+        a.grad = dgrad ? dgrad + (size_t)2 * N * k : nullptr;
+        cudaError_t e = cudaSuccess;
+        if (c->form == PWA_FORM_AMP)
+            e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream);
+        else
+            return fail(c, PWA_ENOTSUP, "form %d not available in this build", c->form);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PWA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+        }
+    }
+    return PWA_OK;
+}
+
+int eval_host(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
+{
+    int rc = check_eval_args(c, V, K, nll);
+    if (rc)
+        return rc;
+    DeviceGuard g(c->device);
+    const int N = c->N;
+    const size_t gK = (size_t)2 * N * K;
+    double *h_stat = c->h_io + K + gK;
+    int *hs = reinterpret_cast<int *>(h_stat);
+    hs[0] = 0;
+    hs[1] = 0;
+    memcpy(h_stat + 1, V, gK * sizeof(double));
+    double *d_stat = c->d_io + K + gK;
+    CK(c, cudaMemcpyAsync(d_stat, h_stat, (1 + gK) * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+    int *ds = reinterpret_cast<int *>(d_stat);
+    rc = enqueue_eval(c, d_stat + 1, K, c->d_io, grad ? c->d_io + K : nullptr, ds, ds + 1);
+    if (rc)
+        return rc;
+    CK(c, cudaMemcpyAsync(c->h_io, c->d_io, (K + gK + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (hs[1] != K)
+        return fail(c, PWA_ETIMEOUT, "only %d of %d evaluations finished", hs[1], K);
+    memcpy(nll, c->h_io, K * sizeof(double));
+    if (grad)
+        memcpy(grad, c->h_io + K, gK * sizeof(double));
+    return status_from_flags(c, hs[0]);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+}  // namespace
+
+namespace pwa {
+
+cudaError_t encode_planes_map(CUtensorMap *map, const float *base, int64_t n, int64_t pitch,
+                              int rows, int box_x, int box_y)
+{
+    auto fn = get_encode_fn();
+    if (!fn)
+        return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)box_x, (cuuint32_t)box_y};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+}  // namespace pwa
+
+extern "C" {
+
+int pwa_version(void) { return 100; }
+
+const char *pwa_last_error(const pwa_ctx *ctx) { return ctx ? ctx->err : g_create_err; }
+
+int pwa_table_bytes(int n_waves, int64_t n_events, int64_t *bytes)
+{
+    if (!bytes || n_waves < 1 || n_waves > kMaxWaves || n_events < 0)
+        return PWA_EINVAL;
+    *bytes = (int64_t)n_waves * n_waves * (int64_t)sizeof(float) * n_events;
+    return PWA_OK;
+}
+
+int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
+{
+    g_create_err[0] = 0;
+    if (!out || !cfg)
+        return fail(nullptr, PWA_EINVAL, "null out or cfg");
+    *out = nullptr;
+    if (cfg->n_waves < 1 || cfg->n_waves > kMaxWaves)
+        return fail(nullptr, PWA_EINVAL, "n_waves=%d outside [1, %d]", cfg->n_waves, kMaxWaves);
+    if (cfg->max_k < 1 || cfg->max_k > 65536)
+        return fail(nullptr, PWA_EINVAL, "max_k=%d outside [1, 65536]", cfg->max_k);
+    const int forms = cfg->forms ? cfg->forms : PWA_FORM_AMP;
+    if (forms & ~(PWA_FORM_AMP | PWA_FORM_TABLE))
+        return fail(nullptr, PWA_EINVAL, "unknown form bits 0x%x", forms);
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, PWA_ECUDA, "device %d not available (%d devices)", device, ndev);
+    }
+    DeviceGuard g(device);
+    cudaSetDevice(device);
+    pwa_ctx *c = new pwa_ctx();
+    c->device = device;
+    c->cfg = *cfg;
+    c->cfg.forms = forms;
+    c->N = cfg->n_waves;
+    c->form = (forms & PWA_FORM_AMP) ? PWA_FORM_AMP : PWA_FORM_TABLE;
+    int rc = PWA_OK;
+    auto bail = [&](int code) {
+        snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
+        pwa_destroy(c);
+        return code;
+    };
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess)
+        return bail(fail(c, PWA_ECUDA, "cannot query the SM count"));
+    if (cfg->stream) {
+        c->stream = static_cast<cudaStream_t>(cfg->stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(fail(c, PWA_ECUDA, "cudaStreamCreate failed"));
+        c->own_stream = true;
+    }
+    cudaError_t e = amp_configure();
+    if (e != cudaSuccess)
+        return bail(fail(c, PWA_ECUDA, "kernel configuration: %s", cudaGetErrorString(e)));
+    const size_t nio = io_doubles(c->N, cfg->max_k);
+    if ((rc = dev_alloc(c, (void **)&c->d_io, nio * sizeof(double), "io")))
+        return bail(rc);
+    if (cudaMallocHost((void **)&c->h_io, nio * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_io = nullptr;
+        return bail(fail(c, PWA_ENOMEM, "pinned host buffer"));
+    }
+    const size_t nwork = amp_partials_doubles(c->N, c->num_sms) + 8;
+    if ((rc = dev_alloc(c, (void **)&c->d_work, nwork * sizeof(double), "work")))
+        return bail(rc);
+    if (cudaMemset(c->d_work, 0, nwork * sizeof(double)) != cudaSuccess)
+        return bail(fail(c, PWA_ECUDA, "memset"));
+    c->ticket = reinterpret_cast<unsigned *>(c->d_work + nwork - 4);
+    c->async_status = reinterpret_cast<int *>(c->d_work + nwork - 2);
+    if ((rc = dev_alloc(c, (void **)&c->M, (size_t)2 * c->N * c->N * sizeof(double), "M")))
+        return bail(rc);
+    *out = c;
+    return PWA_OK;
+}
+
+int pwa_destroy(pwa_ctx *c)
+{
+    if (!c)
+        return PWA_OK;
+    DeviceGuard g(c->device);
+    if (c->stream)
+        cudaStreamSynchronize(c->stream);
+    free_sample(c);
+    dev_free(c->M);
+    dev_free(c->d_io);
+    dev_free(c->d_work);
+    if (c->h_io)
+        cudaFreeHost(c->h_io);
+    if (c->own_stream && c->stream)
+        cudaStreamDestroy(c->stream);
+    delete c;
+    return PWA_OK;
+}
+
+int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void *mc_amp,
+                    int64_t n_mc_acc, double n_mc_gen, int amp_dtype)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!data_amp || !mc_amp)
+        return fail(c, PWA_EINVAL, "null amplitude pointer");
+    if (n_data < 1 || n_mc_acc < 1)
+        return fail(c, PWA_EINVAL, "n_data=%lld and n_mc_acc=%lld must be >= 1",
+                    (long long)n_data, (long long)n_mc_acc);
+    if (!(n_mc_gen >= (double)n_mc_acc))
+        return fail(c, PWA_EINVAL, "n_mc_gen=%g must be >= n_mc_acc=%lld", n_mc_gen,
+                    (long long)n_mc_acc);
+    if (amp_dtype != PWA_C64 && amp_dtype != PWA_C128)
+        return fail(c, PWA_EINVAL, "amp_dtype=%d is neither PWA_C64 nor PWA_C128", amp_dtype);
+    if (n_data > ((int64_t)1 << 31) - 1024 || n_mc_acc > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "samples are limited to 2^31 - 1024 events");
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_sample(c);
+    int rc = load_planes(c, data_amp, n_data, amp_dtype, &c->data);
+    if (!rc)
+        rc = load_planes(c, mc_amp, n_mc_acc, amp_dtype, &c->mc);
+    if (!rc && (c->cfg.forms & PWA_FORM_TABLE)) {
+        c->table_pitch = c->data.pitch;
+        rc = dev_alloc(c, (void **)&c->table, (size_t)c->N * c->N * c->table_pitch * sizeof(float),
+                       "table");
+        if (!rc) {
+            cudaError_t e = launch_table_build(c->data, c->table, c->table_pitch, c->stream);
+            if (e != cudaSuccess)
+                rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!rc) {
+        cudaError_t e = encode_planes_map(&c->data_map, c->data.ptr, c->data.n, c->data.pitch,
+                                          2 * c->N, amp_box_events(c->N), amp_box_rows(c->N));
+        if (e != cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "tensor map encode failed");
+    }
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "loading: %s", cudaGetErrorString(e));
+    }
+    if (rc) {
+        free_sample(c);
+        return rc;
+    }
+    c->n_data = n_data;
+    c->n_mc = n_mc_acc;
+    c->n_gen = n_mc_gen;
+    c->loaded = true;
+    c->has_norm = false;
+    return PWA_OK;
+}
+
+int pwa_build_norm(pwa_ctx *c, double *M_out)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!c->loaded)
+        return fail(c, PWA_ESTATE, "pwa_load_events must come first");
+    DeviceGuard g(c->device);
+    double *scratch = nullptr;
+    int rc = dev_alloc(c, (void **)&scratch, norm_scratch_bytes(c->N, c->num_sms), "norm scratch");
+    if (rc)
+        return rc;
+    cudaError_t e = launch_build_norm(c->mc, c->n_gen, c->M, scratch, c->num_sms, c->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(c->stream);
+    cudaFree(scratch);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "build_norm: %s", cudaGetErrorString(e));
+    }
+    if (M_out)
+        CK(c, cudaMemcpy(M_out, c->M, (size_t)2 * c->N * c->N * sizeof(double),
+                         cudaMemcpyDeviceToHost));
+    c->has_norm = true;
+    return PWA_OK;
+}
+
+int pwa_set_form(pwa_ctx *c, int form)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (form != PWA_FORM_AMP && form != PWA_FORM_TABLE)
+        return fail(c, PWA_EINVAL, "unknown form %d", form);
+    if (!(c->cfg.forms & form))
+        return fail(c, PWA_ESTATE, "form %d was not requested at pwa_create", form);
+    c->form = form;
+    return PWA_OK;
+}
+
+int pwa_nll(pwa_ctx *c, const double *V, int K, double *nll)
+{
+    if (!c)
+        return PWA_EINVAL;
+    return eval_host(c, V, K, nll, nullptr);
+}
+
+int pwa_nll_grad(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!grad)
+        return fail(c, PWA_EINVAL, "null grad");
+    return eval_host(c, V, K, nll, grad);
+}
+
+int pwa_nll_grad_async(pwa_ctx *c, const double *d_V, int K, double *d_nll, double *d_grad)
+{
+    if (!c)
+        return PWA_EINVAL;
+    int rc = check_eval_args(c, d_V, K, d_nll);
+    if (rc)
+        return rc;
+    DeviceGuard g(c->device);
+    return enqueue_eval(c, d_V, K, d_nll, d_grad, c->async_status, nullptr);
+}
+
+int pwa_sync(pwa_ctx *c)
+{
+    if (!c)
+        return PWA_EINVAL;
+    DeviceGuard g(c->device);
+    int flags = 0;
+    CK(c, cudaMemcpyAsync(&flags, c->async_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemsetAsync(c->async_status, 0, sizeof(int), c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return status_from_flags(c, flags);
+}
+
+}  // extern "C"

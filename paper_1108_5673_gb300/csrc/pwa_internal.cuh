@@ -1,0 +1,196 @@
+// Internal declarations shared by the CUDA translation units of libpwa.
+// Device helpers here are thin inline-PTX wrappers for sm_103a: mbarrier,
+// TMA (cp.async.bulk.tensor) and a bounded wait built on %globaltimer.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pwa.h"
+
+namespace pwa {
+
+// Device-side status bits, OR-ed into a status word by the kernels.
+enum : int {
+    FLAG_DOMAIN = 1,   // an intensity was <= 0 or not finite
+    FLAG_TIMEOUT = 2,  // a bounded wait gave up
+};
+
+// Upper bound on any single device-side wait (nanoseconds).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+constexpr int kMaxWaves = 48;
+
+// --------------------------------------------------------------------------
+// PTX wrappers
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long global_timer_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase with the given parity to complete; gives up after
+// kWaitLimitNs and returns false (the caller records FLAG_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity))
+        return true;
+    const unsigned long long t0 = global_timer_ns();
+    for (;;) {
+        for (int i = 0; i < 64; ++i)
+            if (mbar_try_wait(bar, parity))
+                return true;
+        if (global_timer_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
+}
+
+// 2D tiled TMA load global -> shared, completion signalled on `bar`.
+// x is the innermost coordinate (elements); x * sizeof(elem) must be a
+// multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y,
+                                            uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Split x > 0 (finite, possibly subnormal) as x = f * 2^e with
+// f in [1/sqrt(2), sqrt(2)], so that ln x = e ln 2 + ln f with |ln f| <= 0.35.
+__device__ __forceinline__ float split_exponent(float x, int &e)
+{
+    int bits = __float_as_int(x);
+    int ex = (bits >> 23) & 0xff;
+    int adj = 0;
+    if (ex == 0) {  // subnormal: scale into the normal range first
+        x *= 16777216.0f;
+        bits = __float_as_int(x);
+        ex = (bits >> 23) & 0xff;
+        adj = -24;
+    }
+    int k = ex - 127;
+    float f = __int_as_float((bits & 0x007fffff) | 0x3f800000);
+    if (f > 1.41421356f) {
+        f *= 0.5f;
+        k += 1;
+    }
+    e = k + adj;
+    return f;
+}
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// --------------------------------------------------------------------------
+// Host-side launch interfaces between translation units
+// --------------------------------------------------------------------------
+
+// Per-launch arguments of the fused data-term kernels (both forms).
+struct EvalArgs {
+    int n_waves;
+    int64_t n_events;
+    const double *V;   // [n_waves] complex128 (device), the parameter set
+    const double *M;   // [n_waves][n_waves] complex128 (device)
+    double *partials;  // scratch [grid][stride] doubles
+    unsigned *ticket;  // zero on entry; reset to zero by the last block
+    int *status;       // status bits are OR-ed here
+    int *done;         // incremented by the last block (may be null)
+    double *nll;       // [1] output
+    double *grad;      // [n_waves] complex output (null: NLL only)
+};
+
+// Structure-of-arrays store: plane 2a holds Re A_a, plane 2a+1 holds Im A_a,
+// each plane `pitch` floats long with events contiguous.
+struct Planes {
+    float *ptr;
+    int64_t pitch;  // floats per plane (multiple of 256)
+    int64_t n;      // valid events
+    int n_waves;
+};
+
+// Encode a 2D tensor map over `rows` planes of `pitch` floats with a box of
+// box_x events x box_y planes. Returns cudaSuccess or an error.
+cudaError_t encode_planes_map(CUtensorMap *map, const float *base, int64_t n, int64_t pitch,
+                              int rows, int box_x, int box_y);
+
+// k_pack.cu
+cudaError_t launch_pack(const void *src, int dtype, int64_t n, int n_waves, float *planes,
+                        int64_t pitch, cudaStream_t s);
+cudaError_t launch_table_build(const Planes &amp, float *table, int64_t table_pitch,
+                               cudaStream_t s);
+
+// k_norm.cu
+size_t norm_scratch_bytes(int n_waves, int num_sms);
+cudaError_t launch_build_norm(const Planes &mc, double n_gen, double *M, double *scratch,
+                              int num_sms, cudaStream_t s);
+
+// k_nll_amp.cu
+int amp_grid(int n_waves, int num_sms);
+size_t amp_partials_doubles(int n_waves, int num_sms);
+cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
+                           int num_sms, cudaStream_t s);
+int amp_box_events(int n_waves);
+cudaError_t amp_configure();  // once per device: opt in to large shared memory
+int amp_box_rows(int n_waves);
+
+}  // namespace pwa

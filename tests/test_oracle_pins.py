@@ -348,3 +348,11 @@ def test_truth_recovery_accept_reject():
     t = np.concatenate([Tf.real, Tf.imag[1:]])
     pulls = (x - t) / np.sqrt(np.diag(cov))
     assert np.all(np.abs(pulls) < 5), pulls
+
+
+def test_blas_norm_matrix_matches_loops():
+    """The chunked library-matmul M used for large samples equals the plain loops."""
+    wl = synth.mixture_workload("t", synth.waves_linear(7), 10, 50_000)
+    M = oracle.norm_matrix(wl.A_mc, wl.n_gen)
+    Mb = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen, chunk=7000)
+    assert rel(Mb, M) < 1e-13
