@@ -3,20 +3,26 @@
 // and the normalisation term (Sec. 4: single precision per event, double
 // precision final sum).
 //
-// Per event i (one thread handles EPT adjacent events of a tile):
-//   S_i = sum_a Vhi_a A_a(i)            FP32, two partial accumulators
+// Per event i (each consumer thread handles two adjacent events of a tile,
+// packed in the two halves of FP32x2 registers):
+//   S_i = sum_a Vhi_a A_a(i)            FP32 compensated dot product (Dot2)
 //   I_i = |S_i|^2                        FP32
 //   ln I_i = e_i ln 2 + ln f_i           f_i in [2^-1/2, 2^1/2], e_i summed exactly
 //   r_i = S_i / I_i,  g_a += conj(A_a(i)) r_i
 // Vhi is V rounded to float. The remainder dV = V - Vhi is applied to the
 // NLL to first order in the final sum: NLL(V) = NLL(Vhi) + 2 Re(g_data^H dV)
 // (the second-order term is ~N_data * 2^-48 and far below FP32 rounding).
+// The compensated S keeps the per-event error of ln I near one float
+// rounding even where the waves interfere destructively (|S_i| much smaller
+// than sum_a |V_a A_a(i)|): a plain FP32 sum there loses digits in proportion
+// to that ratio, and over 1M events the loss adds up to ~1e-3 in the NLL.
 //
-// Data movement: a persistent grid (one CTA per SM) streams tiles of TE
+// Data movement: a persistent grid (one CTA per SM) streams tiles of 256
 // events x 2N planes from the structure-of-arrays store into a ring of
 // shared-memory stages with TMA (cp.async.bulk.tensor.2d); one producer
-// thread issues the copies, CW consumer warps compute. Every wait is bounded
-// (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
+// thread issues the copies; two groups of four consumer warps take
+// alternate tiles. Every wait is bounded (FLAG_TIMEOUT) so a stalled
+// pipeline returns instead of hanging.
 //
 // Cross-block reduction: each CTA writes 2N+2 doubles of partial sums; the
 // last CTA to finish (atomic ticket) adds them in block order, so the result
@@ -31,30 +37,22 @@ constexpr double kLn2 = 0.69314718055994530942;
 
 template <int N>
 struct AmpCfg {
-    static constexpr int CW = 4;                       // consumer warps
-    static constexpr int EPT = (N <= 24) ? 2 : 1;      // events per thread per tile
-    static constexpr int TE = CW * 32 * EPT;           // events per tile
+    static constexpr int GROUPS = 2;                   // consumer groups (alternate tiles)
+    static constexpr int GW = 4;                       // warps per group
+    static constexpr int CW = GROUPS * GW;             // consumer warps
+    static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
     static constexpr int ROWS = 2 * N;
     static constexpr uint32_t STAGE_BYTES = ROWS * TE * 4;
     static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
-    static constexpr bool AREG = (N <= 24);            // keep A in registers between passes
+    static constexpr bool VREG = (N <= 8);             // V pairs in registers (else smem)
+    static constexpr bool GPACK = (N <= 12);           // packed per-event gradient sums
     static constexpr int THREADS = (CW + 1) * 32;
     static constexpr int NC = 2 * N + 2;               // partial components
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
 };
 
-template <int EPT>
-__device__ __forceinline__ void lds_ept(const float *p, float (&x)[EPT])
-{
-    if constexpr (EPT == 2) {
-        float2 v = *reinterpret_cast<const float2 *>(p);
-        x[0] = v.x;
-        x[1] = v.y;
-    } else {
-        x[0] = *p;
-    }
-}
+__device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
 
 template <int N, bool GRAD>
 __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
@@ -62,14 +60,15 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
                    int *work_flags)
 {
     using C = AmpCfg<N>;
-    constexpr int TE = C::TE, EPT = C::EPT, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
+    constexpr int TE = C::TE, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
+    constexpr int GROUPS = C::GROUPS, GW = C::GW;
     constexpr int NC = C::NC;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tiles = reinterpret_cast<float *>(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
     uint64_t *empty = full + STAGES;
 
-    __shared__ float2 Vs[N];
+    __shared__ f2 Vd[2][N];  // (vr, vr) and (vi, vi) of Vhi, duplicated for packed use
     __shared__ double red[CW][NC];
     __shared__ double fin[NC];
     __shared__ double mv_s[2 * N];
@@ -80,7 +79,7 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CW);
+            mbar_init(&empty[s], GW);
         }
         fence_barrier_init();
         s_flags = 0;
@@ -93,25 +92,24 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
             tiles[(size_t)s * ROWS * TE + i] = 0.f;
     if (threadIdx.x < N) {
         const int w = threadIdx.x;
-        Vs[w] = (w < a.n_waves) ? make_float2(__double2float_rn(a.V[2 * w]),
-                                              __double2float_rn(a.V[2 * w + 1]))
-                                : make_float2(0.f, 0.f);
+        const float vr = (w < a.n_waves) ? __double2float_rn(a.V[2 * w]) : 0.f;
+        const float vi = (w < a.n_waves) ? __double2float_rn(a.V[2 * w + 1]) : 0.f;
+        Vd[0][w] = pk2(vr, vr);
+        Vd[1][w] = pk2(vi, vi);
     }
     __syncthreads();
 
+    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
+    const int n_my = (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     int flags = 0;
     double lacc = 0.0;
     long long eacc = 0;
-    float g[GRAD ? 2 * N : 1];
-#pragma unroll
-    for (int c = 0; c < (GRAD ? 2 * N : 1); ++c)
-        g[c] = 0.f;
 
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer: one thread issues the TMA copies ----------------
             int j = 0;
-            for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+            for (; j < n_my; ++j) {
                 const int s = j % STAGES;
                 const uint32_t u = j / STAGES;
                 if (j >= STAGES && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
@@ -119,7 +117,8 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
                     break;
                 }
                 mbar_arrive_expect_tx(&full[s], stage_tx);
-                tma_load_2d(tiles + (size_t)s * ROWS * TE, &map, tile * TE, 0, &full[s]);
+                tma_load_2d(tiles + (size_t)s * ROWS * TE, &map,
+                            ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[s]);
             }
             // no copy may still be landing in shared memory when the CTA exits
             for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q)
@@ -127,60 +126,60 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
                     flags |= FLAG_TIMEOUT;
         }
     } else {
-        // ---- consumers ----------------------------------------------------
-        const int ct = threadIdx.x - 32;
-        float vr[N], vi[N];
+        // ---- consumers: group grp takes tiles j = grp, grp + GROUPS, ... ---
+        const int cw = warp - 1;
+        const int grp = cw / GW;
+        const int ct = (cw % GW) * 32 + lane;  // thread within its group
+        f2 vr2[C::VREG ? N : 1], vi2[C::VREG ? N : 1];
+        if constexpr (C::VREG) {
 #pragma unroll
-        for (int w = 0; w < N; ++w) {
-            vr[w] = Vs[w].x;
-            vi[w] = Vs[w].y;
+            for (int w = 0; w < N; ++w) {
+                vr2[w] = Vd[0][w];
+                vi2[w] = Vd[1][w];
+            }
         }
+        constexpr int NG = C::GPACK ? 2 * N : 1;
+        constexpr int NGS = C::GPACK ? 1 : 2 * N;
+        f2 gp[NG];     // packed per-event-half gradient sums (Re, Im per wave)
+        float gs[NGS]; // scalar gradient sums
+#pragma unroll
+        for (int c = 0; c < NG; ++c)
+            gp[c] = 0ull;
+#pragma unroll
+        for (int c = 0; c < NGS; ++c)
+            gs[c] = 0.f;
+        const f2 Z = 0ull;
         int bad = 0;
-        int j = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++j) {
+        for (int j = grp; j < n_my; j += GROUPS) {
             const int s = j % STAGES;
             const uint32_t u = j / STAGES;
             if (!mbar_wait(&full[s], u & 1)) {
                 flags |= FLAG_TIMEOUT;
                 break;
             }
-            const float *T = tiles + (size_t)s * ROWS * TE + ct * EPT;
-            const int64_t ev0 = (int64_t)tile * TE + ct * EPT;
+            const float *T = tiles + (size_t)s * ROWS * TE + 2 * ct;
+            const int64_t ev0 = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * TE + 2 * ct;
 
-            float sr0[EPT], si0[EPT], sr1[EPT], si1[EPT];
-            float ar[C::AREG ? N : 1][EPT], ai[C::AREG ? N : 1][EPT];
-#pragma unroll
-            for (int e = 0; e < EPT; ++e)
-                sr0[e] = si0[e] = sr1[e] = si1[e] = 0.f;
+            // S for the two events, compensated
+            f2 sR = Z, cR = Z, sI = Z, cI = Z;
 #pragma unroll
             for (int w = 0; w < N; ++w) {
-                float xr[EPT], xi[EPT];
-                lds_ept<EPT>(T + (2 * w) * TE, xr);
-                lds_ept<EPT>(T + (2 * w + 1) * TE, xi);
-#pragma unroll
-                for (int e = 0; e < EPT; ++e) {
-                    if constexpr (C::AREG) {
-                        ar[w][e] = xr[e];
-                        ai[w][e] = xi[e];
-                    }
-                    if (w & 1) {
-                        sr1[e] = fmaf(vr[w], xr[e], sr1[e]);
-                        sr1[e] = fmaf(-vi[w], xi[e], sr1[e]);
-                        si1[e] = fmaf(vr[w], xi[e], si1[e]);
-                        si1[e] = fmaf(vi[w], xr[e], si1[e]);
-                    } else {
-                        sr0[e] = fmaf(vr[w], xr[e], sr0[e]);
-                        sr0[e] = fmaf(-vi[w], xi[e], sr0[e]);
-                        si0[e] = fmaf(vr[w], xi[e], si0[e]);
-                        si0[e] = fmaf(vi[w], xr[e], si0[e]);
-                    }
-                }
+                const f2 ar = lds2(T + (2 * w) * TE), ai = lds2(T + (2 * w + 1) * TE);
+                const f2 nar = sub2(Z, ar), nai = sub2(Z, ai);
+                const f2 xr = C::VREG ? vr2[w] : Vd[0][w];
+                const f2 xi = C::VREG ? vi2[w] : Vd[1][w];
+                // Re S += vr ar - vi ai ; Im S += vr ai + vi ar
+                dot2_step(sR, cR, xr, ar, nar);
+                dot2_step(sR, cR, xi, nai, ai);
+                dot2_step(sI, cI, xr, ai, nai);
+                dot2_step(sI, cI, xi, ar, nar);
             }
-            float rr[EPT], ri[EPT];
+            float Sr[2], Si[2], rr[2], ri[2];
+            upk2(add2(sR, cR), Sr[0], Sr[1]);
+            upk2(add2(sI, cI), Si[0], Si[1]);
 #pragma unroll
-            for (int e = 0; e < EPT; ++e) {
-                const float Sr = sr0[e] + sr1[e], Si = si0[e] + si1[e];
-                const float I = fmaf(Sr, Sr, Si * Si);
+            for (int e = 0; e < 2; ++e) {
+                const float I = fmaf(Sr[e], Sr[e], Si[e] * Si[e]);
                 const bool in = (ev0 + e) < a.n_events;
                 const bool ok = (I > 0.f) && (I < INFINITY);
                 rr[e] = 0.f;
@@ -192,32 +191,31 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
                         lacc += (double)logf(f);
                         eacc += ex;
                         const float rI = __frcp_rn(I);
-                        rr[e] = Sr * rI;
-                        ri[e] = Si * rI;
+                        rr[e] = Sr[e] * rI;
+                        ri[e] = Si[e] * rI;
                     } else {
                         bad = 1;
                     }
                 }
             }
             if constexpr (GRAD) {
+                const f2 RR = pk2(rr[0], rr[1]), RI = pk2(ri[0], ri[1]);
+                const f2 NRR = pk2(-rr[0], -rr[1]);
 #pragma unroll
                 for (int w = 0; w < N; ++w) {
-                    float xr[EPT], xi[EPT];
-                    if constexpr (C::AREG) {
-#pragma unroll
-                        for (int e = 0; e < EPT; ++e) {
-                            xr[e] = ar[w][e];
-                            xi[e] = ai[w][e];
-                        }
+                    const f2 ar = lds2(T + (2 * w) * TE), ai = lds2(T + (2 * w + 1) * TE);
+                    // conj(A) r = (ar rr + ai ri) + i (ar ri - ai rr)
+                    if constexpr (C::GPACK) {
+                        gp[2 * w] = fma2(ar, RR, fma2(ai, RI, gp[2 * w]));
+                        gp[2 * w + 1] = fma2(ar, RI, fma2(ai, NRR, gp[2 * w + 1]));
                     } else {
-                        lds_ept<EPT>(T + (2 * w) * TE, xr);
-                        lds_ept<EPT>(T + (2 * w + 1) * TE, xi);
-                    }
-#pragma unroll
-                    for (int e = 0; e < EPT; ++e) {
-                        // conj(A) * r = (xr rr + xi ri) + i (xr ri - xi rr)
-                        g[2 * w] = fmaf(xr[e], rr[e], fmaf(xi[e], ri[e], g[2 * w]));
-                        g[2 * w + 1] = fmaf(xr[e], ri[e], fmaf(-xi[e], rr[e], g[2 * w + 1]));
+                        float a0, a1, b0, b1;
+                        upk2(ar, a0, a1);
+                        upk2(ai, b0, b1);
+                        gs[2 * w] = fmaf(a0, rr[0], fmaf(b0, ri[0], gs[2 * w]));
+                        gs[2 * w] = fmaf(a1, rr[1], fmaf(b1, ri[1], gs[2 * w]));
+                        gs[2 * w + 1] = fmaf(a0, ri[0], fmaf(-b0, rr[0], gs[2 * w + 1]));
+                        gs[2 * w + 1] = fmaf(a1, ri[1], fmaf(-b1, rr[1], gs[2 * w + 1]));
                     }
                 }
             }
@@ -231,22 +229,23 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
         // ---- per-warp reduction of this thread's sums -------------------
         const double l_w = warp_sum(lacc);
         const double e_w = warp_sum((double)eacc);
-        const int cw = warp - 1;
         if (lane == 0) {
             red[cw][0] = l_w;
             red[cw][1] = e_w;
         }
-        if constexpr (GRAD) {
 #pragma unroll
-            for (int c = 0; c < 2 * N; ++c) {
-                const double v = warp_sum((double)g[c]);
-                if (lane == 0)
-                    red[cw][2 + c] = v;
+        for (int c = 0; c < 2 * N; ++c) {
+            double v;
+            if constexpr (C::GPACK) {
+                float h0, h1;
+                upk2(gp[c], h0, h1);
+                v = (double)h0 + (double)h1;
+            } else {
+                v = (double)gs[c];
             }
-        } else {
+            v = warp_sum(v);
             if (lane == 0)
-                for (int c = 0; c < 2 * N; ++c)
-                    red[cw][2 + c] = 0.0;
+                red[cw][2 + c] = GRAD ? v : 0.0;
         }
     }
     if (flags)

@@ -125,6 +125,61 @@ __device__ __forceinline__ float split_exponent(float x, int &e)
     return f;
 }
 
+// ---- packed FP32 pairs (two events per 64-bit register pair) -------------
+// Blackwell executes these as one instruction for both halves.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk2(float lo, float hi)
+{
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2 v, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c)
+{
+    f2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b)
+{
+    f2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 add2(f2 a, f2 b)
+{
+    f2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b)
+{
+    f2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// One step of the compensated dot product (Ogita, Rump and Oishi, "Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26 (2005), algorithm Dot2):
+// (s, c) += x * y with the product split exactly by FMA (TwoProduct) and the
+// sum by Knuth's TwoSum. yn must equal -y. Uses hn = x * yn = -(x*y rounded),
+// r = fma(x, y, hn) = the exact product error.
+__device__ __forceinline__ void dot2_step(f2 &s, f2 &c, f2 x, f2 y, f2 yn)
+{
+    const f2 hn = mul2(x, yn);
+    const f2 r = fma2(x, y, hn);
+    const f2 t = sub2(s, hn);           // s + h
+    const f2 bb = sub2(t, s);
+    const f2 err = sub2(sub2(s, sub2(t, bb)), add2(hn, bb));
+    s = t;
+    c = add2(c, add2(err, r));
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
