@@ -122,8 +122,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -146,7 +146,9 @@ def main():
 
     wl = synth.paper_scale()
     V = synth.start_points(N_WAVES, 1, seed=synth.SEED_STARTS + rank)[0]
-    stream = torch.cuda.current_stream()
+    # one explicit stream for the library, the L2 flush and the timing events
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     L = pwa.Likelihood(N_WAVES, device=local, max_k=1, stream=stream.cuda_stream)
     L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
     t0 = time.perf_counter()

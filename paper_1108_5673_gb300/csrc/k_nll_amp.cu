@@ -5,13 +5,15 @@
 //
 // Per event i (each consumer thread handles two adjacent events of a tile,
 // packed in the two halves of FP32x2 registers):
-//   S_i = sum_a Vhi_a A_a(i)            FP32 compensated dot product (Dot2)
+//   S_i = sum_a (Vhi_a + Vlo_a) A_a(i)  FP32 compensated dot product (Dot2)
 //   I_i = |S_i|^2                        FP32
 //   ln I_i = e_i ln 2 + ln f_i           f_i in [2^-1/2, 2^1/2], e_i summed exactly
 //   r_i = S_i / I_i,  g_a += conj(A_a(i)) r_i
-// Vhi is V rounded to float. The remainder dV = V - Vhi is applied to the
-// NLL to first order in the final sum: NLL(V) = NLL(Vhi) + 2 Re(g_data^H dV)
-// (the second-order term is ~N_data * 2^-48 and far below FP32 rounding).
+// V is carried as a float pair Vhi + Vlo (48 significant bits): rounding V
+// to one float would shift ln I of every event coherently (an NLL bias of
+// order N_data * 2^-24) and, at events where S is small, perturb S/I
+// visibly. The products Vlo_a A_a are added plainly into the compensation
+// term, since they are ~2^-24 of the leading ones.
 // The compensated S keeps the per-event error of ln I near one float
 // rounding even where the waves interfere destructively (|S_i| much smaller
 // than sum_a |V_a A_a(i)|): a plain FP32 sum there loses digits in proportion
@@ -68,7 +70,7 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
     uint64_t *empty = full + STAGES;
 
-    __shared__ f2 Vd[2][N];  // (vr, vr) and (vi, vi) of Vhi, duplicated for packed use
+    __shared__ f2 Vd[4][N];  // (vr,vr), (vi,vi) of Vhi and of Vlo, duplicated for packed use
     __shared__ double red[CW][NC];
     __shared__ double fin[NC];
     __shared__ double mv_s[2 * N];
@@ -92,10 +94,14 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
             tiles[(size_t)s * ROWS * TE + i] = 0.f;
     if (threadIdx.x < N) {
         const int w = threadIdx.x;
-        const float vr = (w < a.n_waves) ? __double2float_rn(a.V[2 * w]) : 0.f;
-        const float vi = (w < a.n_waves) ? __double2float_rn(a.V[2 * w + 1]) : 0.f;
+        const double dr = (w < a.n_waves) ? a.V[2 * w] : 0.0;
+        const double di = (w < a.n_waves) ? a.V[2 * w + 1] : 0.0;
+        const float vr = __double2float_rn(dr), vi = __double2float_rn(di);
+        const float lr = __double2float_rn(dr - (double)vr), li = __double2float_rn(di - (double)vi);
         Vd[0][w] = pk2(vr, vr);
         Vd[1][w] = pk2(vi, vi);
+        Vd[2][w] = pk2(lr, lr);
+        Vd[3][w] = pk2(li, li);
     }
     __syncthreads();
 
@@ -173,6 +179,9 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
                 dot2_step(sR, cR, xi, nai, ai);
                 dot2_step(sI, cI, xr, ai, nai);
                 dot2_step(sI, cI, xi, ar, nar);
+                const f2 lr = Vd[2][w], li = Vd[3][w];
+                cR = fma2(lr, ar, fma2(li, nai, cR));
+                cI = fma2(lr, ai, fma2(li, ar, cI));
             }
             float Sr[2], Si[2], rr[2], ri[2];
             upk2(add2(sR, cR), Sr[0], Sr[1]);
@@ -298,17 +307,10 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
     __syncthreads();
     if (threadIdx.x == 0) {
         const int wf = __ldcg(work_flags);
-        double nv = 0.0, corr = 0.0;
-        for (int w = 0; w < Nw; ++w) {
-            const double vr = a.V[2 * w], vi = a.V[2 * w + 1];
-            nv += vr * mv_s[2 * w] + vi * mv_s[2 * w + 1];
-            if (GRAD) {
-                const double dvr = vr - (double)__double2float_rn(vr);
-                const double dvi = vi - (double)__double2float_rn(vi);
-                corr += -fin[2 + 2 * w] * dvr - fin[3 + 2 * w] * dvi;
-            }
-        }
-        const double data = -(fin[0] + fin[1] * kLn2) + 2.0 * corr;
+        double nv = 0.0;
+        for (int w = 0; w < Nw; ++w)
+            nv += a.V[2 * w] * mv_s[2 * w] + a.V[2 * w + 1] * mv_s[2 * w + 1];
+        const double data = -(fin[0] + fin[1] * kLn2);
         double nll = data + nv;
         if (wf & FLAG_DOMAIN)
             nll = INFINITY;
@@ -329,9 +331,8 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
     }
 }
 
-// Without the gradient the first-order correction needs g_data, which the
-// NLL-only kernel does not form; it therefore evaluates with the gradient
-// sums enabled but discards them (the extra FMAs hide under the HBM time).
+// The NLL-only call runs the same kernel and discards the gradient sums (the
+// extra FMAs hide under the HBM time).
 
 template <int N>
 cudaError_t configure_n()
