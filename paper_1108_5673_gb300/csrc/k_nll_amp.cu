@@ -5,30 +5,40 @@
 //
 // Per event i (each consumer thread handles two adjacent events of a tile,
 // packed in the two halves of FP32x2 registers):
-//   S_i = sum_a (Vhi_a + Vlo_a) A_a(i)  FP32 compensated dot product (Dot2)
-//   I_i = |S_i|^2                        FP32
-//   ln I_i = e_i ln 2 + ln f_i           f_i in [2^-1/2, 2^1/2], e_i summed exactly
+//   S_i = sum_a (Vhi_a + Vlo_a) A_a(i)   FP32, error-free extraction (below)
+//   I_i = |S_i|^2                         FP32
+//   ln I_i = e_i ln 2 + ln f_i            f_i in [2^-1/2, 2^1/2], e_i summed exactly
 //   r_i = S_i / I_i,  g_a += conj(A_a(i)) r_i
-// V is carried as a float pair Vhi + Vlo (48 significant bits): rounding V
-// to one float would shift ln I of every event coherently (an NLL bias of
-// order N_data * 2^-24) and, at events where S is small, perturb S/I
-// visibly. The products Vlo_a A_a are added plainly into the compensation
-// term, since they are ~2^-24 of the leading ones.
-// The compensated S keeps the per-event error of ln I near one float
-// rounding even where the waves interfere destructively (|S_i| much smaller
-// than sum_a |V_a A_a(i)|): a plain FP32 sum there loses digits in proportion
-// to that ratio, and over 1M events the loss adds up to ~1e-3 in the NLL.
+//
+// Accuracy of S. A plain FP32 sum of the 4N real products loses digits where
+// the waves interfere destructively (|S_i| much smaller than
+// B_i = sum_a |V_a|_1 |A_a(i)|_1); over 1M events those losses add up to
+// ~1e-3 in the NLL. Instead every product p = c * a is split exactly against
+// a power of two sigma >= 2 max_i B_i fixed per call:
+//     t = fma(c, a, sigma)       rounds c*a to a multiple of ulp(sigma)/2
+//     q = t - sigma              exact (Sterbenz), the high part of c*a
+//     r = fma(c, a, -q)          the remainder, |r| <= ulp(sigma)
+// The high parts are multiples of sigma 2^-24 whose running sum stays below
+// sigma, so it is accumulated exactly; the remainders are summed in FP32 with
+// an error ~2^-48 sigma. S = hi + lo is then correct to about one float
+// rounding however small it is relative to B_i (the same guarantee as a
+// doubled-precision dot product, at half its cost). sigma comes from V and
+// the per-wave maxima of |A| over the sample, so no per-event pre-pass is
+// needed. V is carried as a float pair Vhi + Vlo; the products Vlo A are
+// ~2^-24 of the leading ones and go straight into the low sum.
 //
 // Data movement: a persistent grid (one CTA per SM) streams tiles of 256
 // events x 2N planes from the structure-of-arrays store into a ring of
 // shared-memory stages with TMA (cp.async.bulk.tensor.2d); one producer
-// thread issues the copies; two groups of four consumer warps take
-// alternate tiles. Every wait is bounded (FLAG_TIMEOUT) so a stalled
-// pipeline returns instead of hanging.
+// thread issues the copies; GROUPS groups of four consumer warps take tiles
+// in turn. Every wait is bounded (FLAG_TIMEOUT) so a stalled pipeline
+// returns instead of hanging.
 //
 // Cross-block reduction: each CTA writes 2N+2 doubles of partial sums; the
 // last CTA to finish (atomic ticket) adds them in block order, so the result
 // is bitwise reproducible from run to run.
+#include <stdlib.h>
+
 #include "pwa_internal.cuh"
 
 namespace pwa {
@@ -37,9 +47,9 @@ namespace {
 
 constexpr double kLn2 = 0.69314718055994530942;
 
-template <int N>
+template <int N, int G>
 struct AmpCfg {
-    static constexpr int GROUPS = 2;                   // consumer groups (alternate tiles)
+    static constexpr int GROUPS = G;                   // consumer groups (tiles in turn)
     static constexpr int GW = 4;                       // warps per group
     static constexpr int CW = GROUPS * GW;             // consumer warps
     static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
@@ -47,21 +57,34 @@ struct AmpCfg {
     static constexpr uint32_t STAGE_BYTES = ROWS * TE * 4;
     static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
-    static constexpr bool VREG = (N <= 8);             // V pairs in registers (else smem)
-    static constexpr bool GPACK = (N <= 12);           // packed per-event gradient sums
     static constexpr int THREADS = (CW + 1) * 32;
     static constexpr int NC = 2 * N + 2;               // partial components
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
 };
 
+// Per-wave coefficients, each duplicated into both halves of a packed pair.
+struct alignas(16) WaveCoef {
+    f2 vr, vi, nvi;  // Vhi: Re, Im, -Im
+    f2 lr, li, nli;  // Vlo: Re, Im, -Im
+};
+
 __device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
 
-template <int N, bool GRAD>
-__global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
+// (hi, lo) += c * a, error-free high part against sg (see the file comment).
+__device__ __forceinline__ void extract_acc(f2 &hi, f2 &lo, f2 c, f2 a, f2 sg)
+{
+    const f2 t = fma2(c, a, sg);
+    const f2 nq = sub2(sg, t);       // -q, exact
+    hi = sub2(hi, nq);               // hi + q, exact
+    lo = add2(lo, fma2(c, a, nq));   // + remainder
+}
+
+template <int N, int G>
+__global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     nll_amp_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs a, const int n_tiles,
                    int *work_flags)
 {
-    using C = AmpCfg<N>;
+    using C = AmpCfg<N, G>;
     constexpr int TE = C::TE, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
     constexpr int GROUPS = C::GROUPS, GW = C::GW;
     constexpr int NC = C::NC;
@@ -70,7 +93,8 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
     uint64_t *empty = full + STAGES;
 
-    __shared__ f2 Vd[4][N];  // (vr,vr), (vi,vi) of Vhi and of Vlo, duplicated for packed use
+    __shared__ WaveCoef Vc[N];
+    __shared__ float s_sigma;
     __shared__ double red[CW][NC];
     __shared__ double fin[NC];
     __shared__ double mv_s[2 * N];
@@ -94,19 +118,42 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
             tiles[(size_t)s * ROWS * TE + i] = 0.f;
     if (threadIdx.x < N) {
         const int w = threadIdx.x;
-        const double dr = (w < a.n_waves) ? a.V[2 * w] : 0.0;
-        const double di = (w < a.n_waves) ? a.V[2 * w + 1] : 0.0;
+        const bool on = w < a.n_waves;
+        const double dr = on ? a.V[2 * w] : 0.0, di = on ? a.V[2 * w + 1] : 0.0;
         const float vr = __double2float_rn(dr), vi = __double2float_rn(di);
         const float lr = __double2float_rn(dr - (double)vr), li = __double2float_rn(di - (double)vi);
-        Vd[0][w] = pk2(vr, vr);
-        Vd[1][w] = pk2(vi, vi);
-        Vd[2][w] = pk2(lr, lr);
-        Vd[3][w] = pk2(li, li);
+        Vc[w].vr = pk2(vr, vr);
+        Vc[w].vi = pk2(vi, vi);
+        Vc[w].nvi = pk2(-vi, -vi);
+        Vc[w].lr = pk2(lr, lr);
+        Vc[w].li = pk2(li, li);
+        Vc[w].nli = pk2(-li, -li);
+    }
+    if (warp == 1) {
+        // sigma = a power of two >= 2 * sum_a |V_a|_1 * max_i |A_a(i)|_1, with margin
+        float b = 0.f;
+        for (int w = lane; w < a.n_waves; w += 32) {
+            const float v1 = fabsf(__double2float_ru(fabs(a.V[2 * w]))) +
+                             fabsf(__double2float_ru(fabs(a.V[2 * w + 1])));
+            b = fmaf(v1, a.amax[w], b);
+        }
+        b = warp_sum(b);
+        if (lane == 0) {
+            const float target = 2.5f * b;  // covers rounding of the bound itself
+            int e = 0;
+            if (target > 0.f) {
+                e = ((__float_as_int(target) >> 23) & 0xff) - 126;  // target < 2^e
+                if (e < -100)
+                    e = -100;
+            }
+            s_sigma = (target > 0.f) ? ldexpf(1.0f, e) : 0.f;
+        }
     }
     __syncthreads();
 
     // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
-    const int n_my = (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int n_my =
+        (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     int flags = 0;
     double lacc = 0.0;
     long long eacc = 0;
@@ -136,25 +183,13 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
         const int cw = warp - 1;
         const int grp = cw / GW;
         const int ct = (cw % GW) * 32 + lane;  // thread within its group
-        f2 vr2[C::VREG ? N : 1], vi2[C::VREG ? N : 1];
-        if constexpr (C::VREG) {
-#pragma unroll
-            for (int w = 0; w < N; ++w) {
-                vr2[w] = Vd[0][w];
-                vi2[w] = Vd[1][w];
-            }
-        }
-        constexpr int NG = C::GPACK ? 2 * N : 1;
-        constexpr int NGS = C::GPACK ? 1 : 2 * N;
-        f2 gp[NG];     // packed per-event-half gradient sums (Re, Im per wave)
-        float gs[NGS]; // scalar gradient sums
-#pragma unroll
-        for (int c = 0; c < NG; ++c)
-            gp[c] = 0ull;
-#pragma unroll
-        for (int c = 0; c < NGS; ++c)
-            gs[c] = 0.f;
+        const float sigma = s_sigma;
+        const f2 SG = pk2(sigma, sigma);
         const f2 Z = 0ull;
+        float gs[2 * N];
+#pragma unroll
+        for (int c = 0; c < 2 * N; ++c)
+            gs[c] = 0.f;
         int bad = 0;
         for (int j = grp; j < n_my; j += GROUPS) {
             const int s = j % STAGES;
@@ -166,26 +201,22 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
             const float *T = tiles + (size_t)s * ROWS * TE + 2 * ct;
             const int64_t ev0 = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * TE + 2 * ct;
 
-            // S for the two events, compensated
-            f2 sR = Z, cR = Z, sI = Z, cI = Z;
+            f2 hR = Z, lR = Z, hI = Z, lI = Z;
 #pragma unroll
             for (int w = 0; w < N; ++w) {
                 const f2 ar = lds2(T + (2 * w) * TE), ai = lds2(T + (2 * w + 1) * TE);
-                const f2 nar = sub2(Z, ar), nai = sub2(Z, ai);
-                const f2 xr = C::VREG ? vr2[w] : Vd[0][w];
-                const f2 xi = C::VREG ? vi2[w] : Vd[1][w];
-                // Re S += vr ar - vi ai ; Im S += vr ai + vi ar
-                dot2_step(sR, cR, xr, ar, nar);
-                dot2_step(sR, cR, xi, nai, ai);
-                dot2_step(sI, cI, xr, ai, nai);
-                dot2_step(sI, cI, xi, ar, nar);
-                const f2 lr = Vd[2][w], li = Vd[3][w];
-                cR = fma2(lr, ar, fma2(li, nai, cR));
-                cI = fma2(lr, ai, fma2(li, ar, cI));
+                const WaveCoef &cf = Vc[w];
+                // Re S = vr ar - vi ai ; Im S = vr ai + vi ar
+                extract_acc(hR, lR, cf.vr, ar, SG);
+                extract_acc(hR, lR, cf.nvi, ai, SG);
+                extract_acc(hI, lI, cf.vr, ai, SG);
+                extract_acc(hI, lI, cf.vi, ar, SG);
+                lR = fma2(cf.lr, ar, fma2(cf.nli, ai, lR));
+                lI = fma2(cf.lr, ai, fma2(cf.li, ar, lI));
             }
             float Sr[2], Si[2], rr[2], ri[2];
-            upk2(add2(sR, cR), Sr[0], Sr[1]);
-            upk2(add2(sI, cI), Si[0], Si[1]);
+            upk2(add2(hR, lR), Sr[0], Sr[1]);
+            upk2(add2(hI, lI), Si[0], Si[1]);
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const float I = fmaf(Sr[e], Sr[e], Si[e] * Si[e]);
@@ -207,26 +238,16 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
                     }
                 }
             }
-            if constexpr (GRAD) {
-                const f2 RR = pk2(rr[0], rr[1]), RI = pk2(ri[0], ri[1]);
-                const f2 NRR = pk2(-rr[0], -rr[1]);
 #pragma unroll
-                for (int w = 0; w < N; ++w) {
-                    const f2 ar = lds2(T + (2 * w) * TE), ai = lds2(T + (2 * w + 1) * TE);
-                    // conj(A) r = (ar rr + ai ri) + i (ar ri - ai rr)
-                    if constexpr (C::GPACK) {
-                        gp[2 * w] = fma2(ar, RR, fma2(ai, RI, gp[2 * w]));
-                        gp[2 * w + 1] = fma2(ar, RI, fma2(ai, NRR, gp[2 * w + 1]));
-                    } else {
-                        float a0, a1, b0, b1;
-                        upk2(ar, a0, a1);
-                        upk2(ai, b0, b1);
-                        gs[2 * w] = fmaf(a0, rr[0], fmaf(b0, ri[0], gs[2 * w]));
-                        gs[2 * w] = fmaf(a1, rr[1], fmaf(b1, ri[1], gs[2 * w]));
-                        gs[2 * w + 1] = fmaf(a0, ri[0], fmaf(-b0, rr[0], gs[2 * w + 1]));
-                        gs[2 * w + 1] = fmaf(a1, ri[1], fmaf(-b1, rr[1], gs[2 * w + 1]));
-                    }
-                }
+            for (int w = 0; w < N; ++w) {
+                float a0, a1, b0, b1;
+                upk2(lds2(T + (2 * w) * TE), a0, a1);
+                upk2(lds2(T + (2 * w + 1) * TE), b0, b1);
+                // conj(A) r = (ar rr + ai ri) + i (ar ri - ai rr)
+                gs[2 * w] = fmaf(a0, rr[0], fmaf(b0, ri[0], gs[2 * w]));
+                gs[2 * w] = fmaf(a1, rr[1], fmaf(b1, ri[1], gs[2 * w]));
+                gs[2 * w + 1] = fmaf(a0, ri[0], fmaf(-b0, rr[0], gs[2 * w + 1]));
+                gs[2 * w + 1] = fmaf(a1, ri[1], fmaf(-b1, rr[1], gs[2 * w + 1]));
             }
             __syncwarp();
             if (lane == 0)
@@ -244,17 +265,9 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
         }
 #pragma unroll
         for (int c = 0; c < 2 * N; ++c) {
-            double v;
-            if constexpr (C::GPACK) {
-                float h0, h1;
-                upk2(gp[c], h0, h1);
-                v = (double)h0 + (double)h1;
-            } else {
-                v = (double)gs[c];
-            }
-            v = warp_sum(v);
+            const double v = warp_sum((double)gs[c]);
             if (lane == 0)
-                red[cw][2 + c] = GRAD ? v : 0.0;
+                red[cw][2 + c] = v;
         }
     }
     if (flags)
@@ -337,16 +350,37 @@ __global__ void __launch_bounds__(AmpCfg<N>::THREADS, 1)
 template <int N>
 cudaError_t configure_n()
 {
-    return cudaFuncSetAttribute(nll_amp_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)AmpCfg<N>::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(nll_amp_kernel<N, 2>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)AmpCfg<N, 2>::SMEM);
+    cudaError_t f = cudaFuncSetAttribute(nll_amp_kernel<N, 3>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)AmpCfg<N, 3>::SMEM);
+    return e != cudaSuccess ? e : f;
+}
+
+// Consumer groups per CTA: 2 (9 warps, up to 168 registers per thread) or
+// 3 (13 warps, 128 registers). PWA_AMP_GROUPS overrides the default.
+int amp_groups()
+{
+    static const int g = [] {
+        const char *v = getenv("PWA_AMP_GROUPS");
+        return (v && atoi(v) == 3) ? 3 : (v && atoi(v) == 2) ? 2 : 0;
+    }();
+    return g;
 }
 
 template <int N>
 cudaError_t launch_n(const CUtensorMap *map, const EvalArgs &a, int grid, int n_tiles,
                      int *work_flags, cudaStream_t s)
 {
-    using C = AmpCfg<N>;
-    nll_amp_kernel<N, true><<<grid, C::THREADS, C::SMEM, s>>>(*map, a, n_tiles, work_flags);
+    const int g = amp_groups() ? amp_groups() : (N <= 12 ? 3 : 2);
+    if (g == 3)
+        nll_amp_kernel<N, 3><<<grid, AmpCfg<N, 3>::THREADS, AmpCfg<N, 3>::SMEM, s>>>(
+            *map, a, n_tiles, work_flags);
+    else
+        nll_amp_kernel<N, 2><<<grid, AmpCfg<N, 2>::THREADS, AmpCfg<N, 2>::SMEM, s>>>(
+            *map, a, n_tiles, work_flags);
     return cudaGetLastError();
 }
 
@@ -363,18 +397,7 @@ int pad_waves(int n)
 
 int amp_box_events(int n_waves)
 {
-    switch (pad_waves(n_waves)) {
-    case 4: return AmpCfg<4>::TE;
-    case 8: return AmpCfg<8>::TE;
-    case 12: return AmpCfg<12>::TE;
-    case 16: return AmpCfg<16>::TE;
-    case 20: return AmpCfg<20>::TE;
-    case 24: return AmpCfg<24>::TE;
-    case 32: return AmpCfg<32>::TE;
-    case 40: return AmpCfg<40>::TE;
-    case 48: return AmpCfg<48>::TE;
-    }
-    return -1;
+    return pad_waves(n_waves) > 0 ? AmpCfg<4, 2>::TE : -1;  // the same for every N and G
 }
 
 int amp_box_rows(int n_waves) { return 2 * n_waves; }

@@ -8,6 +8,8 @@
 //  table: planes -> per-event Hermitian table of Sec. 2, coefficient-major
 //         t[p][i]: p < N holds |A_a|^2, then for each pair a < b in
 //         row-major order two planes Re(A_a conj A_b), Im(A_a conj A_b).
+#include <algorithm>
+
 #include "pwa_internal.cuh"
 
 namespace pwa {
@@ -62,7 +64,30 @@ __global__ void table_kernel(const float *__restrict__ planes, int64_t pitch, in
         }
 }
 
+__global__ void amp_max_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n, int N,
+                               float *__restrict__ amax)
+{
+    const int w = blockIdx.y;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(planes[(2 * w) * pitch + i]) + fabsf(planes[(2 * w + 1) * pitch + i]));
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)  // non-negative floats order like their bit patterns
+        atomicMax(reinterpret_cast<int *>(amax + w), __float_as_int(m));
+}
+
 }  // namespace
+
+cudaError_t launch_amp_max(const Planes &amp, float *amax, cudaStream_t s)
+{
+    if (amp.n <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)std::min<int64_t>((amp.n + 255) / 256, 256), (unsigned)amp.n_waves);
+    amp_max_kernel<<<grid, 256, 0, s>>>(amp.ptr, amp.pitch, amp.n, amp.n_waves, amax);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack(const void *src, int dtype, int64_t n, int n_waves, float *planes,
                         int64_t pitch, cudaStream_t s)

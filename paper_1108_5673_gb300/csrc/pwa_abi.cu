@@ -36,7 +36,8 @@ struct pwa_ctx {
     int64_t table_pitch = 0;
     CUtensorMap data_map;
     bool loaded = false, has_norm = false;
-    double *M = nullptr;  // [N][N] complex
+    double *M = nullptr;     // [N][N] complex
+    float *amax = nullptr;   // [N] max over data events of |Re A_a| + |Im A_a|
 
     // per-call buffers
     double *d_io = nullptr;  // [nll K | grad 2NK | status,done | V 2NK]
@@ -223,6 +224,7 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         a.n_events = c->n_data;
         a.V = dV + (size_t)2 * N * k;
         a.M = c->M;
+        a.amax = c->amax;
         a.partials = c->d_work;
         a.ticket = c->ticket;
         a.status = status;
@@ -384,6 +386,8 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     c->async_status = reinterpret_cast<int *>(c->d_work + nwork - 2);
     if ((rc = dev_alloc(c, (void **)&c->M, (size_t)2 * c->N * c->N * sizeof(double), "M")))
         return bail(rc);
+    if ((rc = dev_alloc(c, (void **)&c->amax, (size_t)c->N * sizeof(float), "amax")))
+        return bail(rc);
     *out = c;
     return PWA_OK;
 }
@@ -397,6 +401,7 @@ int pwa_destroy(pwa_ctx *c)
         cudaStreamSynchronize(c->stream);
     free_sample(c);
     dev_free(c->M);
+    dev_free(c->amax);
     dev_free(c->d_io);
     dev_free(c->d_work);
     if (c->h_io)
@@ -439,6 +444,13 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
             if (e != cudaSuccess)
                 rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
         }
+    }
+    if (!rc) {
+        cudaError_t e = cudaMemsetAsync(c->amax, 0, c->N * sizeof(float), c->stream);
+        if (e == cudaSuccess)
+            e = launch_amp_max(c->data, c->amax, c->stream);
+        if (e != cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "amplitude maxima: %s", cudaGetErrorString(e));
     }
     if (!rc) {
         cudaError_t e = encode_planes_map(&c->data_map, c->data.ptr, c->data.n, c->data.pitch,

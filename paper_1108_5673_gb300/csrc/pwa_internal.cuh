@@ -206,6 +206,7 @@ struct EvalArgs {
     int64_t n_events;
     const double *V;   // [n_waves] complex128 (device), the parameter set
     const double *M;   // [n_waves][n_waves] complex128 (device)
+    const float *amax; // [n_waves] max over data events of |Re A_a| + |Im A_a|
     double *partials;  // scratch [grid][stride] doubles
     unsigned *ticket;  // zero on entry; reset to zero by the last block
     int *status;       // status bits are OR-ed here
@@ -233,6 +234,8 @@ cudaError_t launch_pack(const void *src, int dtype, int64_t n, int n_waves, floa
                         int64_t pitch, cudaStream_t s);
 cudaError_t launch_table_build(const Planes &amp, float *table, int64_t table_pitch,
                                cudaStream_t s);
+// amax[a] = max_i |Re A_a(i)| + |Im A_a(i)| (amax must be zeroed first)
+cudaError_t launch_amp_max(const Planes &amp, float *amax, cudaStream_t s);
 
 // k_norm.cu
 size_t norm_scratch_bytes(int n_waves, int num_sms);
