@@ -31,8 +31,8 @@
 // events x 2N planes from the structure-of-arrays store into a ring of
 // shared-memory stages with TMA (cp.async.bulk.tensor.2d); one producer
 // thread issues the copies; GROUPS groups of four consumer warps take tiles
-// in turn. Every wait is bounded (FLAG_TIMEOUT) so a stalled pipeline
-// returns instead of hanging.
+// in turn, each group cycling through its own stages of the ring. Every wait
+// is bounded (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
 //
 // Cross-block reduction: each CTA writes 2N+2 doubles of partial sums; the
 // last CTA to finish (atomic ticket) adds them in block order, so the result
@@ -55,8 +55,12 @@ struct AmpCfg {
     static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
     static constexpr int ROWS = 2 * N;
     static constexpr uint32_t STAGE_BYTES = ROWS * TE * 4;
-    static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
-    static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 8 ? 8 : STAGES_RAW);
+    // Each group owns SPG stages of the ring, so a stage's successive uses
+    // always belong to the same group: a waiter can then never be a full
+    // barrier phase behind (parity waits only tell apart adjacent phases).
+    static constexpr int SPG_RAW = (200 * 1024) / (STAGE_BYTES * G);
+    static constexpr int SPG = SPG_RAW < 1 ? 1 : (SPG_RAW > 4 ? 4 : SPG_RAW);
+    static constexpr int STAGES = G * SPG;
     static constexpr int THREADS = (CW + 1) * 32;
     static constexpr int NC = 2 * N + 2;               // partial components
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
@@ -163,9 +167,10 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
             // ---- producer: one thread issues the TMA copies ----------------
             int j = 0;
             for (; j < n_my; ++j) {
-                const int s = j % STAGES;
-                const uint32_t u = j / STAGES;
-                if (j >= STAGES && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
+                const int jj = j / GROUPS;
+                const int s = (j % GROUPS) * C::SPG + jj % C::SPG;
+                const uint32_t u = jj / C::SPG;
+                if (u > 0 && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
                     flags |= FLAG_TIMEOUT;
                     break;
                 }
@@ -174,9 +179,13 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
                             ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[s]);
             }
             // no copy may still be landing in shared memory when the CTA exits
-            for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q)
-                if (!mbar_wait(&full[q % STAGES], (q / STAGES) & 1))
+            // (the last STAGES tiles issued are the latest use of every stage)
+            for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q) {
+                const int qq = q / GROUPS;
+                const int s = (q % GROUPS) * C::SPG + qq % C::SPG;
+                if (!mbar_wait(&full[s], (qq / C::SPG) & 1))
                     flags |= FLAG_TIMEOUT;
+            }
         }
     } else {
         // ---- consumers: group grp takes tiles j = grp, grp + GROUPS, ... ---
@@ -191,9 +200,9 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         for (int c = 0; c < 2 * N; ++c)
             gs[c] = 0.f;
         int bad = 0;
-        for (int j = grp; j < n_my; j += GROUPS) {
-            const int s = j % STAGES;
-            const uint32_t u = j / STAGES;
+        for (int j = grp, jj = 0; j < n_my; j += GROUPS, ++jj) {
+            const int s = grp * C::SPG + jj % C::SPG;
+            const uint32_t u = jj / C::SPG;
             if (!mbar_wait(&full[s], u & 1)) {
                 flags |= FLAG_TIMEOUT;
                 break;

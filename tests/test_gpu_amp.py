@@ -158,3 +158,30 @@ def test_paper_scale_one_million_events(pwa):
     wl = synth.paper_scale()
     Vs = [scaled_truth(wl)] + list(synth.start_points(20, 3))
     check(pwa, wl, Vs)
+
+
+def test_back_to_back_async_launches(pwa):
+    """Hundreds of stream-ordered launches over a sample with many tiles per
+    CTA (the benchmark's pattern) give bitwise-identical results."""
+    torch = pytest.importorskip("torch")
+    wl = case(20, 600_000, 2000, seed=9)
+    V = synth.random_V(20, 77)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        with pwa.Likelihood(20, max_k=1, stream=s.cuda_stream) as L:
+            L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+            L.build_norm()
+            n_host, g_host = L.nll_grad(V[None])
+            dV = torch.from_numpy(V[None]).cuda()
+            R = 300
+            dn = torch.empty(R, dtype=torch.float64, device="cuda")
+            dg = torch.empty(R, 20, dtype=torch.complex128, device="cuda")
+            junk = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+            for r in range(R):
+                if r % 3 == 0:
+                    junk.fill_(r & 0xff)
+                L.nll_grad_async(dV, dn[r:r + 1], dg[r:r + 1])
+            assert L.sync() == pwa.PWA_OK
+            n_dev, g_dev = dn.cpu().numpy(), dg.cpu().numpy()
+    assert np.all(n_dev == n_host[0])
+    assert np.all(g_dev == g_host[0])
