@@ -64,6 +64,8 @@ struct AmpCfg {
     static constexpr int THREADS = (CW + 1) * 32;
     static constexpr int NC = 2 * N + 2;               // partial components
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
+    // dynamic shared memory must leave room for the static arrays (< 16 KB)
+    static constexpr bool FITS = SMEM <= 210 * 1024;
 };
 
 // Per-wave coefficients, each duplicated into both halves of a packed pair.
@@ -359,13 +361,18 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
 template <int N>
 cudaError_t configure_n()
 {
+    static_assert(AmpCfg<N, 2>::FITS, "two consumer groups must fit for every N");
     cudaError_t e = cudaFuncSetAttribute(nll_amp_kernel<N, 2>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)AmpCfg<N, 2>::SMEM);
-    cudaError_t f = cudaFuncSetAttribute(nll_amp_kernel<N, 3>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)AmpCfg<N, 3>::SMEM);
-    return e != cudaSuccess ? e : f;
+    if constexpr (AmpCfg<N, 3>::FITS) {
+        cudaError_t f = cudaFuncSetAttribute(nll_amp_kernel<N, 3>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)AmpCfg<N, 3>::SMEM);
+        if (e == cudaSuccess)
+            e = f;
+    }
+    return e;
 }
 
 // Consumer groups per CTA: 2 (9 warps, up to 168 registers per thread) or
@@ -384,12 +391,15 @@ cudaError_t launch_n(const CUtensorMap *map, const EvalArgs &a, int grid, int n_
                      int *work_flags, cudaStream_t s)
 {
     const int g = amp_groups() ? amp_groups() : (N <= 12 ? 3 : 2);
-    if (g == 3)
-        nll_amp_kernel<N, 3><<<grid, AmpCfg<N, 3>::THREADS, AmpCfg<N, 3>::SMEM, s>>>(
-            *map, a, n_tiles, work_flags);
-    else
-        nll_amp_kernel<N, 2><<<grid, AmpCfg<N, 2>::THREADS, AmpCfg<N, 2>::SMEM, s>>>(
-            *map, a, n_tiles, work_flags);
+    if constexpr (AmpCfg<N, 3>::FITS) {
+        if (g == 3) {
+            nll_amp_kernel<N, 3><<<grid, AmpCfg<N, 3>::THREADS, AmpCfg<N, 3>::SMEM, s>>>(
+                *map, a, n_tiles, work_flags);
+            return cudaGetLastError();
+        }
+    }
+    nll_amp_kernel<N, 2><<<grid, AmpCfg<N, 2>::THREADS, AmpCfg<N, 2>::SMEM, s>>>(
+        *map, a, n_tiles, work_flags);
     return cudaGetLastError();
 }
 
