@@ -9,6 +9,10 @@
 //   I_i = |S_i|^2                         FP32
 //   ln I_i = e_i ln 2 + ln f_i            f_i in [2^-1/2, 2^1/2], e_i summed exactly
 //   r_i = S_i / I_i,  g_a += conj(A_a(i)) r_i
+// Per-thread sums stay off the FP64 pipe (a small fraction of the FP32 rate on
+// this part): ln f_i is scaled by 2^23 and split into its integer part, summed
+// exactly in an int32, and its fraction, summed in FP32; both become doubles
+// once per thread for the block reduction.
 //
 // Accuracy of S. A plain FP32 sum of the 4N real products loses digits where
 // the waves interfere destructively (|S_i| much smaller than
@@ -161,8 +165,9 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     const int n_my =
         (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     int flags = 0;
-    double lacc = 0.0;
-    long long eacc = 0;
+    long long l_int = 0;      // sum of round(2^23 ln f)
+    int eacc = 0;             // sum of exponents
+    float l_frac = 0.f;       // sum of the remainders (units of 2^-23)
 
     if (warp == 0) {
         if (lane == 0) {
@@ -239,7 +244,11 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
                     if (ok) {
                         int ex;
                         const float f = split_exponent(I, ex);
-                        lacc += (double)logf(f);
+                        // 2^23 ln f = k + r exactly: k integer (|k| < 2^22), |r| <= 1/2
+                        const float y = logf(f) * 8388608.0f;
+                        const float t = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer
+                        l_int += __float_as_int(t) - 0x4B400000;
+                        l_frac += y - (t - 12582912.0f);
                         eacc += ex;
                         const float rI = __frcp_rn(I);
                         rr[e] = Sr[e] * rI;
@@ -268,6 +277,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
             flags |= FLAG_DOMAIN;
 
         // ---- per-warp reduction of this thread's sums -------------------
+        const double lacc = ((double)l_int + (double)l_frac) * 0x1p-23;
         const double l_w = warp_sum(lacc);
         const double e_w = warp_sum((double)eacc);
         if (lane == 0) {
