@@ -38,9 +38,13 @@
 // in turn, each group cycling through its own stages of the ring. Every wait
 // is bounded (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
 //
-// Cross-block reduction: each CTA writes 2N+2 doubles of partial sums; the
-// last CTA to finish (atomic ticket) adds them in block order, so the result
-// is bitwise reproducible from run to run.
+// Reductions avoid the FP64 pipe (about 1% of the FP32 rate on this part):
+// integer parts of the log sum are added exactly as integers, the rest as
+// float-float pairs. Each CTA writes its partials; the last CTA to finish
+// (atomic ticket) adds them in block order, so results are bitwise
+// reproducible from run to run. M V, the one O(N^2) double-precision
+// product, is formed at the start by a helper warp of CTAs 0..N-1 (one row
+// each), off the critical path.
 #include <stdlib.h>
 
 #include "pwa_internal.cuh"
@@ -65,12 +69,44 @@ struct AmpCfg {
     static constexpr int SPG_RAW = (200 * 1024) / (STAGE_BYTES * G);
     static constexpr int SPG = SPG_RAW < 1 ? 1 : (SPG_RAW > 4 ? 4 : SPG_RAW);
     static constexpr int STAGES = G * SPG;
-    static constexpr int THREADS = (CW + 1) * 32;
-    static constexpr int NC = 2 * N + 2;               // partial components
+    static constexpr int THREADS = (CW + 2) * 32;      // + producer warp + helper warp
+    static constexpr int NF = 2 * N + 1;               // float partials: ln-fraction, gradient
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
     // dynamic shared memory must leave room for the static arrays (< 16 KB)
     static constexpr bool FITS = SMEM <= 210 * 1024;
 };
+
+// Layout of the per-launch scratch (EvalArgs::partials) for a grid of G CTAs:
+//   pi  [G][2] int64   per-CTA sum of round(2^23 ln f) and of exponents
+//   pf  [G][2N+1]      per-CTA float-float sums: ln-f remainders, gradient
+//   mv  [2 kMaxWaves]  M V (double), written by the helper warps
+//   flags              status bits of this launch (reset by the last CTA)
+struct AmpScratch {
+    long long *pi;
+    float2 *pf;
+    double *mv;
+    int *flags;
+};
+
+__host__ __device__ inline AmpScratch amp_scratch(void *base, int grid)
+{
+    char *p = static_cast<char *>(base);
+    AmpScratch s;
+    s.pi = reinterpret_cast<long long *>(p);
+    p += (size_t)grid * 2 * sizeof(long long);
+    s.pf = reinterpret_cast<float2 *>(p);
+    p += (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2);
+    s.mv = reinterpret_cast<double *>(p);
+    p += 2 * kMaxWaves * sizeof(double);
+    s.flags = reinterpret_cast<int *>(p);
+    return s;
+}
+
+inline size_t amp_scratch_bytes(int grid)
+{
+    return (size_t)grid * 2 * sizeof(long long) + (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2) +
+           2 * kMaxWaves * sizeof(double) + 64;
+}
 
 // Per-wave coefficients, each duplicated into both halves of a packed pair.
 struct alignas(16) WaveCoef {
@@ -97,7 +133,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     using C = AmpCfg<N, G>;
     constexpr int TE = C::TE, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
     constexpr int GROUPS = C::GROUPS, GW = C::GW;
-    constexpr int NC = C::NC;
+    constexpr int NF = C::NF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tiles = reinterpret_cast<float *>(smem_raw);
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
@@ -105,11 +141,13 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
 
     __shared__ WaveCoef Vc[N];
     __shared__ float s_sigma;
-    __shared__ double red[CW][NC];
-    __shared__ double fin[NC];
-    __shared__ double mv_s[2 * N];
+    __shared__ long long red_i[CW][2];
+    __shared__ float red_f[CW][NF];
+    __shared__ long long fin_i[2];
+    __shared__ double fin_f[NF];
     __shared__ int s_flags;
     __shared__ int s_last;
+    AmpScratch sc = amp_scratch(a.partials, gridDim.x);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -194,7 +232,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
                     flags |= FLAG_TIMEOUT;
             }
         }
-    } else {
+    } else if (warp <= CW) {
         // ---- consumers: group grp takes tiles j = grp, grp + GROUPS, ... ---
         const int cw = warp - 1;
         const int grp = cw / GW;
@@ -276,19 +314,45 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         if (bad)
             flags |= FLAG_DOMAIN;
 
-        // ---- per-warp reduction of this thread's sums -------------------
-        const double lacc = ((double)l_int + (double)l_frac) * 0x1p-23;
-        const double l_w = warp_sum(lacc);
-        const double e_w = warp_sum((double)eacc);
+        // ---- per-warp reduction of this thread's sums (fixed order) ------
+        const long long li = warp_sum(l_int);
+        const long long ei = warp_sum((long long)eacc);
+        const float lf = warp_sum(l_frac);
         if (lane == 0) {
-            red[cw][0] = l_w;
-            red[cw][1] = e_w;
+            red_i[cw][0] = li;
+            red_i[cw][1] = ei;
+            red_f[cw][0] = lf;
         }
 #pragma unroll
         for (int c = 0; c < 2 * N; ++c) {
-            const double v = warp_sum((double)gs[c]);
+            const float v = warp_sum(gs[c]);
             if (lane == 0)
-                red[cw][2 + c] = v;
+                red_f[cw][1 + c] = v;
+        }
+    } else if (warp == CW + 1) {
+        // ---- helper warp: row blockIdx.x of M V in FP64 (once per launch) --
+        const int Nw = a.n_waves;
+        const int row = blockIdx.x;
+        if (row < Nw) {
+            double re = 0.0, im = 0.0;
+            if (lane < Nw) {
+                const double mr = a.M[2 * (row * Nw + lane)], mi = a.M[2 * (row * Nw + lane) + 1];
+                const double vr = a.V[2 * lane], vi = a.V[2 * lane + 1];
+                re = fma(mr, vr, -mi * vi);
+                im = fma(mr, vi, mi * vr);
+            }
+            for (int b = lane + 32; b < Nw; b += 32) {
+                const double mr = a.M[2 * (row * Nw + b)], mi = a.M[2 * (row * Nw + b) + 1];
+                const double vr = a.V[2 * b], vi = a.V[2 * b + 1];
+                re = fma(mr, vr, fma(-mi, vi, re));
+                im = fma(mr, vi, fma(mi, vr, im));
+            }
+            re = warp_sum(re);
+            im = warp_sum(im);
+            if (lane == 0) {
+                sc.mv[2 * row] = re;
+                sc.mv[2 * row + 1] = im;
+            }
         }
     }
     if (flags)
@@ -296,11 +360,17 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     __syncthreads();
 
     // ---- block partial, fixed order over warps -------------------------
-    for (int c = threadIdx.x; c < NC; c += blockDim.x) {
-        double v = 0.0;
+    if (threadIdx.x < 2) {
+        long long v = 0;
         for (int w = 0; w < CW; ++w)
-            v += red[w][c];
-        a.partials[(size_t)blockIdx.x * NC + c] = v;
+            v += red_i[w][threadIdx.x];
+        sc.pi[2 * blockIdx.x + threadIdx.x] = v;
+    }
+    for (int c = threadIdx.x; c < NF; c += blockDim.x) {
+        dfloat v = {0.f, 0.f};
+        for (int w = 0; w < CW; ++w)
+            v = df_add(v, dfloat{red_f[w][c], 0.f});
+        sc.pf[(size_t)blockIdx.x * NF + c] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -317,34 +387,38 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     // ---- last CTA: deterministic final sum + normalisation term ---------
     __threadfence();
     const int nwarps = blockDim.x >> 5;
-    for (int c = warp; c < NC; c += nwarps) {
-        double v = 0.0;
-        for (int b = lane; b < (int)gridDim.x; b += 32)
-            v += __ldcg(&a.partials[(size_t)b * NC + c]);
+    if (warp == 0) {
+        long long v0 = 0, v1 = 0;
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            v0 += __ldcg(&sc.pi[2 * b]);
+            v1 += __ldcg(&sc.pi[2 * b + 1]);
+        }
+        v0 = warp_sum(v0);
+        v1 = warp_sum(v1);
+        if (lane == 0) {
+            fin_i[0] = v0;
+            fin_i[1] = v1;
+        }
+    }
+    for (int c = warp; c < NF; c += nwarps) {
+        dfloat v = {0.f, 0.f};
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const float2 p = __ldcg(&sc.pf[(size_t)b * NF + c]);
+            v = df_add(v, dfloat{p.x, p.y});
+        }
         v = warp_sum(v);
         if (lane == 0)
-            fin[c] = v;
-    }
-    // (M V)_a in FP64, one thread per wave
-    const int Nw = a.n_waves;
-    for (int w = threadIdx.x; w < Nw; w += blockDim.x) {
-        double re = 0.0, im = 0.0;
-        for (int b = 0; b < Nw; ++b) {
-            const double mr = a.M[2 * (w * Nw + b)], mi = a.M[2 * (w * Nw + b) + 1];
-            const double vr = a.V[2 * b], vi = a.V[2 * b + 1];
-            re = fma(mr, vr, fma(-mi, vi, re));
-            im = fma(mr, vi, fma(mi, vr, im));
-        }
-        mv_s[2 * w] = re;
-        mv_s[2 * w + 1] = im;
+            fin_f[c] = (double)v.hi + (double)v.lo;
     }
     __syncthreads();
+    const int Nw = a.n_waves;
     if (threadIdx.x == 0) {
         const int wf = __ldcg(work_flags);
         double nv = 0.0;
         for (int w = 0; w < Nw; ++w)
-            nv += a.V[2 * w] * mv_s[2 * w] + a.V[2 * w + 1] * mv_s[2 * w + 1];
-        const double data = -(fin[0] + fin[1] * kLn2);
+            nv += a.V[2 * w] * __ldcg(&sc.mv[2 * w]) + a.V[2 * w + 1] * __ldcg(&sc.mv[2 * w + 1]);
+        const double lnsum = ((double)fin_i[0] + fin_f[0]) * 0x1p-23 + (double)fin_i[1] * kLn2;
+        const double data = -lnsum;
         double nll = data + nv;
         if (wf & FLAG_DOMAIN)
             nll = INFINITY;
@@ -353,7 +427,8 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         a.nll[0] = nll;
         if (a.grad) {
             for (int c = 0; c < 2 * Nw; ++c)
-                a.grad[c] = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) ? 0.0 : (-fin[2 + c] + mv_s[c]);
+                a.grad[c] = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) ? 0.0
+                                                                 : (-fin_f[1 + c] + __ldcg(&sc.mv[c]));
         }
         if (wf)
             atomicOr(a.status, wf);
@@ -450,11 +525,9 @@ int amp_grid(int n_waves, int num_sms)
 
 size_t amp_partials_doubles(int n_waves, int num_sms)
 {
-    return (size_t)amp_grid(n_waves, num_sms) * (2 * kMaxWaves + 2) + 64;
+    return amp_scratch_bytes(amp_grid(n_waves, num_sms)) / sizeof(double) + 8;
 }
 
-// The work-flag word lives just past the partials in the same scratch
-// buffer (EvalArgs::partials), so one allocation serves both.
 cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
                            int num_sms, cudaStream_t s)
 {
@@ -463,7 +536,7 @@ cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const Eval
     if (te <= 0)
         return cudaErrorInvalidValue;
     const int n_tiles = (int)((amp.n + te - 1) / te);
-    int *work_flags = reinterpret_cast<int *>(a.partials + (size_t)grid * (2 * kMaxWaves + 2));
+    int *work_flags = amp_scratch(a.partials, grid).flags;
     switch (pad_waves(amp.n_waves)) {
     case 4: return launch_n<4>(map, a, grid, n_tiles, work_flags, s);
     case 8: return launch_n<8>(map, a, grid, n_tiles, work_flags, s);

@@ -180,6 +180,44 @@ __device__ __forceinline__ void dot2_step(f2 &s, f2 &c, f2 x, f2 y, f2 yn)
     c = add2(c, add2(err, r));
 }
 
+// ---- float-float ("double-float") sums on the FP32 pipe -------------------
+// FP64 throughput on this part is ~1% of FP32, so reductions that need more
+// than float precision carry an unevaluated sum hi + lo of two floats
+// (Knuth's TwoSum for the high parts).
+struct dfloat {
+    float hi, lo;
+};
+
+__device__ __forceinline__ dfloat df_add(dfloat a, dfloat b)
+{
+    const float s = a.hi + b.hi;
+    const float bb = s - a.hi;
+    float e = (a.hi - (s - bb)) + (b.hi - bb);
+    e += a.lo + b.lo;
+    const float h = s + e;
+    return {h, e - (h - s)};
+}
+
+__device__ __forceinline__ dfloat warp_sum(dfloat v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dfloat w;
+        w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+        w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+        v = df_add(v, w);
+    }
+    return v;
+}
+
+__device__ __forceinline__ long long warp_sum(long long v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 __device__ __forceinline__ double warp_sum(double v)
 {
 #pragma unroll
