@@ -17,19 +17,21 @@
 // Accuracy of S. A plain FP32 sum of the 4N real products loses digits where
 // the waves interfere destructively (|S_i| much smaller than
 // B_i = sum_a |V_a|_1 |A_a(i)|_1); over 1M events those losses add up to
-// ~1e-3 in the NLL. Instead every product p = c * a is split exactly against
-// a power of two sigma >= 2 max_i B_i fixed per call:
-//     t = fma(c, a, sigma)       rounds c*a to a multiple of ulp(sigma)/2
-//     q = t - sigma              exact (Sterbenz), the high part of c*a
-//     r = fma(c, a, -q)          the remainder, |r| <= ulp(sigma)
-// The high parts are multiples of sigma 2^-24 whose running sum stays below
-// sigma, so it is accumulated exactly; the remainders are summed in FP32 with
-// an error ~2^-48 sigma. S = hi + lo is then correct to about one float
-// rounding however small it is relative to B_i (the same guarantee as a
-// doubled-precision dot product, at half its cost). sigma comes from V and
-// the per-wave maxima of |A| over the sample, so no per-event pre-pass is
-// needed. V is carried as a float pair Vhi + Vlo; the products Vlo A are
-// ~2^-24 of the leading ones and go straight into the low sum.
+// several 1e-3 in the NLL. Instead every product p = c * a is split exactly
+// against sigma = 1.5 * 2^k, with 2^(k-1) >= max_i B_i fixed per call:
+//     t = fma(c, a, sigma)    lies in [2^k, 2^(k+1)]: c*a rounded to a
+//                             multiple of u_k = 2^(k-23)
+//     bits(t) - bits(sigma) = q / u_k, the high part of c*a as an integer
+//     r = fma(c, a, sigma - t)   the remainder c*a - q (sigma - t is exact)
+// The high parts are summed exactly as 32-bit integers (on the integer
+// pipe, wrapping harmlessly since the final sum is below 2^23), the
+// remainders in FP32 with an error ~2^-48 sigma. S = hi + lo is then correct
+// to about one float rounding however small it is relative to B_i (the
+// guarantee of a doubled-precision dot product, at well under its cost).
+// sigma comes from V and the per-wave maxima of |A| over the sample, so no
+// per-event pre-pass is needed. V is carried as a float pair Vhi + Vlo; the
+// products Vlo A are ~2^-24 of the leading ones and go straight into the
+// low sums.
 //
 // Data movement: a persistent grid (one CTA per SM) streams tiles of 256
 // events x 2N planes from the structure-of-arrays store into a ring of
@@ -110,19 +112,22 @@ inline size_t amp_scratch_bytes(int grid)
 
 // Per-wave coefficients, each duplicated into both halves of a packed pair.
 struct alignas(16) WaveCoef {
-    f2 vr, vi, nvi;  // Vhi: Re, Im, -Im
-    f2 lr, li, nli;  // Vlo: Re, Im, -Im
+    f2 vr, vi;  // Vhi
+    f2 lr, li;  // Vlo
 };
 
 __device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
 
-// (hi, lo) += c * a, error-free high part against sg (see the file comment).
-__device__ __forceinline__ void extract_acc(f2 &hi, f2 &lo, f2 c, f2 a, f2 sg)
+// Split c*a for both events of the pair (see the file comment): returns the
+// remainders and the bit patterns of t, whose sum gives the high parts.
+__device__ __forceinline__ f2 extract(f2 c, f2 a, f2 sg, unsigned &t0, unsigned &t1)
 {
     const f2 t = fma2(c, a, sg);
-    const f2 nq = sub2(sg, t);       // -q, exact
-    hi = sub2(hi, nq);               // hi + q, exact
-    lo = add2(lo, fma2(c, a, nq));   // + remainder
+    float x0, x1;
+    upk2(t, x0, x1);
+    t0 = __float_as_uint(x0);
+    t1 = __float_as_uint(x1);
+    return fma2(c, a, sub2(sg, t));
 }
 
 template <int N, int G>
@@ -140,7 +145,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     uint64_t *empty = full + STAGES;
 
     __shared__ WaveCoef Vc[N];
-    __shared__ float s_sigma;
+    __shared__ float s_sigma, s_unit;
     __shared__ long long red_i[CW][2];
     __shared__ float red_f[CW][NF];
     __shared__ long long fin_i[2];
@@ -172,13 +177,11 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         const float lr = __double2float_rn(dr - (double)vr), li = __double2float_rn(di - (double)vi);
         Vc[w].vr = pk2(vr, vr);
         Vc[w].vi = pk2(vi, vi);
-        Vc[w].nvi = pk2(-vi, -vi);
         Vc[w].lr = pk2(lr, lr);
         Vc[w].li = pk2(li, li);
-        Vc[w].nli = pk2(-li, -li);
     }
     if (warp == 1) {
-        // sigma = a power of two >= 2 * sum_a |V_a|_1 * max_i |A_a(i)|_1, with margin
+        // 2^(k-1) >= 1.25 sum_a |V_a|_1 max_i |A_a(i)|_1 (margin for rounding)
         float b = 0.f;
         for (int w = lane; w < a.n_waves; w += 32) {
             const float v1 = fabsf(__double2float_ru(fabs(a.V[2 * w]))) +
@@ -187,14 +190,14 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         }
         b = warp_sum(b);
         if (lane == 0) {
-            const float target = 2.5f * b;  // covers rounding of the bound itself
-            int e = 0;
-            if (target > 0.f) {
-                e = ((__float_as_int(target) >> 23) & 0xff) - 126;  // target < 2^e
-                if (e < -100)
-                    e = -100;
-            }
-            s_sigma = (target > 0.f) ? ldexpf(1.0f, e) : 0.f;
+            const float target = 2.5f * b;
+            int k = -100;  // floor keeps u_k normal
+            if (target > 0.f)
+                k = max(k, ((__float_as_int(target) >> 23) & 0xff) - 126);  // target < 2^k
+            if (!(target < 1e30f))
+                k = 100;   // non-finite bound: the results will flag the domain error
+            s_sigma = 1.5f * ldexpf(1.0f, k);
+            s_unit = ldexpf(1.0f, k - 23);
         }
     }
     __syncthreads();
@@ -237,8 +240,10 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         const int cw = warp - 1;
         const int grp = cw / GW;
         const int ct = (cw % GW) * 32 + lane;  // thread within its group
-        const float sigma = s_sigma;
+        const float sigma = s_sigma, unit = s_unit;
         const f2 SG = pk2(sigma, sigma);
+        // bits(t) - bits(sigma) summed over the 2N terms of Im S: remove the offset once
+        const unsigned im_offset = 2u * (unsigned)N * __float_as_uint(sigma);
         const f2 Z = 0ull;
         float gs[2 * N];
 #pragma unroll
@@ -255,22 +260,38 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
             const float *T = tiles + (size_t)s * ROWS * TE + 2 * ct;
             const int64_t ev0 = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * TE + 2 * ct;
 
-            f2 hR = Z, lR = Z, hI = Z, lI = Z;
+            // Re S = vr ar - vi ai ; Im S = vr ai + vi ar
+            unsigned hR0 = 0, hR1 = 0, hI0 = 0, hI1 = 0;  // high parts (units of u_k)
+            f2 lR = Z, lRm = Z, lI = Z;                    // remainders; lRm is subtracted
 #pragma unroll
             for (int w = 0; w < N; ++w) {
                 const f2 ar = lds2(T + (2 * w) * TE), ai = lds2(T + (2 * w + 1) * TE);
-                const WaveCoef &cf = Vc[w];
-                // Re S = vr ar - vi ai ; Im S = vr ai + vi ar
-                extract_acc(hR, lR, cf.vr, ar, SG);
-                extract_acc(hR, lR, cf.nvi, ai, SG);
-                extract_acc(hI, lI, cf.vr, ai, SG);
-                extract_acc(hI, lI, cf.vi, ar, SG);
-                lR = fma2(cf.lr, ar, fma2(cf.nli, ai, lR));
+                const WaveCoef cf = Vc[w];
+                unsigned x0, x1;
+                lR = add2(lR, extract(cf.vr, ar, SG, x0, x1));
+                hR0 += x0;
+                hR1 += x1;
+                lRm = add2(lRm, extract(cf.vi, ai, SG, x0, x1));
+                hR0 -= x0;
+                hR1 -= x1;
+                lI = add2(lI, extract(cf.vr, ai, SG, x0, x1));
+                hI0 += x0;
+                hI1 += x1;
+                lI = add2(lI, extract(cf.vi, ar, SG, x0, x1));
+                hI0 += x0;
+                hI1 += x1;
+                lR = fma2(cf.lr, ar, lR);
+                lRm = fma2(cf.li, ai, lRm);
                 lI = fma2(cf.lr, ai, fma2(cf.li, ar, lI));
             }
             float Sr[2], Si[2], rr[2], ri[2];
-            upk2(add2(hR, lR), Sr[0], Sr[1]);
-            upk2(add2(hI, lI), Si[0], Si[1]);
+            {
+                const f2 hR = pk2((float)(int)hR0 * unit, (float)(int)hR1 * unit);
+                const f2 hI = pk2((float)(int)(hI0 - im_offset) * unit,
+                                  (float)(int)(hI1 - im_offset) * unit);
+                upk2(add2(hR, sub2(lR, lRm)), Sr[0], Sr[1]);
+                upk2(add2(hI, lI), Si[0], Si[1]);
+            }
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const float I = fmaf(Sr[e], Sr[e], Si[e] * Si[e]);
