@@ -155,6 +155,14 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     AmpScratch sc = amp_scratch(a.partials, gridDim.x);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...; tile j goes
+    // to group j % GROUPS and to that group's stage (j / GROUPS) % SPG
+    const int n_my =
+        (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const uint32_t stage_tx = 2u * (uint32_t)a.n_waves * TE * 4u;
+    auto stage_of = [](int j) { return (j % GROUPS) * C::SPG + (j / GROUPS) % C::SPG; };
+    auto use_of = [](int j) { return (uint32_t)((j / GROUPS) / C::SPG); };
+    const int n_first = n_my < STAGES ? n_my : STAGES;  // first use of every stage
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -162,10 +170,15 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         }
         fence_barrier_init();
         s_flags = 0;
+        // start streaming before the prologue below (its global loads take ~1 us)
+        for (int j = 0; j < n_first; ++j) {
+            mbar_arrive_expect_tx(&full[stage_of(j)], stage_tx);
+            tma_load_2d(tiles + (size_t)stage_of(j) * ROWS * TE, &map,
+                        ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[stage_of(j)]);
+        }
     }
     // Rows of padded waves (n_waves < N) are never written by TMA: zero them
     // once so that they contribute nothing (their V is zero as well).
-    const uint32_t stage_tx = 2u * (uint32_t)a.n_waves * TE * 4u;
     for (int s = 0; s < STAGES; ++s)
         for (int i = 2 * a.n_waves * TE + threadIdx.x; i < ROWS * TE; i += blockDim.x)
             tiles[(size_t)s * ROWS * TE + i] = 0.f;
@@ -202,9 +215,6 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     }
     __syncthreads();
 
-    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...
-    const int n_my =
-        (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     int flags = 0;
     long long l_int = 0;      // sum of round(2^23 ln f)
     int eacc = 0;             // sum of exponents
@@ -213,11 +223,10 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     if (warp == 0) {
         if (lane == 0) {
             // ---- producer: one thread issues the TMA copies ----------------
-            int j = 0;
+            int j = n_first;
             for (; j < n_my; ++j) {
-                const int jj = j / GROUPS;
-                const int s = (j % GROUPS) * C::SPG + jj % C::SPG;
-                const uint32_t u = jj / C::SPG;
+                const int s = stage_of(j);
+                const uint32_t u = use_of(j);
                 if (u > 0 && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
                     flags |= FLAG_TIMEOUT;
                     break;
@@ -229,9 +238,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
             // no copy may still be landing in shared memory when the CTA exits
             // (the last STAGES tiles issued are the latest use of every stage)
             for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q) {
-                const int qq = q / GROUPS;
-                const int s = (q % GROUPS) * C::SPG + qq % C::SPG;
-                if (!mbar_wait(&full[s], (qq / C::SPG) & 1))
+                if (!mbar_wait(&full[stage_of(q)], use_of(q) & 1))
                     flags |= FLAG_TIMEOUT;
             }
         }
@@ -250,9 +257,9 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         for (int c = 0; c < 2 * N; ++c)
             gs[c] = 0.f;
         int bad = 0;
-        for (int j = grp, jj = 0; j < n_my; j += GROUPS, ++jj) {
-            const int s = grp * C::SPG + jj % C::SPG;
-            const uint32_t u = jj / C::SPG;
+        for (int j = grp; j < n_my; j += GROUPS) {
+            const int s = stage_of(j);
+            const uint32_t u = use_of(j);
             if (!mbar_wait(&full[s], u & 1)) {
                 flags |= FLAG_TIMEOUT;
                 break;
@@ -406,13 +413,30 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         return;
 
     // ---- last CTA: deterministic final sum + normalisation term ---------
+    // Every partial is first staged in shared memory (the stage buffers are
+    // free now) with independent loads, so the L2 latency is paid once.
     __threadfence();
+    const int Nw = a.n_waves;
+    const int G_ = gridDim.x;
+    float2 *spf = reinterpret_cast<float2 *>(tiles);                 // [G][NF]
+    long long *spi = reinterpret_cast<long long *>(spf + (size_t)G_ * NF);  // [G][2]
+    double *smv = reinterpret_cast<double *>(spi + 2 * G_);          // [2N] M V
+    double *sv = smv + 2 * N;                                         // [2N] V
+    for (int i = threadIdx.x; i < G_ * NF; i += blockDim.x)
+        spf[i] = __ldcg(&sc.pf[i]);
+    for (int i = threadIdx.x; i < 2 * G_; i += blockDim.x)
+        spi[i] = __ldcg(&sc.pi[i]);
+    for (int i = threadIdx.x; i < 2 * Nw; i += blockDim.x) {
+        smv[i] = __ldcg(&sc.mv[i]);
+        sv[i] = a.V[i];
+    }
+    __syncthreads();
     const int nwarps = blockDim.x >> 5;
     if (warp == 0) {
         long long v0 = 0, v1 = 0;
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            v0 += __ldcg(&sc.pi[2 * b]);
-            v1 += __ldcg(&sc.pi[2 * b + 1]);
+        for (int b = lane; b < G_; b += 32) {
+            v0 += spi[2 * b];
+            v1 += spi[2 * b + 1];
         }
         v0 = warp_sum(v0);
         v1 = warp_sum(v1);
@@ -423,38 +447,42 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     }
     for (int c = warp; c < NF; c += nwarps) {
         dfloat v = {0.f, 0.f};
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const float2 p = __ldcg(&sc.pf[(size_t)b * NF + c]);
+        for (int b = lane; b < G_; b += 32) {
+            const float2 p = spf[(size_t)b * NF + c];
             v = df_add(v, dfloat{p.x, p.y});
         }
         v = warp_sum(v);
         if (lane == 0)
             fin_f[c] = (double)v.hi + (double)v.lo;
     }
+    // V^H M V = sum_a Re(conj(V_a) (M V)_a), one warp
+    double nv = 0.0;
+    if (warp == nwarps - 1) {
+        for (int w = lane; w < Nw; w += 32)
+            nv += sv[2 * w] * smv[2 * w] + sv[2 * w + 1] * smv[2 * w + 1];
+        nv = warp_sum(nv);
+    }
     __syncthreads();
-    const int Nw = a.n_waves;
-    if (threadIdx.x == 0) {
-        const int wf = __ldcg(work_flags);
-        double nv = 0.0;
-        for (int w = 0; w < Nw; ++w)
-            nv += a.V[2 * w] * __ldcg(&sc.mv[2 * w]) + a.V[2 * w + 1] * __ldcg(&sc.mv[2 * w + 1]);
+    const int wf = __ldcg(work_flags);
+    const bool invalid = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) != 0;
+    if (a.grad)
+        for (int c = threadIdx.x; c < 2 * Nw; c += blockDim.x)
+            a.grad[c] = invalid ? 0.0 : (-fin_f[1 + c] + smv[c]);
+    if (warp == nwarps - 1 && lane == 0) {
         const double lnsum = ((double)fin_i[0] + fin_f[0]) * 0x1p-23 + (double)fin_i[1] * kLn2;
-        const double data = -lnsum;
-        double nll = data + nv;
+        double nll = -lnsum + nv;
         if (wf & FLAG_DOMAIN)
             nll = INFINITY;
         if (wf & FLAG_TIMEOUT)
             nll = NAN;
         a.nll[0] = nll;
-        if (a.grad) {
-            for (int c = 0; c < 2 * Nw; ++c)
-                a.grad[c] = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) ? 0.0
-                                                                 : (-fin_f[1 + c] + __ldcg(&sc.mv[c]));
-        }
         if (wf)
             atomicOr(a.status, wf);
         if (a.done)
             atomicAdd(a.done, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         *work_flags = 0;
         *a.ticket = 0u;
         __threadfence();
@@ -492,13 +520,22 @@ int amp_groups()
     return g;
 }
 
+// The last CTA stages all partials in its (then idle) stage buffers.
+template <int N, int G>
+constexpr bool finalize_fits(int grid)
+{
+    return (size_t)grid * (2 * N + 1) * 8 + (size_t)grid * 16 + 32 * N <= AmpCfg<N, G>::SMEM;
+}
+
 template <int N>
 cudaError_t launch_n(const CUtensorMap *map, const EvalArgs &a, int grid, int n_tiles,
                      int *work_flags, cudaStream_t s)
 {
+    if (!finalize_fits<N, 2>(grid))
+        return cudaErrorInvalidConfiguration;
     const int g = amp_groups() ? amp_groups() : (N <= 12 ? 3 : 2);
     if constexpr (AmpCfg<N, 3>::FITS) {
-        if (g == 3) {
+        if (g == 3 && finalize_fits<N, 3>(grid)) {
             nll_amp_kernel<N, 3><<<grid, AmpCfg<N, 3>::THREADS, AmpCfg<N, 3>::SMEM, s>>>(
                 *map, a, n_tiles, work_flags);
             return cudaGetLastError();
