@@ -422,10 +422,39 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     long long *spi = reinterpret_cast<long long *>(spf + (size_t)G_ * NF);  // [G][2]
     double *smv = reinterpret_cast<double *>(spi + 2 * G_);          // [2N] M V
     double *sv = smv + 2 * N;                                         // [2N] V
-    for (int i = threadIdx.x; i < G_ * NF; i += blockDim.x)
-        spf[i] = __ldcg(&sc.pf[i]);
-    for (int i = threadIdx.x; i < 2 * G_; i += blockDim.x)
-        spi[i] = __ldcg(&sc.pi[i]);
+    {
+        // batches of independent loads: one L2 round trip per batch, not per element
+        constexpr int U = 16;
+        const int total = G_ * NF;
+        for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
+            float2 r[U];
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int i = base + k * blockDim.x;
+                r[k] = (i < total) ? __ldcg(&sc.pf[i]) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int k = 0; k < U; ++k) {
+                const int i = base + k * blockDim.x;
+                if (i < total)
+                    spf[i] = r[k];
+            }
+        }
+        for (int base = threadIdx.x; base < 2 * G_; base += 4 * blockDim.x) {
+            long long r[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = base + k * blockDim.x;
+                r[k] = (i < 2 * G_) ? __ldcg(&sc.pi[i]) : 0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int i = base + k * blockDim.x;
+                if (i < 2 * G_)
+                    spi[i] = r[k];
+            }
+        }
+    }
     for (int i = threadIdx.x; i < 2 * Nw; i += blockDim.x) {
         smv[i] = __ldcg(&sc.mv[i]);
         sv[i] = a.V[i];
