@@ -604,10 +604,15 @@ cudaError_t amp_configure()
     return e;
 }
 
+// One persistent CTA per SM; PWA_AMP_GRID overrides it (a tuning knob).
 int amp_grid(int n_waves, int num_sms)
 {
     (void)n_waves;
-    return num_sms;
+    static const int forced = [] {
+        const char *v = getenv("PWA_AMP_GRID");
+        return v ? atoi(v) : 0;
+    }();
+    return (forced > 0 && forced <= 4 * num_sms) ? forced : num_sms;
 }
 
 size_t amp_partials_doubles(int n_waves, int num_sms)
