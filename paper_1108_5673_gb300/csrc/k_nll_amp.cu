@@ -413,46 +413,49 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
         return;
 
     // ---- last CTA: deterministic final sum + normalisation term ---------
-    // Every partial is first staged in shared memory (the stage buffers are
-    // free now) with independent loads, so the L2 latency is paid once.
+    // Each of the 2N+1 float components and the 2 integer ones is split into
+    // SUB interleaved sub-sums over the CTAs, one per thread, with all of a
+    // thread's loads issued before its adds (one L2 round trip); the
+    // sub-sums are then combined in a fixed order.
     __threadfence();
     const int Nw = a.n_waves;
     const int G_ = gridDim.x;
-    float2 *spf = reinterpret_cast<float2 *>(tiles);                 // [G][NF]
-    long long *spi = reinterpret_cast<long long *>(spf + (size_t)G_ * NF);  // [G][2]
-    double *smv = reinterpret_cast<double *>(spi + 2 * G_);          // [2N] M V
-    double *sv = smv + 2 * N;                                         // [2N] V
-    {
-        // batches of independent loads: one L2 round trip per batch, not per element
-        constexpr int U = 16;
-        const int total = G_ * NF;
-        for (int base = threadIdx.x; base < total; base += U * blockDim.x) {
-            float2 r[U];
+    constexpr int SUB = 7, MAXB = 24;
+    dfloat *sub_f = reinterpret_cast<dfloat *>(tiles);                  // [NF][SUB]
+    long long *sub_i = reinterpret_cast<long long *>(sub_f + NF * SUB);  // [2][SUB]
+    double *smv = reinterpret_cast<double *>(sub_i + 2 * SUB);          // [2N] M V
+    double *sv = smv + 2 * N;                                             // [2N] V
+    for (int item = threadIdx.x; item < (NF + 2) * SUB; item += blockDim.x) {
+        const int c = item / SUB, k = item % SUB;
+        if (c < NF) {
+            dfloat v = {0.f, 0.f};
+            for (int b0 = k; b0 < G_; b0 += SUB * MAXB) {
+                float2 r[MAXB];
 #pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int i = base + k * blockDim.x;
-                r[k] = (i < total) ? __ldcg(&sc.pf[i]) : make_float2(0.f, 0.f);
-            }
+                for (int q = 0; q < MAXB; ++q) {
+                    const int b = b0 + q * SUB;
+                    r[q] = (b < G_) ? __ldcg(&sc.pf[(size_t)b * NF + c]) : make_float2(0.f, 0.f);
+                }
 #pragma unroll
-            for (int k = 0; k < U; ++k) {
-                const int i = base + k * blockDim.x;
-                if (i < total)
-                    spf[i] = r[k];
+                for (int q = 0; q < MAXB; ++q)
+                    v = df_add(v, dfloat{r[q].x, r[q].y});
             }
-        }
-        for (int base = threadIdx.x; base < 2 * G_; base += 4 * blockDim.x) {
-            long long r[4];
+            sub_f[c * SUB + k] = v;
+        } else {
+            const int ci = c - NF;
+            long long v = 0;
+            for (int b0 = k; b0 < G_; b0 += SUB * MAXB) {
+                long long r[MAXB];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int i = base + k * blockDim.x;
-                r[k] = (i < 2 * G_) ? __ldcg(&sc.pi[i]) : 0;
-            }
+                for (int q = 0; q < MAXB; ++q) {
+                    const int b = b0 + q * SUB;
+                    r[q] = (b < G_) ? __ldcg(&sc.pi[2 * b + ci]) : 0;
+                }
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int i = base + k * blockDim.x;
-                if (i < 2 * G_)
-                    spi[i] = r[k];
+                for (int q = 0; q < MAXB; ++q)
+                    v += r[q];
             }
+            sub_i[ci * SUB + k] = v;
         }
     }
     for (int i = threadIdx.x; i < 2 * Nw; i += blockDim.x) {
@@ -461,28 +464,18 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     }
     __syncthreads();
     const int nwarps = blockDim.x >> 5;
-    if (warp == 0) {
-        long long v0 = 0, v1 = 0;
-        for (int b = lane; b < G_; b += 32) {
-            v0 += spi[2 * b];
-            v1 += spi[2 * b + 1];
-        }
-        v0 = warp_sum(v0);
-        v1 = warp_sum(v1);
-        if (lane == 0) {
-            fin_i[0] = v0;
-            fin_i[1] = v1;
-        }
-    }
-    for (int c = warp; c < NF; c += nwarps) {
-        dfloat v = {0.f, 0.f};
-        for (int b = lane; b < G_; b += 32) {
-            const float2 p = spf[(size_t)b * NF + c];
-            v = df_add(v, dfloat{p.x, p.y});
-        }
-        v = warp_sum(v);
-        if (lane == 0)
+    for (int c = threadIdx.x; c < NF + 2; c += blockDim.x) {
+        if (c < NF) {
+            dfloat v = sub_f[c * SUB];
+            for (int k = 1; k < SUB; ++k)
+                v = df_add(v, sub_f[c * SUB + k]);
             fin_f[c] = (double)v.hi + (double)v.lo;
+        } else {
+            long long v = 0;
+            for (int k = 0; k < SUB; ++k)
+                v += sub_i[(c - NF) * SUB + k];
+            fin_i[c - NF] = v;
+        }
     }
     // V^H M V = sum_a Re(conj(V_a) (M V)_a), one warp
     double nv = 0.0;
@@ -549,11 +542,12 @@ int amp_groups()
     return g;
 }
 
-// The last CTA stages all partials in its (then idle) stage buffers.
+// The last CTA keeps its sub-sums in its (then idle) stage buffers.
 template <int N, int G>
 constexpr bool finalize_fits(int grid)
 {
-    return (size_t)grid * (2 * N + 1) * 8 + (size_t)grid * 16 + 32 * N <= AmpCfg<N, G>::SMEM;
+    (void)grid;
+    return (size_t)(2 * N + 3) * 7 * 8 + 32 * N <= AmpCfg<N, G>::SMEM;
 }
 
 template <int N>
