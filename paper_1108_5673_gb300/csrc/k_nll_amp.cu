@@ -44,9 +44,10 @@
 // integer parts of the log sum are added exactly as integers, the rest as
 // float-float pairs. Each CTA writes its partials; the last CTA to finish
 // (atomic ticket) adds them in block order, so results are bitwise
-// reproducible from run to run. M V, the one O(N^2) double-precision
-// product, is formed at the start by a helper warp of CTAs 0..N-1 (one row
-// each), off the critical path.
+// reproducible from run to run. M V and V^H M V, the only double-precision
+// arithmetic, are formed at the start by a helper warp of CTA 0, off the
+// critical path; the last CTA only converts its float-float and integer
+// sums to double once.
 #include <stdlib.h>
 
 #include "pwa_internal.cuh"
@@ -81,7 +82,7 @@ struct AmpCfg {
 // Layout of the per-launch scratch (EvalArgs::partials) for a grid of G CTAs:
 //   pi  [G][2] int64   per-CTA sum of round(2^23 ln f) and of exponents
 //   pf  [G][2N+1]      per-CTA float-float sums: ln-f remainders, gradient
-//   mv  [2 kMaxWaves]  M V (double), written by the helper warps
+//   mv  [2 kMaxWaves + 1]  M V and then V^H M V (double), by CTA 0's helper warp
 //   flags              status bits of this launch (reset by the last CTA)
 struct AmpScratch {
     long long *pi;
@@ -99,7 +100,7 @@ __host__ __device__ inline AmpScratch amp_scratch(void *base, int grid)
     s.pf = reinterpret_cast<float2 *>(p);
     p += (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2);
     s.mv = reinterpret_cast<double *>(p);
-    p += 2 * kMaxWaves * sizeof(double);
+    p += (2 * kMaxWaves + 2) * sizeof(double);
     s.flags = reinterpret_cast<int *>(p);
     return s;
 }
@@ -107,7 +108,7 @@ __host__ __device__ inline AmpScratch amp_scratch(void *base, int grid)
 inline size_t amp_scratch_bytes(int grid)
 {
     return (size_t)grid * 2 * sizeof(long long) + (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2) +
-           2 * kMaxWaves * sizeof(double) + 64;
+           (2 * kMaxWaves + 2) * sizeof(double) + 64;
 }
 
 // Per-wave coefficients, each duplicated into both halves of a packed pair.
@@ -148,8 +149,6 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     __shared__ float s_sigma, s_unit;
     __shared__ long long red_i[CW][2];
     __shared__ float red_f[CW][NF];
-    __shared__ long long fin_i[2];
-    __shared__ double fin_f[NF];
     __shared__ int s_flags;
     __shared__ int s_last;
     AmpScratch sc = amp_scratch(a.partials, gridDim.x);
@@ -357,31 +356,26 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
             if (lane == 0)
                 red_f[cw][1 + c] = v;
         }
-    } else if (warp == CW + 1) {
-        // ---- helper warp: row blockIdx.x of M V in FP64 (once per launch) --
+    } else if (warp == CW + 1 && blockIdx.x == 0) {
+        // ---- helper warp of CTA 0: M V and V^H M V in FP64 -------------
+        // One row per lane; this overlaps the streaming of the data.
         const int Nw = a.n_waves;
-        const int row = blockIdx.x;
-        if (row < Nw) {
+        double nv = 0.0;
+        for (int row = lane; row < Nw; row += 32) {
             double re = 0.0, im = 0.0;
-            if (lane < Nw) {
-                const double mr = a.M[2 * (row * Nw + lane)], mi = a.M[2 * (row * Nw + lane) + 1];
-                const double vr = a.V[2 * lane], vi = a.V[2 * lane + 1];
-                re = fma(mr, vr, -mi * vi);
-                im = fma(mr, vi, mi * vr);
-            }
-            for (int b = lane + 32; b < Nw; b += 32) {
+            for (int b = 0; b < Nw; ++b) {
                 const double mr = a.M[2 * (row * Nw + b)], mi = a.M[2 * (row * Nw + b) + 1];
                 const double vr = a.V[2 * b], vi = a.V[2 * b + 1];
                 re = fma(mr, vr, fma(-mi, vi, re));
                 im = fma(mr, vi, fma(mi, vr, im));
             }
-            re = warp_sum(re);
-            im = warp_sum(im);
-            if (lane == 0) {
-                sc.mv[2 * row] = re;
-                sc.mv[2 * row + 1] = im;
-            }
+            sc.mv[2 * row] = re;
+            sc.mv[2 * row + 1] = im;
+            nv = fma(a.V[2 * row], re, fma(a.V[2 * row + 1], im, nv));  // Re(conj(V) (M V))
         }
+        nv = warp_sum(nv);
+        if (lane == 0)
+            sc.mv[2 * kMaxWaves] = nv;
     }
     if (flags)
         atomicOr(&s_flags, flags);
@@ -416,15 +410,14 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     // Each of the 2N+1 float components and the 2 integer ones is split into
     // SUB interleaved sub-sums over the CTAs, one per thread, with all of a
     // thread's loads issued before its adds (one L2 round trip); the
-    // sub-sums are then combined in a fixed order.
-    __threadfence();
+    // sub-sums are then combined in a fixed order. (The partials are read
+    // with L2 loads after the ticket, so no further fence is needed.)
     const int Nw = a.n_waves;
     const int G_ = gridDim.x;
     constexpr int SUB = 7, MAXB = 24;
     dfloat *sub_f = reinterpret_cast<dfloat *>(tiles);                  // [NF][SUB]
     long long *sub_i = reinterpret_cast<long long *>(sub_f + NF * SUB);  // [2][SUB]
     double *smv = reinterpret_cast<double *>(sub_i + 2 * SUB);          // [2N] M V
-    double *sv = smv + 2 * N;                                             // [2N] V
     for (int item = threadIdx.x; item < (NF + 2) * SUB; item += blockDim.x) {
         const int c = item / SUB, k = item % SUB;
         if (c < NF) {
@@ -460,54 +453,43 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     }
     for (int i = threadIdx.x; i < 2 * Nw; i += blockDim.x) {
         smv[i] = __ldcg(&sc.mv[i]);
-        sv[i] = a.V[i];
-    }
-    __syncthreads();
-    const int nwarps = blockDim.x >> 5;
-    for (int c = threadIdx.x; c < NF + 2; c += blockDim.x) {
-        if (c < NF) {
-            dfloat v = sub_f[c * SUB];
-            for (int k = 1; k < SUB; ++k)
-                v = df_add(v, sub_f[c * SUB + k]);
-            fin_f[c] = (double)v.hi + (double)v.lo;
-        } else {
-            long long v = 0;
-            for (int k = 0; k < SUB; ++k)
-                v += sub_i[(c - NF) * SUB + k];
-            fin_i[c - NF] = v;
-        }
-    }
-    // V^H M V = sum_a Re(conj(V_a) (M V)_a), one warp
-    double nv = 0.0;
-    if (warp == nwarps - 1) {
-        for (int w = lane; w < Nw; w += 32)
-            nv += sv[2 * w] * smv[2 * w] + sv[2 * w + 1] * smv[2 * w + 1];
-        nv = warp_sum(nv);
     }
     __syncthreads();
     const int wf = __ldcg(work_flags);
     const bool invalid = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) != 0;
-    if (a.grad)
-        for (int c = threadIdx.x; c < 2 * Nw; c += blockDim.x)
-            a.grad[c] = invalid ? 0.0 : (-fin_f[1 + c] + smv[c]);
-    if (warp == nwarps - 1 && lane == 0) {
-        const double lnsum = ((double)fin_i[0] + fin_f[0]) * 0x1p-23 + (double)fin_i[1] * kLn2;
-        double nll = -lnsum + nv;
-        if (wf & FLAG_DOMAIN)
-            nll = INFINITY;
-        if (wf & FLAG_TIMEOUT)
-            nll = NAN;
-        a.nll[0] = nll;
-        if (wf)
-            atomicOr(a.status, wf);
-        if (a.done)
-            atomicAdd(a.done, 1);
+    for (int c = threadIdx.x; c < NF; c += blockDim.x) {
+        dfloat v = sub_f[c * SUB];
+        for (int k = 1; k < SUB; ++k)
+            v = df_add(v, sub_f[c * SUB + k]);
+        if (c > 0) {
+            // gradient: - sum_i conj(A) S / I + (M V)
+            if (a.grad)
+                a.grad[c - 1] = invalid ? 0.0 : (smv[c - 1] - (double)v.hi) - (double)v.lo;
+        } else {
+            // ln sum: integer part and exponents are exact; the rest is small
+            long long li = 0, ei = 0;
+            for (int k = 0; k < SUB; ++k) {
+                li += sub_i[k];
+                ei += sub_i[SUB + k];
+            }
+            const double lnsum =
+                fma((double)ei, kLn2, ((double)li + ((double)v.hi + (double)v.lo)) * 0x1p-23);
+            double nll = __ldcg(&sc.mv[2 * kMaxWaves]) - lnsum;
+            if (wf & FLAG_DOMAIN)
+                nll = INFINITY;
+            if (wf & FLAG_TIMEOUT)
+                nll = NAN;
+            a.nll[0] = nll;
+            if (wf)
+                atomicOr(a.status, wf);
+            if (a.done)
+                atomicAdd(a.done, 1);
+        }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
         *work_flags = 0;
         *a.ticket = 0u;
-        __threadfence();
     }
 }
 
