@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
     __syncthreads();
     const int wf = __ldcg(work_flags);
     const bool invalid = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) != 0;
-    for (int c = threadIdx.x; c < NF; c += blockDim.x) {
+    for (int c = threadIdx.x; c < 2 * Nw + 1; c += blockDim.x) {  // padded waves excluded
         dfloat v = sub_f[c * SUB];
         for (int k = 1; k < SUB; ++k)
             v = df_add(v, sub_f[c * SUB + k]);

@@ -185,3 +185,26 @@ def test_back_to_back_async_launches(pwa):
             n_dev, g_dev = dn.cpu().numpy(), dg.cpu().numpy()
     assert np.all(n_dev == n_host[0])
     assert np.all(g_dev == g_host[0])
+
+
+@pytest.mark.parametrize("N", [3, 25, 41])
+def test_async_outputs_written_exactly(pwa, N):
+    """Wave counts below the kernel's padded width: the device outputs are
+    written for exactly K x N gradient entries and K NLLs, nothing past them."""
+    torch = pytest.importorskip("torch")
+    wl = case(N, 2000, 2000, seed=N)
+    K = 2
+    Vs = np.stack([synth.random_V(N, 1), synth.random_V(N, 2)])
+    with pwa.Likelihood(N, max_k=K) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        n_host, g_host = L.nll_grad(Vs)
+        dV = torch.from_numpy(Vs).cuda()
+        guard = 12345.0
+        dn = torch.full((K + 8,), guard, dtype=torch.float64, device="cuda")
+        dg = torch.full((K * N + 64,), guard, dtype=torch.complex128, device="cuda")
+        L.nll_grad_async(dV, dn[:K], dg[:K * N])
+        assert L.sync() == pwa.PWA_OK
+        n_dev, g_dev = dn.cpu().numpy(), dg.cpu().numpy()
+    assert np.all(n_dev[:K] == n_host) and np.all(n_dev[K:] == guard)
+    assert np.all(g_dev[:K * N].reshape(K, N) == g_host) and np.all(g_dev[K * N:] == guard)
