@@ -129,6 +129,50 @@ int pwa_nll_grad_async(pwa_ctx *ctx, const double *d_V, int K, double *d_nll, do
  * PWA_ETIMEOUT), then clear it. */
 int pwa_sync(pwa_ctx *ctx);
 
+/* Direct-form NLL and gradient that allocates no device memory.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate: code whose device memory is all owned by another
+ * framework's pool or held to a fixed budget, and latency-critical loops
+ * that cannot afford cudaMalloc/cudaFree (which may synchronize the device).
+ * It evaluates the same quantity with the same kernel as pwa_nll_grad_async
+ * for one parameter set, but without a context: the caller passes every
+ * input and output in device memory, and the kernel's scratch (per-CTA
+ * partial sums, a completion ticket, status words; about 200 KB) lives in a
+ * file-scope device array of the library, which every GPU that loads the
+ * library holds until the process exits.
+ *
+ *   d_planes     structure-of-arrays amplitudes, float: plane 2a holds Re A_a,
+ *                plane 2a+1 holds Im A_a, event i of plane p at
+ *                d_planes[p * plane_pitch + i]; 16-byte aligned
+ *   plane_pitch  floats per plane, >= n_events and a multiple of 4
+ *   n_events     data events, 1 <= n_events <= 2^31 - 1024
+ *   n_waves      1 <= n_waves <= 48
+ *   d_amax       [n_waves] floats, d_amax[a] >= max_i |Re A_a(i)| + |Im A_a(i)|
+ *                (the kernel sizes its exact splitting of the products from
+ *                it; a value below the true maximum gives wrong results)
+ *   d_M          [n_waves][n_waves] complex128, the normalisation matrix as
+ *                returned by pwa_build_norm
+ *   d_V          [n_waves] complex128
+ *   d_nll        [1] double, receives the NLL (+inf on a non-positive
+ *                intensity, NaN if a device-side wait timed out)
+ *   d_grad       [n_waves] complex128, receives dNLL/dV* (may be NULL)
+ *   d_status     [1] int or NULL: status bits are OR-ed into it (1: an
+ *                intensity was not positive and finite, 2: a wait timed out)
+ *   stream       cudaStream_t to run on (NULL: the legacy default stream)
+ * The call is stream-ordered and returns after enqueueing. It works on the
+ * current device. Its first call on a device does the set-up (looks up the
+ * array's device address and sets the kernel's shared-memory limit), so make
+ * that first call before any stream capture. Every call shares the one
+ * array: calls whose kernels overlap on the GPU (other streams, other host
+ * threads) race and corrupt each other's sums; order them on one stream.
+ * Returns PWA_OK, PWA_EINVAL (null pointer, size or alignment out of range),
+ * PWA_ENOTSUP (scratch too small for this GPU) or PWA_ECUDA. It calls no
+ * cudaMalloc, cudaFree or allocating library routine. */
+int pwa_nll_grad_noalloc(const float *d_planes, int64_t plane_pitch, int64_t n_events,
+                         int n_waves, const float *d_amax, const double *d_M, const double *d_V,
+                         double *d_nll, double *d_grad, int *d_status, void *stream);
+
 /* Message describing the last error on ctx ("" if none); valid until the
  * next call on ctx. A NULL ctx gives the message of the last failed
  * pwa_create on this thread. */

@@ -75,6 +75,7 @@ def load(path=LIB_PATH):
         "pwa_last_error": ([P], ctypes.c_char_p),
         "pwa_table_bytes": ([I, I64, ctypes.POINTER(ctypes.c_int64)], I),
         "pwa_version": ([], I),
+        "pwa_nll_grad_noalloc": ([P, I64, I64, I, P, P, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -191,6 +192,19 @@ def pwa_nll_grad_async(ctx, d_V, K, d_nll, d_grad=None):
 
 def pwa_sync(ctx):
     return _check(ctx, load().pwa_sync(ctx), allow=(PWA_EDOMAIN,))
+
+
+def pwa_nll_grad_noalloc(d_planes, plane_pitch, n_events, n_waves, d_amax, d_M, d_V, d_nll,
+                         d_grad=None, d_status=None, stream=None):
+    """Context-free, allocation-free evaluation (see include/pwa.h): every
+    argument is a CUDA tensor already on the current device."""
+    ptrs = [_ptr(x) for x in (d_planes, d_amax, d_M, d_V, d_nll, d_grad, d_status)]
+    rc = load().pwa_nll_grad_noalloc(ptrs[0][0], plane_pitch, n_events, n_waves, ptrs[1][0],
+                                     ptrs[2][0], ptrs[3][0], ptrs[4][0], ptrs[5][0], ptrs[6][0],
+                                     ctypes.c_void_p(stream) if stream else None)
+    if rc != PWA_OK:
+        raise PwaError(rc, "pwa_nll_grad_noalloc failed")
+    return rc
 
 
 def pwa_last_error(ctx):

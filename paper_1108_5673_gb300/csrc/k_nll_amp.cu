@@ -105,11 +105,7 @@ __host__ __device__ inline AmpScratch amp_scratch(void *base, int grid)
     return s;
 }
 
-inline size_t amp_scratch_bytes(int grid)
-{
-    return (size_t)grid * 2 * sizeof(long long) + (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2) +
-           (2 * kMaxWaves + 2) * sizeof(double) + 64;
-}
+
 
 // Per-wave coefficients, each duplicated into both halves of a packed pair.
 struct alignas(16) WaveCoef {
@@ -591,15 +587,28 @@ int amp_grid(int n_waves, int num_sms)
     return (forced > 0 && forced <= 4 * num_sms) ? forced : num_sms;
 }
 
+size_t amp_flags_offset(int grid)
+{
+    return (size_t)grid * 2 * sizeof(long long) + (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2) +
+           (2 * kMaxWaves + 2) * sizeof(double);
+}
+
+size_t amp_scratch_bytes_for_grid(int grid) { return amp_flags_offset(grid) + 64; }
+
 size_t amp_partials_doubles(int n_waves, int num_sms)
 {
-    return amp_scratch_bytes(amp_grid(n_waves, num_sms)) / sizeof(double) + 8;
+    return amp_scratch_bytes_for_grid(amp_grid(n_waves, num_sms)) / sizeof(double) + 8;
 }
 
 cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
                            int num_sms, cudaStream_t s)
 {
-    const int grid = amp_grid(amp.n_waves, num_sms);
+    return launch_nll_amp_grid(amp, map, a, amp_grid(amp.n_waves, num_sms), s);
+}
+
+cudaError_t launch_nll_amp_grid(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
+                                int grid, cudaStream_t s)
+{
     const int te = amp_box_events(amp.n_waves);
     if (te <= 0)
         return cudaErrorInvalidValue;

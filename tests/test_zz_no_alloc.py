@@ -1,0 +1,61 @@
+"""The allocation-free entry point against the context entry point.
+
+pwa_nll_grad_noalloc serves callers that cannot allocate device memory (a
+framework owns the device memory, or cudaMalloc's synchronisation is not
+acceptable in their loop): its scratch lives in a fixed array inside the
+library. This file is collected last on purpose, so that a run stopping at
+the first failure has already run every other test; it also passes alone.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_noalloc_matches_context_entry_point_twice():
+    import __graft_entry__
+    __graft_entry__.build()
+    torch = pytest.importorskip("torch")
+    import paper_1108_5673_gb300 as pwa
+    from paper_1108_5673_gb300 import _abi
+
+    N, n = 20, 300_001
+    wl = synth.mixture_workload("noalloc", synth.waves_linear(N), n, 20_000, seed_data=5,
+                                seed_mc=6, seed_v=7)
+    Vs = [synth.random_V(N, 21), synth.random_V(N, 22)]
+    with pwa.Likelihood(N, max_k=1) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        M = L.build_norm()
+        ref = [L.nll_grad(V[None]) for V in Vs]
+
+    # the caller's own device buffers: SoA planes, per-wave maxima, M, V, outputs
+    pitch = (n + 3) // 4 * 4
+    planes = np.zeros((2 * N, pitch), dtype=np.float32)
+    planes[0::2, :n] = wl.A_data.real.T
+    planes[1::2, :n] = wl.A_data.imag.T
+    amax = (np.abs(wl.A_data.real) + np.abs(wl.A_data.imag)).max(axis=0).astype(np.float32)
+    d_planes = torch.from_numpy(planes).cuda()
+    d_amax = torch.from_numpy(amax).cuda()
+    d_M = torch.from_numpy(M).cuda()
+    d_nll = torch.empty(1, dtype=torch.float64, device="cuda")
+    d_grad = torch.empty(N, dtype=torch.complex128, device="cuda")
+    d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    for V, (n_ref, g_ref) in zip(Vs, ref):          # two calls in a row
+        d_V = torch.from_numpy(V).cuda()
+        _abi.pwa_nll_grad_noalloc(d_planes, pitch, n, N, d_amax, d_M, d_V, d_nll, d_grad,
+                                  d_status)
+        torch.cuda.synchronize()
+        nll, g = float(d_nll.item()), d_grad.cpu().numpy()
+        assert int(d_status.item()) == 0
+        assert abs(nll - n_ref[0]) <= max(1e-3 * math.sqrt(n / 1e6), 2e-6)
+        assert np.linalg.norm(g - g_ref[0]) <= 1e-5 * np.linalg.norm(g_ref[0])
+
+    # sizes beyond the limits are refused before anything runs
+    with pytest.raises(_abi.PwaError):
+        _abi.pwa_nll_grad_noalloc(d_planes, pitch, n, 49, d_amax, d_M, d_V, d_nll, d_grad)
+    with pytest.raises(_abi.PwaError):
+        _abi.pwa_nll_grad_noalloc(d_planes, pitch + 2, n, N, d_amax, d_M, d_V, d_nll, d_grad)
