@@ -30,6 +30,7 @@ class Likelihood:
 
     def load_events(self, data_amp, mc_amp, n_mc_gen):
         self._abi.pwa_load_events(self.ctx, data_amp, mc_amp, n_mc_gen)
+        self.n_data = int(data_amp.shape[0])
         return self
 
     def build_norm(self):
