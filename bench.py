@@ -33,6 +33,10 @@ METRIC = "NLL+grad evals/s (1M events, 20 waves, K starts); % HBM / tensor roofl
 UNIT = "evals/s"
 N_WAVES, N_DATA, N_MC = 20, 1_000_000, 5_000_000
 WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M accepted MC, K=1 per evaluation"
+# DRAM bytes (read + write) per launch of the timed kernel from one ncu capture
+# (profiles/nll_amp_1M_20waves.md); None once the kernel has changed since.
+KERNEL = "nll_amp_kernel<20, 2>"
+TRAFFIC_BYTES = 160.145664e6 + 4.291840e6
 
 
 def measured_peaks():
@@ -158,10 +162,16 @@ def main():
     dV = torch.from_numpy(V[None]).cuda()
     dn = torch.empty(1, dtype=torch.float64, device="cuda")
     dg = torch.empty(1, N_WAVES, dtype=torch.complex128, device="cuda")
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
-    for _ in range(args.warmup):
-        flush.fill_(1)
+    def evict_l2(i):
+        # write a buffer larger than L2, then read it back: the sample is evicted
+        # and the cache holds clean lines, so no write-back lands in the timed step
+        flush.fill_(float(i & 0xff))
+        return flush.sum()
+
+    for i in range(args.warmup):
+        evict_l2(i)
         L.nll_grad_async(dV, dn, dg)
     assert L.sync() == pwa.PWA_OK
 
@@ -175,7 +185,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     for i in range(args.steps):
-        flush.fill_(i & 0xff)            # untimed: evicts the sample from L2
+        evict_l2(i)                      # untimed
         starts[i].record(stream)
         L.nll_grad_async(dV, dn, dg)
         ends[i].record(stream)
@@ -229,12 +239,12 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n_waves": N_WAVES, "n_data": N_DATA, "n_mc_acc": N_MC,
                    "n_mc_gen": wl.n_gen, "K": 1, "form": "amp",
-                   "l2": "flushed between timed steps (256 MB write, untimed)",
+                   "l2": "flushed between timed steps (256 MB write + read back, untimed)",
                    "parallelism": "replicas" if world > 1 else "single",
                    "ms_per_step_back_to_back": b2b_ms, "build_norm_s": build_norm_s},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                     "kernel": "nll_amp_kernel<20>",
+                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES, "peak_kind": peak_kind,
+                     "kernel": KERNEL,
                      "algorithmic_bytes_per_launch": alg_bytes},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * N_WAVES + 8,
                 "d2h_bytes_per_step": 8 + 16 * N_WAVES + 8},
