@@ -61,7 +61,7 @@ typedef struct pwa_ctx pwa_ctx;
 typedef struct pwa_config {
     int n_waves;   /* number of partial waves N, 1 <= N <= 48 */
     int forms;     /* bitmask of PWA_FORM_* stores built by pwa_load_events;
-                      0 means PWA_FORM_AMP */
+                      0 means PWA_FORM_AMP; PWA_FORM_TABLE needs n_waves <= 24 */
     int precision; /* reserved for the batched tensor-core path; 0 */
     int max_k;     /* largest K accepted by the evaluation calls (>= 1) */
     void *stream;  /* cudaStream_t to run on; NULL = a stream the context owns */

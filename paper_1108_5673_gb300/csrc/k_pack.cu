@@ -78,7 +78,31 @@ __global__ void amp_max_kernel(const float *__restrict__ planes, int64_t pitch, 
         atomicMax(reinterpret_cast<int *>(amax + w), __float_as_int(m));
 }
 
+__global__ void plane_absmax_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n,
+                                    float *__restrict__ out)
+{
+    const int r = blockIdx.y;
+    float m = 0.f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(planes[(int64_t)r * pitch + i]));
+    for (int o = 16; o > 0; o >>= 1)
+        m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(reinterpret_cast<int *>(out + r), __float_as_int(m));
+}
+
 }  // namespace
+
+cudaError_t launch_plane_absmax(const float *planes, int64_t pitch, int64_t n, int rows, float *out,
+                                cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    dim3 grid((unsigned)std::min<int64_t>((n + 255) / 256, 64), (unsigned)rows);
+    plane_absmax_kernel<<<grid, 256, 0, s>>>(planes, pitch, n, out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_amp_max(const Planes &amp, float *amax, cudaStream_t s)
 {

@@ -34,7 +34,9 @@ struct pwa_ctx {
     Planes data{}, mc{};
     float *table = nullptr;
     int64_t table_pitch = 0;
-    CUtensorMap data_map;
+    float *tmax = nullptr;  // [N^2] max over events of |t_p|
+    CUtensorMap data_map, table_map;
+    size_t work_bytes = 0;
     bool loaded = false, has_norm = false;
     double *M = nullptr;     // [N][N] complex
     float *amax = nullptr;   // [N] max over data events of |Re A_a| + |Im A_a|
@@ -148,6 +150,7 @@ void free_sample(pwa_ctx *c)
     dev_free(c->data.ptr);
     dev_free(c->mc.ptr);
     dev_free(c->table);
+    dev_free(c->tmax);
     c->loaded = c->has_norm = false;
 }
 
@@ -235,7 +238,7 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         if (c->form == PWA_FORM_AMP)
             e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream);
         else
-            return fail(c, PWA_ENOTSUP, "form %d not available in this build", c->form);
+            e = launch_nll_table(c->n_data, N, &c->table_map, a, c->tmax, c->num_sms, c->stream);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(c, PWA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -366,7 +369,11 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
             return bail(fail(c, PWA_ECUDA, "cudaStreamCreate failed"));
         c->own_stream = true;
     }
+    if ((forms & PWA_FORM_TABLE) && c->N > table_max_waves())
+        return bail(fail(c, PWA_ENOTSUP, "the table form supports up to %d waves", table_max_waves()));
     cudaError_t e = amp_configure();
+    if (e == cudaSuccess && (forms & PWA_FORM_TABLE))
+        e = table_configure();
     if (e != cudaSuccess)
         return bail(fail(c, PWA_ECUDA, "kernel configuration: %s", cudaGetErrorString(e)));
     const size_t nio = io_doubles(c->N, cfg->max_k);
@@ -377,7 +384,10 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
         c->h_io = nullptr;
         return bail(fail(c, PWA_ENOMEM, "pinned host buffer"));
     }
-    const size_t nwork = amp_partials_doubles(c->N, c->num_sms) + 8;
+    size_t nwork = amp_partials_doubles(c->N, c->num_sms) + 8;
+    if (forms & PWA_FORM_TABLE)
+        nwork = std::max(nwork, table_scratch_bytes(c->N, c->num_sms) / sizeof(double) + 16);
+    c->work_bytes = nwork * sizeof(double);
     if ((rc = dev_alloc(c, (void **)&c->d_work, nwork * sizeof(double), "work")))
         return bail(rc);
     if (cudaMemset(c->d_work, 0, nwork * sizeof(double)) != cudaSuccess)
@@ -439,8 +449,18 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
         c->table_pitch = c->data.pitch;
         rc = dev_alloc(c, (void **)&c->table, (size_t)c->N * c->N * c->table_pitch * sizeof(float),
                        "table");
+        if (!rc)
+            rc = dev_alloc(c, (void **)&c->tmax, (size_t)c->N * c->N * sizeof(float), "tmax");
         if (!rc) {
+            const int P = c->N * c->N;
             cudaError_t e = launch_table_build(c->data, c->table, c->table_pitch, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(c->tmax, 0, P * sizeof(float), c->stream);
+            if (e == cudaSuccess)
+                e = launch_plane_absmax(c->table, c->table_pitch, n_data, P, c->tmax, c->stream);
+            if (e == cudaSuccess)
+                e = encode_planes_map(&c->table_map, c->table, n_data, c->table_pitch, P,
+                                      table_box_events(), table_box_rows(c->N));
             if (e != cudaSuccess)
                 rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
         }
@@ -509,6 +529,12 @@ int pwa_set_form(pwa_ctx *c, int form)
         return fail(c, PWA_EINVAL, "unknown form %d", form);
     if (!(c->cfg.forms & form))
         return fail(c, PWA_ESTATE, "form %d was not requested at pwa_create", form);
+    if (form != c->form) {
+        // the two kernels lay out the shared scratch differently: start clean
+        DeviceGuard g(c->device);
+        CK(c, cudaMemsetAsync(c->d_work, 0, c->work_bytes, c->stream));
+        CK(c, cudaStreamSynchronize(c->stream));
+    }
     c->form = form;
     return PWA_OK;
 }

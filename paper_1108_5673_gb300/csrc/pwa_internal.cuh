@@ -274,6 +274,18 @@ cudaError_t launch_table_build(const Planes &amp, float *table, int64_t table_pi
                                cudaStream_t s);
 // amax[a] = max_i |Re A_a(i)| + |Im A_a(i)| (amax must be zeroed first)
 cudaError_t launch_amp_max(const Planes &amp, float *amax, cudaStream_t s);
+// out[r] = max_i |planes[r][i]| for r < rows (out must be zeroed first)
+cudaError_t launch_plane_absmax(const float *planes, int64_t pitch, int64_t n, int rows, float *out,
+                                cudaStream_t s);
+
+// k_nll_table.cu
+int table_max_waves();
+int table_box_events();
+int table_box_rows(int n_waves);
+size_t table_scratch_bytes(int n_waves, int grid);
+cudaError_t table_configure();
+cudaError_t launch_nll_table(int64_t n_events, int n_waves, const CUtensorMap *map,
+                             const EvalArgs &a, const float *tmax, int grid, cudaStream_t s);
 
 // k_norm.cu
 size_t norm_scratch_bytes(int n_waves, int num_sms);
