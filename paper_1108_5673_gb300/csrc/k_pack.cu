@@ -41,27 +41,31 @@ __global__ void pack_kernel(const T2 *__restrict__ src, int64_t n, int N, float 
     }
 }
 
+// Each entry is the float nearest to its exact value: the products of two
+// floats are exact in double and each entry adds two of them, so the double
+// result carries one rounding and the final rounding to float is the only
+// one that matters. (One-time work; FP64 is acceptable here.)
 __global__ void table_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n, int N,
                              float *__restrict__ table, int64_t tpitch)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n)
         return;
-    float ar[kMaxWaves], ai[kMaxWaves];
     for (int w = 0; w < N; ++w) {
-        ar[w] = planes[(2 * w) * pitch + i];
-        ai[w] = planes[(2 * w + 1) * pitch + i];
+        const double ar = planes[(2 * w) * pitch + i], ai = planes[(2 * w + 1) * pitch + i];
+        table[w * tpitch + i] = __double2float_rn(ar * ar + ai * ai);
     }
-    for (int w = 0; w < N; ++w)
-        table[w * tpitch + i] = fmaf(ar[w], ar[w], ai[w] * ai[w]);
     int p = N;
-    for (int x = 0; x < N; ++x)
+    for (int x = 0; x < N; ++x) {
+        const double xr = planes[(2 * x) * pitch + i], xi = planes[(2 * x + 1) * pitch + i];
         for (int y = x + 1; y < N; ++y) {
-            // A_x conj(A_y) = (ar_x ar_y + ai_x ai_y) + i (ai_x ar_y - ar_x ai_y)
-            table[(int64_t)p * tpitch + i] = fmaf(ar[x], ar[y], ai[x] * ai[y]);
-            table[(int64_t)(p + 1) * tpitch + i] = fmaf(ai[x], ar[y], -(ar[x] * ai[y]));
+            const double yr = planes[(2 * y) * pitch + i], yi = planes[(2 * y + 1) * pitch + i];
+            // A_x conj(A_y) = (xr yr + xi yi) + i (xi yr - xr yi)
+            table[(int64_t)p * tpitch + i] = __double2float_rn(xr * yr + xi * yi);
+            table[(int64_t)(p + 1) * tpitch + i] = __double2float_rn(xi * yr - xr * yi);
             p += 2;
         }
+    }
 }
 
 __global__ void amp_max_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n, int N,

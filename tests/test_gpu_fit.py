@@ -44,7 +44,7 @@ def test_fit_matches_oracle_fit(pwa):
     with pwa.Likelihood(4) as L:
         L.load_events(A, A_mc, n_gen)
         L.build_norm()
-        Vg, fg, info = fit.fit_lbfgs(L, V0)
+        Vg, fg, info = fit.fit_lbfgs(L, V0, grad_tol=1e-6, change_tol=1e-13)
 
     def f(x):
         n, g, _ = oracle.nll_amp(A, M, x[:4] + 1j * x[4:])
