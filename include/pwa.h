@@ -51,6 +51,9 @@ extern "C" {
 /* ---- forms of the data term (Sec. 2, after Eq. 3) ----------------------- */
 #define PWA_FORM_AMP 1   /* direct: S_i = sum_a V_a A_a(i), I_i = |S_i|^2 */
 #define PWA_FORM_TABLE 2 /* precomputed per-event table A_a A*_b (upper triangle) */
+#define PWA_FORM_TC 4    /* batched K parameter sets on the tensor cores: BF16-rounded
+                            amplitudes and BF16 operands, FP32 accumulation (the
+                            thousands of restarts of Sec. 2 evaluated together) */
 
 /* ---- amplitude element types ------------------------------------------- */
 #define PWA_C64 1  /* float pairs: used as given */
@@ -62,7 +65,7 @@ typedef struct pwa_config {
     int n_waves;   /* number of partial waves N, 1 <= N <= 48 */
     int forms;     /* bitmask of PWA_FORM_* stores built by pwa_load_events;
                       0 means PWA_FORM_AMP; PWA_FORM_TABLE needs n_waves <= 24 */
-    int precision; /* reserved for the batched tensor-core path; 0 */
+    int precision; /* reserved; the tensor-core form uses BF16 operands */
     int max_k;     /* largest K accepted by the evaluation calls (>= 1) */
     void *stream;  /* cudaStream_t to run on; NULL = a stream the context owns */
 } pwa_config;
@@ -100,8 +103,11 @@ int pwa_load_events(pwa_ctx *ctx, const void *data_amp, int64_t n_data,
  * Errors: PWA_ESTATE (no events loaded), PWA_ECUDA. */
 int pwa_build_norm(pwa_ctx *ctx, double *M_out);
 
-/* Select which store evaluates the data term: PWA_FORM_AMP (default) or
- * PWA_FORM_TABLE. Both give the same NLL up to rounding.
+/* Select which store evaluates the data term: PWA_FORM_AMP (default),
+ * PWA_FORM_TABLE or PWA_FORM_TC. The first two give the same NLL up to
+ * rounding; PWA_FORM_TC evaluates the BF16-rounded amplitudes (a different
+ * sample at the 1e-3 level) with FP32 accumulation and is meant for many
+ * parameter sets per call.
  * Errors: PWA_EINVAL (unknown form), PWA_ESTATE (store not built). */
 int pwa_set_form(pwa_ctx *ctx, int form);
 

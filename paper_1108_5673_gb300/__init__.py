@@ -9,10 +9,11 @@ streams.
 
 The compiled library is built by `paper_1108_5673_gb300.build.build()`.
 """
-from ._abi import (PWA_C64, PWA_C128, PWA_EDOMAIN, PWA_FORM_AMP, PWA_FORM_TABLE, PWA_OK,
-                   PwaError)
+from ._abi import (PWA_C64, PWA_C128, PWA_EDOMAIN, PWA_FORM_AMP, PWA_FORM_TABLE, PWA_FORM_TC,
+                   PWA_OK, PwaError)
 
-__all__ = ["Likelihood", "PwaError", "PWA_FORM_AMP", "PWA_FORM_TABLE", "PWA_OK", "PWA_EDOMAIN",
+__all__ = ["Likelihood", "PwaError", "PWA_FORM_AMP", "PWA_FORM_TABLE", "PWA_FORM_TC", "PWA_OK",
+           "PWA_EDOMAIN",
            "PWA_C64", "PWA_C128"]
 
 

@@ -30,6 +30,7 @@ PWA_ETIMEOUT = -6
 PWA_ENOTSUP = -7
 PWA_FORM_AMP = 1
 PWA_FORM_TABLE = 2
+PWA_FORM_TC = 4
 PWA_C64 = 1
 PWA_C128 = 2
 

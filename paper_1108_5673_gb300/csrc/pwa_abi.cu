@@ -35,7 +35,8 @@ struct pwa_ctx {
     float *table = nullptr;
     int64_t table_pitch = 0;
     float *tmax = nullptr;  // [N^2] max over events of |t_p|
-    CUtensorMap data_map, table_map;
+    void *xbf = nullptr;    // BF16 planes [F][pitch] of the data (tensor-core form)
+    CUtensorMap data_map, table_map, xbf_map;
     size_t work_bytes = 0;
     bool loaded = false, has_norm = false;
     double *M = nullptr;     // [N][N] complex
@@ -151,6 +152,7 @@ void free_sample(pwa_ctx *c)
     dev_free(c->mc.ptr);
     dev_free(c->table);
     dev_free(c->tmax);
+    dev_free(c->xbf);
     c->loaded = c->has_norm = false;
 }
 
@@ -221,6 +223,20 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
                  int *done)
 {
     const int N = c->N;
+    if (c->form == PWA_FORM_TC) {
+        const int kmax = batched_max_k(N);
+        for (int k0 = 0; k0 < K; k0 += kmax) {
+            const int kk = std::min(kmax, K - k0);
+            cudaError_t e = launch_batched(&c->xbf_map, c->n_data, N, dV + (size_t)2 * N * k0, kk, c->M,
+                                           c->d_work, c->num_sms, status, done, dnll + k0,
+                                           dgrad ? dgrad + (size_t)2 * N * k0 : nullptr, c->stream);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(c, PWA_ECUDA, "batched launch: %s", cudaGetErrorString(e));
+            }
+        }
+        return PWA_OK;
+    }
     for (int k = 0; k < K; ++k) {
         EvalArgs a{};
         a.n_waves = N;
@@ -237,8 +253,10 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         cudaError_t e = cudaSuccess;
         if (c->form == PWA_FORM_AMP)
             e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream);
-        else
+        else if (c->form == PWA_FORM_TABLE)
             e = launch_nll_table(c->n_data, N, &c->table_map, a, c->tmax, c->num_sms, c->stream);
+        else
+            return fail(c, PWA_EINVAL, "internal: tensor-core form in the per-set loop");
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(c, PWA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
@@ -312,6 +330,23 @@ cudaError_t encode_planes_map(CUtensorMap *map, const float *base, int64_t n, in
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// BF16 planes [rows][pitch] with 128-byte swizzle, box 64 events x rows.
+cudaError_t encode_bf16_planes_map(CUtensorMap *map, const void *base, int64_t n, int64_t pitch,
+                                   int rows)
+{
+    auto fn = get_encode_fn();
+    if (!fn)
+        return cudaErrorNotSupported;
+    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
+                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 }  // namespace pwa
 
 extern "C" {
@@ -339,7 +374,7 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     if (cfg->max_k < 1 || cfg->max_k > 65536)
         return fail(nullptr, PWA_EINVAL, "max_k=%d outside [1, 65536]", cfg->max_k);
     const int forms = cfg->forms ? cfg->forms : PWA_FORM_AMP;
-    if (forms & ~(PWA_FORM_AMP | PWA_FORM_TABLE))
+    if (forms & ~(PWA_FORM_AMP | PWA_FORM_TABLE | PWA_FORM_TC))
         return fail(nullptr, PWA_EINVAL, "unknown form bits 0x%x", forms);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
@@ -374,6 +409,8 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     cudaError_t e = amp_configure();
     if (e == cudaSuccess && (forms & PWA_FORM_TABLE))
         e = table_configure();
+    if (e == cudaSuccess && (forms & PWA_FORM_TC))
+        e = batched_configure();
     if (e != cudaSuccess)
         return bail(fail(c, PWA_ECUDA, "kernel configuration: %s", cudaGetErrorString(e)));
     const size_t nio = io_doubles(c->N, cfg->max_k);
@@ -387,6 +424,9 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     size_t nwork = amp_partials_doubles(c->N, c->num_sms) + 8;
     if (forms & PWA_FORM_TABLE)
         nwork = std::max(nwork, table_scratch_bytes(c->N, c->num_sms) / sizeof(double) + 16);
+    if (forms & PWA_FORM_TC)
+        nwork = std::max(nwork, batched_scratch_bytes(c->N, std::min(cfg->max_k, batched_max_k(c->N)),
+                                                      c->num_sms) / sizeof(double) + 16);
     c->work_bytes = nwork * sizeof(double);
     if ((rc = dev_alloc(c, (void **)&c->d_work, nwork * sizeof(double), "work")))
         return bail(rc);
@@ -465,6 +505,18 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
                 rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
         }
     }
+    if (!rc && (c->cfg.forms & PWA_FORM_TC)) {
+        const int F = batched_features(c->N);
+        rc = dev_alloc(c, &c->xbf, (size_t)F * c->data.pitch * 2, "bf16 planes");
+        if (!rc) {
+            cudaError_t e = launch_to_bf16(c->data.ptr, c->data.pitch, 2 * c->N, c->xbf, c->data.pitch,
+                                           F, c->stream);
+            if (e == cudaSuccess)
+                e = encode_bf16_planes_map(&c->xbf_map, c->xbf, c->data.n, c->data.pitch, F);
+            if (e != cudaSuccess)
+                rc = fail(c, PWA_ECUDA, "bf16 store: %s", cudaGetErrorString(e));
+        }
+    }
     if (!rc) {
         cudaError_t e = cudaMemsetAsync(c->amax, 0, c->N * sizeof(float), c->stream);
         if (e == cudaSuccess)
@@ -525,7 +577,7 @@ int pwa_set_form(pwa_ctx *c, int form)
 {
     if (!c)
         return PWA_EINVAL;
-    if (form != PWA_FORM_AMP && form != PWA_FORM_TABLE)
+    if (form != PWA_FORM_AMP && form != PWA_FORM_TABLE && form != PWA_FORM_TC)
         return fail(c, PWA_EINVAL, "unknown form %d", form);
     if (!(c->cfg.forms & form))
         return fail(c, PWA_ESTATE, "form %d was not requested at pwa_create", form);

@@ -102,6 +102,94 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
+// ---- tcgen05 (5th-generation tensor cores) --------------------------------
+// Shared-memory matrix descriptor for a 128-byte-swizzled operand: start
+// address, leading and stride byte offsets (16-byte units), version 1,
+// layout SWIZZLE_128B. K-major: rows 128 B apart in 8-row (1 KB) atoms, SBO =
+// 1 KB, LBO unused. MN-major: 64 M/N elements per 128-B row, rows = K, SBO =
+// 1 KB between 8-row groups along K, LBO = byte stride between 64-element
+// blocks along M/N. Swizzle atoms must be 1 KB aligned in shared memory.
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t saddr, uint32_t lbo_bytes,
+                                                    uint32_t sbo_bytes)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor, kind::f16 with BF16 operands and FP32 accumulation.
+__device__ __forceinline__ uint32_t umma_idesc_bf16(int M, int N, int a_mn_major, int b_mn_major)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) |
+           ((uint32_t)b_mn_major << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                          uint32_t accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+        "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once every tcgen05 operation issued so far by this thread is done.
+__device__ __forceinline__ void umma_commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst_smem, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 32 lanes x 32 consecutive 32-bit columns of tensor memory (this warp's lane quarter).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+                   "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
 // Split x > 0 (finite, possibly subnormal) as x = f * 2^e with
 // f in [1/sqrt(2), sqrt(2)], so that ln x = e ln 2 + ln f with |ln f| <= 0.35.
 __device__ __forceinline__ float split_exponent(float x, int &e)
@@ -266,6 +354,8 @@ struct Planes {
 // box_x events x box_y planes. Returns cudaSuccess or an error.
 cudaError_t encode_planes_map(CUtensorMap *map, const float *base, int64_t n, int64_t pitch,
                               int rows, int box_x, int box_y);
+cudaError_t encode_bf16_planes_map(CUtensorMap *map, const void *base, int64_t n, int64_t pitch,
+                                   int rows);
 
 // k_pack.cu
 cudaError_t launch_pack(const void *src, int dtype, int64_t n, int n_waves, float *planes,
@@ -277,6 +367,19 @@ cudaError_t launch_amp_max(const Planes &amp, float *amax, cudaStream_t s);
 // out[r] = max_i |planes[r][i]| for r < rows (out must be zeroed first)
 cudaError_t launch_plane_absmax(const float *planes, int64_t pitch, int64_t n, int rows, float *out,
                                 cudaStream_t s);
+
+// bf16 copy of the planes (rows_out >= rows_in; extra rows and events are zero)
+cudaError_t launch_to_bf16(const float *planes, int64_t pitch, int rows_in, void *out,
+                           int64_t pitch_out, int rows_out, cudaStream_t s);
+
+// k_batched.cu
+int batched_features(int n_waves);   // 2 N rounded up to a multiple of 16
+int batched_max_k(int n_waves);      // parameter sets per launch
+size_t batched_scratch_bytes(int n_waves, int K, int grid);
+cudaError_t batched_configure();
+cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, const double *V,
+                           int K, const double *M, void *scratch, int grid, int *status, int *done,
+                           double *nll, double *grad, cudaStream_t s);
 
 // k_nll_table.cu
 int table_max_waves();
