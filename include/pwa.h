@@ -51,9 +51,19 @@ extern "C" {
 /* ---- forms of the data term (Sec. 2, after Eq. 3) ----------------------- */
 #define PWA_FORM_AMP 1   /* direct: S_i = sum_a V_a A_a(i), I_i = |S_i|^2 */
 #define PWA_FORM_TABLE 2 /* precomputed per-event table A_a A*_b (upper triangle) */
-#define PWA_FORM_TC 4    /* batched K parameter sets on the tensor cores: BF16-rounded
-                            amplitudes and BF16 operands, FP32 accumulation (the
-                            thousands of restarts of Sec. 2 evaluated together) */
+#define PWA_FORM_TC 4    /* batched K parameter sets on the tensor cores (the thousands
+                            of restarts of Sec. 2 evaluated together): amplitudes in
+                            block floating point (one exponent per event, see
+                            PWA_PREC_*), V in 24-bit block floating point per set plus
+                            a first-order correction, BF16 integer operands whose FP32
+                            tensor-core sums are exact */
+
+/* ---- amplitude encoding of the tensor-core form (pwa_config.precision) --- */
+#define PWA_PREC_DEFAULT 0 /* PWA_PREC_BFP16 */
+#define PWA_PREC_BFP16 1   /* A = 2^(E-8) (x0 + x1/256), |x0| <= 256, |x1| <= 128 integers:
+                              16 bits below the event's largest component */
+#define PWA_PREC_BFP8 2    /* A = 2^(E-8) x0: 8 bits below the event's largest
+                              component; about half the tensor-core work */
 
 /* ---- amplitude element types ------------------------------------------- */
 #define PWA_C64 1  /* float pairs: used as given */
@@ -65,7 +75,8 @@ typedef struct pwa_config {
     int n_waves;   /* number of partial waves N, 1 <= N <= 48 */
     int forms;     /* bitmask of PWA_FORM_* stores built by pwa_load_events;
                       0 means PWA_FORM_AMP; PWA_FORM_TABLE needs n_waves <= 24 */
-    int precision; /* reserved; the tensor-core form uses BF16 operands */
+    int precision; /* PWA_PREC_*: amplitude encoding of the tensor-core form
+                      (ignored by the other forms) */
     int max_k;     /* largest K accepted by the evaluation calls (>= 1) */
     void *stream;  /* cudaStream_t to run on; NULL = a stream the context owns */
 } pwa_config;

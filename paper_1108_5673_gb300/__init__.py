@@ -10,23 +10,24 @@ streams.
 The compiled library is built by `paper_1108_5673_gb300.build.build()`.
 """
 from ._abi import (PWA_C64, PWA_C128, PWA_EDOMAIN, PWA_FORM_AMP, PWA_FORM_TABLE, PWA_FORM_TC,
-                   PWA_OK, PwaError)
+                   PWA_OK, PWA_PREC_BFP8, PWA_PREC_BFP16, PWA_PREC_DEFAULT, PwaError)
 
 __all__ = ["Likelihood", "PwaError", "PWA_FORM_AMP", "PWA_FORM_TABLE", "PWA_FORM_TC", "PWA_OK",
-           "PWA_EDOMAIN",
-           "PWA_C64", "PWA_C128"]
+           "PWA_EDOMAIN", "PWA_C64", "PWA_C128", "PWA_PREC_DEFAULT", "PWA_PREC_BFP16",
+           "PWA_PREC_BFP8"]
 
 
 class Likelihood:
     """One library context: a loaded sample, its normalisation matrix, and
     evaluations of NLL(V) and dNLL/dV* (Wirtinger) for K parameter sets."""
 
-    def __init__(self, n_waves, device=0, forms=PWA_FORM_AMP, max_k=1, stream=None):
+    def __init__(self, n_waves, device=0, forms=PWA_FORM_AMP, max_k=1, stream=None,
+                 precision=PWA_PREC_DEFAULT):
         from . import _abi
         self._abi = _abi
         self.n_waves = n_waves
         self.max_k = max_k
-        self.ctx = _abi.pwa_create(device, n_waves, forms, 0, max_k, stream)
+        self.ctx = _abi.pwa_create(device, n_waves, forms, precision, max_k, stream)
         self.last_status = PWA_OK
 
     def load_events(self, data_amp, mc_amp, n_mc_gen):

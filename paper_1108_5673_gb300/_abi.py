@@ -33,6 +33,9 @@ PWA_FORM_TABLE = 2
 PWA_FORM_TC = 4
 PWA_C64 = 1
 PWA_C128 = 2
+PWA_PREC_DEFAULT = 0
+PWA_PREC_BFP16 = 1
+PWA_PREC_BFP8 = 2
 
 ERROR_NAMES = {PWA_EINVAL: "PWA_EINVAL", PWA_ENOMEM: "PWA_ENOMEM", PWA_ECUDA: "PWA_ECUDA",
                PWA_ESTATE: "PWA_ESTATE", PWA_EDOMAIN: "PWA_EDOMAIN",

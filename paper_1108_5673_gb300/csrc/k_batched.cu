@@ -4,34 +4,61 @@
 // The paper runs thousands of fits from different starting parameters and
 // models (Sec. 2); evaluating K parameter sets against the same events turns
 // the direct form into two chained products per tile of 128 events:
-//   S[e][(k,re/im)] = sum_f X[e][f] W[(k,re/im)][f]            (GEMM 1)
+//   S[e][(k,re/im)] = sum_f A[e][f] W[(k,re/im)][f]            (GEMM 1)
 //   I = Sre^2 + Sim^2,  ln I,  R = S / I                      (epilogue)
-//   G[(k,re/im)][f] += sum_e R[e][(k,re/im)] X[e][f]           (GEMM 2)
-// where X holds the amplitudes as features f = (Re A_a, Im A_a) and W the
-// parameter sets (row (k,re): vr on Re A_a, -vi on Im A_a; row (k,im): vi on
-// Re A_a, vr on Im A_a). The gradient is g_a = -(G[(k,re)][2a] +
-// G[(k,im)][2a+1]) - i (G[(k,im)][2a] - G[(k,re)][2a+1]) + (M V)_a.
+//   G[(k,re/im)][f] += sum_e R[e][(k,re/im)] A[e][f]           (GEMM 2)
+// with features f = (Re A_a, Im A_a) and W the parameter sets (row (k,re):
+// vr on Re A_a, -vi on Im A_a; row (k,im): vi on Re A_a, vr on Im A_a). The
+// data part of the gradient is g_a = -(G[(k,re)][2a] + G[(k,im)][2a+1])
+// - i (G[(k,im)][2a] - G[(k,re)][2a+1]); M V is added in the final kernel.
 //
-// Operands: the amplitudes are a BF16 structure-of-arrays copy (the values
-// this path consumes are the BF16-rounded amplitudes); V is split into two
-// BF16 pieces (16 significant bits) and the NLL is corrected to first order
-// for the remainder, 2 Re(g^H dV), in double in the final kernel; R is one
-// BF16 piece. Products are exact in FP32 and accumulate in FP32.
+// Exact sums on the tensor cores. The FP32 accumulation of the tensor cores
+// does not round to nearest when it adds products of different exponents, and
+// the error it leaves is one-sided: summed over a million events it shifts the
+// NLL far beyond its tolerance. This path therefore makes every tensor-core
+// sum an exact integer sum:
+//  * amplitudes (features of event i): A = 2^(E_i - 8) (x0 + x1 / 256) with a
+//    shared exponent E_i per event and integer slices |x0| <= 256,
+//    |x1| <= 128 (16-bit block floating point, XS = 2) or A = 2^(E_i - 8) x0
+//    (8-bit, XS = 1): these are the values this path consumes;
+//  * parameter set k: W = 2^(T_k - 8) (w0 + w1 / 2^8 + w2 / 2^16), shared
+//    exponent T_k per set, integer slices |w0| <= 256, |w1|, |w2| <= 128; the
+//    remainder V - V_r (below 2^-24 |V|) is accounted for to first order,
+//    2 Re(g^H (V - V_r)), in the final kernel.
+// Integers of at most 9 bits are exact in BF16, their products exact in FP32,
+// and the accumulators (one per power of 2^-8)
+//   acc0 = x0 w0,  acc1 = x0 w1 + x1 w0,  acc2 = x0 w2 + x1 w1,  acc3 = x1 w2
+// (sums over features; the x1 terms only for XS = 2) stay below 2^23 for
+// F <= 96 features, so each is exact whatever the accumulation order or
+// rounding, and S = 2^(E_i + T_k - 16) Q with
+// Q = acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8 (FP32 roundings to nearest).
+// ln I = ln 2 (2 (E_i + T_k - 16) + log2 |Q|^2): the exponent parts are summed
+// exactly once per call; log2 |Q|^2 is evaluated with a polynomial of
+// max error 8e-10 (log2_poly.py) and summed as fixed point with resolution
+// 2^-19 in 32-bit integer warp sums and 64-bit per-set accumulators, so the
+// NLL sum is exact and independent of order. For the gradient
+// R A = 2^(8 - T_k) (Q / |Q|^2) (x0 + x1 / 256): GEMM 2 multiplies
+// R' = Q / |Q|^2, rounded to BF16, by both slices (N = XS F columns).
 //
-// Layout in shared memory (all 128-byte swizzled, 1 KB aligned):
-//  X tile  [2 blocks of 64 events][F feature rows][128 B]: for GEMM 1 the
-//          MN-major A operand (events contiguous), for GEMM 2 the K-major B
-//          operand (K = events) -- the same bytes serve both products.
-//  W       [chunk][piece][F/64 blocks][128 rows][128 B], K-major B of GEMM 1.
-//  R^T     [2 blocks of 64 events][128 rows][128 B], K-major A of GEMM 2,
-//          written by the epilogue threads.
-// Tensor memory (512 columns): two S buffers of 128 columns, then the G^T
-// accumulators of every chunk (F columns each) for the whole launch.
+// Layout in shared memory (128-byte swizzled, 1 KB aligned):
+//  W   [chunk][half][slice w0,w1,w2][F/64 blocks][64 rows][128 B]: K-major B
+//      operands of GEMM 1, copied once per launch from an image the prep
+//      kernel builds.
+//  X   [stage][2 blocks of 64 events][XS F rows (x0 then x1)][128 B]: MN-major
+//      A operand of GEMM 1 (events contiguous) and K-major B operand of GEMM 2
+//      (K = events) -- the same bytes serve both products.
+//  R'  [2 blocks of 64 rows (k,re/im)][128 events][128 B]: MN-major A operand
+//      of GEMM 2, written by the epilogue (each thread stores its event's row).
+// Tensor memory (512 columns): acc0..acc3 of one half chunk (32 sets, 64
+// columns each), then the G^T accumulators of every chunk (XS F columns each)
+// for the whole launch.
 //
-// Warps: 0-7 epilogue (warp w reads TMEM lane quarter w%4 and half w/4 of
-// each chunk's columns), 8 producer (TMA), 9 MMA issuer (one thread), 10
-// helper (M V and V^H M V in FP64). Every wait is bounded.
+// Warps: 0-15 epilogue (warp w reads TMEM lane quarter w%4 and the 8 sets
+// w/4 of each half chunk), 16 producer (TMA), 17 MMA issuer (one thread),
+// 18 helper (M V and V^H M V in FP64). Every wait is bounded.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "pwa_internal.cuh"
 
@@ -39,50 +66,70 @@ namespace pwa {
 
 namespace {
 
-constexpr int kBM = 128;       // events per tile
-constexpr int kKC = 64;        // parameter sets per chunk (2 kKC = 128 S columns)
-constexpr int kXS = 3;         // X stages
-constexpr int kPieces = 2;     // BF16 pieces of V
-constexpr int kEpiWarps = 8;
+constexpr int kBM = 128;        // events per tile
+constexpr int kKC = 64;         // parameter sets per chunk (GEMM 2: M = 2 kKC = 128)
+constexpr int kHS = 32;         // parameter sets per half chunk (one GEMM 1 / epilogue step)
+constexpr int kXS = 2;          // X stages
+constexpr int kMaxChunks = 4;
+constexpr int kEpiWarps = 16;
 constexpr int kThreads = (kEpiWarps + 3) * 32;
+constexpr uint32_t kWBlock = 64 * 128;      // 64 rows x 64 BF16 features
+constexpr uint32_t kRBytes = 2 * 128 * 128;
+constexpr int kWSlices = 3;                 // BF16 slices of V
+// tensor-memory columns: accumulators acc0..acc3 at 64 j, then G^T
+__host__ __device__ constexpr int s_cols(int xs) { return xs == 2 ? 256 : 192; }
 constexpr double kLn2 = 0.69314718055994530942;
+constexpr int kFixBits = 19;                // fixed-point resolution of log2 sums
 
-// The V pieces, shared by the main and the final kernel.
-__host__ __device__ inline void split_bf16(double v, float &hi, float &lo)
+// Integer slices of v * 2^(8 - T): v ~ 2^(T-8) (w0 + w1 / 2^8 + w2 / 2^16).
+__host__ __device__ inline void split_slices(double v, int T, double (&w)[kWSlices])
 {
-    const __nv_bfloat16 h = __double2bfloat16(v);
-    hi = __bfloat162float(h);
-    lo = __bfloat162float(__double2bfloat16(v - (double)hi));
+    double x = ldexp(v, 8 - T);
+    for (int p = 0; p < kWSlices; ++p) {
+        w[p] = rint(x);
+        x = (x - w[p]) * 256.0;
+    }
+}
+
+__host__ __device__ inline double round_slices(double v, int T)
+{
+    double w[kWSlices];
+    split_slices(v, T, w);
+    return ldexp(w[0] + (w[1] + w[2] / 256.0) / 256.0, T - 8);
 }
 
 struct BatchArgs {
-    int n_waves, F, K, n_chunks;
+    int n_waves, F, XS, K, n_chunks;
     int64_t n_events;
-    const double *V;      // [K][N] complex
-    const double *M;      // [N][N] complex
-    float *gpart;         // [grid][n_chunks][128][F]
-    float2 *lpart;        // [grid][4][n_chunks * 64] float-float ln sums
-    unsigned *kflags;     // [n_chunks * 2] domain bits per parameter set (OR)
-    double *mv;           // [K][2N + 1]: M V and V^H M V
+    const double *V;            // [K][N] complex
+    const double *M;            // [N][N] complex
+    const long long *sum_e;     // sum over events of the event exponents
+    unsigned char *wimg;        // W image (byte-identical to shared memory)
+    int *T;                     // [K] set exponents
+    float *gpart;               // [grid][n_chunks][128][F]
+    long long *lpart;           // [grid][4][n_chunks * 64] fixed-point log2 sums
+    unsigned *kflags;           // [n_chunks * 2] domain bits per half chunk
+    double *mv;                 // [K][2N + 1]: M V and V^H M V
     int *status;
 };
 
 struct Smem {
-    uint32_t w_off, x_off, r_off, bytes;
+    uint32_t w_off, x_off, r_off, w_bytes, bytes;
 };
 
-__host__ __device__ inline Smem batch_smem(int F, int n_chunks)
+__host__ __device__ inline Smem batch_smem(int F, int xs, int n_chunks)
 {
     const int kb = (F + 63) / 64;
     Smem s;
+    s.w_bytes = (uint32_t)n_chunks * 2 * kWSlices * kb * kWBlock;
     s.w_off = 0;
-    s.x_off = s.w_off + (uint32_t)n_chunks * kPieces * kb * 128 * 128;
-    s.r_off = s.x_off + (uint32_t)kXS * 2 * F * 128;
-    s.bytes = s.r_off + 2 * 128 * 128 + 1024;  // + alignment slack
+    s.x_off = s.w_bytes;
+    s.r_off = s.x_off + (uint32_t)kXS * 2 * xs * F * 128;
+    s.bytes = s.r_off + kRBytes + 1024;  // + alignment slack
     return s;
 }
 
-__device__ __forceinline__ uint32_t sw128(int row, int byte_in_row)
+__host__ __device__ inline uint32_t sw128(int row, int byte_in_row)
 {
     return (row >> 3) * 1024 + (row & 7) * 128 + ((((byte_in_row >> 4) ^ (row & 7)) & 7) << 4) +
            (byte_in_row & 15);
@@ -95,76 +142,115 @@ __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi)
     return r;
 }
 
-template <int F>
+// Fixed-point 2^19 log2(1 + z) for two values, z in [sqrt(1/2) - 1, sqrt(2) - 1];
+// the last step adds 1.5 * 2^23 so that the float's low bits hold the
+// rounded-to-nearest integer. Coefficients: log2_poly.py (a_j * 2^19).
+__device__ __forceinline__ f2 log2_fixed2(f2 z)
+{
+    f2 p = pk2(4.891085156e+04f, 4.891085156e+04f);
+    p = fma2(p, z, pk2(-8.236935156e+04f, -8.236935156e+04f));
+    p = fma2(p, z, pk2(8.752553125e+04f, 8.752553125e+04f));
+    p = fma2(p, z, pk2(-9.489117188e+04f, -9.489117188e+04f));
+    p = fma2(p, z, pk2(1.081302109e+05f, 1.081302109e+05f));
+    p = fma2(p, z, pk2(-1.260154688e+05f, -1.260154688e+05f));
+    p = fma2(p, z, pk2(1.512498594e+05f, 1.512498594e+05f));
+    p = fma2(p, z, pk2(-1.890981094e+05f, -1.890981094e+05f));
+    p = fma2(p, z, pk2(2.521303281e+05f, 2.521303281e+05f));
+    p = fma2(p, z, pk2(-3.781938438e+05f, -3.781938438e+05f));
+    p = fma2(p, z, pk2(7.563876875e+05f, 7.563876875e+05f));
+    return fma2(p, z, pk2(12582912.0f, 12582912.0f));
+}
+
+// ---- per-call preparation: W image and set exponents ------------------------
+// One block per (chunk, half, slice).
+__global__ void batched_prep(const BatchArgs a)
+{
+    const int blk = blockIdx.x;
+    const int p = blk % kWSlices, h = (blk / kWSlices) & 1, c = blk / (2 * kWSlices);
+    const int Nw = a.n_waves, KB = (a.F + 63) / 64;
+    __shared__ int s_T[kHS];
+    if (threadIdx.x < kHS) {
+        const int k = c * kKC + h * kHS + threadIdx.x;
+        int e = 0;
+        if (k < a.K) {
+            double m = 0.0;
+            bool finite = true;
+            for (int w = 0; w < Nw; ++w) {
+                const double vr = a.V[2 * ((size_t)k * Nw + w)], vi = a.V[2 * ((size_t)k * Nw + w) + 1];
+                finite = finite && isfinite(vr) && isfinite(vi);
+                m = fmax(m, fmax(fabs(vr), fabs(vi)));
+            }
+            if (finite && m > 0.0)
+                frexp(m, &e);
+            if (p == 0) {
+                a.T[k] = e;
+                if (!finite)  // every intensity of this set is undefined
+                    atomicOr(&a.kflags[c * 2 + h], 1u << threadIdx.x);
+            }
+        }
+        s_T[threadIdx.x] = e;
+    }
+    __syncthreads();
+    unsigned char *out = a.wimg + (size_t)blk * KB * kWBlock;
+    for (int idx = threadIdx.x; idx < KB * 64 * 64; idx += blockDim.x) {
+        const int kb = idx >> 12, r = (idx >> 6) & 63, fb = idx & 63;
+        const int f = kb * 64 + fb, sl = r >> 1, t = r & 1;
+        const int k = c * kKC + h * kHS + sl;
+        float val = 0.f;
+        if (k < a.K && f < 2 * Nw) {
+            const int w = f >> 1, u = f & 1;
+            const double vr = a.V[2 * ((size_t)k * Nw + w)], vi = a.V[2 * ((size_t)k * Nw + w) + 1];
+            const double coef = t == 0 ? (u == 0 ? vr : -vi) : (u == 0 ? vi : vr);
+            double ws[kWSlices];
+            split_slices(coef, s_T[sl], ws);
+            val = isfinite(coef) ? (float)ws[p] : 0.f;
+        }
+        *reinterpret_cast<__nv_bfloat16 *>(out + kb * kWBlock + sw128(r, fb * 2)) = __float2bfloat16_rn(val);
+    }
+}
+
+// ---- main kernel ----------------------------------------------------------------
+template <int F, int XS>
 __global__ void __launch_bounds__(kThreads, 1)
     batched_kernel(const __grid_constant__ CUtensorMap xmap, const BatchArgs a, const int n_tiles)
 {
     constexpr int KB = (F + 63) / 64;
+    constexpr int kGCol = s_cols(XS);
+    constexpr uint32_t kXBlk = XS * F * 128;    // one 64-event block: x0 (and x1) rows
+    constexpr uint32_t kXBytes = 2 * kXBlk;     // one stage
     extern __shared__ unsigned char smem_dyn[];
-    __shared__ uint64_t x_full[kXS], x_empty[kXS], s_full[2], s_free[2], r_full, r_free, g_done;
+    __shared__ uint64_t w_full, x_full[kXS], x_empty[kXS], s_full, s_free, r_full, r_free, g_done;
     __shared__ uint32_t tmem_base;
     __shared__ int s_flags;
-    __shared__ unsigned s_kflags[2 * 8];
+    __shared__ unsigned s_kflags[2 * kMaxChunks];
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NCH = a.n_chunks;
-    const Smem L = batch_smem(F, NCH);
+    const Smem L = batch_smem(F, XS, NCH);
     unsigned char *base = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     unsigned char *sW = base + L.w_off;
     unsigned char *sX = base + L.x_off;
     unsigned char *sR = base + L.r_off;
-    const uint32_t x_bytes = 2 * F * 128;
     const int n_my =
         (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int steps = n_my * NCH * 2;
 
     if (threadIdx.x == 0) {
+        mbar_init(&w_full, 1);
         for (int s = 0; s < kXS; ++s) {
             mbar_init(&x_full[s], 1);
             mbar_init(&x_empty[s], 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(&s_full[b], 1);
-            mbar_init(&s_free[b], kEpiWarps);
-        }
+        mbar_init(&s_full, 1);
+        mbar_init(&s_free, kEpiWarps);
         mbar_init(&r_full, kEpiWarps);
         mbar_init(&r_free, 1);
         mbar_init(&g_done, 1);
         fence_barrier_init();
         s_flags = 0;
     }
-    if (threadIdx.x < 16)
+    if (threadIdx.x < 2 * kMaxChunks)
         s_kflags[threadIdx.x] = 0;
-    // W pieces from V: row r = 2k' + t of chunk c, feature f = 2 a + u
-    {
-        const int rows_total = NCH * 128;
-        for (int idx = threadIdx.x; idx < rows_total * F; idx += blockDim.x) {
-            const int row_g = idx / F, f = idx - row_g * F;
-            const int c = row_g >> 7, r = row_g & 127;
-            const int k = c * kKC + (r >> 1), t = r & 1, w = f >> 1, u = f & 1;
-            float hi = 0.f, lo = 0.f;
-            if (k < a.K && w < a.n_waves) {
-                const double vr = a.V[2 * (k * a.n_waves + w)], vi = a.V[2 * (k * a.n_waves + w) + 1];
-                const double coef = t == 0 ? (u == 0 ? vr : -vi) : (u == 0 ? vi : vr);
-                split_bf16(coef, hi, lo);
-            }
-            const uint32_t rb = sw128(r, (f & 63) * 2);
-            for (int p = 0; p < kPieces; ++p) {
-                unsigned char *piece = sW + ((size_t)(c * kPieces + p) * KB + (f >> 6)) * 128 * 128;
-                *reinterpret_cast<__nv_bfloat16 *>(piece + rb) = __float2bfloat16_rn(p == 0 ? hi : lo);
-            }
-        }
-        // feature padding inside a 128-byte row block (F not a multiple of 64)
-        if (F % 64) {
-            for (int idx = threadIdx.x; idx < NCH * kPieces * 128 * (64 - F % 64); idx += blockDim.x) {
-                const int pad = 64 - F % 64;
-                const int cp = idx / (128 * pad), rem = idx - cp * 128 * pad;
-                const int r = rem / pad, f = F % 64 + rem % pad;
-                unsigned char *piece = sW + ((size_t)cp * KB + (KB - 1)) * 128 * 128;
-                *reinterpret_cast<__nv_bfloat16 *>(piece + sw128(r, f * 2)) = __float2bfloat16_rn(0.f);
-            }
-        }
-    }
-    fence_async_smem();
     if (warp == kEpiWarps + 1)
         tmem_alloc(&tmem_base, 512);
     tc_fence_before();
@@ -176,6 +262,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp == kEpiWarps) {
         // ---- producer ------------------------------------------------------
         if (lane == 0) {
+            mbar_arrive_expect_tx(&w_full, L.w_bytes);
+            bulk_load(sW, a.wimg, L.w_bytes, &w_full);
             int j = 0;
             for (; j < n_my; ++j) {
                 const int s = j % kXS;
@@ -185,66 +273,74 @@ __global__ void __launch_bounds__(kThreads, 1)
                     break;
                 }
                 const int e0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
-                mbar_arrive_expect_tx(&x_full[s], x_bytes);
-                tma_load_2d(sX + (size_t)s * x_bytes, &xmap, e0, 0, &x_full[s]);
-                tma_load_2d(sX + (size_t)s * x_bytes + F * 128, &xmap, e0 + 64, 0, &x_full[s]);
+                mbar_arrive_expect_tx(&x_full[s], kXBytes);
+                tma_load_2d(sX + (size_t)s * kXBytes, &xmap, e0, 0, &x_full[s]);
+                tma_load_2d(sX + (size_t)s * kXBytes + kXBlk, &xmap, e0 + 64, 0, &x_full[s]);
             }
+            // copies still in flight complete before the block may exit
             for (int q = (j > kXS ? j - kXS : 0); q < j; ++q)
                 if (!mbar_wait(&x_full[q % kXS], (q / kXS) & 1))
                     flags |= FLAG_TIMEOUT;
+            if (!mbar_wait(&w_full, 0))
+                flags |= FLAG_TIMEOUT;
         }
     } else if (warp == kEpiWarps + 1) {
-        // ---- MMA issuer -------------------------------------------------------
+        // ---- MMA issuer ---------------------------------------------------
         if (lane == 0) {
-            const uint32_t id1 = umma_idesc_bf16(128, 128, 1, 0);
-            const uint32_t id2 = umma_idesc_bf16(128, F, 0, 0);
+            const uint32_t id1 = umma_idesc_bf16(128, 64, 1, 0);
+            const uint32_t id2 = umma_idesc_bf16(128, XS * F, 1, 0);
             const uint32_t xbase = smem_u32(sX), wbase = smem_u32(sW), rbase = smem_u32(sR);
-            const int total = n_my * NCH;
-            // GEMM 2 of chunk q (pipelined one chunk behind GEMM 1)
-            auto gemm2 = [&](int q) -> bool {
-                const int j = q / NCH, c = q % NCH, s = j % kXS;
-                if (!mbar_wait(&r_full, q & 1))
+            // GEMM 2 of chunk step cq (pipelined behind GEMM 1 of the next step)
+            auto gemm2 = [&](int cq) -> bool {
+                const int j = cq / NCH, c = cq % NCH, s = j % kXS;
+                if (!mbar_wait(&r_full, cq & 1))
                     return false;
                 tc_fence_after();
-                const uint32_t xs = xbase + s * x_bytes;
+                const uint32_t xs = xbase + s * kXBytes;
                 for (int ks = 0; ks < kBM / 16; ++ks) {
-                    const uint32_t blk = ks >> 2, off = (ks & 3) * 32;
-                    const uint64_t da = umma_desc_sw128(rbase + blk * 128 * 128 + off, 16, 1024);
-                    const uint64_t db = umma_desc_sw128(xs + blk * F * 128 + off, 16, 1024);
-                    umma_bf16(tmem + 256 + c * F, da, db, id2, (j > 0 || ks > 0) ? 1u : 0u);
+                    const uint64_t da = umma_desc_sw128(rbase + ks * 2048, 128 * 128, 1024);
+                    const uint64_t db = umma_desc_sw128(xs + (ks >> 2) * kXBlk + (ks & 3) * 32, 16, 1024);
+                    umma_bf16(tmem + kGCol + c * XS * F, da, db, id2, (j > 0 || ks > 0) ? 1u : 0u);
                 }
                 umma_commit(&r_free);
                 if (c == NCH - 1)
                     umma_commit(&x_empty[s]);
                 return true;
             };
-            bool ok = true;
-            for (int q = 0; q < total && ok; ++q) {
-                const int j = q / NCH, c = q % NCH, s = j % kXS, b = q & 1;
-                if (c == 0 && !mbar_wait(&x_full[s], (j / kXS) & 1)) {
+            bool ok = mbar_wait(&w_full, 0);
+            for (int q = 0; q < steps && ok; ++q) {
+                const int j = q / (2 * NCH), ch = q % (2 * NCH), c = ch >> 1, h = ch & 1, s = j % kXS;
+                if (ch == 0 && !mbar_wait(&x_full[s], (j / kXS) & 1)) {
                     ok = false;
                     break;
                 }
-                if (q >= 2 && !mbar_wait(&s_free[b], ((q >> 1) - 1) & 1)) {
+                if (q >= 1 && !mbar_wait(&s_free, (q - 1) & 1)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                // GEMM 1: S[b] = X (MN-major) . W_c^T, both V pieces
-                const uint32_t xs = xbase + s * x_bytes;
-                for (int p = 0; p < kPieces; ++p)
-                    for (int ks = 0; ks < F / 16; ++ks) {
-                        const uint64_t da = umma_desc_sw128(xs + ks * 2048, F * 128, 1024);
-                        const uint32_t wp = wbase + ((c * kPieces + p) * KB + (ks >> 2)) * 128 * 128;
-                        const uint64_t db = umma_desc_sw128(wp + (ks & 3) * 32, 16, 1024);
-                        umma_bf16(tmem + b * 128, da, db, id1, (p > 0 || ks > 0) ? 1u : 0u);
-                    }
-                umma_commit(&s_full[b]);
-                if (q >= 1)
-                    ok = gemm2(q - 1);
+                const uint32_t xs = xbase + s * kXBytes;
+                const uint32_t wb = wbase + (uint32_t)((c * 2 + h) * kWSlices) * KB * kWBlock;
+                // slice pair (x slice i, w slice p) goes to accumulator i + p
+#pragma unroll
+                for (int i = 0; i < XS; ++i)
+#pragma unroll
+                    for (int p = 0; p < kWSlices; ++p)
+#pragma unroll
+                        for (int ks = 0; ks < F / 16; ++ks) {
+                            const uint64_t xd = umma_desc_sw128(xs + i * F * 128 + ks * 2048, kXBlk, 1024);
+                            const uint64_t wd = umma_desc_sw128(
+                                wb + (uint32_t)(p * KB + (ks >> 2)) * kWBlock + (ks & 3) * 32, 16, 1024);
+                            // the first product into each accumulator starts it
+                            const bool first = ks == 0 && (i == 0 || p == kWSlices - 1);
+                            umma_bf16(tmem + 64 * (i + p), xd, wd, id1, first ? 0u : 1u);
+                        }
+                umma_commit(&s_full);
+                if (h == 0 && q >= 2)
+                    ok = gemm2((q >> 1) - 1);
             }
-            if (ok && total > 0)
-                ok = gemm2(total - 1);
+            if (ok && steps > 0)
+                ok = gemm2((steps >> 1) - 1);
             umma_commit(&g_done);
             // tensor memory is released only after every product has finished
             if (!mbar_wait(&g_done, 0))
@@ -253,111 +349,150 @@ __global__ void __launch_bounds__(kThreads, 1)
                 flags |= FLAG_TIMEOUT;
         }
     } else if (warp < kEpiWarps) {
-        // ---- epilogue -----------------------------------------------------------
-        const int qq = warp & 3, h = warp >> 2;
-        const int lane_row = qq * 32 + lane;          // TMEM lane = event row of the tile
+        // ---- epilogue -------------------------------------------------------
+        const int qq = warp & 3, sg = warp >> 2;
+        const int e = qq * 32 + lane;                  // event row of the tile = TMEM lane
         const uint32_t lane_addr = (uint32_t)(qq * 32) << 16;
-        dfloat acc[4] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-        unsigned kbad[4] = {0u, 0u, 0u, 0u};
-        const int blk = lane_row >> 6, e64 = lane_row & 63;
+        long long lacc[2 * kMaxChunks];
+#pragma unroll
+        for (int i = 0; i < 2 * kMaxChunks; ++i)
+            lacc[i] = 0;
+        const f2 inv256 = pk2(1.0f / 256.0f, 1.0f / 256.0f);
         bool ok = true;
-        for (int q = 0; q < n_my * NCH && ok; ++q) {
-            const int j = q / NCH, c = q % NCH, b = q & 1;
-            if (!mbar_wait(&s_full[b], (q >> 1) & 1)) {
+        for (int q = 0; q < steps && ok; ++q) {
+            const int j = q / (2 * NCH), ch = q % (2 * NCH), h = ch & 1, cq = q >> 1;
+            if (!mbar_wait(&s_full, q & 1)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            uint32_t v[2][32];
-            tmem_ld32(tmem + lane_addr + b * 128 + 64 * h, v[0]);
-            tmem_ld32(tmem + lane_addr + b * 128 + 64 * h + 32, v[1]);
-            tmem_ld_wait();
+            // Q pieces of this warp's 8 sets: acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8
+            f2 t[8];
+            {
+                uint32_t va[16], vb[16];
+                tmem_ld16(tmem + lane_addr + 64 * 2 + 16 * sg, va);
+                if (XS == 2)
+                    tmem_ld16(tmem + lane_addr + 64 * 3 + 16 * sg, vb);
+                tmem_ld_wait();
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    t[s] = pk2(__uint_as_float(va[2 * s]), __uint_as_float(va[2 * s + 1]));
+                    if (XS == 2)
+                        t[s] = fma2(pk2(__uint_as_float(vb[2 * s]), __uint_as_float(vb[2 * s + 1])), inv256, t[s]);
+                }
+                tmem_ld16(tmem + lane_addr + 64 * 1 + 16 * sg, va);
+                tmem_ld16(tmem + lane_addr + 16 * sg, vb);
+                tmem_ld_wait();
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    t[s] = fma2(t[s], inv256, pk2(__uint_as_float(va[2 * s]), __uint_as_float(va[2 * s + 1])));
+                    t[s] = fma2(t[s], inv256, pk2(__uint_as_float(vb[2 * s]), __uint_as_float(vb[2 * s + 1])));
+                }
+            }
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
-                mbar_arrive(&s_free[b]);
-            const int64_t ev = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * kBM + lane_row;
-            const bool valid = ev < a.n_events;
-            float ln[32];
-            unsigned rpk[32];  // bf16 (re, im) of R for the 32 parameter sets of this half
+                mbar_arrive(&s_free);
+            const int64_t ev = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * kBM + e;
+            uint32_t rpk[8];
+            int l[8];
+            if (ev < a.n_events) {
+                float Iv[8], z[8];
+                int kx[8];
+                unsigned mn = 0xffffffffu;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const float re = __uint_as_float(v[k >> 4][(2 * k) & 31]);
-                const float im = __uint_as_float(v[k >> 4][(2 * k + 1) & 31]);
-                const float I = fmaf(re, re, im * im);
-                float l = 0.f, rr = 0.f, ri = 0.f;
-                if (valid) {
-                    if (I > 0.f && I < INFINITY) {
-                        int ex;
-                        const float f = split_exponent(I, ex);
-                        l = fmaf((float)ex, 0.693147180559945f, __logf(f));
-                        const float inv = __frcp_rn(I);
-                        rr = re * inv;
-                        ri = im * inv;
-                    } else {
-                        kbad[c] |= 1u << k;
-                    }
+                for (int s = 0; s < 8; ++s) {
+                    const f2 qv = t[s];
+                    float re, im;
+                    upk2(qv, re, im);
+                    const float I = fmaf(re, re, im * im);
+                    Iv[s] = I;
+                    const int bits = __float_as_int(I);
+                    mn = min(mn, (unsigned)bits);
+                    const float r = rcp_approx(I);
+                    float rr, ri;
+                    upk2(mul2(qv, pk2(r, r)), rr, ri);
+                    rpk[s] = pack_bf16x2(rr, ri);
+                    // I = 2^k (1 + z), 1 + z in [sqrt(1/2), sqrt(2))
+                    const int k = (bits - 0x3F3504F3) >> 23;
+                    kx[s] = k;
+                    z[s] = __int_as_float(bits - (k << 23)) - 1.0f;
                 }
-                ln[k] = l;
-                rpk[k] = pack_bf16x2(rr, ri);
-            }
-            // reduce-scatter the 32 log values over the 32 lanes: lane k ends
-            // with the sum over the warp's events for parameter set k
 #pragma unroll
-            for (int width = 16; width >= 1; width >>= 1) {
-                const bool upper = (lane & width) != 0;
+                for (int s = 0; s < 8; s += 2) {
+                    float y0, y1;
+                    upk2(log2_fixed2(pk2(z[s], z[s + 1])), y0, y1);
+                    l[s] = __float_as_int(y0) - 0x4B400000 + (kx[s] << kFixBits);
+                    l[s + 1] = __float_as_int(y1) - 0x4B400000 + (kx[s + 1] << kFixBits);
+                }
+                if (mn == 0u) {  // some Q = 0 (rare): record the parameter sets, if real
+                    const int nvs = a.K - (ch >> 1) * kKC - h * kHS - 8 * sg;
+                    for (int s = 0; s < 8; ++s)
+                        if (s < nvs && Iv[s] == 0.f)
+                            atomicOr(&s_kflags[ch], 1u << (8 * sg + s));
+                }
+            } else {
 #pragma unroll
-                for (int k = 0; k < width; ++k) {
-                    const float send = upper ? ln[k] : ln[k + width];
-                    const float keep = upper ? ln[k + width] : ln[k];
-                    ln[k] = keep + __shfl_xor_sync(0xffffffffu, send, width);
+                for (int s = 0; s < 8; ++s) {
+                    rpk[s] = 0u;
+                    l[s] = 0;
                 }
             }
-            // lane L now holds, in ln[0], the sum for parameter set L of this half
-            acc[c] = df_add(acc[c], dfloat{ln[0], 0.f});
-            // R^T may be overwritten once GEMM 2 of the previous chunk is done
-            if (q >= 1 && !mbar_wait(&r_free, (q - 1) & 1)) {
+            // fixed-point log2 sums over the warp's 32 events; lane s keeps set s
+            int mine = 0;
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const int t = __reduce_add_sync(0xffffffffu, l[s]);
+                mine = lane == s ? t : mine;
+            }
+            lacc[ch] += mine;
+            // R' may be overwritten once GEMM 2 of the previous chunk step is done
+            if (h == 0 && cq >= 1 && !mbar_wait(&r_free, (cq - 1) & 1)) {
                 ok = false;
                 break;
             }
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                const int row = 64 * h + 2 * k;
-                unsigned char *rb = sR + blk * 128 * 128;
-                *reinterpret_cast<unsigned short *>(rb + sw128(row, e64 * 2)) = (unsigned short)(rpk[k] & 0xffff);
-                *reinterpret_cast<unsigned short *>(rb + sw128(row + 1, e64 * 2)) = (unsigned short)(rpk[k] >> 16);
+            unsigned char *rrow = sR + h * (128 * 128);
+            *reinterpret_cast<uint4 *>(rrow + sw128(e, 32 * sg)) = make_uint4(rpk[0], rpk[1], rpk[2], rpk[3]);
+            *reinterpret_cast<uint4 *>(rrow + sw128(e, 32 * sg + 16)) =
+                make_uint4(rpk[4], rpk[5], rpk[6], rpk[7]);
+            if (h == 1) {
+                fence_async_smem();
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&r_full);
             }
-            fence_async_smem();
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&r_full);
         }
         if (!ok)
             flags |= FLAG_TIMEOUT;
-        // parameter-set bits and log partials
-        for (int c = 0; c < NCH; ++c) {
-            const unsigned m = __reduce_or_sync(0xffffffffu, kbad[c]);
-            if (lane == 0 && m)
-                atomicOr(&s_kflags[2 * c + h], m);
-        }
-        for (int c = 0; c < NCH; ++c)
-            a.lpart[((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + c * kKC + 32 * h + lane] =
-                make_float2(acc[c].hi, acc[c].lo);
-        // G^T of every chunk: rows = this warp's lane quarter, half the columns
+        if (lane < 8)
+            for (int ch = 0; ch < 2 * NCH; ++ch)
+                a.lpart[((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + (ch >> 1) * kKC + (ch & 1) * kHS +
+                        8 * sg + lane] = lacc[ch];
+        // G^T of every chunk: rows = this warp's lane quarter, 8-column groups
         if (ok && mbar_wait(&g_done, 0)) {
             tc_fence_after();
-            // F/2 is a multiple of 8: eight-column loads cover it exactly
             for (int c = 0; c < NCH; ++c) {
-                for (int c0 = h * (F / 2); c0 < (h + 1) * (F / 2); c0 += 8) {
-                    uint32_t g[8];
-                    tmem_ld8(tmem + lane_addr + 256 + c * F + c0, g);
-                    tmem_ld_wait();
+                for (int c0 = 8 * sg; c0 < F; c0 += 32) {
+                    uint32_t g[8], g1[8];
+                    if (n_my > 0) {
+                        tmem_ld8(tmem + lane_addr + kGCol + c * XS * F + c0, g);
+                        if (XS == 2)
+                            tmem_ld8(tmem + lane_addr + kGCol + c * XS * F + F + c0, g1);
+                        tmem_ld_wait();
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; ++i)
+                            g[i] = g1[i] = 0u;
+                    }
+                    float gv[8];
+#pragma unroll
+                    for (int i = 0; i < 8; ++i)
+                        gv[i] = XS == 2 ? fmaf(__uint_as_float(g1[i]), 1.0f / 256.0f, __uint_as_float(g[i]))
+                                        : __uint_as_float(g[i]);
                     float4 *dst = reinterpret_cast<float4 *>(
-                        a.gpart + (((size_t)blockIdx.x * NCH + c) * 128 + lane_row) * F + c0);
-                    dst[0] = make_float4(__uint_as_float(g[0]), __uint_as_float(g[1]),
-                                         __uint_as_float(g[2]), __uint_as_float(g[3]));
-                    dst[1] = make_float4(__uint_as_float(g[4]), __uint_as_float(g[5]),
-                                         __uint_as_float(g[6]), __uint_as_float(g[7]));
+                        a.gpart + (((size_t)blockIdx.x * NCH + c) * 128 + e) * F + c0);
+                    dst[0] = make_float4(gv[0], gv[1], gv[2], gv[3]);
+                    dst[1] = make_float4(gv[4], gv[5], gv[6], gv[7]);
                 }
             }
         } else {
@@ -399,16 +534,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Final sums over CTAs (fixed order, float-float), M V, first-order
-// correction for the V remainder; one block per parameter set.
+// Final sums over CTAs (fixed order), M V, the first-order correction for
+// V - V_r; one block per parameter set.
 __global__ void batched_finalize(const BatchArgs a, int grid, int *done, double *nll, double *grad)
 {
     const int k = blockIdx.x, Nw = a.n_waves, F = a.F, NCH = a.n_chunks;
     const int c = k / kKC, kl = k % kKC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ double s_corr[2];
-    __shared__ double s_ln;
+    __shared__ long long s_l;
     const bool bad = (a.kflags[2 * c + (kl >> 5)] >> (kl & 31)) & 1u;
+    const int T = a.T[k];
+    const double gscale = ldexp(1.0, 8 - T);
     double corr = 0.0;
     for (int w = threadIdx.x; w < Nw; w += blockDim.x) {
         // Re conj(A) r = G[(k,re)][2w] + G[(k,im)][2w+1];  Im = G[(k,im)][2w] - G[(k,re)][2w+1]
@@ -416,7 +553,7 @@ __global__ void batched_finalize(const BatchArgs a, int grid, int *done, double 
         const size_t cta_stride = (size_t)NCH * 128 * F;
         const float *g0 = a.gpart + (size_t)c * 128 * F;
         for (int b0 = 0; b0 < grid; b0 += 16) {
-            float2 re_row[16], im_row[16];  // (G[(k,re)][2w], G[(k,re)][2w+1]), same for im
+            float2 re_row[16], im_row[16];
 #pragma unroll
             for (int t = 0; t < 16; ++t) {
                 const float *g = g0 + (size_t)(b0 + t) * cta_stride;
@@ -432,13 +569,10 @@ __global__ void batched_finalize(const BatchArgs a, int grid, int *done, double 
                 s_im = df_add(s_im, df_add(dfloat{im_row[t].x, 0.f}, dfloat{-re_row[t].y, 0.f}));
             }
         }
-        const double gre = -((double)s_re.hi + (double)s_re.lo);
-        const double gim = -((double)s_im.hi + (double)s_im.lo);
+        const double gre = -gscale * ((double)s_re.hi + (double)s_re.lo);
+        const double gim = -gscale * ((double)s_im.hi + (double)s_im.lo);
         const double *V = a.V + 2 * ((size_t)k * Nw + w);
-        float h0, l0, h1, l1;
-        split_bf16(V[0], h0, l0);
-        split_bf16(V[1], h1, l1);
-        const double dvr = V[0] - ((double)h0 + (double)l0), dvi = V[1] - ((double)h1 + (double)l1);
+        const double dvr = V[0] - round_slices(V[0], T), dvi = V[1] - round_slices(V[1], T);
         corr += 2.0 * (gre * dvr + gim * dvi);
         const double *mv = a.mv + (size_t)k * (2 * Nw + 1);
         if (grad) {
@@ -450,112 +584,209 @@ __global__ void batched_finalize(const BatchArgs a, int grid, int *done, double 
     if (lane == 0)
         s_corr[warp] = corr;
     if (warp == 0) {
-        dfloat l = {0.f, 0.f};
-        for (int i0 = lane; i0 < grid * 4; i0 += 32 * 8) {
-            float2 p[8];
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const int i = i0 + 32 * t;
-                p[t] = i < grid * 4 ? a.lpart[(size_t)i * (NCH * kKC) + k] : make_float2(0.f, 0.f);
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t)
-                l = df_add(l, dfloat{p[t].x, p[t].y});
-        }
+        long long l = 0;
+        for (int i = lane; i < grid * 4; i += 32)
+            l += a.lpart[(size_t)i * (NCH * kKC) + k];
         l = warp_sum(l);
         if (lane == 0)
-            s_ln = (double)l.hi + (double)l.lo;
+            s_l = l;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
+        const long long ex = 2 * *a.sum_e + 2 * a.n_events * (long long)(T - 16);
+        const double lnsum = kLn2 * ((double)ex + ldexp((double)s_l, -kFixBits));
         const double nv = a.mv[(size_t)k * (2 * Nw + 1) + 2 * Nw];
-        double v = -s_ln + nv + s_corr[0] + (blockDim.x > 32 ? s_corr[1] : 0.0);
-        if (bad)
+        double v = -lnsum + nv + s_corr[0] + (blockDim.x > 32 ? s_corr[1] : 0.0);
+        if (bad) {
             v = INFINITY;
+            atomicOr(a.status, FLAG_DOMAIN);
+        }
         nll[k] = v;
         if (done)
             atomicAdd(done, 1);
     }
 }
 
-constexpr int kMaxSmem = 215 * 1024;
+// ---- block-floating-point encoding of the data (once per load) ---------------
+// One thread per event: shared exponent E = exponent of the largest |feature|
+// (max = m 2^E, m in [1/2, 1)), slices x0 = rint(A 2^(8-E)) and, for XS = 2,
+// x1 = rint((A 2^(8-E) - x0) 256).
+__global__ void batched_encode_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n,
+                                      int rows_in, int F, int xs, __nv_bfloat16 *__restrict__ out,
+                                      long long *sum_e)
+{
+    long long es = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pitch;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool valid = i < n;
+        float m = 0.f;
+        if (valid)
+            for (int r = 0; r < rows_in; ++r)
+                m = fmaxf(m, fabsf(planes[(int64_t)r * pitch + i]));
+        int E = 0;
+        if (m > 0.f)
+            frexpf(m, &E);
+        for (int r = 0; r < F; ++r) {
+            float x0 = 0.f, x1 = 0.f;
+            if (valid && r < rows_in) {
+                const float x = ldexpf(planes[(int64_t)r * pitch + i], 8 - E);
+                x0 = rintf(x);
+                x1 = rintf((x - x0) * 256.f);
+            }
+            out[(int64_t)r * pitch + i] = __float2bfloat16_rn(x0);
+            if (xs == 2)
+                out[(int64_t)(F + r) * pitch + i] = __float2bfloat16_rn(x1);
+        }
+        if (valid)
+            es += E;
+    }
+    es = warp_sum(es);
+    __shared__ long long s_e[8];
+    if ((threadIdx.x & 31) == 0)
+        s_e[threadIdx.x >> 5] = es;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+            t += s_e[w];
+        atomicAdd(reinterpret_cast<unsigned long long *>(sum_e), (unsigned long long)t);
+    }
+}
 
-template <int F>
+constexpr int kMaxSmem = 226 * 1024;
+
+template <int F, int XS>
 cudaError_t configure_f()
 {
-    return cudaFuncSetAttribute(batched_kernel<F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(batched_kernel<F, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 kMaxSmem);
+}
+
+template <int XS>
+cudaError_t configure_xs()
+{
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t r : {configure_f<16, XS>(), configure_f<32, XS>(), configure_f<48, XS>(),
+                          configure_f<64, XS>(), configure_f<80, XS>(), configure_f<96, XS>()})
+        if (r != cudaSuccess)
+            e = r;
+    return e;
+}
+
+template <int XS>
+cudaError_t launch_main(int F, int grid, uint32_t smem, cudaStream_t s, const CUtensorMap *xmap,
+                        const BatchArgs &a, int n_tiles)
+{
+    switch (F) {
+    case 16: batched_kernel<16, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    case 32: batched_kernel<32, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    case 48: batched_kernel<48, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    case 64: batched_kernel<64, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    case 80: batched_kernel<80, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    case 96: batched_kernel<96, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+struct ScratchLayout {
+    size_t wimg, gpart, lpart, mv, T, kflags, total;
+};
+
+ScratchLayout scratch_layout(int F, int xs, int n_waves, int K, int grid)
+{
+    const int nch = (K + kKC - 1) / kKC;
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    ScratchLayout s;
+    s.wimg = 0;
+    s.gpart = up(s.wimg + batch_smem(F, xs, nch).w_bytes);
+    s.lpart = up(s.gpart + (size_t)grid * nch * 128 * F * 4);
+    s.mv = up(s.lpart + (size_t)grid * 4 * nch * kKC * 8);
+    s.T = up(s.mv + (size_t)K * (2 * n_waves + 1) * 8);
+    s.kflags = up(s.T + (size_t)K * 4);
+    s.total = up(s.kflags + (size_t)nch * 2 * 4);
+    return s;
 }
 
 }  // namespace
 
 int batched_features(int n_waves) { return (2 * n_waves + 15) / 16 * 16; }
 
-int batched_max_k(int n_waves)
+int batched_max_k(int n_waves, int xs)
 {
     const int F = batched_features(n_waves);
-    int nch = 4;
-    while (nch > 0 && (256 + nch * F > 512 || batch_smem(F, nch).bytes > kMaxSmem))
+    int nch = kMaxChunks;
+    while (nch > 0 &&
+           (s_cols(xs) + nch * xs * F > 512 || (int)batch_smem(F, xs, nch).bytes > kMaxSmem))
         --nch;
     return nch * kKC;
 }
 
-size_t batched_scratch_bytes(int n_waves, int K, int grid)
+size_t batched_scratch_bytes(int n_waves, int xs, int K, int grid)
 {
-    const int F = batched_features(n_waves), nch = (K + kKC - 1) / kKC;
-    return (size_t)grid * nch * 128 * F * 4 + (size_t)grid * 4 * nch * kKC * 8 + (size_t)nch * 2 * 4 +
-           (size_t)K * (2 * n_waves + 1) * 8 + 256;
+    return scratch_layout(batched_features(n_waves), xs, n_waves, K, grid).total;
 }
 
 cudaError_t batched_configure()
 {
-    cudaError_t e = cudaSuccess;
-    for (cudaError_t r : {configure_f<16>(), configure_f<32>(), configure_f<48>(), configure_f<64>(),
-                          configure_f<80>(), configure_f<96>()})
-        if (r != cudaSuccess)
-            e = r;
-    return e;
+    const cudaError_t e1 = configure_xs<1>(), e2 = configure_xs<2>();
+    return e1 != cudaSuccess ? e1 : e2;
 }
 
-// K <= batched_max_k(n_waves) parameter sets; scratch >= batched_scratch_bytes.
-cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, const double *V,
-                           int K, const double *M, void *scratch, int grid, int *status, int *done,
-                           double *nll, double *grad, cudaStream_t s)
+cudaError_t launch_batched_encode(const float *planes, int64_t pitch, int64_t n, int n_waves, int xs,
+                                  void *out, long long *sum_e, cudaStream_t s)
+{
+    if (xs != 1 && xs != 2)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(sum_e, 0, sizeof(long long), s);
+    if (e != cudaSuccess)
+        return e;
+    const int blocks = (int)std::min<int64_t>((pitch + 255) / 256, 4096);
+    batched_encode_kernel<<<blocks, 256, 0, s>>>(planes, pitch, n, 2 * n_waves,
+                                                 batched_features(n_waves), xs,
+                                                 static_cast<__nv_bfloat16 *>(out), sum_e);
+    return cudaGetLastError();
+}
+
+// K <= batched_max_k(n_waves, xs) parameter sets; scratch >= batched_scratch_bytes.
+cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, int xs,
+                           const long long *sum_e, const double *V, int K, const double *M,
+                           void *scratch, int grid, int *status, int *done, double *nll,
+                           double *grad, cudaStream_t s)
 {
     const int F = batched_features(n_waves), nch = (K + kKC - 1) / kKC;
+    if ((xs != 1 && xs != 2) || K < 1 || K > batched_max_k(n_waves, xs) || grid < 1)
+        return cudaErrorInvalidValue;
+    const ScratchLayout sl = scratch_layout(F, xs, n_waves, K, grid);
+    char *p = static_cast<char *>(scratch);
     BatchArgs a{};
     a.n_waves = n_waves;
     a.F = F;
+    a.XS = xs;
     a.K = K;
     a.n_chunks = nch;
     a.n_events = n_events;
     a.V = V;
     a.M = M;
-    char *p = static_cast<char *>(scratch);
-    a.gpart = reinterpret_cast<float *>(p);
-    p += (size_t)grid * nch * 128 * F * 4;
-    a.lpart = reinterpret_cast<float2 *>(p);
-    p += (size_t)grid * 4 * nch * kKC * 8;
-    a.kflags = reinterpret_cast<unsigned *>(p);
-    p += (size_t)nch * 2 * 4;
-    p = reinterpret_cast<char *>(((uintptr_t)p + 7) & ~(uintptr_t)7);
-    a.mv = reinterpret_cast<double *>(p);
+    a.sum_e = sum_e;
+    a.wimg = reinterpret_cast<unsigned char *>(p + sl.wimg);
+    a.gpart = reinterpret_cast<float *>(p + sl.gpart);
+    a.lpart = reinterpret_cast<long long *>(p + sl.lpart);
+    a.mv = reinterpret_cast<double *>(p + sl.mv);
+    a.T = reinterpret_cast<int *>(p + sl.T);
+    a.kflags = reinterpret_cast<unsigned *>(p + sl.kflags);
     a.status = status;
     cudaError_t e = cudaMemsetAsync(a.kflags, 0, nch * 2 * 4, s);
     if (e != cudaSuccess)
         return e;
-    const int n_tiles = (int)((n_events + kBM - 1) / kBM);
-    const uint32_t smem = batch_smem(F, nch).bytes;
-    switch (F) {
-    case 16: batched_kernel<16><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 32: batched_kernel<32><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 48: batched_kernel<48><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 64: batched_kernel<64><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 80: batched_kernel<80><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 96: batched_kernel<96><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    default: return cudaErrorInvalidValue;
-    }
+    batched_prep<<<nch * 2 * kWSlices, 256, 0, s>>>(a);
     e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return e;
+    const int n_tiles = (int)((n_events + kBM - 1) / kBM);
+    const uint32_t smem = batch_smem(F, xs, nch).bytes;
+    e = xs == 2 ? launch_main<2>(F, grid, smem, s, xmap, a, n_tiles)
+                : launch_main<1>(F, grid, smem, s, xmap, a, n_tiles);
     if (e != cudaSuccess)
         return e;
     batched_finalize<<<K, 64, 0, s>>>(a, grid, done, nll, grad);

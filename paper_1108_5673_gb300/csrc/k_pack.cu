@@ -98,26 +98,7 @@ __global__ void plane_absmax_kernel(const float *__restrict__ planes, int64_t pi
         atomicMax(reinterpret_cast<int *>(out + r), __float_as_int(m));
 }
 
-__global__ void to_bf16_kernel(const float *__restrict__ planes, int64_t pitch, int rows_in,
-                               __nv_bfloat16 *__restrict__ out, int64_t pitch_out, int rows_out)
-{
-    const int r = blockIdx.y;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pitch_out;
-         i += (int64_t)gridDim.x * blockDim.x)
-        out[(int64_t)r * pitch_out + i] =
-            __float2bfloat16_rn(r < rows_in && i < pitch ? planes[(int64_t)r * pitch + i] : 0.f);
-}
-
 }  // namespace
-
-cudaError_t launch_to_bf16(const float *planes, int64_t pitch, int rows_in, void *out,
-                           int64_t pitch_out, int rows_out, cudaStream_t s)
-{
-    dim3 grid((unsigned)std::min<int64_t>((pitch_out + 255) / 256, 1024), (unsigned)rows_out);
-    to_bf16_kernel<<<grid, 256, 0, s>>>(planes, pitch, rows_in, static_cast<__nv_bfloat16 *>(out),
-                                         pitch_out, rows_out);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_plane_absmax(const float *planes, int64_t pitch, int64_t n, int rows, float *out,
                                 cudaStream_t s)

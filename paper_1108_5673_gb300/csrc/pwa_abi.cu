@@ -35,7 +35,9 @@ struct pwa_ctx {
     float *table = nullptr;
     int64_t table_pitch = 0;
     float *tmax = nullptr;  // [N^2] max over events of |t_p|
-    void *xbf = nullptr;    // BF16 planes [F][pitch] of the data (tensor-core form)
+    void *xbf = nullptr;    // BF16 slices [2F][pitch] of the data (tensor-core form)
+    long long *xsum = nullptr;  // sum of the per-event exponents (inside xbf)
+    int xs = 2;                 // BF16 slices of the amplitudes (tensor-core form)
     CUtensorMap data_map, table_map, xbf_map;
     size_t work_bytes = 0;
     bool loaded = false, has_norm = false;
@@ -224,11 +226,14 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
 {
     const int N = c->N;
     if (c->form == PWA_FORM_TC) {
-        const int kmax = batched_max_k(N);
-        for (int k0 = 0; k0 < K; k0 += kmax) {
-            const int kk = std::min(kmax, K - k0);
-            cudaError_t e = launch_batched(&c->xbf_map, c->n_data, N, dV + (size_t)2 * N * k0, kk, c->M,
-                                           c->d_work, c->num_sms, status, done, dnll + k0,
+        // launches of near-equal size (multiples of 64 sets): each launch reads the data once
+        const int kmax = batched_max_k(N, c->xs);
+        const int nl = (K + kmax - 1) / kmax;
+        const int per = ((K + nl - 1) / nl + 63) / 64 * 64;
+        for (int k0 = 0; k0 < K; k0 += per) {
+            const int kk = std::min(per, K - k0);
+            cudaError_t e = launch_batched(&c->xbf_map, c->n_data, N, c->xs, c->xsum, dV + (size_t)2 * N * k0,
+                                           kk, c->M, c->d_work, c->num_sms, status, done, dnll + k0,
                                            dgrad ? dgrad + (size_t)2 * N * k0 : nullptr, c->stream);
             if (e != cudaSuccess) {
                 cudaGetLastError();
@@ -376,6 +381,9 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     const int forms = cfg->forms ? cfg->forms : PWA_FORM_AMP;
     if (forms & ~(PWA_FORM_AMP | PWA_FORM_TABLE | PWA_FORM_TC))
         return fail(nullptr, PWA_EINVAL, "unknown form bits 0x%x", forms);
+    if (cfg->precision != PWA_PREC_DEFAULT && cfg->precision != PWA_PREC_BFP16 &&
+        cfg->precision != PWA_PREC_BFP8)
+        return fail(nullptr, PWA_EINVAL, "unknown precision %d", cfg->precision);
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
         cudaGetLastError();
@@ -388,6 +396,7 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     c->cfg = *cfg;
     c->cfg.forms = forms;
     c->N = cfg->n_waves;
+    c->xs = cfg->precision == PWA_PREC_BFP8 ? 1 : 2;
     c->form = (forms & PWA_FORM_AMP) ? PWA_FORM_AMP : PWA_FORM_TABLE;
     int rc = PWA_OK;
     auto bail = [&](int code) {
@@ -425,7 +434,8 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     if (forms & PWA_FORM_TABLE)
         nwork = std::max(nwork, table_scratch_bytes(c->N, c->num_sms) / sizeof(double) + 16);
     if (forms & PWA_FORM_TC)
-        nwork = std::max(nwork, batched_scratch_bytes(c->N, std::min(cfg->max_k, batched_max_k(c->N)),
+        nwork = std::max(nwork, batched_scratch_bytes(c->N, c->xs,
+                                                      std::min(cfg->max_k, batched_max_k(c->N, c->xs)),
                                                       c->num_sms) / sizeof(double) + 16);
     c->work_bytes = nwork * sizeof(double);
     if ((rc = dev_alloc(c, (void **)&c->d_work, nwork * sizeof(double), "work")))
@@ -507,14 +517,17 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
     }
     if (!rc && (c->cfg.forms & PWA_FORM_TC)) {
         const int F = batched_features(c->N);
-        rc = dev_alloc(c, &c->xbf, (size_t)F * c->data.pitch * 2, "bf16 planes");
+        const size_t slice_bytes = (size_t)c->xs * F * c->data.pitch * 2;
+        rc = dev_alloc(c, &c->xbf, slice_bytes + 256, "bf16 planes");
         if (!rc) {
-            cudaError_t e = launch_to_bf16(c->data.ptr, c->data.pitch, 2 * c->N, c->xbf, c->data.pitch,
-                                           F, c->stream);
+            // the exponent sum sits after the slices
+            c->xsum = reinterpret_cast<long long *>(static_cast<char *>(c->xbf) + slice_bytes);
+            cudaError_t e = launch_batched_encode(c->data.ptr, c->data.pitch, c->data.n, c->N, c->xs,
+                                                  c->xbf, c->xsum, c->stream);
             if (e == cudaSuccess)
-                e = encode_bf16_planes_map(&c->xbf_map, c->xbf, c->data.n, c->data.pitch, F);
+                e = encode_bf16_planes_map(&c->xbf_map, c->xbf, c->data.n, c->data.pitch, c->xs * F);
             if (e != cudaSuccess)
-                rc = fail(c, PWA_ECUDA, "bf16 store: %s", cudaGetErrorString(e));
+                rc = fail(c, PWA_ECUDA, "block-floating-point store: %s", cudaGetErrorString(e));
         }
     }
     if (!rc) {

@@ -180,6 +180,36 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Contiguous global -> shared copy by the bulk-copy engine (addresses 16-byte
+// aligned, bytes a multiple of 16), completion signalled on `bar`.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Approximate reciprocal (special-function unit), flush-to-zero.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
@@ -368,18 +398,23 @@ cudaError_t launch_amp_max(const Planes &amp, float *amax, cudaStream_t s);
 cudaError_t launch_plane_absmax(const float *planes, int64_t pitch, int64_t n, int rows, float *out,
                                 cudaStream_t s);
 
-// bf16 copy of the planes (rows_out >= rows_in; extra rows and events are zero)
-cudaError_t launch_to_bf16(const float *planes, int64_t pitch, int rows_in, void *out,
-                           int64_t pitch_out, int rows_out, cudaStream_t s);
-
 // k_batched.cu
-int batched_features(int n_waves);   // 2 N rounded up to a multiple of 16
-int batched_max_k(int n_waves);      // parameter sets per launch
-size_t batched_scratch_bytes(int n_waves, int K, int grid);
+// xs = number of BF16 slices of the amplitudes (1: 8-bit, 2: 16-bit block
+// floating point).
+int batched_features(int n_waves);        // 2 N rounded up to a multiple of 16
+int batched_max_k(int n_waves, int xs);   // parameter sets per launch
+size_t batched_scratch_bytes(int n_waves, int xs, int K, int grid);
 cudaError_t batched_configure();
-cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, const double *V,
-                           int K, const double *M, void *scratch, int grid, int *status, int *done,
-                           double *nll, double *grad, cudaStream_t s);
+// Block-floating-point copy of the data planes for the tensor-core form:
+// out = [xs F][pitch] BF16 (slice x0 rows 0..F-1, slice x1 rows F..2F-1; rows
+// past 2 n_waves and events past n are zero); *sum_e (zeroed here) receives
+// the sum over events of the event exponents.
+cudaError_t launch_batched_encode(const float *planes, int64_t pitch, int64_t n, int n_waves, int xs,
+                                  void *out, long long *sum_e, cudaStream_t s);
+cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, int xs,
+                           const long long *sum_e, const double *V, int K, const double *M,
+                           void *scratch, int grid, int *status, int *done, double *nll,
+                           double *grad, cudaStream_t s);
 
 // k_nll_table.cu
 int table_max_waves();
