@@ -41,9 +41,10 @@
 // R' = Q / |Q|^2, rounded to BF16, by both slices (N = XS F columns).
 //
 // Layout in shared memory (128-byte swizzled, 1 KB aligned):
-//  W   [chunk][half][slice w0,w1,w2][F/64 blocks][64 rows][128 B]: K-major B
-//      operands of GEMM 1, copied once per launch from an image the prep
-//      kernel builds.
+//  W   [chunk][half][F/64 blocks][slice w0,w1,w2][64 rows][128 B]: K-major B
+//      operands of GEMM 1 (the three slices of a block are adjacent, so one
+//      product covers w0|w1|w2 as 192 columns), copied once per launch from an
+//      image the prep kernel builds.
 //  X   [stage][2 blocks of 64 events][XS F rows (x0 then x1)][128 B]: MN-major
 //      A operand of GEMM 1 (events contiguous) and K-major B operand of GEMM 2
 //      (K = events) -- the same bytes serve both products.
@@ -107,7 +108,7 @@ struct BatchArgs {
     unsigned char *wimg;        // W image (byte-identical to shared memory)
     int *T;                     // [K] set exponents
     float *gpart;               // [grid][n_chunks][128][F]
-    long long *lpart;           // [grid][4][n_chunks * 64] fixed-point log2 sums
+    long long *lpart;           // [grid][4][n_chunks * 64] fixed-point log2 sums (zeroed per launch)
     unsigned *kflags;           // [n_chunks * 2] domain bits per half chunk
     double *mv;                 // [K][2N + 1]: M V and V^H M V
     int *status;
@@ -191,7 +192,7 @@ __global__ void batched_prep(const BatchArgs a)
         s_T[threadIdx.x] = e;
     }
     __syncthreads();
-    unsigned char *out = a.wimg + (size_t)blk * KB * kWBlock;
+    unsigned char *out = a.wimg + (size_t)(c * 2 + h) * KB * kWSlices * kWBlock + (size_t)p * kWBlock;
     for (int idx = threadIdx.x; idx < KB * 64 * 64; idx += blockDim.x) {
         const int kb = idx >> 12, r = (idx >> 6) & 63, fb = idx & 63;
         const int f = kb * 64 + fb, sl = r >> 1, t = r & 1;
@@ -205,7 +206,8 @@ __global__ void batched_prep(const BatchArgs a)
             split_slices(coef, s_T[sl], ws);
             val = isfinite(coef) ? (float)ws[p] : 0.f;
         }
-        *reinterpret_cast<__nv_bfloat16 *>(out + kb * kWBlock + sw128(r, fb * 2)) = __float2bfloat16_rn(val);
+        *reinterpret_cast<__nv_bfloat16 *>(out + kb * kWSlices * kWBlock + sw128(r, fb * 2)) =
+            __float2bfloat16_rn(val);
     }
 }
 
@@ -287,9 +289,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kEpiWarps + 1) {
         // ---- MMA issuer ---------------------------------------------------
         if (lane == 0) {
-            const uint32_t id1 = umma_idesc_bf16(128, 64, 1, 0);
+            const uint32_t id64 = umma_idesc_bf16(128, 64, 1, 0);
+            const uint32_t id128 = umma_idesc_bf16(128, 128, 1, 0);
+            const uint32_t id192 = umma_idesc_bf16(128, 192, 1, 0);
             const uint32_t id2 = umma_idesc_bf16(128, XS * F, 1, 0);
             const uint32_t xbase = smem_u32(sX), wbase = smem_u32(sW), rbase = smem_u32(sR);
+            // descriptors without their start address (added as address / 16 below)
+            const uint64_t dA = umma_desc_sw128(0, kXBlk, 1024);      // X, MN-major
+            const uint64_t dR = umma_desc_sw128(0, 128 * 128, 1024);  // R', MN-major
+            const uint64_t dK = umma_desc_sw128(0, 16, 1024);         // K-major operands
             // GEMM 2 of chunk step cq (pipelined behind GEMM 1 of the next step)
             auto gemm2 = [&](int cq) -> bool {
                 const int j = cq / NCH, c = cq % NCH, s = j % kXS;
@@ -297,10 +305,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     return false;
                 tc_fence_after();
                 const uint32_t xs = xbase + s * kXBytes;
+#pragma unroll
                 for (int ks = 0; ks < kBM / 16; ++ks) {
-                    const uint64_t da = umma_desc_sw128(rbase + ks * 2048, 128 * 128, 1024);
-                    const uint64_t db = umma_desc_sw128(xs + (ks >> 2) * kXBlk + (ks & 3) * 32, 16, 1024);
-                    umma_bf16(tmem + kGCol + c * XS * F, da, db, id2, (j > 0 || ks > 0) ? 1u : 0u);
+                    const uint32_t ra = rbase + ks * 2048;
+                    const uint32_t xa = xs + (ks >> 2) * kXBlk + (ks & 3) * 32;
+                    umma_bf16(tmem + kGCol + c * XS * F, dR + (ra >> 4), dK + (xa >> 4), id2,
+                              (j > 0 || ks > 0) ? 1u : 0u);
                 }
                 umma_commit(&r_free);
                 if (c == NCH - 1)
@@ -320,21 +330,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t xs = xbase + s * kXBytes;
-                const uint32_t wb = wbase + (uint32_t)((c * 2 + h) * kWSlices) * KB * kWBlock;
-                // slice pair (x slice i, w slice p) goes to accumulator i + p
+                const uint32_t wb = wbase + (uint32_t)(c * 2 + h) * KB * kWSlices * kWBlock;
+                // accumulator j (64 columns at 64 j) collects the slice products x_i w_p, i + p = j
 #pragma unroll
-                for (int i = 0; i < XS; ++i)
-#pragma unroll
-                    for (int p = 0; p < kWSlices; ++p)
-#pragma unroll
-                        for (int ks = 0; ks < F / 16; ++ks) {
-                            const uint64_t xd = umma_desc_sw128(xs + i * F * 128 + ks * 2048, kXBlk, 1024);
-                            const uint64_t wd = umma_desc_sw128(
-                                wb + (uint32_t)(p * KB + (ks >> 2)) * kWBlock + (ks & 3) * 32, 16, 1024);
-                            // the first product into each accumulator starts it
-                            const bool first = ks == 0 && (i == 0 || p == kWSlices - 1);
-                            umma_bf16(tmem + 64 * (i + p), xd, wd, id1, first ? 0u : 1u);
-                        }
+                for (int ks = 0; ks < F / 16; ++ks) {
+                    const uint32_t x0a = xs + ks * 2048;
+                    const uint32_t wa = wb + (ks >> 2) * kWSlices * kWBlock + (ks & 3) * 32;
+                    const uint32_t acc = ks > 0 ? 1u : 0u;
+                    if (XS == 2) {
+                        const uint32_t x1a = x0a + F * 128;
+                        umma_bf16(tmem + 64, dA + (x1a >> 4), dK + (wa >> 4), id192, acc);   // acc1..3 x1 [w0|w1|w2]
+                        umma_bf16(tmem, dA + (x0a >> 4), dK + (wa >> 4), id64, acc);         // acc0    x0 w0
+                        umma_bf16(tmem + 64, dA + (x0a >> 4), dK + ((wa + kWBlock) >> 4), id128,
+                                  1u);                                                       // acc1..2 x0 [w1|w2]
+                    } else {
+                        umma_bf16(tmem, dA + (x0a >> 4), dK + (wa >> 4), id192, acc);        // acc0..2 x0 [w0|w1|w2]
+                    }
+                }
                 umma_commit(&s_full);
                 if (h == 0 && q >= 2)
                     ok = gemm2((q >> 1) - 1);
@@ -353,10 +365,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int qq = warp & 3, sg = warp >> 2;
         const int e = qq * 32 + lane;                  // event row of the tile = TMEM lane
         const uint32_t lane_addr = (uint32_t)(qq * 32) << 16;
-        long long lacc[2 * kMaxChunks];
-#pragma unroll
-        for (int i = 0; i < 2 * kMaxChunks; ++i)
-            lacc[i] = 0;
         const f2 inv256 = pk2(1.0f / 256.0f, 1.0f / 256.0f);
         bool ok = true;
         for (int q = 0; q < steps && ok; ++q) {
@@ -369,24 +377,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             // Q pieces of this warp's 8 sets: acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8
             f2 t[8];
             {
-                uint32_t va[16], vb[16];
-                tmem_ld16(tmem + lane_addr + 64 * 2 + 16 * sg, va);
+                uint32_t v0[16], v1[16], v2[16], v3[16];
+                tmem_ld16(tmem + lane_addr + 16 * sg, v0);
+                tmem_ld16(tmem + lane_addr + 64 + 16 * sg, v1);
+                tmem_ld16(tmem + lane_addr + 128 + 16 * sg, v2);
                 if (XS == 2)
-                    tmem_ld16(tmem + lane_addr + 64 * 3 + 16 * sg, vb);
+                    tmem_ld16(tmem + lane_addr + 192 + 16 * sg, v3);
                 tmem_ld_wait();
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
-                    t[s] = pk2(__uint_as_float(va[2 * s]), __uint_as_float(va[2 * s + 1]));
+                    f2 u = pk2(__uint_as_float(v2[2 * s]), __uint_as_float(v2[2 * s + 1]));
                     if (XS == 2)
-                        t[s] = fma2(pk2(__uint_as_float(vb[2 * s]), __uint_as_float(vb[2 * s + 1])), inv256, t[s]);
-                }
-                tmem_ld16(tmem + lane_addr + 64 * 1 + 16 * sg, va);
-                tmem_ld16(tmem + lane_addr + 16 * sg, vb);
-                tmem_ld_wait();
-#pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    t[s] = fma2(t[s], inv256, pk2(__uint_as_float(va[2 * s]), __uint_as_float(va[2 * s + 1])));
-                    t[s] = fma2(t[s], inv256, pk2(__uint_as_float(vb[2 * s]), __uint_as_float(vb[2 * s + 1])));
+                        u = fma2(pk2(__uint_as_float(v3[2 * s]), __uint_as_float(v3[2 * s + 1])), inv256, u);
+                    u = fma2(u, inv256, pk2(__uint_as_float(v1[2 * s]), __uint_as_float(v1[2 * s + 1])));
+                    t[s] = fma2(u, inv256, pk2(__uint_as_float(v0[2 * s]), __uint_as_float(v0[2 * s + 1])));
                 }
             }
             tc_fence_before();
@@ -445,7 +449,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int t = __reduce_add_sync(0xffffffffu, l[s]);
                 mine = lane == s ? t : mine;
             }
-            lacc[ch] += mine;
+            if (lane < 8)  // no return value: a fire-and-forget reduction
+                atomicAdd(reinterpret_cast<unsigned long long *>(
+                              a.lpart + ((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + (ch >> 1) * kKC +
+                              (ch & 1) * kHS + 8 * sg + lane),
+                          (unsigned long long)(long long)mine);
             // R' may be overwritten once GEMM 2 of the previous chunk step is done
             if (h == 0 && cq >= 1 && !mbar_wait(&r_free, (cq - 1) & 1)) {
                 ok = false;
@@ -464,10 +472,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (!ok)
             flags |= FLAG_TIMEOUT;
-        if (lane < 8)
-            for (int ch = 0; ch < 2 * NCH; ++ch)
-                a.lpart[((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + (ch >> 1) * kKC + (ch & 1) * kHS +
-                        8 * sg + lane] = lacc[ch];
         // G^T of every chunk: rows = this warp's lane quarter, 8-column groups
         if (ok && mbar_wait(&g_done, 0)) {
             tc_fence_after();
@@ -777,6 +781,8 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
     a.kflags = reinterpret_cast<unsigned *>(p + sl.kflags);
     a.status = status;
     cudaError_t e = cudaMemsetAsync(a.kflags, 0, nch * 2 * 4, s);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(a.lpart, 0, (size_t)grid * 4 * nch * kKC * 8, s);
     if (e != cudaSuccess)
         return e;
     batched_prep<<<nch * 2 * kWSlices, 256, 0, s>>>(a);
