@@ -146,6 +146,41 @@ int pwa_nll_grad_async(pwa_ctx *ctx, const double *d_V, int K, double *d_nll, do
  * PWA_ETIMEOUT), then clear it. */
 int pwa_sync(pwa_ctx *ctx);
 
+/* ---- free Breit-Wigner masses and widths (Sec. 2) ------------------------
+ * The precomputed normalisation matrix and per-event table assume fixed
+ * masses and widths (Sec. 2, after Eq. 3). With the masses and widths of the
+ * first n_free waves free, their amplitudes A_r = BW(m; M_r, G_r) Y_r(Omega),
+ * BW(m; M, G) = 1 / (M^2 - m^2 - i M G), are recomputed on every call and the
+ * normalisation term of Eq. 3 is the MC sum (1 / n_mc_gen) sum_j |S_j|^2.
+ *
+ * Load both samples (copied by the library; host or device pointers):
+ *   n_free       R, 1 <= R <= 8 and R <= n_waves; needs n_waves <= 32
+ *   m_data       [n_data] double, the mass variable m of each event (rounded
+ *                to the nearest float on load)
+ *   Y_data       [n_data][R] angular factors of the free waves, interleaved
+ *                complex of amp_dtype (PWA_C64 or PWA_C128, rounded to float)
+ *   Afix_data    [n_data][n_waves - R] amplitudes of the fixed waves (NULL
+ *                when R = n_waves)
+ *   m_mc, Y_mc, Afix_mc, n_mc_acc: the same for the accepted MC events;
+ *   n_mc_gen >= n_mc_acc generated MC events.
+ * Independent of pwa_load_events. Errors: PWA_EINVAL (null pointer, sizes),
+ * PWA_ENOTSUP (n_waves > 32 or n_free > 8), PWA_ENOMEM, PWA_ECUDA. */
+int pwa_load_resonance_events(pwa_ctx *ctx, int n_free, const double *m_data, const void *Y_data,
+                              const void *Afix_data, int64_t n_data, const double *m_mc,
+                              const void *Y_mc, const void *Afix_mc, int64_t n_mc_acc,
+                              double n_mc_gen, int amp_dtype);
+
+/* NLL of Eq. 3 and its gradients with free masses and widths (host pointers):
+ *   V       [n_waves] complex128
+ *   mass    [n_free] double; width [n_free] double
+ *   nll     [1]; gV [n_waves] complex128, dNLL/dV* (may be NULL);
+ *   gM, gW  [n_free] double, dNLL/dM_r and dNLL/dG_r (may be NULL)
+ * Returns PWA_EDOMAIN (nll = +inf, gradients 0) if a data intensity was not
+ * positive and finite; PWA_ESTATE before pwa_load_resonance_events;
+ * PWA_EINVAL for null V, mass, width or nll; PWA_ECUDA, PWA_ETIMEOUT. */
+int pwa_nll_grad_res(pwa_ctx *ctx, const double *V, const double *mass, const double *width,
+                     double *nll, double *gV, double *gM, double *gW);
+
 /* Direct-form NLL and gradient that allocates no device memory.
  *
  * The paper has no counterpart to this call; it exists for callers that

@@ -50,6 +50,23 @@ class Likelihood:
         nll, g, self.last_status = self._abi.pwa_nll_grad(self.ctx, V)
         return nll, g
 
+    def load_resonance_events(self, wl):
+        """Samples for free masses and widths (a synth.ResonanceWorkload or any
+        object with the same fields: n_free, m_data, Y_data, Afix_data, m_mc,
+        Y_mc, Afix_mc, n_gen)."""
+        afd = wl.Afix_data if wl.Afix_data.shape[1] else None
+        afm = wl.Afix_mc if wl.Afix_mc.shape[1] else None
+        self._abi.pwa_load_resonance_events(self.ctx, wl.n_free, wl.m_data, wl.Y_data, afd,
+                                            wl.m_mc, wl.Y_mc, afm, wl.n_gen)
+        self.n_free = wl.n_free
+        self.n_data_res = len(wl.m_data)
+        return self
+
+    def nll_grad_res(self, V, mass, width):
+        """(nll, dNLL/dV* [N] complex, dNLL/dM [R], dNLL/dGamma [R])."""
+        nll, gV, gM, gW, self.last_status = self._abi.pwa_nll_grad_res(self.ctx, V, mass, width)
+        return nll, gV, gM, gW
+
     def nll_grad_async(self, d_V, d_nll, d_grad=None):
         self._abi.pwa_nll_grad_async(self.ctx, d_V, d_V.shape[0], d_nll, d_grad)
 

@@ -80,6 +80,8 @@ def load(path=LIB_PATH):
         "pwa_table_bytes": ([I, I64, ctypes.POINTER(ctypes.c_int64)], I),
         "pwa_version": ([], I),
         "pwa_nll_grad_noalloc": ([P, I64, I64, I, P, P, P, P, P, P, P], I),
+        "pwa_load_resonance_events": ([P, I, P, P, P, I64, P, P, P, I64, D, I], I),
+        "pwa_nll_grad_res": ([P, P, P, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -209,6 +211,51 @@ def pwa_nll_grad_noalloc(d_planes, plane_pitch, n_events, n_waves, d_amax, d_M, 
     if rc != PWA_OK:
         raise PwaError(rc, "pwa_nll_grad_noalloc failed")
     return rc
+
+
+def pwa_load_resonance_events(ctx, n_free, m_data, Y_data, Afix_data, m_mc, Y_mc, Afix_mc,
+                              n_mc_gen):
+    """m_*: [n] masses (any float type, passed as float64); Y_*: [n, n_free]
+    and Afix_*: [n, n_waves - n_free] complex64 or complex128 (Afix may be None
+    when every wave is free)."""
+    def kind(x):
+        dt = str(getattr(x, "dtype", ""))
+        if "complex64" in dt:
+            return PWA_C64
+        if "complex128" in dt:
+            return PWA_C128
+        raise ValueError("amplitudes must be complex64 or complex128, got %s" % dt)
+    k = kind(Y_data)
+    for x in (Y_mc, Afix_data, Afix_mc):
+        if x is not None and kind(x) != k:
+            raise ValueError("Y and Afix of both samples must share one dtype")
+    for x in (m_data, m_mc):
+        if getattr(x, "is_cuda", False) and "float64" not in str(x.dtype):
+            raise ValueError("device mass arrays must be float64")
+    md, a1 = _ptr(m_data, np.float64)
+    mm, a2 = _ptr(m_mc, np.float64)
+    yd, a3 = _ptr(Y_data)
+    ym, a4 = _ptr(Y_mc)
+    fd, a5 = _ptr(Afix_data)
+    fm, a6 = _ptr(Afix_mc)
+    return _check(ctx, load().pwa_load_resonance_events(
+        ctx, int(n_free), md, yd, fd, int(len(m_data)), mm, ym, fm, int(len(m_mc)),
+        float(n_mc_gen), k))
+
+
+def pwa_nll_grad_res(ctx, V, mass, width):
+    """Host V [n_waves] complex128, mass/width [n_free]. Returns
+    (nll, gV [n_waves] complex128 = dNLL/dV*, gM, gW, status)."""
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    mass = np.ascontiguousarray(mass, dtype=np.float64)
+    width = np.ascontiguousarray(width, dtype=np.float64)
+    nll = np.empty(1)
+    gV = np.empty_like(V)
+    gM, gW = np.empty_like(mass), np.empty_like(width)
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = _check(ctx, load().pwa_nll_grad_res(ctx, p(V), p(mass), p(width), p(nll), p(gV), p(gM),
+                                             p(gW)), allow=(PWA_EDOMAIN,))
+    return float(nll[0]), gV, gM, gW, rc
 
 
 def pwa_last_error(ctx):

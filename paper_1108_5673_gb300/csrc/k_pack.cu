@@ -98,7 +98,22 @@ __global__ void plane_absmax_kernel(const float *__restrict__ planes, int64_t pi
         atomicMax(reinterpret_cast<int *>(out + r), __float_as_int(m));
 }
 
+__global__ void to_float_kernel(const double *__restrict__ src, int64_t n, float *__restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __double2float_rn(src[i]);
+}
+
 }  // namespace
+
+cudaError_t launch_to_float(const double *src, int64_t n, float *dst, cudaStream_t s)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    to_float_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, s>>>(src, n, dst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_plane_absmax(const float *planes, int64_t pitch, int64_t n, int rows, float *out,
                                 cudaStream_t s)

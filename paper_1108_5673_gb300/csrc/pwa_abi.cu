@@ -38,6 +38,14 @@ struct pwa_ctx {
     void *xbf = nullptr;    // BF16 slices [2F][pitch] of the data (tensor-core form)
     long long *xsum = nullptr;  // sum of the per-event exponents (inside xbf)
     int xs = 2;                 // BF16 slices of the amplitudes (tensor-core form)
+    // free-resonance form
+    float *res_data = nullptr, *res_mc = nullptr;
+    int64_t res_data_pitch = 0, res_mc_pitch = 0, res_n_data = 0, res_n_mc = 0;
+    int res_R = 0;
+    double res_ngen = 0.0;
+    bool res_loaded = false;
+    double *d_res = nullptr;    // partials, ticket, io
+    double *h_res = nullptr;    // pinned io mirror
     CUtensorMap data_map, table_map, xbf_map;
     size_t work_bytes = 0;
     bool loaded = false, has_norm = false;
@@ -148,6 +156,17 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 size_t io_doubles(int N, int max_k) { return (size_t)max_k * (1 + 4 * (size_t)N) + 1; }
 
+void free_res(pwa_ctx *c)
+{
+    dev_free(c->res_data);
+    dev_free(c->res_mc);
+    dev_free(c->d_res);
+    if (c->h_res)
+        cudaFreeHost(c->h_res);
+    c->h_res = nullptr;
+    c->res_loaded = false;
+}
+
 void free_sample(pwa_ctx *c)
 {
     dev_free(c->data.ptr);
@@ -158,26 +177,21 @@ void free_sample(pwa_ctx *c)
     c->loaded = c->has_norm = false;
 }
 
-// Copy one sample into planes [2N][pitch]: device sources are packed
+// Copy n events of nw complex waves (event-major, host or device) into the
+// 2 nw planes starting at dst (pitch floats apart): device sources are packed
 // directly; host sources go through a bounded device staging buffer.
-int load_planes(pwa_ctx *c, const void *src, int64_t n, int dtype, Planes *out)
+int pack_rows(pwa_ctx *c, const void *src, int64_t n, int dtype, int nw, float *dst, int64_t pitch)
 {
-    const int N = c->N;
-    out->n = n;
-    out->n_waves = N;
-    out->pitch = round_up(n, 256);
-    int rc = dev_alloc(c, (void **)&out->ptr, (size_t)2 * N * out->pitch * sizeof(float), "planes");
-    if (rc)
-        return rc;
-    CK(c, cudaMemsetAsync(out->ptr, 0, (size_t)2 * N * out->pitch * sizeof(float), c->stream));
-    const size_t esz = (dtype == PWA_C64 ? 8 : 16) * (size_t)N;
+    if (nw == 0 || n == 0)
+        return PWA_OK;
+    const size_t esz = (dtype == PWA_C64 ? 8 : 16) * (size_t)nw;
     if (is_device_pointer(src)) {
-        CK(c, launch_pack(src, dtype, n, N, out->ptr, out->pitch, c->stream));
+        CK(c, launch_pack(src, dtype, n, nw, dst, pitch, c->stream));
         return PWA_OK;
     }
     const int64_t chunk = (int64_t)((64u << 20) / esz) > 0 ? (int64_t)((64u << 20) / esz) : 1;
     void *staging = nullptr;
-    rc = dev_alloc(c, &staging, (size_t)std::min<int64_t>(chunk, n) * esz, "staging");
+    int rc = dev_alloc(c, &staging, (size_t)std::min<int64_t>(chunk, n) * esz, "staging");
     if (rc)
         return rc;
     for (int64_t s = 0; s < n; s += chunk) {
@@ -185,7 +199,7 @@ int load_planes(pwa_ctx *c, const void *src, int64_t n, int dtype, Planes *out)
         cudaError_t e = cudaMemcpyAsync(staging, static_cast<const char *>(src) + s * esz, m * esz,
                                         cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess)
-            e = launch_pack(staging, dtype, m, N, out->ptr + s, out->pitch, c->stream);
+            e = launch_pack(staging, dtype, m, nw, dst + s, pitch, c->stream);
         if (e != cudaSuccess) {
             cudaStreamSynchronize(c->stream);
             cudaFree(staging);
@@ -199,6 +213,67 @@ int load_planes(pwa_ctx *c, const void *src, int64_t n, int dtype, Planes *out)
         return fail(c, PWA_ECUDA, "loading amplitudes: %s", cudaGetErrorString(e));
     return PWA_OK;
 }
+
+// Copy one sample into planes [2N][pitch].
+int load_planes(pwa_ctx *c, const void *src, int64_t n, int dtype, Planes *out)
+{
+    const int N = c->N;
+    out->n = n;
+    out->n_waves = N;
+    out->pitch = round_up(n, 256);
+    int rc = dev_alloc(c, (void **)&out->ptr, (size_t)2 * N * out->pitch * sizeof(float), "planes");
+    if (rc)
+        return rc;
+    CK(c, cudaMemsetAsync(out->ptr, 0, (size_t)2 * N * out->pitch * sizeof(float), c->stream));
+    return pack_rows(c, src, n, dtype, N, out->ptr, out->pitch);
+}
+
+// n doubles (host or device) rounded to floats at dst.
+int load_floats(pwa_ctx *c, const double *src, int64_t n, float *dst)
+{
+    if (is_device_pointer(src)) {
+        CK(c, launch_to_float(src, n, dst, c->stream));
+        return PWA_OK;
+    }
+    const int64_t chunk = 8 << 20;
+    double *staging = nullptr;
+    int rc = dev_alloc(c, (void **)&staging, (size_t)std::min<int64_t>(chunk, n) * 8, "staging");
+    if (rc)
+        return rc;
+    cudaError_t e = cudaSuccess;
+    for (int64_t s = 0; s < n && e == cudaSuccess; s += chunk) {
+        const int64_t m = std::min(chunk, n - s);
+        e = cudaMemcpyAsync(staging, src + s, m * 8, cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = launch_to_float(staging, m, dst + s, c->stream);
+    }
+    const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(staging);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "loading masses: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    return PWA_OK;
+}
+
+// One sample of the free-resonance form: planes [1 + 2N][pitch] + padding.
+int load_res_sample(pwa_ctx *c, int R, const double *m, const void *Y, const void *Afix, int64_t n,
+                    int dtype, float **out, int64_t *pitch)
+{
+    const int N = c->N;
+    *pitch = round_up(n, 256);
+    const size_t bytes = ((size_t)(1 + 2 * N) * *pitch + 256) * sizeof(float);
+    int rc = dev_alloc(c, (void **)out, bytes, "resonance planes");
+    if (rc)
+        return rc;
+    CK(c, cudaMemsetAsync(*out, 0, bytes, c->stream));
+    if ((rc = load_floats(c, m, n, *out)))
+        return rc;
+    if ((rc = pack_rows(c, Y, n, dtype, R, *out + *pitch, *pitch)))
+        return rc;
+    return pack_rows(c, Afix, n, dtype, N - R, *out + (size_t)(1 + 2 * R) * *pitch, *pitch);
+}
+
 
 int status_from_flags(pwa_ctx *c, int flags)
 {
@@ -360,6 +435,125 @@ int pwa_version(void) { return 100; }
 
 const char *pwa_last_error(const pwa_ctx *ctx) { return ctx ? ctx->err : g_create_err; }
 
+static size_t res_grid(const pwa_ctx *c) { return (size_t)c->num_sms; }
+
+int pwa_load_resonance_events(pwa_ctx *c, int n_free, const double *m_data, const void *Y_data,
+                              const void *Afix_data, int64_t n_data, const double *m_mc,
+                              const void *Y_mc, const void *Afix_mc, int64_t n_mc_acc,
+                              double n_mc_gen, int amp_dtype)
+{
+    if (!c)
+        return PWA_EINVAL;
+    const int N = c->N;
+    if (N > res_max_waves() || n_free > res_max_free())
+        return fail(c, PWA_ENOTSUP, "free resonances need n_waves <= %d and n_free <= %d",
+                    res_max_waves(), res_max_free());
+    if (n_free < 1 || n_free > N)
+        return fail(c, PWA_EINVAL, "n_free=%d outside [1, n_waves=%d]", n_free, N);
+    if (!m_data || !Y_data || !m_mc || !Y_mc || (n_free < N && (!Afix_data || !Afix_mc)))
+        return fail(c, PWA_EINVAL, "null sample pointer");
+    if (n_data < 1 || n_mc_acc < 1 || n_data > ((int64_t)1 << 31) - 1024 ||
+        n_mc_acc > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "sample sizes must be in [1, 2^31 - 1024]");
+    if (!(n_mc_gen >= (double)n_mc_acc))
+        return fail(c, PWA_EINVAL, "n_mc_gen=%g must be >= n_mc_acc=%lld", n_mc_gen,
+                    (long long)n_mc_acc);
+    if (amp_dtype != PWA_C64 && amp_dtype != PWA_C128)
+        return fail(c, PWA_EINVAL, "amp_dtype=%d is neither PWA_C64 nor PWA_C128", amp_dtype);
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_res(c);
+    int rc = load_res_sample(c, n_free, m_data, Y_data, Afix_data, n_data, amp_dtype, &c->res_data,
+                             &c->res_data_pitch);
+    if (!rc)
+        rc = load_res_sample(c, n_free, m_mc, Y_mc, Afix_mc, n_mc_acc, amp_dtype, &c->res_mc,
+                             &c->res_mc_pitch);
+    const size_t npart = res_partials_doubles(N, n_free, (int)res_grid(c));
+    const size_t nio = 4 * (size_t)N + 4 * (size_t)n_free + 2;
+    if (!rc)
+        rc = dev_alloc(c, (void **)&c->d_res, (npart + 1 + nio) * sizeof(double), "resonance io");
+    if (!rc && cudaMemsetAsync(c->d_res, 0, (npart + 1 + nio) * sizeof(double), c->stream) != cudaSuccess)
+        rc = fail(c, PWA_ECUDA, "memset");
+    if (!rc && cudaMallocHost((void **)&c->h_res, nio * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_res = nullptr;
+        rc = fail(c, PWA_ENOMEM, "pinned host buffer");
+    }
+    if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
+        rc = fail(c, PWA_ECUDA, "loading the resonance samples");
+    if (rc) {
+        free_res(c);
+        return rc;
+    }
+    c->res_R = n_free;
+    c->res_n_data = n_data;
+    c->res_n_mc = n_mc_acc;
+    c->res_ngen = n_mc_gen;
+    c->res_loaded = true;
+    return PWA_OK;
+}
+
+int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const double *width,
+                     double *nll, double *gV, double *gM, double *gW)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!V || !mass || !width || !nll)
+        return fail(c, PWA_EINVAL, "null V, mass, width or nll");
+    if (!c->res_loaded)
+        return fail(c, PWA_ESTATE, "pwa_load_resonance_events must come first");
+    DeviceGuard g(c->device);
+    const int N = c->N, R = c->res_R;
+    const size_t npart = res_partials_doubles(N, R, (int)res_grid(c));
+    double *d_io = c->d_res + npart + 1, *h = c->h_res;
+    // io: V [2N] | mass [R] | width [R] | status, done | out [1 + 2N + 2R]
+    memcpy(h, V, 2 * N * sizeof(double));
+    memcpy(h + 2 * N, mass, R * sizeof(double));
+    memcpy(h + 2 * N + R, width, R * sizeof(double));
+    int *hs = reinterpret_cast<int *>(h + 2 * N + 2 * R);
+    hs[0] = hs[1] = 0;
+    const size_t nin = 2 * (size_t)N + 2 * R + 1, nout = 1 + 2 * (size_t)N + 2 * R;
+    CK(c, cudaMemcpyAsync(d_io, h, nin * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    ResArgs a{};
+    a.n_waves = N;
+    a.n_free = R;
+    a.data = c->res_data;
+    a.data_pitch = c->res_data_pitch;
+    a.n_data = c->res_n_data;
+    a.mc = c->res_mc;
+    a.mc_pitch = c->res_mc_pitch;
+    a.n_mc = c->res_n_mc;
+    a.inv_ngen = 1.0 / c->res_ngen;
+    a.V = d_io;
+    a.mass = d_io + 2 * N;
+    a.width = d_io + 2 * N + R;
+    a.partials = c->d_res;
+    a.ticket = reinterpret_cast<unsigned *>(c->d_res + npart);
+    int *ds = reinterpret_cast<int *>(d_io + 2 * N + 2 * R);
+    a.status = ds;
+    a.done = ds + 1;
+    a.out = d_io + nin;
+    cudaError_t e = launch_nll_res(a, (int)res_grid(c), c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "resonance kernel launch: %s", cudaGetErrorString(e));
+    }
+    CK(c, cudaMemcpyAsync(h + 2 * N + 2 * R, d_io + 2 * N + 2 * R, (1 + nout) * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    if (hs[1] != 1)
+        return fail(c, PWA_ETIMEOUT, "the resonance evaluation did not finish");
+    const double *o = h + nin;
+    *nll = o[0];
+    if (gV)
+        memcpy(gV, o + 1, 2 * N * sizeof(double));
+    if (gM)
+        memcpy(gM, o + 1 + 2 * N, R * sizeof(double));
+    if (gW)
+        memcpy(gW, o + 1 + 2 * N + R, R * sizeof(double));
+    return status_from_flags(c, hs[0]);
+}
+
 int pwa_table_bytes(int n_waves, int64_t n_events, int64_t *bytes)
 {
     if (!bytes || n_waves < 1 || n_waves > kMaxWaves || n_events < 0)
@@ -460,6 +654,7 @@ int pwa_destroy(pwa_ctx *c)
     if (c->stream)
         cudaStreamSynchronize(c->stream);
     free_sample(c);
+    free_res(c);
     dev_free(c->M);
     dev_free(c->amax);
     dev_free(c->d_io);

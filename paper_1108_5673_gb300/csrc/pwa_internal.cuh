@@ -420,6 +420,28 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
                            void *scratch, int grid, int *status, int *done, double *nll,
                            double *grad, cudaStream_t s);
 
+// k_nll_res.cu: free Breit-Wigner masses and widths
+struct ResArgs {
+    int n_waves, n_free, pstride;
+    const float *data;   // [1 + 2N][data_pitch] (+ padding): m, then Re/Im of Y_r or A_a
+    int64_t data_pitch, n_data;
+    const float *mc;
+    int64_t mc_pitch, n_mc;
+    double inv_ngen;
+    const double *V, *mass, *width;  // device
+    double *partials;    // [grid][2][pstride]
+    unsigned *ticket;    // zero on entry, left at zero
+    int *status;         // status bits OR-ed here
+    int *done;           // incremented once (may be null)
+    double *out;         // [1 + 2N + 2R]: nll, dNLL/dV*, dNLL/dM, dNLL/dG
+};
+int res_max_waves();
+int res_max_free();
+size_t res_partials_doubles(int n_waves, int n_free, int grid);
+cudaError_t launch_nll_res(const ResArgs &a, int grid, cudaStream_t s);
+// dst[i] = (float)src[i] (round to nearest)
+cudaError_t launch_to_float(const double *src, int64_t n, float *dst, cudaStream_t s);
+
 // k_nll_table.cu
 int table_max_waves();
 int table_box_events();

@@ -55,6 +55,34 @@ def nll(V, lik):
     return PwaNLL.apply(V, lik)
 
 
+class PwaResNLL(torch.autograd.Function):
+    """NLL(V, masses, widths) with free Breit-Wigner parameters. x is a real
+    tensor (Re V [N], Im V [N], mass [R], width [R]); forward calls
+    pwa_nll_grad_res (the amplitudes of the free waves are recomputed on the
+    device from the stored m and Y on every call, nothing is cached between
+    forward and backward but the gradient itself), backward returns
+    (2 Re g, 2 Im g, dNLL/dM, dNLL/dGamma) with g = dNLL/dV*."""
+
+    @staticmethod
+    def forward(ctx, x, lik):
+        v = x.detach().to("cpu").double().numpy()
+        N, R = lik.n_waves, lik.n_free
+        V = v[:N] + 1j * v[N:2 * N]
+        nll, gV, gM, gW = lik.nll_grad_res(V, v[2 * N:2 * N + R], v[2 * N + R:2 * N + 2 * R])
+        ctx.g = np.concatenate([2.0 * gV.real, 2.0 * gV.imag, gM, gW])
+        ctx.device, ctx.dtype = x.device, x.dtype
+        return torch.tensor(nll, dtype=torch.float64, device=x.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        return grad_out * torch.from_numpy(ctx.g).to(device=ctx.device, dtype=ctx.dtype), None
+
+
+def nll_res(x, lik):
+    """Differentiable NLL with free masses and widths (see PwaResNLL)."""
+    return PwaResNLL.apply(x, lik)
+
+
 def fit_lbfgs(lik, V0, max_iter=500, history=10, grad_tol=None, change_tol=1e-10):
     """Minimise NLL over (Re V, Im V) from the complex start V0.
 

@@ -244,3 +244,46 @@ def multistart_scale(n_data=4_000_000, n_mc_acc=10_000_000, n_waves=32, **kw):
 def start_points(n_waves, k, seed=SEED_STARTS):
     """K starting parameter sets, Re/Im ~ N(0,1): [k, n_waves] complex128."""
     return random_V(n_waves, seed, k)
+
+
+@dataclass
+class ResonanceWorkload:
+    """Samples for fits with free masses and widths of the first n_free waves:
+    the mass variable m, the angular factors Y of the free waves and the full
+    amplitudes of the fixed ones (float32 / complex64, event-major)."""
+    name: str
+    waves: list
+    n_free: int
+    m_data: np.ndarray     # [n_data] float32
+    Y_data: np.ndarray     # [n_data, n_free] complex64
+    Afix_data: np.ndarray  # [n_data, N - n_free] complex64
+    m_mc: np.ndarray
+    Y_mc: np.ndarray
+    Afix_mc: np.ndarray
+    n_gen: int
+    V_true: np.ndarray
+    mass: np.ndarray       # [n_free] the generated masses
+    width: np.ndarray      # [n_free] the generated widths
+
+
+def resonance_workload(name, waves, n_free, n_data, n_mc_acc, seed_data=SEED_DATA, seed_mc=SEED_MC,
+                       seed_v=SEED_VTRUE):
+    """Data-like events from `data_sample_mixture` and accepted MC from
+    `mc_sample`, split into (m, Y of the free waves, amplitudes of the fixed
+    waves); m is rounded to float32."""
+    V = random_V(len(waves), seed_v)
+    ev_d = data_sample_mixture(n_data, waves, V, seed_data)
+    ev_m, n_gen = mc_sample(n_mc_acc, seed_mc)
+    free, fixed = waves[:n_free], waves[n_free:]
+    return ResonanceWorkload(
+        name, waves, n_free,
+        ev_d["m"].astype(np.float32), angular(ev_d, free), amplitudes(ev_d, fixed),
+        ev_m["m"].astype(np.float32), angular(ev_m, free), amplitudes(ev_m, fixed),
+        n_gen, V, np.array([w.mass for w in free]), np.array([w.width for w in free]))
+
+
+def free_resonance_scale(n_data=2_000_000, n_mc_acc=5_000_000, n_waves=20, n_free=4, **kw):
+    """Free masses and widths: 20 waves of which 4 Breit-Wigners are free,
+    2M data events, 5M accepted MC."""
+    return resonance_workload("pwa_2M_events_20_waves_4_free", waves_linear(n_waves), n_free,
+                              n_data, n_mc_acc, **kw)
