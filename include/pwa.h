@@ -181,6 +181,35 @@ int pwa_load_resonance_events(pwa_ctx *ctx, int n_free, const double *m_data, co
 int pwa_nll_grad_res(pwa_ctx *ctx, const double *V, const double *mass, const double *width,
                      double *nll, double *gV, double *gM, double *gW);
 
+/* ---- uneven model batch (Sec. 2: various trial models are fitted) --------
+ * A batch of n_models independent models, each with its own number of waves,
+ * data sample and MC sample, evaluated for K parameter sets per model in one
+ * CUDA-graph launch (captured on the first call for a given K and replayed;
+ * the models' batched tensor-core evaluations run on several streams inside
+ * the graph, so small models overlap). Each model uses the tensor-core form.
+ *
+ *   pwa_batch_create: n_waves[n_models] (each 1..48), max_k per model (1..
+ *                     the tensor-core limit for the largest model), precision
+ *                     PWA_PREC_*, stream as in pwa_config (NULL: owned).
+ *   pwa_batch_load_model: loads model m's samples exactly as pwa_load_events
+ *                     and builds its normalisation matrix.
+ *   pwa_batch_nll_grad: V_all host, models concatenated: model m's [K][n_waves[m]]
+ *                     complex128 block follows model m-1's. nll host [n_models][K];
+ *                     grad host, laid out like V_all (may be NULL).
+ * Returns PWA_EDOMAIN if some set of some model had a non-positive intensity
+ * (that set's nll is +inf, its gradient 0), PWA_ESTATE if a model is not
+ * loaded, PWA_EINVAL for bad sizes or pointers, PWA_ENOTSUP if max_k exceeds
+ * the tensor-core limit of a model's size, PWA_ENOMEM, PWA_ECUDA,
+ * PWA_ETIMEOUT. pwa_batch_last_error gives the message. */
+typedef struct pwa_batch pwa_batch;
+int pwa_batch_create(pwa_batch **out, int device, int n_models, const int *n_waves, int max_k,
+                     int precision, void *stream);
+int pwa_batch_destroy(pwa_batch *b);
+int pwa_batch_load_model(pwa_batch *b, int model, const void *data_amp, int64_t n_data,
+                         const void *mc_amp, int64_t n_mc_acc, double n_mc_gen, int amp_dtype);
+int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, double *grad);
+const char *pwa_batch_last_error(const pwa_batch *b);
+
 /* Direct-form NLL and gradient that allocates no device memory.
  *
  * The paper has no counterpart to this call; it exists for callers that

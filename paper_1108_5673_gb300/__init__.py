@@ -9,10 +9,12 @@ streams.
 
 The compiled library is built by `paper_1108_5673_gb300.build.build()`.
 """
+import numpy as np
+
 from ._abi import (PWA_C64, PWA_C128, PWA_EDOMAIN, PWA_FORM_AMP, PWA_FORM_TABLE, PWA_FORM_TC,
                    PWA_OK, PWA_PREC_BFP8, PWA_PREC_BFP16, PWA_PREC_DEFAULT, PwaError)
 
-__all__ = ["Likelihood", "PwaError", "PWA_FORM_AMP", "PWA_FORM_TABLE", "PWA_FORM_TC", "PWA_OK",
+__all__ = ["Likelihood", "ModelBatch", "PwaError", "PWA_FORM_AMP", "PWA_FORM_TABLE", "PWA_FORM_TC", "PWA_OK",
            "PWA_EDOMAIN", "PWA_C64", "PWA_C128", "PWA_PREC_DEFAULT", "PWA_PREC_BFP16",
            "PWA_PREC_BFP8"]
 
@@ -78,6 +80,51 @@ class Likelihood:
         if self.ctx is not None:
             self._abi.pwa_destroy(self.ctx)
             self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ModelBatch:
+    """Several trial models, each with its own waves and samples, evaluated
+    for K parameter sets per model in one graph launch (tensor-core form)."""
+
+    def __init__(self, n_waves, max_k, device=0, precision=PWA_PREC_DEFAULT, stream=None):
+        from . import _abi
+        self._abi = _abi
+        self.n_waves = list(n_waves)
+        self.max_k = max_k
+        self.b = _abi.pwa_batch_create(device, self.n_waves, max_k, precision, stream)
+        self.last_status = PWA_OK
+
+    def load_model(self, m, data_amp, mc_amp, n_mc_gen):
+        self._abi.pwa_batch_load_model(self.b, m, data_amp, mc_amp, n_mc_gen)
+
+    def nll_grad(self, Vs):
+        """Vs: list over models of [K, n_waves[m]] complex arrays. Returns
+        (nll [n_models, K], list of [K, n_waves[m]] gradients)."""
+        K = Vs[0].shape[0]
+        flat = np.concatenate([np.asarray(V, dtype=np.complex128).reshape(-1) for V in Vs])
+        nll, g, self.last_status = self._abi.pwa_batch_nll_grad(self.b, flat, K, len(self.n_waves))
+        out, o = [], 0
+        for n in self.n_waves:
+            out.append(g[o:o + K * n].reshape(K, n))
+            o += K * n
+        return nll, out
+
+    def close(self):
+        if self.b is not None:
+            self._abi.pwa_batch_destroy(self.b)
+            self.b = None
 
     def __enter__(self):
         return self

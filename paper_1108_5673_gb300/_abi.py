@@ -82,6 +82,11 @@ def load(path=LIB_PATH):
         "pwa_nll_grad_noalloc": ([P, I64, I64, I, P, P, P, P, P, P, P], I),
         "pwa_load_resonance_events": ([P, I, P, P, P, I64, P, P, P, I64, D, I], I),
         "pwa_nll_grad_res": ([P, P, P, P, P, P, P, P], I),
+        "pwa_batch_create": ([ctypes.POINTER(ctypes.c_void_p), I, I, P, I, I, P], I),
+        "pwa_batch_destroy": ([P], I),
+        "pwa_batch_load_model": ([P, I, P, I64, P, I64, D, I], I),
+        "pwa_batch_nll_grad": ([P, P, I, P, P], I),
+        "pwa_batch_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -256,6 +261,50 @@ def pwa_nll_grad_res(ctx, V, mass, width):
     rc = _check(ctx, load().pwa_nll_grad_res(ctx, p(V), p(mass), p(width), p(nll), p(gV), p(gM),
                                              p(gW)), allow=(PWA_EDOMAIN,))
     return float(nll[0]), gV, gM, gW, rc
+
+
+def _bcheck(b, rc, allow=()):
+    if rc != PWA_OK and rc not in allow:
+        msg = load().pwa_batch_last_error(b)
+        raise PwaError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def pwa_batch_create(device, n_waves, max_k, precision=0, stream=None):
+    nw = np.ascontiguousarray(n_waves, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _bcheck(None, load().pwa_batch_create(ctypes.byref(h), device, len(nw),
+                                          nw.ctypes.data_as(ctypes.c_void_p), max_k, precision,
+                                          ctypes.c_void_p(stream) if stream else None))
+    return h
+
+
+def pwa_batch_destroy(b):
+    return load().pwa_batch_destroy(b)
+
+
+def pwa_batch_load_model(b, model, data_amp, mc_amp, n_mc_gen):
+    kinds = {"complex64": PWA_C64, "complex128": PWA_C128}
+    kd = kinds.get(str(data_amp.dtype).replace("torch.", ""))
+    if kd is None or str(mc_amp.dtype) != str(data_amp.dtype):
+        raise ValueError("amplitudes must be complex64 or complex128, both alike")
+    pd, a = _ptr(data_amp)
+    pm, c = _ptr(mc_amp)
+    return _bcheck(b, load().pwa_batch_load_model(b, model, pd, int(data_amp.shape[0]), pm,
+                                                  int(mc_amp.shape[0]), float(n_mc_gen), kd))
+
+
+def pwa_batch_nll_grad(b, V_all, K, n_models, grad=True):
+    """V_all: host complex128, the models' [K][n_waves[m]] blocks concatenated.
+    Returns (nll [n_models][K], grad like V_all or None, status)."""
+    V_all = np.ascontiguousarray(V_all, dtype=np.complex128)
+    nll = np.empty((n_models, K))
+    g = np.empty_like(V_all) if grad else None
+    rc = _bcheck(b, load().pwa_batch_nll_grad(b, V_all.ctypes.data_as(ctypes.c_void_p), K,
+                                              nll.ctypes.data_as(ctypes.c_void_p),
+                                              g.ctypes.data_as(ctypes.c_void_p) if grad else None),
+                 allow=(PWA_EDOMAIN,))
+    return nll, g, rc
 
 
 def pwa_last_error(ctx):

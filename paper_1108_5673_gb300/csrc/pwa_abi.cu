@@ -14,6 +14,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <numeric>
+#include <vector>
 
 #include "pwa_internal.cuh"
 
@@ -591,7 +593,8 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     c->cfg.forms = forms;
     c->N = cfg->n_waves;
     c->xs = cfg->precision == PWA_PREC_BFP8 ? 1 : 2;
-    c->form = (forms & PWA_FORM_AMP) ? PWA_FORM_AMP : PWA_FORM_TABLE;
+    c->form = (forms & PWA_FORM_AMP) ? PWA_FORM_AMP
+              : (forms & PWA_FORM_TABLE) ? PWA_FORM_TABLE : PWA_FORM_TC;
     int rc = PWA_OK;
     auto bail = [&](int code) {
         snprintf(g_create_err, sizeof g_create_err, "%s", c->err);
@@ -836,6 +839,262 @@ int pwa_sync(pwa_ctx *c)
     CK(c, cudaMemsetAsync(c->async_status, 0, sizeof(int), c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
     return status_from_flags(c, flags);
+}
+
+// ---- uneven model batch ------------------------------------------------------
+constexpr int kBatchStreams = 4;
+
+struct pwa_batch {
+    int device = 0;
+    std::vector<pwa_ctx *> models;
+    std::vector<int> n_waves;
+    std::vector<int> order;      // models by sample size, largest first
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t side[kBatchStreams] = {};
+    cudaEvent_t ev_fork = nullptr, ev_join[kBatchStreams] = {};
+    int max_k = 0, sum_n = 0;
+    double *d_buf = nullptr, *h_buf = nullptr;  // V | nll | grad | status
+    cudaGraphExec_t exec = nullptr;
+    int graph_k = 0;
+    char err[512] = {0};
+};
+
+static int bfail(pwa_batch *b, int code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    if (b)
+        vsnprintf(b->err, sizeof b->err, fmt, ap);
+    else
+        vsnprintf(g_create_err, sizeof g_create_err, fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+static void batch_drop_graph(pwa_batch *b)
+{
+    if (b->exec)
+        cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    b->graph_k = 0;
+}
+
+int pwa_batch_destroy(pwa_batch *b)
+{
+    if (!b)
+        return PWA_OK;
+    DeviceGuard g(b->device);
+    if (b->stream)
+        cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    for (pwa_ctx *c : b->models)
+        pwa_destroy(c);
+    for (int s = 0; s < kBatchStreams; ++s) {
+        if (b->side[s])
+            cudaStreamDestroy(b->side[s]);
+        if (b->ev_join[s])
+            cudaEventDestroy(b->ev_join[s]);
+    }
+    if (b->ev_fork)
+        cudaEventDestroy(b->ev_fork);
+    if (b->d_buf)
+        cudaFree(b->d_buf);
+    if (b->h_buf)
+        cudaFreeHost(b->h_buf);
+    if (b->own_stream && b->stream)
+        cudaStreamDestroy(b->stream);
+    delete b;
+    return PWA_OK;
+}
+
+const char *pwa_batch_last_error(const pwa_batch *b) { return b ? b->err : g_create_err; }
+
+int pwa_batch_create(pwa_batch **out, int device, int n_models, const int *n_waves, int max_k,
+                     int precision, void *stream)
+{
+    if (!out || !n_waves || n_models < 1 || n_models > 65536)
+        return bfail(nullptr, PWA_EINVAL, "null out or n_waves, or n_models outside [1, 65536]");
+    *out = nullptr;
+    const int xs = precision == PWA_PREC_BFP8 ? 1 : 2;
+    for (int m = 0; m < n_models; ++m) {
+        if (n_waves[m] < 1 || n_waves[m] > kMaxWaves)
+            return bfail(nullptr, PWA_EINVAL, "model %d: n_waves=%d outside [1, %d]", m, n_waves[m],
+                         kMaxWaves);
+        if (max_k < 1 || max_k > batched_max_k(n_waves[m], xs))
+            return bfail(nullptr, PWA_ENOTSUP, "model %d: max_k=%d outside [1, %d]", m, max_k,
+                         batched_max_k(n_waves[m], xs));
+    }
+    DeviceGuard g(device);
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(nullptr, PWA_ECUDA, "device %d not available", device);
+    }
+    pwa_batch *b = new pwa_batch();
+    b->device = device;
+    b->max_k = max_k;
+    b->n_waves.assign(n_waves, n_waves + n_models);
+    b->sum_n = std::accumulate(b->n_waves.begin(), b->n_waves.end(), 0);
+    auto bail = [&](int code) {
+        snprintf(g_create_err, sizeof g_create_err, "%s", b->err);
+        pwa_batch_destroy(b);
+        return code;
+    };
+    if (stream) {
+        b->stream = static_cast<cudaStream_t>(stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(bfail(b, PWA_ECUDA, "cudaStreamCreate failed"));
+        b->own_stream = true;
+    }
+    for (int s = 0; s < kBatchStreams; ++s)
+        if (cudaStreamCreateWithFlags(&b->side[s], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->ev_join[s], cudaEventDisableTiming) != cudaSuccess)
+            return bail(bfail(b, PWA_ECUDA, "stream or event creation failed"));
+    if (cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+        return bail(bfail(b, PWA_ECUDA, "event creation failed"));
+    for (int m = 0; m < n_models; ++m) {
+        pwa_config cfg{};
+        cfg.n_waves = n_waves[m];
+        cfg.forms = PWA_FORM_TC;
+        cfg.precision = precision;
+        cfg.max_k = max_k;
+        cfg.stream = b->side[m % kBatchStreams];
+        pwa_ctx *c = nullptr;
+        const int rc = pwa_create(&c, device, &cfg);
+        if (rc)
+            return bail(bfail(b, rc, "model %d: %s", m, g_create_err));
+        b->models.push_back(c);
+    }
+    const size_t nd = 4 * (size_t)max_k * b->sum_n + (size_t)n_models * max_k + n_models;
+    if (cudaMalloc((void **)&b->d_buf, nd * sizeof(double)) != cudaSuccess ||
+        cudaMallocHost((void **)&b->h_buf, nd * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(bfail(b, PWA_ENOMEM, "batch io buffers (%zu doubles)", nd));
+    }
+    b->order.resize(n_models);
+    std::iota(b->order.begin(), b->order.end(), 0);
+    *out = b;
+    return PWA_OK;
+}
+
+int pwa_batch_load_model(pwa_batch *b, int model, const void *data_amp, int64_t n_data,
+                         const void *mc_amp, int64_t n_mc_acc, double n_mc_gen, int amp_dtype)
+{
+    if (!b)
+        return PWA_EINVAL;
+    if (model < 0 || model >= (int)b->models.size())
+        return bfail(b, PWA_EINVAL, "model %d outside [0, %zu)", model, b->models.size());
+    pwa_ctx *c = b->models[model];
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->stream);
+    batch_drop_graph(b);
+    int rc = pwa_load_events(c, data_amp, n_data, mc_amp, n_mc_acc, n_mc_gen, amp_dtype);
+    if (!rc)
+        rc = pwa_build_norm(c, nullptr);
+    if (!rc)
+        rc = pwa_set_form(c, PWA_FORM_TC);
+    if (rc)
+        return bfail(b, rc, "model %d: %s", model, c->err);
+    // largest samples first: they set the length of the graph
+    std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) {
+        const pwa_ctx *cx = b->models[x], *cy = b->models[y];
+        return (double)cx->n_data * cx->N > (double)cy->n_data * cy->N;
+    });
+    return PWA_OK;
+}
+
+int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, double *grad)
+{
+    if (!b)
+        return PWA_EINVAL;
+    if (!V_all || !nll)
+        return bfail(b, PWA_EINVAL, "null V_all or nll");
+    if (K < 1 || K > b->max_k)
+        return bfail(b, PWA_EINVAL, "K=%d outside [1, max_k=%d]", K, b->max_k);
+    const int nm = (int)b->models.size();
+    for (int m = 0; m < nm; ++m)
+        if (!b->models[m]->loaded || !b->models[m]->has_norm)
+            return bfail(b, PWA_ESTATE, "model %d has no samples (pwa_batch_load_model)", m);
+    DeviceGuard g(b->device);
+    const size_t nv = 2 * (size_t)K * b->sum_n;  // doubles of V (and of grad)
+    double *dV = b->d_buf, *dN = dV + nv, *dG = dN + (size_t)nm * K;
+    int *dS = reinterpret_cast<int *>(dG + nv);  // [nm][2]: flags, done
+    std::vector<size_t> off(nm);
+    for (int m = 1; m < nm; ++m)
+        off[m] = off[m - 1] + 2 * (size_t)K * b->n_waves[m - 1];
+    if (!b->exec || b->graph_k != K) {
+        batch_drop_graph(b);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+        int rc = PWA_OK;
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(dS, 0, (size_t)nm * 2 * sizeof(int), b->stream);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(b->ev_fork, b->stream);
+        for (int s = 0; s < kBatchStreams && e == cudaSuccess; ++s)
+            e = cudaStreamWaitEvent(b->side[s], b->ev_fork, 0);
+        for (int i = 0; i < nm && e == cudaSuccess && !rc; ++i) {
+            const int m = b->order[i];
+            pwa_ctx *c = b->models[m];
+            c->stream = b->side[i % kBatchStreams];
+            rc = enqueue_eval(c, dV + off[m], K, dN + (size_t)m * K, dG + off[m], dS + 2 * m,
+                              dS + 2 * m + 1);
+            if (rc)
+                bfail(b, rc, "model %d: %s", m, c->err);
+        }
+        for (int s = 0; s < kBatchStreams && e == cudaSuccess; ++s) {
+            e = cudaEventRecord(b->ev_join[s], b->side[s]);
+            if (e == cudaSuccess)
+                e = cudaStreamWaitEvent(b->stream, b->ev_join[s], 0);
+        }
+        const cudaError_t e2 = cudaStreamEndCapture(b->stream, &graph);
+        if (e == cudaSuccess)
+            e = e2;
+        if (e == cudaSuccess && !rc)
+            e = cudaGraphInstantiate(&b->exec, graph, 0);
+        if (graph)
+            cudaGraphDestroy(graph);
+        if (rc || e != cudaSuccess) {
+            cudaGetLastError();
+            b->exec = nullptr;
+            return rc ? rc : bfail(b, PWA_ECUDA, "graph capture: %s", cudaGetErrorString(e));
+        }
+        b->graph_k = K;
+    }
+    double *h = b->h_buf;
+    memcpy(h, V_all, nv * sizeof(double));
+    cudaError_t e = cudaMemcpyAsync(dV, h, nv * sizeof(double), cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaGraphLaunch(b->exec, b->stream);
+    const size_t nout = (size_t)nm * K + (grad ? nv : 0);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + nv, dN, nout * sizeof(double), cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + nv + (size_t)nm * K + nv, dS, (size_t)nm * 2 * sizeof(int),
+                            cudaMemcpyDeviceToHost, b->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bfail(b, PWA_ECUDA, "batch launch: %s", cudaGetErrorString(e));
+    }
+    const int *hs = reinterpret_cast<const int *>(h + nv + (size_t)nm * K + nv);
+    int flags = 0;
+    for (int m = 0; m < nm; ++m) {
+        if (hs[2 * m + 1] != K)
+            return bfail(b, PWA_ETIMEOUT, "model %d: only %d of %d evaluations finished", m,
+                         hs[2 * m + 1], K);
+        flags |= hs[2 * m];
+    }
+    memcpy(nll, h + nv, (size_t)nm * K * sizeof(double));
+    if (grad)
+        memcpy(grad, h + nv + (size_t)nm * K, nv * sizeof(double));
+    if (flags & FLAG_TIMEOUT)
+        return bfail(b, PWA_ETIMEOUT, "a device-side wait timed out; results are invalid");
+    if (flags & FLAG_DOMAIN)
+        return bfail(b, PWA_EDOMAIN, "an intensity was not positive and finite (nll = +inf)");
+    return PWA_OK;
 }
 
 }  // extern "C"
