@@ -1,17 +1,28 @@
 """Throughput of the partial wave analysis likelihood hot path on GB300.
 
-One step = one evaluation of NLL(V) and its gradient dNLL/dV* (Eq. 3) over
-the whole resident sample: 1M data events x 20 waves, with the normalisation
-matrix built once from 5M accepted MC events. Inputs are seeded synthetic
-J/psi -> gamma K+ K- shaped samples (no experiment data is available).
+Default workload (`--workload direct`, the headline): one step = one
+evaluation of NLL(V) and its gradient dNLL/dV* (Eq. 3) over the whole
+resident sample, 1M data events x 20 waves, direct amplitude form, with the
+normalisation matrix built once from 5M accepted MC events. Inputs are seeded
+synthetic J/psi -> gamma K+ K- shaped samples (no experiment data exists here).
+
+Other workloads (one JSON line each, same keys):
+  table   the same sample and evaluation in the per-event table form (Sec. 2)
+  tc      K = 256 starting parameter sets at once on the tensor cores:
+          4M events x 32 waves, M from 10M accepted MC (--precision bfp16|bfp8)
+  res     free masses and widths of 4 of 20 Breit-Wigner waves: 2M data events,
+          5M accepted MC, amplitudes recomputed every call
+  models  64 trial models (n_waves 8..48, 100k..2M data events, MC 2x data),
+          K = 16 parameter sets each, one graph launch per step
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+                  [--workload direct|table|tc|res|models]
 
-Prints one JSON line. `value` is device-timed (CUDA events on the launching
-stream, L2 flushed between steps); `e2e` times the public host call
-(V in from pinned memory, NLL and gradient back) with a wall clock. With
-N > 1 (torchrun) every rank runs an independent replica on its own GPU
-(weak scaling, no collective on the data path); rank 0 prints.
+`value` is device-timed (CUDA events on the launching stream; L2 flushed
+between steps where the inputs fit in it); `e2e` times the public host call
+(inputs from host memory, results back) with a wall clock. With N > 1
+(torchrun) every rank runs an independent replica on its own GPU (weak
+scaling, no collective on the data path); rank 0 prints.
 """
 from __future__ import annotations
 
@@ -33,19 +44,23 @@ METRIC = "NLL+grad evals/s (1M events, 20 waves, K starts); % HBM / tensor roofl
 UNIT = "evals/s"
 N_WAVES, N_DATA, N_MC = 20, 1_000_000, 5_000_000
 WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M accepted MC, K=1 per evaluation"
-# DRAM bytes (read + write) per launch of the timed kernel from one ncu capture
-# (profiles/nll_amp_1M_20waves.md); None once the kernel has changed since.
-KERNEL = "nll_amp_kernel<20, 2>"
-TRAFFIC_BYTES = 160.145664e6 + 4.291840e6
+# DRAM bytes (read + write) per launch of the timed kernel from one ncu
+# capture (profiles/), or None where the kernel changed since the capture.
+TRAFFIC = {"direct": None, "table": None, "tc": None, "res": None, "models": None}
+KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
+           "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
+           "models": "batched_kernel<F, 2> (all sizes)"}
+DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100}
 
 
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return p["hbm_gbs"], "measured"
+        return {"hbm": p["hbm_gbs"], "bf16": p["bf16_tflops"],
+                "bf16_sustained": p["bf16_tflops_sustained"], "kind": "measured"}
     except Exception:
-        return 6800.0, "fallback"
+        return {"hbm": 6800.0, "bf16": 1900.0, "bf16_sustained": 1700.0, "kind": "fallback"}
 
 
 def start_clock_sampler(path):
@@ -82,18 +97,186 @@ def summarise_clocks(path, gpu_index):
             "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_baseline(wl, M, V, budget_s=12.0):
-    """The FP64 oracle as it stands (single-threaded C) on the full sample."""
-    import oracle
-    oracle.nll_amp(wl.A_data, M, V)  # warm (loads the library)
+def timed_oracle(fn, budget_s):
+    """Calls fn() until budget_s has passed (at least twice); seconds per call."""
+    fn()
     t0, n = time.perf_counter(), 0
     while time.perf_counter() - t0 < budget_s or n < 2:
-        oracle.nll_amp(wl.A_data, M, V)
+        fn()
         n += 1
-    dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d full NLL+grad evaluations of the same 1M-event, 20-wave sample "
-                      "(M precomputed), FP64 C oracle, 1 thread" % n}
+    return (time.perf_counter() - t0) / n, n
+
+
+# ---- workloads: each sets up the library and returns a Job ---------------------
+
+class Job:
+    """step(): enqueue one step on `stream` (device-resident inputs);
+    host_step(): one public host call (inputs from host memory, results back)."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def job_direct(pwa, torch, stream, local, rank, form="amp"):
+    import synth
+    wl = synth.paper_scale()
+    V = synth.start_points(N_WAVES, 1, seed=synth.SEED_STARTS + rank)[0]
+    forms = pwa.PWA_FORM_AMP | (pwa.PWA_FORM_TABLE if form == "table" else 0)
+    L = pwa.Likelihood(N_WAVES, device=local, forms=forms, max_k=1, stream=stream.cuda_stream)
+    L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+    t0 = time.perf_counter()
+    L.build_norm()
+    build_norm_s = time.perf_counter() - t0
+    if form == "table":
+        L.set_form(pwa.PWA_FORM_TABLE)
+    dV = torch.from_numpy(V[None]).cuda()
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    dg = torch.empty(1, N_WAVES, dtype=torch.complex128, device="cuda")
+    Vh = V[None].copy()
+
+    def cpu_baseline():
+        import oracle
+        Mo = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen)
+        if form == "table":
+            n = 100_000
+            T = oracle.table(wl.A_data[:n])
+            dt, k = timed_oracle(lambda: oracle.nll_table(T, Mo, V), 12.0)
+            return {"value": 1.0 / (dt * N_DATA / n), "unit": UNIT, "cores": 1, "kind": "oracle",
+                    "sample": "%d table-form NLL+grad evaluations of the first 100k events (FP64 C "
+                              "oracle, 1 thread), scaled to the 1M-event sample" % k}
+        dt, k = timed_oracle(lambda: oracle.nll_amp(wl.A_data, Mo, V), 12.0)
+        return {"value": 1.0 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d full NLL+grad evaluations of the same 1M-event, 20-wave sample "
+                          "(M precomputed), FP64 C oracle, 1 thread" % k}
+
+    table = form == "table"
+    return Job(
+        name=form if table else "direct", lib=L,
+        step=lambda: L.nll_grad_async(dV, dn, dg), host_step=lambda: L.nll_grad(Vh),
+        sync=L.sync, evals_per_step=1, launches_per_step=1, flush=True,
+        workload=("1M data events x 20 waves (FP32 per-event table of 400 floats, table form), "
+                  "M from 5M accepted MC, K=1 per evaluation") if table else WORKLOAD,
+        config={"n_waves": N_WAVES, "n_data": N_DATA, "n_mc_acc": N_MC, "n_mc_gen": wl.n_gen,
+                "K": 1, "form": form, "build_norm_s": build_norm_s},
+        roof={"bound": "hbm", "bytes": (4.0 * N_WAVES ** 2 if table else 8.0 * N_WAVES) * N_DATA},
+        dtype="f32", h2d=16 * N_WAVES + 8, d2h=8 + 16 * N_WAVES + 8, cpu_baseline=cpu_baseline)
+
+
+def job_tc(pwa, torch, stream, local, rank, precision="bfp16"):
+    import synth
+    N, n, n_mc, K = 32, 4_000_000, 10_000_000, 256
+    wl = synth.multistart_scale()
+    Vs = synth.start_points(N, K, seed=synth.SEED_STARTS + rank) * 2.0
+    prec = pwa.PWA_PREC_BFP8 if precision == "bfp8" else pwa.PWA_PREC_BFP16
+    L = pwa.Likelihood(N, device=local, forms=pwa.PWA_FORM_TC, max_k=K, stream=stream.cuda_stream,
+                       precision=prec)
+    L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+    t0 = time.perf_counter()
+    L.build_norm()
+    build_norm_s = time.perf_counter() - t0
+    L.set_form(pwa.PWA_FORM_TC)
+    dV = torch.from_numpy(Vs).cuda()
+    dn = torch.empty(K, dtype=torch.float64, device="cuda")
+    dg = torch.empty(K, N, dtype=torch.complex128, device="cuda")
+
+    def cpu_baseline():
+        import oracle
+        sub = 200_000
+        A = wl.A_data[:sub]
+        Mo = oracle.norm_matrix_blas(wl.A_mc[:1_000_000], wl.n_gen)
+        dt, k = timed_oracle(lambda: oracle.nll_amp(A, Mo, Vs[0]), 12.0)
+        return {"value": 1.0 / (dt * n / sub), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d NLL+grad evaluations of one parameter set on the first 200k of the "
+                          "4M events (FP64 C oracle, 1 thread), scaled to one evaluation of the "
+                          "full sample" % k}
+
+    return Job(
+        name="tc", lib=L, step=lambda: L.nll_grad_async(dV, dn, dg), host_step=lambda: L.nll_grad(Vs),
+        sync=L.sync, evals_per_step=K, launches_per_step=2 * 3, flush=False,
+        workload="4M data events x 32 waves, K=256 parameter sets per call on the tensor cores "
+                 "(%s amplitudes, 24-bit V slices), M from 10M accepted MC" % precision,
+        config={"n_waves": N, "n_data": n, "n_mc_acc": n_mc, "n_mc_gen": wl.n_gen, "K": K,
+                "form": "tc", "precision": precision, "build_norm_s": build_norm_s},
+        roof={"bound": "tensor", "flops": 16.0 * N * K * n},
+        dtype="bf16", h2d=16 * N * K, d2h=8 * K + 16 * N * K, cpu_baseline=cpu_baseline)
+
+
+def job_res(pwa, torch, stream, local, rank):
+    import synth
+    N, R, n, n_mc = 20, 4, 2_000_000, 5_000_000
+    wl = synth.free_resonance_scale()
+    V = synth.start_points(N, 1, seed=synth.SEED_STARTS + rank)[0]
+    mass, width = wl.mass * 1.01, wl.width * 0.95
+    L = pwa.Likelihood(N, device=local, max_k=1, stream=stream.cuda_stream)
+    L.load_resonance_events(wl)
+
+    def cpu_baseline():
+        import oracle
+        sd, sm = 100_000, 250_000
+        args = (wl.m_data[:sd].astype(np.float64), wl.Y_data[:sd], wl.Afix_data[:sd],
+                wl.m_mc[:sm].astype(np.float64), wl.Y_mc[:sm], wl.Afix_mc[:sm], float(wl.n_gen))
+        dt, k = timed_oracle(lambda: oracle.nll_res(*args, V, mass, width), 12.0)
+        return {"value": 1.0 / (dt * (n + n_mc) / (sd + sm)), "unit": UNIT, "cores": 1,
+                "kind": "oracle",
+                "sample": "%d free-resonance NLL+gradient evaluations on the first 100k data and "
+                          "250k MC events (FP64 C oracle, 1 thread), scaled to the full 2M + 5M "
+                          "events" % k}
+
+    step = lambda: L.nll_grad_res(V, mass, width)
+    return Job(
+        name="res", lib=L, step=step, host_step=step, sync=lambda: L.last_status,
+        evals_per_step=1, launches_per_step=1, flush=False,
+        workload="free masses and widths of 4 of 20 Breit-Wigner waves: 2M data + 5M accepted MC "
+                 "events (m, Y of the free waves, fixed amplitudes; FP32), BW recomputed per call",
+        config={"n_waves": N, "n_free": R, "n_data": n, "n_mc_acc": n_mc, "n_mc_gen": wl.n_gen,
+                "K": 1, "form": "res"},
+        roof={"bound": "hbm", "bytes": 4.0 * (1 + 2 * N) * (n + n_mc)},
+        dtype="f32", h2d=16 * N + 16 * R + 8, d2h=8 + 16 * N + 16 * R, cpu_baseline=cpu_baseline,
+        note="value and e2e both time the host call (its copies are a few hundred bytes)")
+
+
+def job_models(pwa, torch, stream, local, rank):
+    import synth
+    spec = synth.model_batch_spec()
+    K = 16
+    B = pwa.ModelBatch([s[0] for s in spec], K, device=local, stream=stream.cuda_stream)
+    t0 = time.perf_counter()
+    for j, (nw, nd, seed) in enumerate(spec):
+        A_d, A_m, n_gen = synth.torch_mixture_workload(synth.waves_linear(nw), nd, 2 * nd, seed + rank)
+        B.load_model(j, A_d, A_m, n_gen)
+        del A_d, A_m
+    torch.cuda.empty_cache()
+    load_s = time.perf_counter() - t0
+    Vs = [synth.start_points(s[0], K, seed=s[2] + 7) * 2.0 for s in spec]
+
+    def cpu_baseline():
+        import oracle
+        nw, nd, seed = spec[0]
+        A_d, A_m, n_gen = synth.torch_mixture_workload(synth.waves_linear(nw), 50_000, 100_000, seed)
+        A_d, A_m = A_d.cpu().numpy(), A_m.cpu().numpy()
+        Mo = oracle.norm_matrix(A_m, n_gen)
+        dt, k = timed_oracle(lambda: oracle.nll_amp(A_d, Mo, Vs[0][0]), 10.0)
+        per_wave_event = dt / (50_000 * nw)
+        t_call = sum(K * s[0] * s[1] for s in spec) * per_wave_event
+        return {"value": 64 * K / t_call, "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d NLL+grad evaluations of model 0 (%d waves) on 50k events (FP64 C "
+                          "oracle, 1 thread), scaled by waves x events to 16 sets of each of the "
+                          "64 models" % (k, nw)}
+
+    return Job(
+        name="models", lib=B, step=lambda: B.nll_grad(Vs), host_step=lambda: B.nll_grad(Vs),
+        sync=lambda: B.last_status, evals_per_step=64 * K, launches_per_step=64 * 3,
+        flush=False,
+        workload="64 trial models (n_waves 8..48, 100k..2M data events each, MC 2x data, 63.4M "
+                 "data events in all), K=16 parameter sets per model, one CUDA-graph launch",
+        config={"n_models": 64, "K": K, "n_data_total": sum(s[1] for s in spec),
+                "n_waves_mean": float(np.mean([s[0] for s in spec])), "form": "tc",
+                "precision": "bfp16", "load_and_norm_s": load_s},
+        roof={"bound": "tensor", "flops": float(sum(16.0 * s[0] * K * s[1] for s in spec))},
+        dtype="bf16", h2d=16 * K * sum(s[0] for s in spec),
+        d2h=8 * 64 * K + 16 * K * sum(s[0] for s in spec), cpu_baseline=cpu_baseline,
+        note="value and e2e both time the host call (V of all models in, results out, ~0.5 MB "
+             "each way)")
 
 
 def run_reference(args):
@@ -126,17 +309,20 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models"])
+    ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS[args.workload] if args.impl == "gb300" else 3
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
 
     import torch
-    import synth
     import paper_1108_5673_gb300 as pwa
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -148,20 +334,18 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    wl = synth.paper_scale()
-    V = synth.start_points(N_WAVES, 1, seed=synth.SEED_STARTS + rank)[0]
     # one explicit stream for the library, the L2 flush and the timing events
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    L = pwa.Likelihood(N_WAVES, device=local, max_k=1, stream=stream.cuda_stream)
-    L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
-    t0 = time.perf_counter()
-    M = L.build_norm()
-    build_norm_s = time.perf_counter() - t0
+    if args.workload in ("direct", "table"):
+        job = job_direct(pwa, torch, stream, local, rank, form="table" if args.workload == "table" else "amp")
+    elif args.workload == "tc":
+        job = job_tc(pwa, torch, stream, local, rank, args.precision)
+    elif args.workload == "res":
+        job = job_res(pwa, torch, stream, local, rank)
+    else:
+        job = job_models(pwa, torch, stream, local, rank)
 
-    dV = torch.from_numpy(V[None]).cuda()
-    dn = torch.empty(1, dtype=torch.float64, device="cuda")
-    dg = torch.empty(1, N_WAVES, dtype=torch.complex128, device="cuda")
     flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")  # 256 MB > L2
 
     def evict_l2(i):
@@ -171,9 +355,11 @@ def main():
         return flush.sum()
 
     for i in range(args.warmup):
-        evict_l2(i)
-        L.nll_grad_async(dV, dn, dg)
-    assert L.sync() == pwa.PWA_OK
+        if job.flush:
+            evict_l2(i)
+        job.step()
+    torch.cuda.synchronize()
+    assert job.sync() in (pwa.PWA_OK,), "warm-up status"
 
     clock_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
                               else ".", "bench_clocks_rank%d.csv" % rank)
@@ -185,30 +371,31 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     for i in range(args.steps):
-        evict_l2(i)                      # untimed
+        if job.flush:
+            evict_l2(i)                  # untimed
         starts[i].record(stream)
-        L.nll_grad_async(dV, dn, dg)
+        job.step()
         ends[i].record(stream)
     torch.cuda.synchronize()
-    status = L.sync()
+    status = job.sync()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     # back-to-back (no flush), for reference only
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nb = max(3, args.steps // 2)
     e0.record(stream)
-    for _ in range(args.steps):
-        L.nll_grad_async(dV, dn, dg)
+    for _ in range(nb):
+        job.step()
     e1.record(stream)
     torch.cuda.synchronize()
-    b2b_ms = e0.elapsed_time(e1) / args.steps
-    # end to end through the public host call (V in, NLL + gradient out)
-    Vh = V[None].copy()
+    b2b_ms = e0.elapsed_time(e1) / nb
+    # end to end through the public host call
     for _ in range(3):
-        L.nll_grad(Vh)
+        job.host_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        L.nll_grad(Vh)
+        job.host_step()
     e2e_s = time.perf_counter() - t0
     if sampler:
         sampler.terminate()
@@ -222,43 +409,50 @@ def main():
         total_ms_max, e2e_max = float(t[0]), float(t[1])
         dist.barrier()
     if rank != 0:
-        L.close()
+        job.lib.close()
         if dist:
             dist.destroy_process_group()
         return
 
-    value = world * args.steps / (total_ms_max / 1e3)
-    e2e_value = world * args.steps / e2e_max
+    ev = job.evals_per_step
+    value = world * ev * args.steps / (total_ms_max / 1e3)
+    e2e_value = world * ev * args.steps / e2e_max
     avg_s = total_ms / args.steps / 1e3
-    alg_bytes = 8.0 * N_WAVES * N_DATA
-    peak, peak_kind = measured_peaks()
-    achieved = alg_bytes / avg_s / 1e9
+    peaks = measured_peaks()
+    if job.roof["bound"] == "hbm":
+        achieved = job.roof["bytes"] / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm"], "algorithmic_bytes_per_launch": job.roof["bytes"]}
+    else:
+        achieved = job.roof["flops"] / avg_s / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16"], "unit": "TFLOP/s",
+                "frac": achieved / peaks["bf16"], "algorithmic_flops_per_step": job.roof["flops"],
+                "peak_note": "bf16 burst; the step time includes the small prep and final kernels"}
+    roof.update({"traffic": TRAFFIC[job.name], "peak_kind": peaks["kind"], "kernel": KERNELS[job.name]})
+    config = {"workload": job.workload}
+    config.update(job.config)
+    config.update({"l2": "flushed between timed steps (256 MB write + read back, untimed)"
+                   if job.flush else "inputs larger than L2 (129 MB), no flush",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "ms_per_step_back_to_back": b2b_ms})
+    if getattr(job, "note", None):
+        config["note"] = job.note
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "n_waves": N_WAVES, "n_data": N_DATA, "n_mc_acc": N_MC,
-                   "n_mc_gen": wl.n_gen, "K": 1, "form": "amp",
-                   "l2": "flushed between timed steps (256 MB write + read back, untimed)",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "ms_per_step_back_to_back": b2b_ms, "build_norm_s": build_norm_s},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES, "peak_kind": peak_kind,
-                     "kernel": KERNEL,
-                     "algorithmic_bytes_per_launch": alg_bytes},
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 * N_WAVES + 8,
-                "d2h_bytes_per_step": 8 + 16 * N_WAVES + 8},
-        "gpu_launches": args.steps,
+        "scaling": "weak", "vs_baseline": None, "dtype": job.dtype, "data": "synthetic",
+        "config": config, "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": job.h2d,
+                "d2h_bytes_per_step": job.d2h},
+        "gpu_launches": job.launches_per_step * args.steps,
         "status": status,
     }
     if sampler:
         out["clocks"] = summarise_clocks(clock_path, local)
     if not args.no_cpu_baseline:
-        import oracle
-        Mo = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen)
-        out["cpu_baseline"] = cpu_oracle_baseline(wl, Mo, V)
+        out["cpu_baseline"] = job.cpu_baseline()
     print(json.dumps(out))
-    L.close()
+    job.lib.close()
     if dist:
         dist.destroy_process_group()
 

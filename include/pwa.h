@@ -254,6 +254,23 @@ int pwa_nll_grad_noalloc(const float *d_planes, int64_t plane_pitch, int64_t n_e
                          int n_waves, const float *d_amax, const double *d_M, const double *d_V,
                          double *d_nll, double *d_grad, int *d_status, void *stream);
 
+/* Autotuner. Times the launch variants of the context's current form on its
+ * loaded sample (a few evaluations of a fixed parameter set each, CUDA events
+ * on the context's stream), and of the free-resonance kernel if resonance
+ * samples are loaded; applies the fastest; records each choice in a JSON
+ * cache file, one line per key (device name, SM count, form, n_waves), and
+ * applies a cached choice instead of timing when the key is present. The
+ * variants: the direct form's consumer groups per block (2 or 3 groups of
+ * four warps, where both fit), the free-resonance kernel's blocks per SM
+ * (1 to 3). The table and tensor-core forms have one launch shape each (set
+ * by their shared- and tensor-memory budgets) and are reported as such.
+ *   cache_path  file to read and update (NULL: time every call, no file)
+ *   choice      receives a one-line summary (may be NULL), choice_len bytes
+ * Results of the evaluation calls do not depend on the choice beyond float
+ * summation order. Errors: PWA_ESTATE (nothing loaded), PWA_ECUDA, PWA_EINVAL
+ * (an unreadable or unwritable cache file). */
+int pwa_autotune(pwa_ctx *ctx, const char *cache_path, char *choice, int choice_len);
+
 /* Message describing the last error on ctx ("" if none); valid until the
  * next call on ctx. A NULL ctx gives the message of the last failed
  * pwa_create on this thread. */

@@ -69,6 +69,11 @@ class Likelihood:
         nll, gV, gM, gW, self.last_status = self._abi.pwa_nll_grad_res(self.ctx, V, mass, width)
         return nll, gV, gM, gW
 
+    def autotune(self, cache_path=None):
+        """Pick the fastest launch variants on the loaded sample (see
+        pwa_autotune); returns a one-line summary of the choices."""
+        return self._abi.pwa_autotune(self.ctx, cache_path)
+
     def nll_grad_async(self, d_V, d_nll, d_grad=None):
         self._abi.pwa_nll_grad_async(self.ctx, d_V, d_V.shape[0], d_nll, d_grad)
 

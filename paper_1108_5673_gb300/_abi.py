@@ -87,6 +87,7 @@ def load(path=LIB_PATH):
         "pwa_batch_load_model": ([P, I, P, I64, P, I64, D, I], I),
         "pwa_batch_nll_grad": ([P, P, I, P, P], I),
         "pwa_batch_last_error": ([P], ctypes.c_char_p),
+        "pwa_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -305,6 +306,13 @@ def pwa_batch_nll_grad(b, V_all, K, n_models, grad=True):
                                               g.ctypes.data_as(ctypes.c_void_p) if grad else None),
                  allow=(PWA_EDOMAIN,))
     return nll, g, rc
+
+
+def pwa_autotune(ctx, cache_path=None):
+    """Returns the one-line summary of the choices applied."""
+    buf = ctypes.create_string_buffer(512)
+    _check(ctx, load().pwa_autotune(ctx, cache_path.encode() if cache_path else None, buf, 512))
+    return buf.value.decode()
 
 
 def pwa_last_error(ctx):

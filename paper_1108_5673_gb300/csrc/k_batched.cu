@@ -235,7 +235,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *sR = base + L.r_off;
     const int n_my =
         (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const int steps = n_my * NCH * 2;
+    // half chunks per tile that hold parameter sets (a last half past K is skipped)
+    const int HPT = (a.K + kHS - 1) / kHS;
+    const int steps = n_my * HPT;
 
     if (threadIdx.x == 0) {
         mbar_init(&w_full, 1);
@@ -319,7 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             bool ok = mbar_wait(&w_full, 0);
             for (int q = 0; q < steps && ok; ++q) {
-                const int j = q / (2 * NCH), ch = q % (2 * NCH), c = ch >> 1, h = ch & 1, s = j % kXS;
+                const int j = q / HPT, ch = q % HPT, c = ch >> 1, h = ch & 1, s = j % kXS;
                 if (ch == 0 && !mbar_wait(&x_full[s], (j / kXS) & 1)) {
                     ok = false;
                     break;
@@ -348,11 +350,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 umma_commit(&s_full);
-                if (h == 0 && q >= 2)
-                    ok = gemm2((q >> 1) - 1);
+                if (h == 0 && q >= 1)  // the previous chunk step is complete
+                    ok = gemm2(j * NCH + c - 1);
             }
             if (ok && steps > 0)
-                ok = gemm2((steps >> 1) - 1);
+                ok = gemm2(n_my * NCH - 1);
             umma_commit(&g_done);
             // tensor memory is released only after every product has finished
             if (!mbar_wait(&g_done, 0))
@@ -368,7 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const f2 inv256 = pk2(1.0f / 256.0f, 1.0f / 256.0f);
         bool ok = true;
         for (int q = 0; q < steps && ok; ++q) {
-            const int j = q / (2 * NCH), ch = q % (2 * NCH), h = ch & 1, cq = q >> 1;
+            const int j = q / HPT, ch = q % HPT, h = ch & 1, cq = j * NCH + (ch >> 1);
+            const bool last_half = h == 1 || ch == HPT - 1;
             if (!mbar_wait(&s_full, q & 1)) {
                 ok = false;
                 break;
@@ -463,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             *reinterpret_cast<uint4 *>(rrow + sw128(e, 32 * sg)) = make_uint4(rpk[0], rpk[1], rpk[2], rpk[3]);
             *reinterpret_cast<uint4 *>(rrow + sw128(e, 32 * sg + 16)) =
                 make_uint4(rpk[4], rpk[5], rpk[6], rpk[7]);
-            if (h == 1) {
+            if (last_half) {
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0)

@@ -530,11 +530,11 @@ constexpr bool finalize_fits(int grid)
 
 template <int N>
 cudaError_t launch_n(const CUtensorMap *map, const EvalArgs &a, int grid, int n_tiles,
-                     int *work_flags, cudaStream_t s)
+                     int *work_flags, cudaStream_t s, int groups)
 {
     if (!finalize_fits<N, 2>(grid))
         return cudaErrorInvalidConfiguration;
-    const int g = amp_groups() ? amp_groups() : (N <= 12 ? 3 : 2);
+    const int g = groups ? groups : amp_groups() ? amp_groups() : (N <= 12 ? 3 : 2);
     if constexpr (AmpCfg<N, 3>::FITS) {
         if (g == 3 && finalize_fits<N, 3>(grid)) {
             nll_amp_kernel<N, 3><<<grid, AmpCfg<N, 3>::THREADS, AmpCfg<N, 3>::SMEM, s>>>(
@@ -601,13 +601,37 @@ size_t amp_partials_doubles(int n_waves, int num_sms)
 }
 
 cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
-                           int num_sms, cudaStream_t s)
+                           int num_sms, cudaStream_t s, int groups)
 {
-    return launch_nll_amp_grid(amp, map, a, amp_grid(amp.n_waves, num_sms), s);
+    return launch_nll_amp_grid(amp, map, a, amp_grid(amp.n_waves, num_sms), s, groups);
+}
+
+template <int N>
+bool groups3_fit()
+{
+    if constexpr (AmpCfg<N, 3>::FITS)
+        return true;
+    return false;
+}
+
+bool amp_groups3_available(int n_waves)
+{
+    switch (pad_waves(n_waves)) {
+    case 4: return groups3_fit<4>();
+    case 8: return groups3_fit<8>();
+    case 12: return groups3_fit<12>();
+    case 16: return groups3_fit<16>();
+    case 20: return groups3_fit<20>();
+    case 24: return groups3_fit<24>();
+    case 32: return groups3_fit<32>();
+    case 40: return groups3_fit<40>();
+    case 48: return groups3_fit<48>();
+    }
+    return false;
 }
 
 cudaError_t launch_nll_amp_grid(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
-                                int grid, cudaStream_t s)
+                                int grid, cudaStream_t s, int groups)
 {
     const int te = amp_box_events(amp.n_waves);
     if (te <= 0)
@@ -615,15 +639,15 @@ cudaError_t launch_nll_amp_grid(const Planes &amp, const CUtensorMap *map, const
     const int n_tiles = (int)((amp.n + te - 1) / te);
     int *work_flags = amp_scratch(a.partials, grid).flags;
     switch (pad_waves(amp.n_waves)) {
-    case 4: return launch_n<4>(map, a, grid, n_tiles, work_flags, s);
-    case 8: return launch_n<8>(map, a, grid, n_tiles, work_flags, s);
-    case 12: return launch_n<12>(map, a, grid, n_tiles, work_flags, s);
-    case 16: return launch_n<16>(map, a, grid, n_tiles, work_flags, s);
-    case 20: return launch_n<20>(map, a, grid, n_tiles, work_flags, s);
-    case 24: return launch_n<24>(map, a, grid, n_tiles, work_flags, s);
-    case 32: return launch_n<32>(map, a, grid, n_tiles, work_flags, s);
-    case 40: return launch_n<40>(map, a, grid, n_tiles, work_flags, s);
-    case 48: return launch_n<48>(map, a, grid, n_tiles, work_flags, s);
+    case 4: return launch_n<4>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 8: return launch_n<8>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 12: return launch_n<12>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 16: return launch_n<16>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 20: return launch_n<20>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 24: return launch_n<24>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 32: return launch_n<32>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 40: return launch_n<40>(map, a, grid, n_tiles, work_flags, s, groups);
+    case 48: return launch_n<48>(map, a, grid, n_tiles, work_flags, s, groups);
     }
     return cudaErrorInvalidValue;
 }

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <atomic>
 #include <numeric>
+#include <string>
 #include <vector>
 
 #include "pwa_internal.cuh"
@@ -40,6 +41,8 @@ struct pwa_ctx {
     void *xbf = nullptr;    // BF16 slices [2F][pitch] of the data (tensor-core form)
     long long *xsum = nullptr;  // sum of the per-event exponents (inside xbf)
     int xs = 2;                 // BF16 slices of the amplitudes (tensor-core form)
+    int tune_groups = 0;        // direct form: consumer groups (0 = default rule)
+    int tune_res_cps = 1;       // free-resonance kernel: blocks per SM
     // free-resonance form
     float *res_data = nullptr, *res_mc = nullptr;
     int64_t res_data_pitch = 0, res_mc_pitch = 0, res_n_data = 0, res_n_mc = 0;
@@ -334,7 +337,7 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         a.grad = dgrad ? dgrad + (size_t)2 * N * k : nullptr;
         cudaError_t e = cudaSuccess;
         if (c->form == PWA_FORM_AMP)
-            e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream);
+            e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream, c->tune_groups);
         else if (c->form == PWA_FORM_TABLE)
             e = launch_nll_table(c->n_data, N, &c->table_map, a, c->tmax, c->num_sms, c->stream);
         else
@@ -437,7 +440,8 @@ int pwa_version(void) { return 100; }
 
 const char *pwa_last_error(const pwa_ctx *ctx) { return ctx ? ctx->err : g_create_err; }
 
-static size_t res_grid(const pwa_ctx *c) { return (size_t)c->num_sms; }
+constexpr int kResMaxBlocksPerSm = 3;
+static size_t res_grid(const pwa_ctx *c) { return (size_t)c->num_sms * c->tune_res_cps; }
 
 int pwa_load_resonance_events(pwa_ctx *c, int n_free, const double *m_data, const void *Y_data,
                               const void *Afix_data, int64_t n_data, const double *m_mc,
@@ -470,7 +474,7 @@ int pwa_load_resonance_events(pwa_ctx *c, int n_free, const double *m_data, cons
     if (!rc)
         rc = load_res_sample(c, n_free, m_mc, Y_mc, Afix_mc, n_mc_acc, amp_dtype, &c->res_mc,
                              &c->res_mc_pitch);
-    const size_t npart = res_partials_doubles(N, n_free, (int)res_grid(c));
+    const size_t npart = res_partials_doubles(N, n_free, c->num_sms * kResMaxBlocksPerSm);
     const size_t nio = 4 * (size_t)N + 4 * (size_t)n_free + 2;
     if (!rc)
         rc = dev_alloc(c, (void **)&c->d_res, (npart + 1 + nio) * sizeof(double), "resonance io");
@@ -506,7 +510,7 @@ int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const doub
         return fail(c, PWA_ESTATE, "pwa_load_resonance_events must come first");
     DeviceGuard g(c->device);
     const int N = c->N, R = c->res_R;
-    const size_t npart = res_partials_doubles(N, R, (int)res_grid(c));
+    const size_t npart = res_partials_doubles(N, R, c->num_sms * kResMaxBlocksPerSm);
     double *d_io = c->d_res + npart + 1, *h = c->h_res;
     // io: V [2N] | mass [R] | width [R] | status, done | out [1 + 2N + 2R]
     memcpy(h, V, 2 * N * sizeof(double));
@@ -1094,6 +1098,236 @@ int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, do
         return bfail(b, PWA_ETIMEOUT, "a device-side wait timed out; results are invalid");
     if (flags & FLAG_DOMAIN)
         return bfail(b, PWA_EDOMAIN, "an intensity was not positive and finite (nll = +inf)");
+    return PWA_OK;
+}
+
+// ---- autotuner -------------------------------------------------------------------
+// Cache file: a JSON object, one entry per line, "key": {"choice": C, "us": T}.
+extern "C++" {
+
+static std::string tune_key(const pwa_ctx *c, const char *what)
+{
+    cudaDeviceProp p;
+    if (cudaGetDeviceProperties(&p, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        snprintf(p.name, sizeof p.name, "device%d", c->device);
+    }
+    char buf[320];
+    snprintf(buf, sizeof buf, "%s|sm%d|%s|N%d", p.name, c->num_sms, what, c->N);
+    for (char *q = buf; *q; ++q)
+        if (*q == '"' || *q == '\\')
+            *q = '_';
+    return buf;
+}
+
+static bool read_cache(const char *path, std::vector<std::pair<std::string, std::string>> &rows)
+{
+    rows.clear();
+    FILE *f = fopen(path, "r");
+    if (!f)
+        return true;  // no file yet
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        const char *a = strchr(line, '"');
+        const char *b = a ? strchr(a + 1, '"') : nullptr;
+        const char *v = b ? strchr(b, '{') : nullptr;
+        const char *w = v ? strchr(v, '}') : nullptr;
+        if (!w)
+            continue;
+        rows.emplace_back(std::string(a + 1, b), std::string(v, w + 1));
+    }
+    fclose(f);
+    return true;
+}
+
+static bool cache_lookup(const char *path, const std::string &key, int *choice)
+{
+    std::vector<std::pair<std::string, std::string>> rows;
+    if (!path || !read_cache(path, rows))
+        return false;
+    for (auto &r : rows)
+        if (r.first == key) {
+            const char *q = strstr(r.second.c_str(), "\"choice\":");
+            return q && sscanf(q + 9, "%d", choice) == 1;
+        }
+    return false;
+}
+
+static bool cache_store(const char *path, const std::string &key, int choice, double us)
+{
+    std::vector<std::pair<std::string, std::string>> rows;
+    read_cache(path, rows);
+    char val[96];
+    snprintf(val, sizeof val, "{\"choice\": %d, \"us\": %.3f}", choice, us);
+    bool found = false;
+    for (auto &r : rows)
+        if (r.first == key) {
+            r.second = val;
+            found = true;
+        }
+    if (!found)
+        rows.emplace_back(key, val);
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f)
+        return false;
+    fprintf(f, "{\n");
+    for (size_t i = 0; i < rows.size(); ++i)
+        fprintf(f, "\"%s\": %s%s\n", rows[i].first.c_str(), rows[i].second.c_str(),
+                i + 1 < rows.size() ? "," : "");
+    fprintf(f, "}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+// Mean time in microseconds of `reps` calls of enqueue() after `warm` untimed ones.
+template <typename F>
+static int time_variant(pwa_ctx *c, F enqueue, int warm, int reps, double *us)
+{
+    cudaEvent_t e0, e1;
+    CK(c, cudaEventCreate(&e0));
+    CK(c, cudaEventCreate(&e1));
+    int rc = PWA_OK;
+    for (int i = 0; i < warm && !rc; ++i)
+        rc = enqueue();
+    cudaEventRecord(e0, c->stream);
+    for (int i = 0; i < reps && !rc; ++i)
+        rc = enqueue();
+    cudaEventRecord(e1, c->stream);
+    float ms = 0.f;
+    if (!rc && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = fail(c, PWA_ECUDA, "timing events failed");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *us = 1e3 * ms / reps;
+    return rc;
+}
+
+}  // extern "C++"
+
+int pwa_autotune(pwa_ctx *c, const char *cache_path, char *choice, int choice_len)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!(c->loaded && c->has_norm) && !c->res_loaded)
+        return fail(c, PWA_ESTATE, "nothing to tune: load a sample first");
+    DeviceGuard g(c->device);
+    std::string summary;
+    char buf[256];
+    if (c->loaded && c->has_norm) {
+        if (c->form == PWA_FORM_AMP) {
+            const std::string key = tune_key(c, "amp-groups");
+            int best = 0;
+            double best_us = 0.0;
+            if (!cache_lookup(cache_path, key, &best)) {
+                // one parameter set, V_a = 1 for every wave, in the io buffer
+                const int N = c->N;
+                std::vector<double> V(2 * N, 0.0);
+                for (int a = 0; a < N; ++a)
+                    V[2 * a] = 1.0;
+                double *dV = c->d_io + 1 + 2 * N + 1;
+                int *ds = reinterpret_cast<int *>(c->d_io + 1 + 2 * N);
+                CK(c, cudaMemcpyAsync(dV, V.data(), 2 * N * sizeof(double), cudaMemcpyHostToDevice,
+                                      c->stream));
+                for (int gr : {2, 3}) {
+                    if (gr == 3 && !amp_groups3_available(N))
+                        continue;
+                    c->tune_groups = gr;
+                    CK(c, cudaMemsetAsync(c->d_work, 0, c->work_bytes, c->stream));
+                    double us = 0.0;
+                    const int rc = time_variant(
+                        c, [&] { return enqueue_eval(c, dV, 1, c->d_io, c->d_io + 1, ds, ds + 1); },
+                        3, 20, &us);
+                    if (rc)
+                        return rc;
+                    if (!best || us < best_us) {
+                        best = gr;
+                        best_us = us;
+                    }
+                }
+                CK(c, cudaMemsetAsync(c->d_work, 0, c->work_bytes, c->stream));
+                CK(c, cudaStreamSynchronize(c->stream));
+                if (cache_path && !cache_store(cache_path, key, best, best_us))
+                    return fail(c, PWA_EINVAL, "cannot write the tuning cache %s", cache_path);
+                snprintf(buf, sizeof buf, "direct form: %d consumer groups (%.1f us, timed)", best, best_us);
+            } else {
+                snprintf(buf, sizeof buf, "direct form: %d consumer groups (cached)", best);
+            }
+            c->tune_groups = best;
+            summary += buf;
+        } else {
+            snprintf(buf, sizeof buf, "%s form: one launch shape",
+                     c->form == PWA_FORM_TABLE ? "table" : "tensor-core");
+            summary += buf;
+        }
+    }
+    if (c->res_loaded) {
+        const std::string key = tune_key(c, "res-blocks-per-sm");
+        int best = 0;
+        double best_us = 0.0;
+        if (!cache_lookup(cache_path, key, &best)) {
+            const int N = c->N, R = c->res_R;
+            const size_t npart = res_partials_doubles(N, R, c->num_sms * kResMaxBlocksPerSm);
+            double *d_io = c->d_res + npart + 1;
+            std::vector<double> h(2 * N + 2 * R, 0.0);
+            for (int a = 0; a < N; ++a)
+                h[2 * a] = 1.0;
+            for (int r = 0; r < R; ++r) {
+                h[2 * N + r] = 1.5;
+                h[2 * N + R + r] = 0.1;
+            }
+            CK(c, cudaMemcpyAsync(d_io, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                  c->stream));
+            ResArgs a{};
+            a.n_waves = N;
+            a.n_free = R;
+            a.data = c->res_data;
+            a.data_pitch = c->res_data_pitch;
+            a.n_data = c->res_n_data;
+            a.mc = c->res_mc;
+            a.mc_pitch = c->res_mc_pitch;
+            a.n_mc = c->res_n_mc;
+            a.inv_ngen = 1.0 / c->res_ngen;
+            a.V = d_io;
+            a.mass = d_io + 2 * N;
+            a.width = d_io + 2 * N + R;
+            a.partials = c->d_res;
+            a.ticket = reinterpret_cast<unsigned *>(c->d_res + npart);
+            int *ds = reinterpret_cast<int *>(d_io + 2 * N + 2 * R);
+            a.status = ds;
+            a.done = nullptr;
+            a.out = d_io + 2 * N + 2 * R + 1;
+            for (int cps = 1; cps <= kResMaxBlocksPerSm; ++cps) {
+                double us = 0.0;
+                const int rc = time_variant(
+                    c,
+                    [&] {
+                        const cudaError_t e = launch_nll_res(a, c->num_sms * cps, c->stream);
+                        return e == cudaSuccess ? PWA_OK
+                                                : fail(c, PWA_ECUDA, "%s", cudaGetErrorString(e));
+                    },
+                    2, 10, &us);
+                if (rc)
+                    return rc;
+                if (!best || us < best_us) {
+                    best = cps;
+                    best_us = us;
+                }
+            }
+            CK(c, cudaStreamSynchronize(c->stream));
+            if (cache_path && !cache_store(cache_path, key, best, best_us))
+                return fail(c, PWA_EINVAL, "cannot write the tuning cache %s", cache_path);
+            snprintf(buf, sizeof buf, "%sfree resonances: %d blocks per SM (%.1f us, timed)",
+                     summary.empty() ? "" : "; ", best, best_us);
+        } else {
+            snprintf(buf, sizeof buf, "%sfree resonances: %d blocks per SM (cached)",
+                     summary.empty() ? "" : "; ", best);
+        }
+        c->tune_res_cps = best;
+        summary += buf;
+    }
+    if (choice && choice_len > 0)
+        snprintf(choice, (size_t)choice_len, "%s", summary.c_str());
     return PWA_OK;
 }
 

@@ -459,15 +459,18 @@ cudaError_t launch_build_norm(const Planes &mc, double n_gen, double *M, double 
 // k_nll_amp.cu
 int amp_grid(int n_waves, int num_sms);
 size_t amp_partials_doubles(int n_waves, int num_sms);
+// groups: consumer groups per CTA (2 or 3; 0 = the default rule or the
+// PWA_AMP_GROUPS environment override). 3 only where amp_groups3_available.
 cudaError_t launch_nll_amp(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
-                           int num_sms, cudaStream_t s);
+                           int num_sms, cudaStream_t s, int groups = 0);
+bool amp_groups3_available(int n_waves);
 int amp_box_events(int n_waves);
 // Same launch with an explicit persistent grid. EvalArgs::partials must hold
 // amp_scratch_bytes_for_grid(grid) bytes; the kernel's work-flag word sits at
 // byte amp_flags_offset(grid) of it and, like the ticket, must be zero on
 // entry (the last CTA leaves both at zero).
 cudaError_t launch_nll_amp_grid(const Planes &amp, const CUtensorMap *map, const EvalArgs &a,
-                                int grid, cudaStream_t s);
+                                int grid, cudaStream_t s, int groups = 0);
 size_t amp_flags_offset(int grid);
 size_t amp_scratch_bytes_for_grid(int grid);
 cudaError_t amp_configure();  // once per device: opt in to large shared memory

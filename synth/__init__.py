@@ -287,3 +287,98 @@ def free_resonance_scale(n_data=2_000_000, n_mc_acc=5_000_000, n_waves=20, n_fre
     2M data events, 5M accepted MC."""
     return resonance_workload("pwa_2M_events_20_waves_4_free", waves_linear(n_waves), n_free,
                               n_data, n_mc_acc, **kw)
+
+
+# ---- the same model, drawn on a GPU (for samples too large for the host) ----
+# Distributions, amplitude model and seeding scheme are those above; the
+# random streams are torch's (Philox on the device), so a given seed gives a
+# different sample from the numpy functions. Used where only the shape and
+# value distribution matter (throughput of the largest workloads).
+
+def _torch_legendre(l, mm, x):
+    import torch
+    s = torch.sqrt(torch.clamp(1.0 - x * x, min=0.0))
+    pmm = torch.ones_like(x)
+    fact = 1.0
+    for _ in range(mm):
+        pmm = -pmm * fact * s
+        fact += 2.0
+    if l == mm:
+        return pmm
+    pm1 = x * (2 * mm + 1) * pmm
+    if l == mm + 1:
+        return pm1
+    p2, p1 = pmm, pm1
+    for ll in range(mm + 2, l + 1):
+        p = ((2 * ll - 1) * x * p1 - (ll + mm - 1) * p2) / (ll - mm)
+        p2, p1 = p1, p
+    return p1
+
+
+def torch_amplitudes(ev, waves):
+    """Event-major complex64 [n, len(waves)] on the events' device, evaluated
+    in float64 like `amplitudes`."""
+    import torch
+    m, c, p = ev["m"], ev["costh"], ev["phi"]
+    out = torch.empty((m.shape[0], len(waves)), dtype=torch.complex64, device=m.device)
+    for a, wv in enumerate(waves):
+        bw = 1.0 / torch.complex(wv.mass * wv.mass - m * m, torch.full_like(m, -wv.mass * wv.width))
+        norm = math.sqrt((2 * wv.l + 1) / (4 * math.pi) * math.factorial(wv.l - wv.m)
+                         / math.factorial(wv.l + wv.m))
+        y = norm * _torch_legendre(wv.l, wv.m, c) * torch.exp(torch.complex(torch.zeros_like(p), wv.m * p))
+        out[:, a] = (bw * y).to(torch.complex64)
+    return out
+
+
+def torch_mixture_workload(waves, n_data, n_mc_acc, seed, device="cuda", batch=1 << 22):
+    """(A_data, A_mc, n_gen): data from the resonance mixture of
+    `data_sample_mixture` (V_true from `random_V(len(waves), seed)`), accepted
+    MC as in `mc_sample`; complex64 tensors on `device`."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    u = lambda k: torch.rand(k, generator=g, device=device, dtype=torch.float64)
+    V = random_V(len(waves), seed)
+    w = torch.tensor(np.abs(V) ** 2, device=device)
+    M = torch.tensor([wv.mass for wv in waves], device=device, dtype=torch.float64)
+    G = torch.tensor([wv.width for wv in waves], device=device, dtype=torch.float64)
+    parts, got = [], 0
+    while got < n_data:
+        a = torch.multinomial(w, batch, replacement=True, generator=g)
+        lo = torch.atan((M_LO - M[a]) / (G[a] / 2)) / math.pi + 0.5
+        hi = torch.atan((M_HI - M[a]) / (G[a] / 2)) / math.pi + 0.5
+        t = lo + (hi - lo) * u(batch)
+        m = torch.clamp(M[a] + (G[a] / 2) * torch.tan(math.pi * (t - 0.5)), M_LO, M_HI)
+        c = 2.0 * u(batch) - 1.0
+        keep = u(batch) < (0.6 + 0.3 * c) / EFF_MAX
+        p = 2.0 * math.pi * u(batch)
+        parts.append((m[keep], c[keep], p[keep]))
+        got += int(keep.sum())
+    ev = {k: torch.cat([q[i] for q in parts])[:n_data] for i, k in enumerate(("m", "costh", "phi"))}
+    A_data = torch_amplitudes(ev, waves)
+    parts, got, n_gen = [], 0, 0
+    while got < n_mc_acc:
+        m = M_LO + (M_HI - M_LO) * u(batch)
+        c = 2.0 * u(batch) - 1.0
+        p = 2.0 * math.pi * u(batch)
+        keep = u(batch) < 0.6 + 0.3 * c
+        idx = torch.nonzero(keep).squeeze(1)
+        need = n_mc_acc - got
+        if idx.numel() >= need:
+            n_gen += int(idx[need - 1]) + 1
+            idx = idx[:need]
+        else:
+            n_gen += batch
+        parts.append((m[idx], c[idx], p[idx]))
+        got += idx.numel()
+    ev = {k: torch.cat([q[i] for q in parts]) for i, k in enumerate(("m", "costh", "phi"))}
+    return A_data, torch_amplitudes(ev, waves), n_gen
+
+
+def model_batch_spec(n_models=64, n_lo=8, n_hi=48, d_lo=100_000, d_hi=2_000_000, seed=SEED_DATA):
+    """The uneven trial-model batch: per model (n_waves ~ U{n_lo..n_hi},
+    n_data ~ U[d_lo, d_hi], seed); its MC sample has 2 n_data accepted events."""
+    rng = np.random.Generator(np.random.Philox(seed))
+    nw = rng.integers(n_lo, n_hi + 1, n_models)
+    nd = rng.integers(d_lo, d_hi + 1, n_models)
+    return [(int(a), int(b), seed + 1000 * (j + 1)) for j, (a, b) in enumerate(zip(nw, nd))]
