@@ -44,12 +44,12 @@ METRIC = "NLL+grad evals/s (1M events, 20 waves, K starts); % HBM / tensor roofl
 UNIT = "evals/s"
 N_WAVES, N_DATA, N_MC = 20, 1_000_000, 5_000_000
 WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M accepted MC, K=1 per evaluation"
-# DRAM bytes (read + write) per launch of the timed kernel from one ncu
-# capture (profiles/), or None where the kernel changed since the capture.
-TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,        # profiles/nll_amp_1M_20waves.md
-           "table": 1600.392e6 + 4.053504e6,           # profiles/nll_table_1M_20waves.md
-           "tc": 2 * (1024.851e6 + 3.764992e6),        # profiles/batched_4M_32waves_K256.md (2 launches)
-           "res": 1148.160e6 + 3.716096e6,             # profiles/nll_res_2M_5M_20waves_4free.md
+# DRAM bytes (read + write) per step of the timed kernel from one ncu
+# capture of the current kernel, or None where there is none.
+TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
+           "table": 1600.392e6 + 4.053504e6,
+           "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
+           "res": 1148.160e6 + 3.716096e6,
            "models": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
