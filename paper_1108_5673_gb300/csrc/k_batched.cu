@@ -367,18 +367,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int qq = warp & 3, sg = warp >> 2;
         const int e = qq * 32 + lane;                  // event row of the tile = TMEM lane
         const uint32_t lane_addr = (uint32_t)(qq * 32) << 16;
-        const f2 inv256 = pk2(1.0f / 256.0f, 1.0f / 256.0f);
+        // per-thread constants: R' store offsets, the atomic partials of this lane
+        const uint32_t st0 = sw128(e, 32 * sg), st1 = sw128(e, 32 * sg + 16);
+        unsigned long long *lp = reinterpret_cast<unsigned long long *>(
+            a.lpart + ((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + 8 * sg + lane);
+        int64_t ev = (int64_t)blockIdx.x * kBM + e;       // this thread's event in tile j
+        const int64_t ev_step = (int64_t)gridDim.x * kBM;
         bool ok = true;
+        int j = 0, ch = 0;                                 // tile, half chunk (q = j HPT + ch)
         for (int q = 0; q < steps && ok; ++q) {
-            const int j = q / HPT, ch = q % HPT, h = ch & 1, cq = j * NCH + (ch >> 1);
+            const int h = ch & 1, cq = j * NCH + (ch >> 1);
             const bool last_half = h == 1 || ch == HPT - 1;
             if (!mbar_wait(&s_full, q & 1)) {
                 ok = false;
                 break;
             }
             tc_fence_after();
-            // Q pieces of this warp's 8 sets: acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8
-            f2 t[8];
+            // Q of this warp's 8 sets: acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8
+            float qr[8], qi[8];
             {
                 uint32_t v0[16], v1[16], v2[16], v3[16];
                 tmem_ld16(tmem + lane_addr + 16 * sg, v0);
@@ -387,20 +393,24 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (XS == 2)
                     tmem_ld16(tmem + lane_addr + 192 + 16 * sg, v3);
                 tmem_ld_wait();
+                constexpr float c8 = 1.0f / 256.0f;
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
-                    f2 u = pk2(__uint_as_float(v2[2 * s]), __uint_as_float(v2[2 * s + 1]));
-                    if (XS == 2)
-                        u = fma2(pk2(__uint_as_float(v3[2 * s]), __uint_as_float(v3[2 * s + 1])), inv256, u);
-                    u = fma2(u, inv256, pk2(__uint_as_float(v1[2 * s]), __uint_as_float(v1[2 * s + 1])));
-                    t[s] = fma2(u, inv256, pk2(__uint_as_float(v0[2 * s]), __uint_as_float(v0[2 * s + 1])));
+                    float ur = __uint_as_float(v2[2 * s]), ui = __uint_as_float(v2[2 * s + 1]);
+                    if (XS == 2) {
+                        ur = fmaf(__uint_as_float(v3[2 * s]), c8, ur);
+                        ui = fmaf(__uint_as_float(v3[2 * s + 1]), c8, ui);
+                    }
+                    ur = fmaf(ur, c8, __uint_as_float(v1[2 * s]));
+                    ui = fmaf(ui, c8, __uint_as_float(v1[2 * s + 1]));
+                    qr[s] = fmaf(ur, c8, __uint_as_float(v0[2 * s]));
+                    qi[s] = fmaf(ui, c8, __uint_as_float(v0[2 * s + 1]));
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0)
                 mbar_arrive(&s_free);
-            const int64_t ev = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * kBM + e;
             uint32_t rpk[8];
             int l[8];
             if (ev < a.n_events) {
@@ -409,17 +419,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 unsigned mn = 0xffffffffu;
 #pragma unroll
                 for (int s = 0; s < 8; ++s) {
-                    const f2 qv = t[s];
-                    float re, im;
-                    upk2(qv, re, im);
-                    const float I = fmaf(re, re, im * im);
+                    const float I = fmaf(qr[s], qr[s], qi[s] * qi[s]);
                     Iv[s] = I;
                     const int bits = __float_as_int(I);
                     mn = min(mn, (unsigned)bits);
                     const float r = rcp_approx(I);
-                    float rr, ri;
-                    upk2(mul2(qv, pk2(r, r)), rr, ri);
-                    rpk[s] = pack_bf16x2(rr, ri);
+                    rpk[s] = pack_bf16x2(qr[s] * r, qi[s] * r);
                     // I = 2^k (1 + z), 1 + z in [sqrt(1/2), sqrt(2))
                     const int k = (bits - 0x3F3504F3) >> 23;
                     kx[s] = k;
@@ -453,24 +458,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mine = lane == s ? t : mine;
             }
             if (lane < 8)  // no return value: a fire-and-forget reduction
-                atomicAdd(reinterpret_cast<unsigned long long *>(
-                              a.lpart + ((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + (ch >> 1) * kKC +
-                              (ch & 1) * kHS + 8 * sg + lane),
-                          (unsigned long long)(long long)mine);
+                atomicAdd(lp + ch * kHS, (unsigned long long)(long long)mine);
             // R' may be overwritten once GEMM 2 of the previous chunk step is done
             if (h == 0 && cq >= 1 && !mbar_wait(&r_free, (cq - 1) & 1)) {
                 ok = false;
                 break;
             }
             unsigned char *rrow = sR + h * (128 * 128);
-            *reinterpret_cast<uint4 *>(rrow + sw128(e, 32 * sg)) = make_uint4(rpk[0], rpk[1], rpk[2], rpk[3]);
-            *reinterpret_cast<uint4 *>(rrow + sw128(e, 32 * sg + 16)) =
-                make_uint4(rpk[4], rpk[5], rpk[6], rpk[7]);
+            *reinterpret_cast<uint4 *>(rrow + st0) = make_uint4(rpk[0], rpk[1], rpk[2], rpk[3]);
+            *reinterpret_cast<uint4 *>(rrow + st1) = make_uint4(rpk[4], rpk[5], rpk[6], rpk[7]);
             if (last_half) {
                 fence_async_smem();
                 __syncwarp();
                 if (lane == 0)
                     mbar_arrive(&r_full);
+            }
+            if (++ch == HPT) {
+                ch = 0;
+                ++j;
+                ev += ev_step;
             }
         }
         if (!ok)

@@ -22,7 +22,8 @@
 //    reciprocal: the Breit-Wigner is then correct to float roundings that vary
 //    from event to event, with no error shared by all events near the peak;
 //  * S uses the compensated dot product (Ogita, Rump and Oishi, Dot2) with V
-//    as a float pair, so destructive interference does not cost digits;
+//    as a float pair, in four independent chains joined by error-free sums,
+//    so destructive interference does not cost digits;
 //  * ln I = e ln 2 + ln f (e summed as an integer, ln f in float-float), the
 //    MC sum of I in float-float, gradients in FP32 per thread and FP64 across
 //    threads and blocks. Data and MC sums are kept apart (their weights
@@ -33,7 +34,8 @@ namespace pwa {
 
 namespace {
 
-constexpr int kResThreads = 256;
+// threads per block: more warps where the register footprint allows it
+__host__ __device__ constexpr int res_threads(int np) { return np <= 20 ? 384 : 256; }
 constexpr int kMaxFree = 8;
 
 struct ResShared {
@@ -47,6 +49,15 @@ struct ResShared {
 
 __device__ __forceinline__ f2 splat(float v) { return pk2(v, v); }
 
+// Knuth's TwoSum on both halves: returns a + b rounded, err = the exact rest.
+__device__ __forceinline__ f2 two_sum2(f2 a, f2 b, f2 &err)
+{
+    const f2 s = add2(a, b);
+    const f2 bb = sub2(s, a);
+    err = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+    return s;
+}
+
 __device__ __forceinline__ void split_pair(double v, float &h, float &l)
 {
     h = __double2float_rn(v);
@@ -54,8 +65,9 @@ __device__ __forceinline__ void split_pair(double v, float &h, float &l)
 }
 
 template <int NP, int RP>
-__global__ void __launch_bounds__(kResThreads, 1) nll_res_kernel(const ResArgs a)
+__global__ void __launch_bounds__(res_threads(NP), 1) nll_res_kernel(const ResArgs a)
 {
+    constexpr int kResThreads = res_threads(NP);
     __shared__ ResShared sh;
     __shared__ float red[kResThreads / 32][2 * 32 + 2 * kMaxFree + 4];
     __shared__ int s_flags, s_last;
@@ -138,19 +150,25 @@ __global__ void __launch_bounds__(kResThreads, 1) nll_res_kernel(const ResArgs a
                     ai[r] = fmaf(br[r], yi, bi[r] * yr);
                 }
             }
-            // S = sum (Vh + Vl) A, compensated: (Sr, Si) += ar (vr, vi) + ai (-vi, vr)
-            f2 s = 0ull, c = 0ull, l = 0ull;
+            // S = sum (Vh + Vl) A, compensated: (Sr, Si) += ar (vr, vi) + ai (-vi, vr),
+            // in four independent chains (waves w mod 4) joined by error-free sums
+            f2 s[4] = {0ull, 0ull, 0ull, 0ull}, c[4] = {0ull, 0ull, 0ull, 0ull}, l = 0ull;
 #pragma unroll
             for (int w = 0; w < NP; ++w) {
                 if (w < N) {
                     const f2 x = splat(ar[w]), y = splat(ai[w]);
-                    dot2_step(s, c, x, sh.va[w], sh.van[w]);
-                    dot2_step(s, c, y, sh.vb[w], sh.vbn[w]);
+                    dot2_step(s[w & 3], c[w & 3], x, sh.va[w], sh.van[w]);
+                    dot2_step(s[w & 3], c[w & 3], y, sh.vb[w], sh.vbn[w]);
                     l = fma2(x, sh.val[w], fma2(y, sh.vbl[w], l));
                 }
             }
+            // (s0 + s1) + (s2 + s3) by TwoSum, the rounding errors join the corrections
+            f2 e01, e23, e;
+            const f2 s01 = two_sum2(s[0], s[1], e01), s23 = two_sum2(s[2], s[3], e23);
+            const f2 st = two_sum2(s01, s23, e);
+            const f2 ct = add2(add2(add2(c[0], c[1]), add2(c[2], c[3])), add2(add2(e01, e23), e));
             float sr, si;
-            upk2(add2(s, add2(c, l)), sr, si);
+            upk2(add2(st, add2(ct, l)), sr, si);
             const float I = fmaf(sr, sr, si * si);
             float wr = 0.f, wi = 0.f;
             if (phase == 0) {
@@ -280,9 +298,9 @@ template <int NP>
 void launch_np(const ResArgs &a, int grid, cudaStream_t s)
 {
     if (a.n_free <= 4)
-        nll_res_kernel<NP, 4><<<grid, kResThreads, 0, s>>>(a);
+        nll_res_kernel<NP, 4><<<grid, res_threads(NP), 0, s>>>(a);
     else
-        nll_res_kernel<NP, kMaxFree><<<grid, kResThreads, 0, s>>>(a);
+        nll_res_kernel<NP, kMaxFree><<<grid, res_threads(NP), 0, s>>>(a);
 }
 
 }  // namespace
