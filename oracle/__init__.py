@@ -50,6 +50,10 @@ def _load():
         lib.oracle_nll_table.argtypes = [P, I64, I, P, P, I, P, P]
         lib.oracle_nll_table.restype = I
         lib.oracle_nll_res.argtypes = [I, I, P, P, P, I64, P, P, P, I64, D, P, P, P, P, P, P, P]
+        lib.oracle_hessian.argtypes = [P, I64, I, P, P, P]
+        lib.oracle_hessian.restype = I
+        lib.oracle_mc_weights.argtypes = [P, I64, I, P, D, P]
+        lib.oracle_fit_fractions.argtypes = [P, I, P, P]
         lib.oracle_nll_res.restype = I
         _lib = lib
     return _lib
@@ -166,3 +170,30 @@ def nll_res(m_d, Y_d, Afix_d, m_mc, Y_mc, Afix_mc, n_gen, V, mass, width):
                                  _p(V), _p(mass), _p(width), ctypes.byref(nll),
                                  _p(gV), _p(gM), _p(gW))
     return nll.value, gV, gM, gW, bad
+
+
+def hessian(A, M, V):
+    """FUMILI Hessian of the NLL in p = (Re V, Im V): [2N, 2N] float64
+    (sum_i grad ln I_i grad ln I_i^T + d^2 V^H M V / dp^2), and n_bad."""
+    A, M, V = _c128(A), _c128(M), _c128(V)
+    n, N = A.shape
+    H = np.empty((2 * N, 2 * N))
+    bad = _load().oracle_hessian(_p(A), n, N, _p(M), _p(V), _p(H))
+    return H, bad
+
+
+def mc_weights(A_mc, V, n_gen):
+    """Per accepted MC event I(Omega_j) / N_gen."""
+    A, V = _c128(A_mc), _c128(V)
+    w = np.empty(A.shape[0])
+    _load().oracle_mc_weights(_p(A), A.shape[0], A.shape[1], _p(V), float(n_gen), _p(w))
+    return w
+
+
+def fit_fractions(M, V):
+    """F[a, b] = Re(conj(V_a) M_ab V_b) / V^H M V."""
+    M, V = _c128(M), _c128(V)
+    N = M.shape[0]
+    F = np.empty((N, N))
+    _load().oracle_fit_fractions(_p(M), N, _p(V), _p(F))
+    return F

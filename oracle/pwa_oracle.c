@@ -26,6 +26,14 @@
  *   An intensity that is not positive and finite makes the evaluation
  *   undefined: the call reports status 1, NLL = +inf and a zero gradient.
  *
+ * Beyond the likelihood itself (the fitter's needs, Sec. 4 and 5):
+ *   FUMILI's Hessian of the NLL in the real parameters p = (Re V, Im V):
+ *     H = sum_i grad(ln I_i) grad(ln I_i)^T + d^2 (V^H M V) / dp^2,
+ *   with grad(ln I_i) = 2 (Re, Im) of conj(A_a(i)) S_i / I_i per wave a and
+ *   d^2 (V^H M V) = 2 [[Re M, -Im M], [Im M, Re M]];
+ *   per-MC-event weights w_j = I(Omega_j) / N_gen (their sum is V^H M V) for
+ *   projections, and the fit fractions F_ab = Re(conj(V_a) M_ab V_b) / V^H M V.
+ *
  * Layouts: complex numbers are interleaved (re, im) doubles.
  *   Amplitudes: event-major A[(i*N + a)*2 + {0,1}].
  *   Table: event-major T[i*N*N + p] with p = a for the real diagonal
@@ -421,4 +429,79 @@ int oracle_nll_res(int N, int R,
     }
     free(gVd); free(gVm); free(gMd); free(gMm); free(gWd); free(gWm);
     return bad;
+}
+
+/* ---- FUMILI Hessian (Sec. 4, 5) ---------------------------------------- */
+/* H[2N][2N] row-major in p = (Re V_0..Re V_{N-1}, Im V_0..Im V_{N-1}).
+ * Returns 1 (and leaves H zero) if an intensity is not positive and finite. */
+int oracle_hessian(const double *A, int64_t n, int N, const double *M, const double *V, double *H)
+{
+    const int P = 2 * N;
+    nsum *h = (nsum *)calloc((size_t)P * P, sizeof(nsum));
+    double *d = (double *)malloc(sizeof(double) * (size_t)P);
+    int bad = 0;
+    for (int64_t i = 0; i < n && !bad; ++i) {
+        const double *Ai = A + (size_t)i * N * 2;
+        nsum sr = {0, 0}, si = {0, 0};
+        for (int a = 0; a < N; ++a) {
+            double pr, pi;
+            cmul(V[2 * a], V[2 * a + 1], Ai[2 * a], Ai[2 * a + 1], &pr, &pi);
+            nadd(&sr, pr);
+            nadd(&si, pi);
+        }
+        const double s_r = nval(&sr), s_i = nval(&si), I = s_r * s_r + s_i * s_i;
+        if (!(I > 0) || !isfinite(I)) {
+            bad = 1;
+            break;
+        }
+        /* d/dRe V_a ln I = 2 Re(conj(A_a) S) / I,  d/dIm V_a ln I = 2 Im(conj(A_a) S) / I */
+        for (int a = 0; a < N; ++a) {
+            double pr, pi;
+            cmul(Ai[2 * a], -Ai[2 * a + 1], s_r, s_i, &pr, &pi);
+            d[a] = 2.0 * pr / I;
+            d[N + a] = 2.0 * pi / I;
+        }
+        for (int x = 0; x < P; ++x)
+            for (int y = 0; y < P; ++y)
+                nadd(&h[x * P + y], d[x] * d[y]);
+    }
+    for (int x = 0; x < P; ++x)
+        for (int y = 0; y < P; ++y)
+            H[x * P + y] = bad ? 0.0 : nval(&h[x * P + y]);
+    if (!bad)
+        for (int a = 0; a < N; ++a)
+            for (int b = 0; b < N; ++b) {
+                const double mr = M[(a * N + b) * 2], mi = M[(a * N + b) * 2 + 1];
+                H[a * P + b] += 2.0 * mr;              /* Re-Re block */
+                H[(N + a) * P + N + b] += 2.0 * mr;    /* Im-Im block */
+                H[a * P + N + b] += -2.0 * mi;         /* Re-Im block */
+                H[(N + a) * P + b] += 2.0 * mi;        /* Im-Re block */
+            }
+    free(h);
+    free(d);
+    return bad;
+}
+
+/* ---- projection weights and fit fractions ------------------------------ */
+/* w[j] = |sum_a V_a A_a(j)|^2 / N_gen over the accepted MC events. */
+void oracle_mc_weights(const double *A, int64_t n, int N, const double *V, double n_gen, double *w)
+{
+    oracle_intensity(A, n, N, V, w);
+    for (int64_t j = 0; j < n; ++j)
+        w[j] /= n_gen;
+}
+
+/* F[a][b] = Re(conj(V_a) M_ab V_b) / V^H M V (the diagonal: the waves' fit
+ * fractions; off-diagonal pairs F_ab + F_ba: their interference). */
+void oracle_fit_fractions(const double *M, int N, const double *V, double *F)
+{
+    double nv;
+    oracle_norm_term(M, N, V, &nv, NULL);
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            double pr, pi, qr, qi;
+            cmul(M[(a * N + b) * 2], M[(a * N + b) * 2 + 1], V[2 * b], V[2 * b + 1], &pr, &pi);
+            cmul(V[2 * a], -V[2 * a + 1], pr, pi, &qr, &qi);
+            F[a * N + b] = qr / nv;
+        }
 }

@@ -356,3 +356,96 @@ def test_blas_norm_matrix_matches_loops():
     M = oracle.norm_matrix(wl.A_mc, wl.n_gen)
     Mb = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen, chunk=7000)
     assert rel(Mb, M) < 1e-13
+
+
+# ---- FUMILI Hessian, projection weights, fit fractions -----------------------
+
+def _real_grad(A, M, V):
+    """dNLL/d(Re V, Im V) from the oracle's Wirtinger gradient g: (2 Re g, 2 Im g)."""
+    _, g, _ = oracle.nll_amp(A, M, V)
+    return np.concatenate([2 * g.real, 2 * g.imag])
+
+
+def _hess_case(N=3, n=40, n_mc=60, seed=3):
+    rng = np.random.Generator(np.random.Philox(seed))
+    A = rng.standard_normal((n, N)) + 1j * rng.standard_normal((n, N))
+    Am = rng.standard_normal((n_mc, N)) + 1j * rng.standard_normal((n_mc, N))
+    M = oracle.norm_matrix(Am, 1.7 * n_mc)
+    V = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    return A, M, V
+
+
+def test_hessian_brute_force():
+    A, M, V = _hess_case()
+    N = A.shape[1]
+    H, bad = oracle.hessian(A, M, V)
+    assert bad == 0
+    Hb = np.zeros((2 * N, 2 * N))
+    for i in range(A.shape[0]):
+        S = sum(V[a] * A[i, a] for a in range(N))
+        I = abs(S) ** 2
+        d = [2 * (np.conj(A[i, a]) * S).real / I for a in range(N)] + \
+            [2 * (np.conj(A[i, a]) * S).imag / I for a in range(N)]
+        for x in range(2 * N):
+            for y in range(2 * N):
+                Hb[x, y] += d[x] * d[y]
+    for a in range(N):
+        for b in range(N):
+            Hb[a, b] += 2 * M[a, b].real
+            Hb[N + a, N + b] += 2 * M[a, b].real
+            Hb[a, N + b] -= 2 * M[a, b].imag
+            Hb[N + a, b] += 2 * M[a, b].imag
+    assert np.max(np.abs(H - Hb)) <= 1e-12 * np.max(np.abs(Hb))
+
+
+def test_hessian_homogeneity_identity():
+    """I is homogeneous of degree 2 in p = (Re V, Im V): p . grad ln I_i = 2, so
+    (sum_i d_i d_i^T) p = 2 sum_i d_i = -2 grad(data NLL), and the MC term is
+    quadratic: H_MC p = grad(V^H M V). Hence H p = -2 grad NLL + 3 grad N."""
+    A, M, V = _hess_case(N=4, seed=5)
+    H, _ = oracle.hessian(A, M, V)
+    p = np.concatenate([V.real, V.imag])
+    _, mv = oracle.norm_term(M, V)
+    gN = np.concatenate([2 * mv.real, 2 * mv.imag])
+    lhs = H @ p
+    rhs = -2 * _real_grad(A, M, V) + 3 * gN
+    assert np.max(np.abs(lhs - rhs)) <= 1e-10 * np.max(np.abs(rhs))
+
+
+def test_hessian_vs_exact_second_derivative():
+    """The exact NLL Hessian (central differences of the pinned gradient) is
+    FUMILI's H minus sum_i d^2 I_i / I_i, with d^2 I = 2 [[Re C, -Im C], [Im C, Re C]]
+    for C_ab = conj(A_a) A_b; checks the form and the parameter ordering."""
+    A, M, V = _hess_case(N=3, n=30, seed=9)
+    N = A.shape[1]
+    H, _ = oracle.hessian(A, M, V)
+    p0 = np.concatenate([V.real, V.imag])
+    h = 1e-5
+    He = np.zeros((2 * N, 2 * N))
+    for k in range(2 * N):
+        pp, pm = p0.copy(), p0.copy()
+        pp[k] += h
+        pm[k] -= h
+        gp = _real_grad(A, M, pp[:N] + 1j * pp[N:])
+        gm = _real_grad(A, M, pm[:N] + 1j * pm[N:])
+        He[:, k] = (gp - gm) / (2 * h)
+    I = oracle.intensity(A, V)
+    C = np.einsum("ia,ib->ab", np.conj(A) / I[:, None], A)
+    D2 = np.block([[2 * C.real, -2 * C.imag], [2 * C.imag, 2 * C.real]])
+    assert np.max(np.abs(He - (H - D2))) <= 1e-6 * np.max(np.abs(He))
+
+
+def test_mc_weights_and_fit_fractions():
+    A, M, V = _hess_case(N=5, seed=11)
+    rng = np.random.Generator(np.random.Philox(12))
+    Am = rng.standard_normal((200, 5)) + 1j * rng.standard_normal((200, 5))
+    n_gen = 333.0
+    Mm = oracle.norm_matrix(Am, n_gen)
+    w = oracle.mc_weights(Am, V, n_gen)
+    assert np.allclose(w, np.abs(Am @ V) ** 2 / n_gen, rtol=1e-13, atol=0)
+    nv, _ = oracle.norm_term(Mm, V)
+    assert abs(w.sum() - nv) <= 1e-12 * nv               # sum of weights = V^H M V
+    F = oracle.fit_fractions(Mm, V)
+    assert abs(F.sum() - 1.0) <= 1e-12                    # fractions + interference = 1
+    for a in range(5):
+        assert abs(F[a, a] - abs(V[a]) ** 2 * Mm[a, a].real / nv) <= 1e-13
