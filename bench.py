@@ -14,9 +14,13 @@ Other workloads (one JSON line each, same keys):
           5M accepted MC, amplitudes recomputed every call
   models  64 trial models (n_waves 8..48, 100k..2M data events, MC 2x data),
           K = 16 parameter sets each, one graph launch per step
+  hessian the FUMILI Hessian (2N x 2N over Re V, Im V) of the direct-form
+          sample (1M events x 20 waves); one step = one Hessian
+  weights projection weights I / N_gen of the 5M accepted MC events of the
+          same sample into a device buffer; one step = one pass
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload direct|table|tc|res|models]
+                  [--workload direct|table|tc|res|models|hessian|weights]
 
 `value` is device-timed (CUDA events on the launching stream; L2 flushed
 between steps where the inputs fit in it); `e2e` times the public host call
@@ -50,11 +54,15 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "table": 1600.392e6 + 4.053504e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
            "res": 1148.160e6 + 3.716096e6,
-           "models": None}
+           "models": None,
+           "hessian": None,
+           "weights": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
-           "models": "batched_kernel<F, 2> (all sizes)"}
-DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100}
+           "models": "batched_kernel<F, 2> (all sizes)", "hessian": "hess_kernel<20>",
+           "weights": "mc_weights_kernel<20>"}
+DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,
+                 "hessian": 2000, "weights": 2000}
 
 
 def measured_peaks():
@@ -283,6 +291,65 @@ def job_models(pwa, torch, stream, local, rank):
              "each way)")
 
 
+def job_fit_extra(pwa, torch, stream, local, rank, what):
+    """FUMILI Hessian of the 1M-event sample, or the projection weights of its
+    5M accepted MC events (host V in; H to the host, or w into a device buffer)."""
+    import synth
+    wl = synth.paper_scale()
+    V = synth.start_points(N_WAVES, 1, seed=synth.SEED_STARTS + rank)[0]
+    L = pwa.Likelihood(N_WAVES, device=local, max_k=1, stream=stream.cuda_stream)
+    L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+    L.build_norm()
+    if what == "hessian":
+        def cpu_baseline():
+            import oracle
+            sub = 20_000
+            Mo = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen)
+            dt, k = timed_oracle(lambda: oracle.hessian(wl.A_data[:sub], Mo, V), 10.0)
+            return {"value": 1.0 / (dt * N_DATA / sub), "unit": "Hessians/s", "cores": 1,
+                    "kind": "oracle",
+                    "sample": "%d FUMILI Hessians of the first 20k events (FP64 C oracle, "
+                              "1 thread), scaled to the 1M-event sample" % k}
+
+        step = lambda: L.hessian(V)
+        P = 2 * N_WAVES
+        return Job(
+            name="hessian", lib=L, step=step, host_step=step, sync=lambda: L.last_status,
+            evals_per_step=1, launches_per_step=2, flush=True,
+            metric="FUMILI Hessian evals/s (1M events, 20 waves); % HBM roofline",
+            unit="Hessians/s",
+            workload="FUMILI Hessian (40 x 40 over Re V, Im V) of 1M data events x 20 waves "
+                     "(FP32 amplitudes), M from 5M accepted MC",
+            config={"n_waves": N_WAVES, "n_data": N_DATA, "n_mc_acc": N_MC, "K": 1},
+            roof={"bound": "hbm", "bytes": 8.0 * N_WAVES * N_DATA},
+            dtype="f32", h2d=16 * N_WAVES, d2h=8 * P * P + 4, cpu_baseline=cpu_baseline,
+            note="value and e2e both time the host call (V in, the 12.8 KB Hessian out)")
+
+    out = torch.empty(N_MC, dtype=torch.float32, device="cuda")
+
+    def cpu_baseline():
+        import oracle
+        sub = 500_000
+        dt, k = timed_oracle(lambda: oracle.mc_weights(wl.A_mc[:sub], V, wl.n_gen), 10.0)
+        return {"value": 1.0 / (dt * N_MC / sub), "unit": "passes/s", "cores": 1, "kind": "oracle",
+                "sample": "%d weight passes over the first 500k accepted MC events (FP64 C oracle, "
+                          "1 thread), scaled to the 5M events" % k}
+
+    step = lambda: L.mc_weights(V, out)
+    return Job(
+        name="weights", lib=L, step=step, host_step=lambda: L.mc_weights(V),
+        sync=lambda: L.last_status, evals_per_step=1, launches_per_step=1, flush=False,
+        metric="projection-weight passes/s (5M accepted MC events, 20 waves); % HBM roofline",
+        unit="passes/s",
+        workload="projection weights I(Omega_j) / N_gen of 5M accepted MC events x 20 waves (FP32 "
+                 "amplitudes, FP32 weights into a device buffer)",
+        config={"n_waves": N_WAVES, "n_mc_acc": N_MC, "n_mc_gen": wl.n_gen},
+        roof={"bound": "hbm", "bytes": (8.0 * N_WAVES + 4.0) * N_MC},
+        dtype="f32", h2d=16 * N_WAVES, d2h=4 * N_MC, cpu_baseline=cpu_baseline,
+        note="value times the call writing into a device buffer; e2e the call returning the "
+             "weights to host memory (20 MB)")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -316,7 +383,7 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models"])
+    ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models", "hessian", "weights"])
     ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -347,6 +414,8 @@ def main():
         job = job_tc(pwa, torch, stream, local, rank, args.precision)
     elif args.workload == "res":
         job = job_res(pwa, torch, stream, local, rank)
+    elif args.workload in ("hessian", "weights"):
+        job = job_fit_extra(pwa, torch, stream, local, rank, args.workload)
     else:
         job = job_models(pwa, torch, stream, local, rank)
 
@@ -442,11 +511,12 @@ def main():
     if getattr(job, "note", None):
         config["note"] = job.note
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": getattr(job, "metric", METRIC), "value": value,
+        "unit": getattr(job, "unit", UNIT), "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": job.dtype, "data": "synthetic",
         "config": config, "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": job.h2d,
+        "e2e": {"value": e2e_value, "unit": getattr(job, "unit", UNIT), "h2d_bytes_per_step": job.h2d,
                 "d2h_bytes_per_step": job.d2h},
         "gpu_launches": job.launches_per_step * args.steps,
         "status": status,

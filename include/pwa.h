@@ -181,6 +181,40 @@ int pwa_load_resonance_events(pwa_ctx *ctx, int n_free, const double *m_data, co
 int pwa_nll_grad_res(pwa_ctx *ctx, const double *V, const double *mass, const double *width,
                      double *nll, double *gV, double *gM, double *gW);
 
+/* ---- what the fitter and the plots take besides the NLL -------------------
+ * FUMILI Hessian (Sec. 4 fits with FUMILI on analytic gradients and Hessian;
+ * Sec. 5 returns the Hessian to the host each iteration). Over the real
+ * parameters p = (Re V_0 .. Re V_{N-1}, Im V_0 .. Im V_{N-1}):
+ *   H = sum_{i in data} d_i d_i^T + d^2(V^H M V)/dp^2,  d_i = grad_p ln I_i,
+ *   (d_i)_a = 2 Re(conj(A_a(i)) S_i) / I_i,  (d_i)_{N+a} = 2 Im(...) / I_i,
+ *   d^2(V^H M V)/dp^2 = 2 [[Re M, -Im M], [Im M, Re M]],
+ * i.e. the exact second derivative of the normalisation term plus the
+ * FUMILI (Gauss-Newton) approximation of the data term's, which drops
+ * -sum_i d^2 I_i / I_i.
+ *   V: host [n_waves] complex128;  H: host [2 n_waves][2 n_waves] double,
+ *   row-major, symmetric.
+ * Uses the context's direct-form store (the data planes loaded by
+ * pwa_load_events); any form may be current. Returns PWA_EDOMAIN (H all
+ * zero) if a data intensity was not positive and finite; PWA_ESTATE before
+ * pwa_build_norm; PWA_EINVAL for null pointers; PWA_ENOMEM, PWA_ECUDA. */
+int pwa_hessian(pwa_ctx *ctx, const double *V, double *H);
+
+/* Projection weights (the "Plots" step of Table 1): the fitted intensity of
+ * each accepted MC event divided by the number generated,
+ *   w[j] = |sum_a V_a A_a(j)|^2 / n_mc_gen,  j < n_mc_acc,
+ * so that sum_j w[j] = V^H M V, the predicted number of events.
+ *   V: host [n_waves] complex128;  w: [n_mc_acc] float, host or device
+ *   pointer (detected; a host buffer is filled through a device copy).
+ * Errors: PWA_ESTATE (no events loaded), PWA_EINVAL, PWA_ENOMEM, PWA_ECUDA. */
+int pwa_mc_weights(pwa_ctx *ctx, const double *V, float *w);
+
+/* Fit fractions: F[a][b] = Re(conj(V_a) M_ab V_b) / V^H M V (host [n_waves]
+ * [n_waves] double). The diagonal holds each wave's fraction of the
+ * predicted yield; F[a][b] + F[b][a] is the interference of waves a and b;
+ * all entries sum to one. Errors: PWA_ESTATE before pwa_build_norm,
+ * PWA_EINVAL, PWA_ECUDA. */
+int pwa_fit_fractions(pwa_ctx *ctx, const double *V, double *F);
+
 /* ---- uneven model batch (Sec. 2: various trial models are fitted) --------
  * A batch of n_models independent models, each with its own number of waves,
  * data sample and MC sample, evaluated for K parameter sets per model in one

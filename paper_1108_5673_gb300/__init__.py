@@ -35,6 +35,7 @@ class Likelihood:
     def load_events(self, data_amp, mc_amp, n_mc_gen):
         self._abi.pwa_load_events(self.ctx, data_amp, mc_amp, n_mc_gen)
         self.n_data = int(data_amp.shape[0])
+        self.n_mc = int(mc_amp.shape[0])
         return self
 
     def build_norm(self):
@@ -51,6 +52,22 @@ class Likelihood:
     def nll_grad(self, V):
         nll, g, self.last_status = self._abi.pwa_nll_grad(self.ctx, V)
         return nll, g
+
+    def hessian(self, V):
+        """FUMILI Hessian of the NLL over p = (Re V, Im V): [2N, 2N] float64."""
+        H, self.last_status = self._abi.pwa_hessian(self.ctx, V, self.n_waves)
+        return H
+
+    def mc_weights(self, V, out=None):
+        """I(Omega_j) / n_mc_gen per accepted MC event, float32 (into `out`, a
+        numpy array or CUDA tensor, when given)."""
+        if out is None:
+            out = np.empty(self.n_mc, dtype=np.float32)
+        return self._abi.pwa_mc_weights(self.ctx, V, out)
+
+    def fit_fractions(self, V):
+        """[N, N]: Re(conj(V_a) M_ab V_b) / V^H M V (diagonal: wave fractions)."""
+        return self._abi.pwa_fit_fractions(self.ctx, V, self.n_waves)
 
     def load_resonance_events(self, wl):
         """Samples for free masses and widths (a synth.ResonanceWorkload or any

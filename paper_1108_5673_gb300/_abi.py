@@ -88,6 +88,9 @@ def load(path=LIB_PATH):
         "pwa_batch_nll_grad": ([P, P, I, P, P], I),
         "pwa_batch_last_error": ([P], ctypes.c_char_p),
         "pwa_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
+        "pwa_hessian": ([P, P, P], I),
+        "pwa_mc_weights": ([P, P, P], I),
+        "pwa_fit_fractions": ([P, P, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -262,6 +265,39 @@ def pwa_nll_grad_res(ctx, V, mass, width):
     rc = _check(ctx, load().pwa_nll_grad_res(ctx, p(V), p(mass), p(width), p(nll), p(gV), p(gM),
                                              p(gW)), allow=(PWA_EDOMAIN,))
     return float(nll[0]), gV, gM, gW, rc
+
+
+def pwa_hessian(ctx, V, n_waves):
+    """FUMILI Hessian over (Re V, Im V): ([2N, 2N] float64, status); an
+    all-zero H with PWA_EDOMAIN when a data intensity was not positive."""
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    H = np.empty((2 * n_waves, 2 * n_waves))
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    rc = _check(ctx, load().pwa_hessian(ctx, p(V), p(H)), allow=(PWA_EDOMAIN,))
+    return H, rc
+
+
+def pwa_mc_weights(ctx, V, w):
+    """Fill w ([n_mc_acc] float32: a numpy array or a CUDA tensor) with
+    I(Omega_j) / n_mc_gen of each accepted MC event; returns w."""
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    if not getattr(w, "is_cuda", False):
+        if not (isinstance(w, np.ndarray) and w.dtype == np.float32 and w.flags.c_contiguous):
+            raise ValueError("host weights must be a contiguous float32 numpy array")
+    elif "float32" not in str(w.dtype):
+        raise ValueError("device weights must be float32")
+    pw, _k = _ptr(w)
+    _check(ctx, load().pwa_mc_weights(ctx, V.ctypes.data_as(ctypes.c_void_p), pw))
+    return w
+
+
+def pwa_fit_fractions(ctx, V, n_waves):
+    """[N, N] float64: Re(conj(V_a) M_ab V_b) / V^H M V."""
+    V = np.ascontiguousarray(V, dtype=np.complex128)
+    F = np.empty((n_waves, n_waves))
+    p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(ctx, load().pwa_fit_fractions(ctx, p(V), p(F)))
+    return F
 
 
 def _bcheck(b, rc, allow=()):

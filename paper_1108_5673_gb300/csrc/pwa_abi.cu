@@ -51,6 +51,11 @@ struct pwa_ctx {
     bool res_loaded = false;
     double *d_res = nullptr;    // partials, ticket, io
     double *h_res = nullptr;    // pinned io mirror
+    // Hessian, projection weights, fit fractions (allocated on first use)
+    double *d_fx = nullptr;     // V [2N] | status [1] | out [max(4N^2, N^2)] | Hessian partials
+    size_t fx_bytes = 0;
+    float *d_w = nullptr;       // projection weights when the caller's buffer is on the host
+    int64_t w_len = 0;
     CUtensorMap data_map, table_map, xbf_map;
     size_t work_bytes = 0;
     bool loaded = false, has_norm = false;
@@ -560,6 +565,109 @@ int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const doub
     return status_from_flags(c, hs[0]);
 }
 
+// ---- Hessian, projection weights, fit fractions -----------------------------
+
+static int fx_buffer(pwa_ctx *c, const double *V, double **dV, int **dstat, double **dout,
+                     double **dpart)
+{
+    const int N = c->N;
+    const size_t nout = 4 * (size_t)N * N, npart = hess_partials_doubles(N, c->num_sms);
+    const size_t bytes = (2 * (size_t)N + 1 + nout + npart) * sizeof(double);
+    if (c->fx_bytes < bytes) {
+        dev_free(c->d_fx);
+        c->fx_bytes = 0;
+        int rc = dev_alloc(c, (void **)&c->d_fx, bytes, "Hessian scratch");
+        if (rc)
+            return rc;
+        c->fx_bytes = bytes;
+    }
+    *dV = c->d_fx;
+    *dstat = reinterpret_cast<int *>(c->d_fx + 2 * N);
+    *dout = c->d_fx + 2 * N + 1;
+    *dpart = *dout + nout;
+    CK(c, cudaMemcpyAsync(*dV, V, 2 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(c, cudaMemsetAsync(*dstat, 0, sizeof(double), c->stream));
+    return PWA_OK;
+}
+
+int pwa_hessian(pwa_ctx *c, const double *V, double *H)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!V || !H)
+        return fail(c, PWA_EINVAL, "null V or H");
+    if (!c->has_norm)
+        return fail(c, PWA_ESTATE, "pwa_build_norm must come first");
+    DeviceGuard g(c->device);
+    double *dV, *dH, *dpart;
+    int *ds;
+    int rc = fx_buffer(c, V, &dV, &ds, &dH, &dpart);
+    if (rc)
+        return rc;
+    CK(c, launch_hessian(c->data, dV, c->M, dpart, c->num_sms, ds, dH, c->stream));
+    const int P = 2 * c->N;
+    int flags = 0;
+    CK(c, cudaMemcpyAsync(H, dH, (size_t)P * P * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaMemcpyAsync(&flags, ds, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return status_from_flags(c, flags);
+}
+
+int pwa_mc_weights(pwa_ctx *c, const double *V, float *w)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!V || !w)
+        return fail(c, PWA_EINVAL, "null V or w");
+    if (!c->loaded)
+        return fail(c, PWA_ESTATE, "pwa_load_events must come first");
+    DeviceGuard g(c->device);
+    double *dV, *dout, *dpart;
+    int *ds;
+    int rc = fx_buffer(c, V, &dV, &ds, &dout, &dpart);
+    if (rc)
+        return rc;
+    const bool on_dev = is_device_pointer(w);
+    float *dw = w;
+    if (!on_dev) {
+        if (c->w_len < c->n_mc) {
+            dev_free(c->d_w);
+            c->w_len = 0;
+            if ((rc = dev_alloc(c, (void **)&c->d_w, (size_t)c->n_mc * sizeof(float), "weights")))
+                return rc;
+            c->w_len = c->n_mc;
+        }
+        dw = c->d_w;
+    }
+    CK(c, launch_mc_weights(c->mc, dV, c->n_gen, dw, c->num_sms * 8, c->stream));
+    if (!on_dev)
+        CK(c, cudaMemcpyAsync(w, dw, (size_t)c->n_mc * sizeof(float), cudaMemcpyDeviceToHost,
+                              c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PWA_OK;
+}
+
+int pwa_fit_fractions(pwa_ctx *c, const double *V, double *F)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!V || !F)
+        return fail(c, PWA_EINVAL, "null V or F");
+    if (!c->has_norm)
+        return fail(c, PWA_ESTATE, "pwa_build_norm must come first");
+    DeviceGuard g(c->device);
+    double *dV, *dF, *dpart;
+    int *ds;
+    int rc = fx_buffer(c, V, &dV, &ds, &dF, &dpart);
+    if (rc)
+        return rc;
+    CK(c, launch_fit_fractions(c->M, dV, c->N, dF, c->stream));
+    CK(c, cudaMemcpyAsync(F, dF, (size_t)c->N * c->N * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PWA_OK;
+}
+
 int pwa_table_bytes(int n_waves, int64_t n_events, int64_t *bytes)
 {
     if (!bytes || n_waves < 1 || n_waves > kMaxWaves || n_events < 0)
@@ -665,6 +773,8 @@ int pwa_destroy(pwa_ctx *c)
     dev_free(c->M);
     dev_free(c->amax);
     dev_free(c->d_io);
+    dev_free(c->d_fx);
+    dev_free(c->d_w);
     dev_free(c->d_work);
     if (c->h_io)
         cudaFreeHost(c->h_io);

@@ -454,6 +454,18 @@ int res_max_waves();
 int res_max_free();
 size_t res_partials_doubles(int n_waves, int n_free, int grid);
 cudaError_t launch_nll_res(const ResArgs &a, int grid, cudaStream_t s);
+
+// k_fit_extras.cu
+// FUMILI Hessian of the NLL over (Re V, Im V): H [2N][2N] doubles (device);
+// partials: hess_partials_doubles(n_waves, grid) doubles of scratch.
+size_t hess_partials_doubles(int n_waves, int grid);
+cudaError_t launch_hessian(const Planes &d, const double *V, const double *M, double *partials,
+                           int grid, int *status, double *H, cudaStream_t s);
+// w[j] = |sum_a V_a A_a(j)|^2 / n_gen for the accepted MC events (float, device).
+cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, float *w, int grid,
+                              cudaStream_t s);
+// F[a][b] = Re(conj(V_a) M_ab V_b) / V^H M V (device doubles).
+cudaError_t launch_fit_fractions(const double *M, const double *V, int N, double *F, cudaStream_t s);
 // dst[i] = (float)src[i] (round to nearest)
 cudaError_t launch_to_float(const double *src, int64_t n, float *dst, cudaStream_t s);
 

@@ -1,0 +1,164 @@
+"""GPU parity of the FUMILI Hessian, the MC projection weights and the fit
+fractions against the FP64 oracle.
+
+Hessian: per-event gradients d_i of ln I in FP32, so each d_i carries a few
+units of 2^-24 relative to |A|/|S|; the products are summed in FP32 over runs
+of a few hundred events and in float-float / FP64 beyond. Bound: max
+|H - H_oracle| <= 3e-6 max |H_oracle|, and exactly symmetric. Weights: S in
+FP32 by four FMA chains of ceil(N/4) waves joined pairwise, so per component
+|dS| <= (gamma_k + u) sqrt(2) T with k = 2 ceil(N/4) + 2, u = 2^-24 (the +u
+for V rounded to float) and T = sum_a |V_a| |A_a|; then
+|d|S|^2| <= 2 |S| |dS| + |dS|^2 and four more roundings of |S|^2 / N_gen give
+|w - w_exact| <= (4k + 10) u T^2 / N_gen. Fit fractions: FP64 from the same M,
+to 1e-10.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+H_TOL = 3e-6
+
+
+@pytest.fixture(scope="module")
+def pwa():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1108_5673_gb300 as pkg
+    return pkg
+
+
+def case(N, n_data, n_mc, seed=0):
+    waves = synth.waves_linear(N)
+    return synth.mixture_workload("h", waves, n_data, n_mc, seed_data=400 + seed,
+                                  seed_mc=500 + seed, seed_v=600 + seed)
+
+
+def real_grad(g):
+    """(d/dRe V, d/dIm V) = (2 Re g, 2 Im g) from the Wirtinger gradient g."""
+    return np.concatenate([2 * g.real, 2 * g.imag])
+
+
+def check_hessian(L, wl, V, Mo):
+    H = L.hessian(V)
+    assert L.last_status == 0
+    Ho, bad = oracle.hessian(wl.A_data, Mo, V)
+    assert bad == 0
+    assert np.array_equal(H, H.T)
+    err = np.max(np.abs(H - Ho)) / np.max(np.abs(Ho))
+    assert err <= H_TOL, err
+    return H
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 8, 13, 20, 24, 25, 32, 40, 48])
+def test_hessian_waves_sweep(pwa, N):
+    wl = case(N, 3000, 4000, seed=N)
+    with pwa.Likelihood(N) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        Mo = oracle.norm_matrix(wl.A_mc, wl.n_gen)
+        for V in (wl.V_true, synth.random_V(N, 70 + N)):
+            check_hessian(L, wl, V, Mo)
+
+
+@pytest.mark.parametrize("n_data", [1, 7, 255, 256, 257, 2049, 10007])
+def test_hessian_ragged_event_counts(pwa, n_data):
+    wl = case(20, n_data, 700, seed=n_data % 89)
+    with pwa.Likelihood(20) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        check_hessian(L, wl, synth.random_V(20, n_data), oracle.norm_matrix(wl.A_mc, wl.n_gen))
+
+
+def test_hessian_any_form_current(pwa):
+    """The Hessian reads the direct-form store whichever form evaluates the NLL."""
+    wl = case(12, 5000, 3000, seed=3)
+    V = synth.random_V(12, 5)
+    with pwa.Likelihood(12, forms=pwa.PWA_FORM_AMP | pwa.PWA_FORM_TABLE) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        H0 = L.hessian(V)
+        L.set_form(pwa.PWA_FORM_TABLE)
+        assert np.array_equal(L.hessian(V), H0)
+
+
+def test_hessian_domain_error(pwa):
+    wl = case(6, 500, 500, seed=9)
+    with pwa.Likelihood(6) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        H = L.hessian(np.zeros(6, complex))
+        assert L.last_status == pwa.PWA_EDOMAIN
+        assert not H.any()
+        # the context stays usable
+        check_hessian(L, wl, wl.V_true, oracle.norm_matrix(wl.A_mc, wl.n_gen))
+
+
+def test_hessian_homogeneity_at_scale(pwa):
+    """At a million events (the bench workload): H p = -2 grad NLL + 3 grad N
+    with the GPU's own gradient, since ln I and V^H M V are homogeneous of
+    degree 2 in p; and H positive definite."""
+    N, n = 20, 1_000_000
+    wl = case(N, n, 1_000_000, seed=1)
+    V = wl.V_true * math.sqrt(n / oracle.norm_term(oracle.norm_matrix_blas(wl.A_mc, wl.n_gen),
+                                                   wl.V_true)[0])
+    with pwa.Likelihood(N) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        M = L.build_norm()
+        H = L.hessian(V)
+        _, g = L.nll_grad(V[None, :])
+    p = np.concatenate([V.real, V.imag])
+    gN = real_grad(M @ V)
+    rhs = -2 * real_grad(g[0]) + 3 * gN
+    assert np.linalg.norm(H @ p - rhs) <= 1e-5 * np.linalg.norm(gN)
+    assert np.linalg.eigvalsh(H).min() > 0
+
+
+@pytest.mark.parametrize("N", [1, 3, 8, 20, 33, 48])
+@pytest.mark.parametrize("where", ["host", "device"])
+def test_mc_weights(pwa, N, where):
+    import torch
+    wl = case(N, 100, 5003, seed=N + 40)
+    V = synth.random_V(N, N + 41)
+    with pwa.Likelihood(N) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        M = L.build_norm()
+        if where == "host":
+            w = L.mc_weights(V)
+        else:
+            out = torch.empty(wl.A_mc.shape[0], dtype=torch.float32, device="cuda:0")
+            w = L.mc_weights(V, out).cpu().numpy()
+    wo = oracle.mc_weights(wl.A_mc, V, wl.n_gen)
+    A = wl.A_mc.astype(np.complex128)
+    T2 = (np.abs(A) * np.abs(V)[None, :]).sum(axis=1) ** 2 / wl.n_gen
+    k = 2 * math.ceil(N / 4) + 2
+    assert np.all(np.abs(w - wo) <= (4 * k + 10) * 2.0 ** -24 * T2)
+    nv = oracle.norm_term(M, V)[0]
+    assert abs(w.astype(np.float64).sum() - nv) <= 1e-6 * nv
+
+
+@pytest.mark.parametrize("N", [1, 2, 7, 20, 48])
+def test_fit_fractions(pwa, N):
+    wl = case(N, 100, 4000, seed=N + 80)
+    V = synth.random_V(N, N + 81)
+    with pwa.Likelihood(N) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        F = L.fit_fractions(V)
+    Fo = oracle.fit_fractions(oracle.norm_matrix(wl.A_mc, wl.n_gen), V)
+    assert np.max(np.abs(F - Fo)) <= 1e-10 * max(1.0, np.abs(Fo).max())
+    assert abs(F.sum() - 1.0) <= 1e-12 * N * N
+    assert np.all(np.diag(F) >= 0)
+
+
+def test_extras_need_state(pwa):
+    with pwa.Likelihood(4) as L:
+        with pytest.raises(pwa.PwaError):
+            L.hessian(np.ones(4, complex))
+        with pytest.raises(pwa.PwaError):
+            L.fit_fractions(np.ones(4, complex))
