@@ -55,6 +55,11 @@ def _load():
         lib.oracle_mc_weights.argtypes = [P, I64, I, P, D, P]
         lib.oracle_fit_fractions.argtypes = [P, I, P, P]
         lib.oracle_nll_res.restype = I
+        lib.oracle_norm_incoh.argtypes = [P, I64, I, I, D, P]
+        lib.oracle_norm_incoh.restype = I
+        lib.oracle_table_incoh.argtypes = [P, I64, I, I, P]
+        lib.oracle_nll_incoh.argtypes = [P, I64, I, I, P, P, I, P, P]
+        lib.oracle_nll_incoh.restype = I
         _lib = lib
     return _lib
 
@@ -197,3 +202,37 @@ def fit_fractions(M, V):
     F = np.empty((N, N))
     _load().oracle_fit_fractions(_p(M), N, _p(V), _p(F))
     return F
+
+
+def norm_matrix_incoh(A_mc, n_gen):
+    """M[a, b] = (1/N_gen) sum_j sum_l conj(A_a^l(j)) A_b^l(j) for A_mc [n, L, N]."""
+    A = _c128(A_mc)
+    n, L, N = A.shape
+    M = np.empty((N, N), dtype=np.complex128)
+    _load().oracle_norm_incoh(_p(A), n, L, N, float(n_gen), _p(M))
+    return M
+
+
+def table_incoh(A):
+    """Per-event table of the incoherent sum, [n, N*N] float64, for A [n, L, N]."""
+    A = _c128(A)
+    n, L, N = A.shape
+    T = np.empty((n, N * N))
+    _load().oracle_table_incoh(_p(A), n, L, N, _p(T))
+    return T
+
+
+def nll_incoh(A, M, V, grad=True):
+    """Eq. 3 with I = sum_l |sum_a V_a A_a^l|^2, A [n, L, N]. Returns as nll_amp."""
+    A, M, V = _c128(A), _c128(M), _c128(V)
+    n, L, N = A.shape
+    single = V.ndim == 1
+    V2 = V.reshape(-1, N)
+    K = V2.shape[0]
+    nll = np.empty(K)
+    g = np.empty_like(V2) if grad else None
+    bad = _load().oracle_nll_incoh(_p(A), n, L, N, _p(M), _p(V2), K, _p(nll),
+                                   _p(g) if grad else None)
+    if single:
+        return nll[0], (g[0] if grad else None), bad
+    return nll, g, bad

@@ -69,3 +69,42 @@ def grad_closed(A, A_mc, n_gen, V):
 
 def rotate(V, phi):
     return [v * cmath.exp(1j * phi) for v in V]
+
+
+def nll_incoh(A, A_mc, n_gen, V):
+    """-ln L of Eq. 3 with the per-event products summed over incoherent
+    components: A, A_mc are lists (events) of lists (components) of lists
+    (waves) of complex amplitudes."""
+    N = len(V)
+    data = 0.0
+    for comps in A:
+        s = 0j
+        for amp in comps:
+            for a in range(N):
+                for b in range(N):
+                    s += V[a] * V[b].conjugate() * amp[a] * amp[b].conjugate()
+        data -= math.log(s.real)
+    norm = 0j
+    for a in range(N):
+        for b in range(N):
+            bracket = 0j
+            for comps in A_mc:
+                for amp in comps:
+                    bracket += amp[a] * amp[b].conjugate()
+            norm += V[a] * V[b].conjugate() * bracket / n_gen
+    return data + norm.real
+
+
+def wirtinger_grad_incoh(A, A_mc, n_gen, V, h=1e-6):
+    """Central differences of nll_incoh, combined as in wirtinger_grad."""
+    out = []
+    for a in range(len(V)):
+        parts = []
+        for step in (h, 1j * h):
+            vp = list(V)
+            vm = list(V)
+            vp[a] += step
+            vm[a] -= step
+            parts.append((nll_incoh(A, A_mc, n_gen, vp) - nll_incoh(A, A_mc, n_gen, vm)) / (2 * h))
+        out.append(complex(parts[0], parts[1]) / 2)
+    return out

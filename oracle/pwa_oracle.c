@@ -34,8 +34,16 @@
  *   per-MC-event weights w_j = I(Omega_j) / N_gen (their sum is V^H M V) for
  *   projections, and the fit fractions F_ab = Re(conj(V_a) M_ab V_b) / V^H M V.
  *
+ * Incoherent sum over L unobserved components (e.g. helicity states of an
+ * undetected photon polarisation): each event carries amplitudes A_a^l(i),
+ * l < L, and Eq. 1 becomes I = sum_l |sum_a V_a A_a^l|^2. Eq. 3 keeps its
+ * form with the per-event products summed over l, A_a A*_b -> sum_l A_a^l
+ * conj(A_b^l), in the data term (the table) and in the MC bracket alike;
+ * g_a = - sum_i sum_l conj(A_a^l(i)) S_i^l / I_i + (M V)_a.
+ *
  * Layouts: complex numbers are interleaved (re, im) doubles.
- *   Amplitudes: event-major A[(i*N + a)*2 + {0,1}].
+ *   Amplitudes: event-major A[(i*N + a)*2 + {0,1}]; with L components
+ *   A[((i*L + l)*N + a)*2 + {0,1}].
  *   Table: event-major T[i*N*N + p] with p = a for the real diagonal
  *   |A_a|^2, then for each pair a < b in row-major order the two reals
  *   Re(A_a conj A_b), Im(A_a conj A_b).
@@ -504,4 +512,128 @@ void oracle_fit_fractions(const double *M, int N, const double *V, double *F)
             cmul(V[2 * a], -V[2 * a + 1], pr, pi, &qr, &qi);
             F[a * N + b] = qr / nv;
         }
+}
+
+/* ---- Incoherent sum over L components ---------------------------------- */
+/* M[a][b] = (1/n_gen) sum_{j < n_acc} sum_{l < L} conj(A_a^l(j)) A_b^l(j). */
+int oracle_norm_incoh(const double *A, int64_t n_acc, int L, int N, double n_gen, double *M)
+{
+    if (N <= 0 || L <= 0 || n_acc < 0 || !(n_gen > 0))
+        return -1;
+    for (int a = 0; a < N; ++a)
+        for (int b = 0; b < N; ++b) {
+            nsum re = {0, 0}, im = {0, 0};
+            for (int64_t j = 0; j < n_acc; ++j)
+                for (int l = 0; l < L; ++l) {
+                    const double *x = A + ((j * L + l) * N) * 2;
+                    double pr, pi;
+                    cmul(x[2 * a], -x[2 * a + 1], x[2 * b], x[2 * b + 1], &pr, &pi);
+                    nadd(&re, pr);
+                    nadd(&im, pi);
+                }
+            M[(a * N + b) * 2] = nval(&re) / n_gen;
+            M[(a * N + b) * 2 + 1] = nval(&im) / n_gen;
+        }
+    return 0;
+}
+
+/* Per-event table of the incoherent sum, T_i[a][b] = sum_l A_a^l conj(A_b^l),
+ * stored like oracle_table (real diagonal, then Re/Im of the pairs a < b). */
+int oracle_table_incoh(const double *A, int64_t n, int L, int N, double *T)
+{
+    const int64_t P = (int64_t)N * N;
+    for (int64_t i = 0; i < n; ++i) {
+        double *t = T + i * P;
+        for (int a = 0; a < N; ++a) {
+            nsum d = {0, 0};
+            for (int l = 0; l < L; ++l) {
+                const double *x = A + ((i * L + l) * N) * 2;
+                nadd(&d, x[2 * a] * x[2 * a] + x[2 * a + 1] * x[2 * a + 1]);
+            }
+            t[a] = nval(&d);
+        }
+        int p = N;
+        for (int a = 0; a < N; ++a)
+            for (int b = a + 1; b < N; ++b) {
+                nsum re = {0, 0}, im = {0, 0};
+                for (int l = 0; l < L; ++l) {
+                    const double *x = A + ((i * L + l) * N) * 2;
+                    double pr, pi;
+                    cmul(x[2 * a], x[2 * a + 1], x[2 * b], -x[2 * b + 1], &pr, &pi);
+                    nadd(&re, pr);
+                    nadd(&im, pi);
+                }
+                t[p++] = nval(&re);
+                t[p++] = nval(&im);
+            }
+    }
+    return 0;
+}
+
+/* Eq. 3 with the incoherent intensity I_i = sum_l |S_i^l|^2,
+ * S_i^l = sum_a V_a A_a^l(i), for K parameter sets; returns and outputs as
+ * oracle_nll_amp. */
+int oracle_nll_incoh(const double *A, int64_t n, int L, int N, const double *M,
+                     const double *V, int K, double *nll, double *grad)
+{
+    int bad_sets = 0;
+    nsum *gr = (nsum *)malloc(sizeof(nsum) * 2 * (size_t)N);
+    double *mv = (double *)malloc(sizeof(double) * 2 * (size_t)N);
+    double *s = (double *)malloc(sizeof(double) * 2 * (size_t)L);
+    for (int k = 0; k < K; ++k) {
+        const double *v = V + (size_t)k * 2 * N;
+        nsum lnsum = {0, 0};
+        int bad = 0;
+        memset(gr, 0, sizeof(nsum) * 2 * (size_t)N);
+        for (int64_t i = 0; i < n && !bad; ++i) {
+            nsum I = {0, 0};
+            for (int l = 0; l < L; ++l) {
+                const double *x = A + ((i * L + l) * N) * 2;
+                nsum sr = {0, 0}, si = {0, 0};
+                for (int a = 0; a < N; ++a) {
+                    double pr, pi;
+                    cmul(v[2 * a], v[2 * a + 1], x[2 * a], x[2 * a + 1], &pr, &pi);
+                    nadd(&sr, pr);
+                    nadd(&si, pi);
+                }
+                s[2 * l] = nval(&sr);
+                s[2 * l + 1] = nval(&si);
+                nadd(&I, s[2 * l] * s[2 * l] + s[2 * l + 1] * s[2 * l + 1]);
+            }
+            const double Iv = nval(&I);
+            if (!(Iv > 0) || !isfinite(Iv)) {
+                bad = 1;
+                break;
+            }
+            nadd(&lnsum, log(Iv));
+            if (grad)
+                for (int l = 0; l < L; ++l) {
+                    const double *x = A + ((i * L + l) * N) * 2;
+                    const double rr = s[2 * l] / Iv, ri = s[2 * l + 1] / Iv;
+                    for (int a = 0; a < N; ++a) {
+                        double pr, pi;
+                        cmul(x[2 * a], -x[2 * a + 1], rr, ri, &pr, &pi);  /* conj(A) S / I */
+                        nadd(&gr[2 * a], pr);
+                        nadd(&gr[2 * a + 1], pi);
+                    }
+                }
+        }
+        double nv;
+        oracle_norm_term(M, N, v, &nv, mv);
+        if (bad) {
+            ++bad_sets;
+            nll[k] = INFINITY;
+            if (grad)
+                memset(grad + (size_t)k * 2 * N, 0, sizeof(double) * 2 * (size_t)N);
+            continue;
+        }
+        nll[k] = -nval(&lnsum) + nv;
+        if (grad)
+            for (int c = 0; c < 2 * N; ++c)
+                grad[(size_t)k * 2 * N + c] = -nval(&gr[c]) + mv[c];
+    }
+    free(gr);
+    free(mv);
+    free(s);
+    return bad_sets;
 }

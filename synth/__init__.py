@@ -16,6 +16,11 @@ number of candidates drawn is N_MC^Gen (Sec. 2, the text after Eq. 2).
 Amplitudes: A_alpha(Omega) = BW(m; M_alpha, Gamma_alpha) * Y_{l_alpha}^{m_alpha}
 (cos theta, phi) with the fixed-width Breit-Wigner 1 / (M^2 - m^2 - i M Gamma)
 and orthonormal spherical harmonics carrying the Condon-Shortley phase.
+
+Incoherent components (an unobserved helicity, e.g. of the radiated photon):
+component l of wave alpha uses the magnetic number
+mu = clip(m_alpha + h_l, -l_alpha, l_alpha) with h = (+1, -1, 0, +2, -2)[l],
+A_alpha^l(Omega) = BW(m; M_alpha, Gamma_alpha) * Y_{l_alpha}^{mu}(cos theta, phi).
 """
 from __future__ import annotations
 
@@ -203,6 +208,28 @@ def angular(events, waves, dtype=np.complex64):
     return out
 
 
+HELICITIES = (1, -1, 0, 2, -2)
+
+
+def helicity_amplitudes(events, waves, n_lambda, dtype=np.complex64, chunk=1 << 20):
+    """Event-major [n, n_lambda, N] amplitudes of the incoherent components:
+    A[i, l, alpha] = BW_alpha(m_i) Y_{l_alpha}^{mu}(Omega_i) with
+    mu = clip(m_alpha + h_l, -l_alpha, l_alpha), h = HELICITIES[l]."""
+    if not 1 <= n_lambda <= len(HELICITIES):
+        raise ValueError("n_lambda must be in [1, %d]" % len(HELICITIES))
+    n = len(events["m"])
+    out = np.empty((n, n_lambda, len(waves)), dtype=dtype)
+    for s in range(0, n, chunk):
+        e = slice(s, min(n, s + chunk))
+        m, c, p = events["m"][e], events["costh"][e], events["phi"][e]
+        for a, wv in enumerate(waves):
+            bw = breit_wigner(m, wv.mass, wv.width)
+            for lam in range(n_lambda):
+                mu = max(-wv.l, min(wv.l, wv.m + HELICITIES[lam]))
+                out[e, lam, a] = bw * ylm(wv.l, mu, c, p)
+    return out
+
+
 def random_V(n_waves, seed=SEED_VTRUE, k=None):
     """Production amplitudes with Re and Im drawn N(0, 1): shape [n_waves] or [k, n_waves]."""
     rng = np.random.Generator(np.random.Philox(seed))
@@ -229,6 +256,17 @@ def mixture_workload(name, waves, n_data, n_mc_acc, seed_data=SEED_DATA, seed_mc
     ev_m, n_gen = mc_sample(n_mc_acc, seed_mc)
     return Workload(name, waves, amplitudes(ev_d, waves, dtype), amplitudes(ev_m, waves, dtype),
                     n_gen, V)
+
+
+def incoherent_workload(name, waves, n_data, n_mc_acc, n_lambda=2, seed_data=SEED_DATA,
+                        seed_mc=SEED_MC, seed_v=SEED_VTRUE, dtype=np.complex64):
+    """As mixture_workload, with [n, n_lambda, N] amplitudes of incoherent
+    components (helicity_amplitudes) for the data and the accepted MC."""
+    V = random_V(len(waves), seed_v)
+    ev_d = data_sample_mixture(n_data, waves, V, seed_data)
+    ev_m, n_gen = mc_sample(n_mc_acc, seed_mc)
+    return Workload(name, waves, helicity_amplitudes(ev_d, waves, n_lambda, dtype),
+                    helicity_amplitudes(ev_m, waves, n_lambda, dtype), n_gen, V)
 
 
 def paper_scale(n_data=1_000_000, n_mc_acc=5_000_000, n_waves=20, **kw):

@@ -449,3 +449,84 @@ def test_mc_weights_and_fit_fractions():
     assert abs(F.sum() - 1.0) <= 1e-12                    # fractions + interference = 1
     for a in range(5):
         assert abs(F[a, a] - abs(V[a]) ** 2 * Mm[a, a].real / nv) <= 1e-13
+
+
+# ---- incoherent sums over unobserved components --------------------------------
+
+def incoh_sample(n_data=20, n_mc=30, n_waves=3, L=2, seed=5):
+    waves = synth.waves_small()[:n_waves]
+    rng = np.random.Generator(np.random.Philox(seed))
+    A = synth.helicity_amplitudes(synth.phase_space(n_data, rng), waves, L, np.complex128)
+    A_mc = synth.helicity_amplitudes(synth.phase_space(n_mc, rng), waves, L, np.complex128)
+    return A, A_mc, synth.random_V(n_waves, seed + 1)
+
+
+@pytest.mark.parametrize("L", [1, 2, 3])
+def test_incoherent_brute_force(L):
+    """NLL and gradient against the literal double sums with the products
+    summed over components, and the gradient against their differences."""
+    A, A_mc, V = incoh_sample(L=L)
+    n_gen = 47.0
+    M = oracle.norm_matrix_incoh(A_mc, n_gen)
+    nll, g, bad = oracle.nll_incoh(A, M, V)
+    assert bad == 0
+    nb = brute.nll_incoh(A.tolist(), A_mc.tolist(), n_gen, list(V))
+    assert abs(nll - nb) <= 1e-12 * abs(nb)
+    gfd = np.array(brute.wirtinger_grad_incoh(A.tolist(), A_mc.tolist(), n_gen, list(V)))
+    assert rel(g, gfd) < 1e-6
+
+
+def test_incoherent_one_component_is_coherent():
+    A, A_mc, V = incoh_sample(n_data=50, n_mc=60, n_waves=4, L=1)
+    M = oracle.norm_matrix_incoh(A_mc, 90.0)
+    assert rel(M, oracle.norm_matrix(A_mc[:, 0, :], 90.0)) < 1e-15
+    n1, g1, _ = oracle.nll_incoh(A, M, V)
+    n0, g0, _ = oracle.nll_amp(A[:, 0, :], M, V)
+    assert abs(n1 - n0) <= 1e-14 * abs(n0) and rel(g1, g0) < 1e-14
+
+
+def test_incoherent_scaled_copies_closed_form():
+    """Components that are copies A^l = c_l A of one amplitude set give
+    I = (sum_l |c_l|^2) |S|^2 and M = (sum_l |c_l|^2) M_coherent, so
+    NLL = NLL_coherent(A, c2 M) - n ln c2 with c2 = sum_l |c_l|^2."""
+    A, A_mc, V = incoh_sample(n_data=40, n_mc=50, n_waves=4, L=1)
+    c = np.array([0.7 + 0.2j, -0.3 + 1.1j, 0.5j])
+    c2 = float(np.sum(np.abs(c) ** 2))
+    Ai = A[:, 0, None, :] * c[None, :, None]
+    Ai_mc = A_mc[:, 0, None, :] * c[None, :, None]
+    M = oracle.norm_matrix_incoh(Ai_mc, 80.0)
+    M0 = oracle.norm_matrix(A_mc[:, 0, :], 80.0)
+    assert rel(M, c2 * M0) < 1e-14
+    n, g, _ = oracle.nll_incoh(Ai, M, V)
+    n0, g0, _ = oracle.nll_amp(A[:, 0, :], c2 * M0, V)
+    assert abs(n - (n0 - len(A) * math.log(c2))) <= 1e-13 * abs(n)
+    # the data gradient is unchanged by the common factor, the MC part scales with it
+    assert rel(g, g0) < 1e-13
+
+
+def test_incoherent_component_phases_and_table_form():
+    """A phase per component leaves the incoherent sum unchanged (a coherent
+    sum over components would not be), and the table form with the products
+    summed over components gives the same NLL and gradient."""
+    A, A_mc, V = incoh_sample(n_data=60, n_mc=70, n_waves=4, L=3)
+    M = oracle.norm_matrix_incoh(A_mc, 100.0)
+    n, g, _ = oracle.nll_incoh(A, M, V)
+    ph = np.exp(1j * np.array([0.4, -2.1, 1.3]))
+    n2, g2, _ = oracle.nll_incoh(A * ph[None, :, None], oracle.norm_matrix_incoh(
+        A_mc * ph[None, :, None], 100.0), V)
+    assert abs(n2 - n) <= 1e-13 * abs(n) and rel(g2, g) < 1e-12
+    coh = lambda X: oracle.intensity(X.sum(axis=1), V)
+    assert rel(coh(A * ph[None, :, None]), coh(A)) > 1e-3
+    nt, gt, _ = oracle.nll_table(oracle.table_incoh(A), M, V)
+    assert abs(nt - n) <= 1e-13 * abs(n) and rel(gt, g) < 1e-12
+
+
+def test_incoherent_euler_identity_and_phase():
+    A, A_mc, V = incoh_sample(n_data=200, n_mc=300, n_waves=4, L=2)
+    M = oracle.norm_matrix_incoh(A_mc, 400.0)
+    n, g, _ = oracle.nll_incoh(A, M, V)
+    nv, _ = oracle.norm_term(M, V)
+    vg = np.vdot(V, g)
+    assert abs(vg.real - (nv - len(A))) < 1e-10 * len(A) and abs(vg.imag) < 1e-10 * len(A)
+    n2, g2, _ = oracle.nll_incoh(A, M, V * np.exp(0.8j))
+    assert abs(n2 - n) < 1e-12 * abs(n) and rel(g2, g * np.exp(0.8j)) < 1e-12
