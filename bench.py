@@ -18,9 +18,13 @@ Other workloads (one JSON line each, same keys):
           sample (1M events x 20 waves); one step = one Hessian
   weights projection weights I / N_gen of the 5M accepted MC events of the
           same sample into a device buffer; one step = one pass
+  incoh   incoherent sum over 2 unobserved components per event (I = sum_l
+          |sum_a V_a A_a^l|^2): 1M data events x 20 waves x 2, direct form
+  incoh_table  the same sample in the table form (table bytes independent of
+          the number of components)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload direct|table|tc|res|models|hessian|weights]
+                  [--workload direct|table|tc|res|models|hessian|weights|incoh|incoh_table]
 
 `value` is device-timed (CUDA events on the launching stream; L2 flushed
 between steps where the inputs fit in it); `e2e` times the public host call
@@ -56,13 +60,16 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "res": 1148.160e6 + 3.716096e6,
            "models": None,
            "hessian": None,
-           "weights": None}
+           "weights": None,
+           "incoh": None,
+           "incoh_table": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
            "models": "batched_kernel<F, 2> (all sizes)", "hessian": "hess_kernel<20>",
-           "weights": "mc_weights_kernel<20>"}
+           "weights": "mc_weights_kernel<20>", "incoh": "nll_incoh_kernel<20, 2>",
+           "incoh_table": "nll_table_kernel<20>"}
 DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,
-                 "hessian": 2000, "weights": 2000}
+                 "hessian": 2000, "weights": 2000, "incoh": 1500, "incoh_table": 1000}
 
 
 def measured_peaks():
@@ -291,6 +298,50 @@ def job_models(pwa, torch, stream, local, rank):
              "each way)")
 
 
+def job_incoh(pwa, torch, stream, local, rank, form="amp"):
+    """Incoherent sum over 2 components: 1M data events x 20 waves x 2, M
+    from 2M accepted MC events x 2 components."""
+    import synth
+    L_, n_mc = 2, 2_000_000
+    wl = synth.incoherent_workload("incoh_1M_events_20_waves_2_components",
+                                   synth.waves_linear(N_WAVES), N_DATA, n_mc, n_lambda=L_)
+    V = synth.start_points(N_WAVES, 1, seed=synth.SEED_STARTS + rank)[0]
+    table = form == "table"
+    forms = pwa.PWA_FORM_TABLE if table else pwa.PWA_FORM_AMP
+    L = pwa.Likelihood(N_WAVES, device=local, forms=forms, max_k=1, stream=stream.cuda_stream)
+    L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+    t0 = time.perf_counter()
+    L.build_norm()
+    build_norm_s = time.perf_counter() - t0
+    dV = torch.from_numpy(V[None]).cuda()
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    dg = torch.empty(1, N_WAVES, dtype=torch.complex128, device="cuda")
+    Vh = V[None].copy()
+
+    def cpu_baseline():
+        import oracle
+        sub = 200_000
+        Mo = oracle.norm_matrix_incoh(wl.A_mc[:200_000], wl.n_gen)
+        dt, k = timed_oracle(lambda: oracle.nll_incoh(wl.A_data[:sub], Mo, V), 10.0)
+        return {"value": 1.0 / (dt * N_DATA / sub), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d incoherent NLL+grad evaluations of the first 200k events (FP64 C "
+                          "oracle, 1 thread), scaled to the 1M-event sample" % k}
+
+    return Job(
+        name="incoh_table" if table else "incoh", lib=L,
+        step=lambda: L.nll_grad_async(dV, dn, dg), host_step=lambda: L.nll_grad(Vh),
+        sync=L.sync, evals_per_step=1, launches_per_step=1, flush=False,
+        metric="NLL+grad evals/s, incoherent sum over 2 components (1M events, 20 waves); "
+               "% HBM roofline",
+        workload="1M data events x 20 waves x 2 incoherent components (FP32 amplitudes, %s), "
+                 "M from 2M accepted MC x 2 components, K=1 per evaluation"
+                 % ("per-event table of 400 floats, table form" if table else "direct form"),
+        config={"n_waves": N_WAVES, "n_lambda": L_, "n_data": N_DATA, "n_mc_acc": n_mc,
+                "n_mc_gen": wl.n_gen, "K": 1, "form": form, "build_norm_s": build_norm_s},
+        roof={"bound": "hbm", "bytes": (4.0 * N_WAVES ** 2 if table else 8.0 * L_ * N_WAVES) * N_DATA},
+        dtype="f32", h2d=16 * N_WAVES + 8, d2h=8 + 16 * N_WAVES + 8, cpu_baseline=cpu_baseline)
+
+
 def job_fit_extra(pwa, torch, stream, local, rank, what):
     """FUMILI Hessian of the 1M-event sample, or the projection weights of its
     5M accepted MC events (host V in; H to the host, or w into a device buffer)."""
@@ -383,7 +434,8 @@ def main():
     ap.add_argument("--steps", type=int, default=None)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models", "hessian", "weights"])
+    ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models", "hessian", "weights",
+                             "incoh", "incoh_table"])
     ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -414,6 +466,8 @@ def main():
         job = job_tc(pwa, torch, stream, local, rank, args.precision)
     elif args.workload == "res":
         job = job_res(pwa, torch, stream, local, rank)
+    elif args.workload in ("incoh", "incoh_table"):
+        job = job_incoh(pwa, torch, stream, local, rank, "table" if args.workload == "incoh_table" else "amp")
     elif args.workload in ("hessian", "weights"):
         job = job_fit_extra(pwa, torch, stream, local, rank, args.workload)
     else:

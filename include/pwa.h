@@ -108,6 +108,31 @@ int pwa_load_events(pwa_ctx *ctx, const void *data_amp, int64_t n_data,
                     const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
                     int amp_dtype);
 
+/* Load a sample whose intensity is an incoherent sum over n_lambda
+ * unobserved components per event (e.g. helicity states of an undetected
+ * polarisation), I(Omega) = sum_l |sum_a V_a A_a^l(Omega)|^2. Eq. 3 keeps its
+ * form with the per-event products A_a A*_b of its data term and of its MC
+ * bracket summed over the components: M[a][b] = (1/N_MC^Gen) sum_j sum_l
+ * conj(A_a^l(j)) A_b^l(j), g_a = - sum_i sum_l conj(A_a^l(i)) S_i^l / I_i +
+ * (M V)_a with S_i^l = sum_b V_b A_b^l(i). (The paper writes the coherent
+ * sum, Eq. 1; this is the reading of Eq. 3 for several components, which
+ * leaves the table form's cost unchanged.)
+ *   data_amp: [n_data][n_lambda][n_waves] complex, host or device pointer
+ *   mc_amp:   [n_mc_acc][n_lambda][n_waves] complex, host or device pointer
+ *   n_lambda: 1 <= n_lambda <= 4 (1 is pwa_load_events)
+ * Afterwards pwa_build_norm, pwa_nll, pwa_nll_grad(_async), pwa_set_form
+ * and pwa_fit_fractions work as for a coherent sample; the direct form
+ * (PWA_FORM_AMP) reads 8 n_lambda n_waves bytes per event and takes up to 24
+ * waves at n_lambda = 2, 16 at 3, 12 at 4; the table form reads 4 n_waves^2
+ * bytes per event whatever n_lambda. Errors as pwa_load_events, plus
+ * PWA_EINVAL (n_lambda out of range, n_mc_acc * n_lambda >= 2^31 - 1024) and
+ * PWA_ENOTSUP (a context with PWA_FORM_TC, or n_waves above the direct
+ * form's limit for n_lambda); pwa_hessian and pwa_mc_weights return
+ * PWA_ENOTSUP on such a sample. */
+int pwa_load_events_incoherent(pwa_ctx *ctx, int n_lambda, const void *data_amp, int64_t n_data,
+                               const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
+                               int amp_dtype);
+
 /* Build the MC normalisation matrix M (the inner bracket of the second term
  * of Eq. 3), once per loaded sample. If M_out is not NULL it receives M as
  * [n_waves][n_waves] complex128, row-major, M_out[a][b] as defined above.

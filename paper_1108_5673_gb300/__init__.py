@@ -33,7 +33,12 @@ class Likelihood:
         self.last_status = PWA_OK
 
     def load_events(self, data_amp, mc_amp, n_mc_gen):
-        self._abi.pwa_load_events(self.ctx, data_amp, mc_amp, n_mc_gen)
+        """[n, N] amplitudes (coherent sum, Eq. 1), or [n, n_lambda, N] for an
+        incoherent sum over n_lambda unobserved components per event."""
+        if len(data_amp.shape) == 3:
+            self._abi.pwa_load_events_incoherent(self.ctx, data_amp, mc_amp, n_mc_gen)
+        else:
+            self._abi.pwa_load_events(self.ctx, data_amp, mc_amp, n_mc_gen)
         self.n_data = int(data_amp.shape[0])
         self.n_mc = int(mc_amp.shape[0])
         return self

@@ -89,6 +89,7 @@ def load(path=LIB_PATH):
         "pwa_batch_last_error": ([P], ctypes.c_char_p),
         "pwa_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
         "pwa_hessian": ([P, P, P], I),
+        "pwa_load_events_incoherent": ([P, I, P, I64, P, I64, D, I], I),
         "pwa_mc_weights": ([P, P, P], I),
         "pwa_fit_fractions": ([P, P, P], I),
     }
@@ -163,6 +164,28 @@ def pwa_load_events(ctx, data_amp, mc_amp, n_mc_gen):
     pm, km_ = _ptr(mc_amp)
     return _check(ctx, load().pwa_load_events(ctx, pd, int(data_amp.shape[0]), pm,
                                               int(mc_amp.shape[0]), float(n_mc_gen), kd))
+
+
+def pwa_load_events_incoherent(ctx, data_amp, mc_amp, n_mc_gen):
+    """data_amp / mc_amp: [n, n_lambda, n_waves] complex64 or complex128 (numpy
+    or CUDA tensor, contiguous): n_lambda incoherent components per event."""
+    def kind(x):
+        dt = str(getattr(x, "dtype", ""))
+        if "complex64" in dt:
+            return PWA_C64
+        if "complex128" in dt:
+            return PWA_C128
+        raise ValueError("amplitudes must be complex64 or complex128, got %s" % dt)
+    kd, km = kind(data_amp), kind(mc_amp)
+    if kd != km:
+        raise ValueError("data and MC amplitudes must share one dtype")
+    if len(data_amp.shape) != 3 or tuple(data_amp.shape[1:]) != tuple(mc_amp.shape[1:]):
+        raise ValueError("amplitudes must be [n, n_lambda, n_waves] with matching trailing shapes")
+    pd, kd_ = _ptr(data_amp)
+    pm, km_ = _ptr(mc_amp)
+    return _check(ctx, load().pwa_load_events_incoherent(
+        ctx, int(data_amp.shape[1]), pd, int(data_amp.shape[0]), pm, int(mc_amp.shape[0]),
+        float(n_mc_gen), kd))
 
 
 def pwa_build_norm(ctx, n_waves):

@@ -70,6 +70,38 @@ __global__ void table_kernel(const float *__restrict__ planes, int64_t pitch, in
     }
 }
 
+// Per-event table of an incoherent sum over L components (planes of L N
+// waves, component l of wave a at plane 2 (l N + a)): products of floats are
+// exact in double, summed over components in double and rounded once.
+__global__ void table_incoh_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n,
+                                   int N, int L, float *__restrict__ table, int64_t tpitch)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n)
+        return;
+    auto re = [&](int l, int w) { return (double)planes[(2 * (l * N + w)) * pitch + i]; };
+    auto im = [&](int l, int w) { return (double)planes[(2 * (l * N + w) + 1) * pitch + i]; };
+    for (int w = 0; w < N; ++w) {
+        double d = 0.0;
+        for (int l = 0; l < L; ++l)
+            d += re(l, w) * re(l, w) + im(l, w) * im(l, w);
+        table[w * tpitch + i] = __double2float_rn(d);
+    }
+    int p = N;
+    for (int x = 0; x < N; ++x)
+        for (int y = x + 1; y < N; ++y) {
+            double tr = 0.0, ti = 0.0;
+            for (int l = 0; l < L; ++l) {
+                // A_x conj(A_y) = (xr yr + xi yi) + i (xi yr - xr yi)
+                tr += re(l, x) * re(l, y) + im(l, x) * im(l, y);
+                ti += im(l, x) * re(l, y) - re(l, x) * im(l, y);
+            }
+            table[(int64_t)p * tpitch + i] = __double2float_rn(tr);
+            table[(int64_t)(p + 1) * tpitch + i] = __double2float_rn(ti);
+            p += 2;
+        }
+}
+
 __global__ void amp_max_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n, int N,
                                float *__restrict__ amax)
 {
@@ -157,6 +189,20 @@ cudaError_t launch_table_build(const Planes &amp, float *table, int64_t table_pi
     const int64_t blocks = (amp.n + 127) / 128;
     table_kernel<<<(unsigned)blocks, 128, 0, s>>>(amp.ptr, amp.pitch, amp.n, amp.n_waves, table,
                                                    table_pitch);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_table_build_incoh(const Planes &amp, int n_lambda, float *table,
+                                     int64_t table_pitch, cudaStream_t s)
+{
+    if (amp.n <= 0)
+        return cudaSuccess;
+    if (n_lambda < 1 || amp.n_waves % n_lambda)
+        return cudaErrorInvalidValue;
+    const int64_t blocks = (amp.n + 127) / 128;
+    table_incoh_kernel<<<(unsigned)blocks, 128, 0, s>>>(amp.ptr, amp.pitch, amp.n,
+                                                        amp.n_waves / n_lambda, n_lambda, table,
+                                                        table_pitch);
     return cudaGetLastError();
 }
 

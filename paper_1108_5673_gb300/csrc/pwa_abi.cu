@@ -41,6 +41,7 @@ struct pwa_ctx {
     void *xbf = nullptr;    // BF16 slices [2F][pitch] of the data (tensor-core form)
     long long *xsum = nullptr;  // sum of the per-event exponents (inside xbf)
     int xs = 2;                 // BF16 slices of the amplitudes (tensor-core form)
+    int n_lambda = 1;           // incoherent components per event (data planes hold L N waves)
     int tune_groups = 0;        // direct form: consumer groups (0 = default rule)
     int tune_res_cps = 1;       // free-resonance kernel: blocks per SM
     // free-resonance form
@@ -52,7 +53,8 @@ struct pwa_ctx {
     double *d_res = nullptr;    // partials, ticket, io
     double *h_res = nullptr;    // pinned io mirror
     // Hessian, projection weights, fit fractions (allocated on first use)
-    double *d_fx = nullptr;     // V [2N] | status [1] | out [max(4N^2, N^2)] | Hessian partials
+    double *d_fx = nullptr;     // V [2N] | status [1] | out [4N^2] | Hessian partials
+    double *h_fx = nullptr;     // pinned mirror of V | status | out
     size_t fx_bytes = 0;
     float *d_w = nullptr;       // projection weights when the caller's buffer is on the host
     int64_t w_len = 0;
@@ -185,6 +187,7 @@ void free_sample(pwa_ctx *c)
     dev_free(c->tmax);
     dev_free(c->xbf);
     c->loaded = c->has_norm = false;
+    c->n_lambda = 1;
 }
 
 // Copy n events of nw complex waves (event-major, host or device) into the
@@ -341,7 +344,9 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         a.nll = dnll + k;
         a.grad = dgrad ? dgrad + (size_t)2 * N * k : nullptr;
         cudaError_t e = cudaSuccess;
-        if (c->form == PWA_FORM_AMP)
+        if (c->form == PWA_FORM_AMP && c->n_lambda > 1)
+            e = launch_nll_incoh(c->data, c->n_lambda, a, c->num_sms, c->stream);
+        else if (c->form == PWA_FORM_AMP)
             e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream, c->tune_groups);
         else if (c->form == PWA_FORM_TABLE)
             e = launch_nll_table(c->n_data, N, &c->table_map, a, c->tmax, c->num_sms, c->stream);
@@ -567,26 +572,54 @@ int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const doub
 
 // ---- Hessian, projection weights, fit fractions -----------------------------
 
+// Device scratch and its pinned host mirror for the Hessian, weight and
+// fraction calls; copies V in (through the mirror) and clears the status word.
 static int fx_buffer(pwa_ctx *c, const double *V, double **dV, int **dstat, double **dout,
                      double **dpart)
 {
     const int N = c->N;
-    const size_t nout = 4 * (size_t)N * N, npart = hess_partials_doubles(N, c->num_sms);
-    const size_t bytes = (2 * (size_t)N + 1 + nout + npart) * sizeof(double);
+    const size_t nio = 2 * (size_t)N + 1 + 4 * (size_t)N * N;
+    const size_t npart = hess_partials_doubles(N, c->num_sms);
+    const size_t bytes = (nio + npart) * sizeof(double);
     if (c->fx_bytes < bytes) {
         dev_free(c->d_fx);
+        if (c->h_fx)
+            cudaFreeHost(c->h_fx);
+        c->h_fx = nullptr;
         c->fx_bytes = 0;
         int rc = dev_alloc(c, (void **)&c->d_fx, bytes, "Hessian scratch");
         if (rc)
             return rc;
+        if (cudaMallocHost((void **)&c->h_fx, nio * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_fx = nullptr;
+            dev_free(c->d_fx);
+            return fail(c, PWA_ENOMEM, "pinned host buffer");
+        }
         c->fx_bytes = bytes;
     }
     *dV = c->d_fx;
     *dstat = reinterpret_cast<int *>(c->d_fx + 2 * N);
     *dout = c->d_fx + 2 * N + 1;
-    *dpart = *dout + nout;
-    CK(c, cudaMemcpyAsync(*dV, V, 2 * N * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    CK(c, cudaMemsetAsync(*dstat, 0, sizeof(double), c->stream));
+    *dpart = *dout + 4 * (size_t)N * N;
+    memcpy(c->h_fx, V, 2 * N * sizeof(double));
+    c->h_fx[2 * N] = 0.0;  // status word(s)
+    CK(c, cudaMemcpyAsync(*dV, c->h_fx, (2 * N + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+    return PWA_OK;
+}
+
+// Copies `count` doubles of the output area back through the pinned mirror
+// (with the status word in front of them), waits, and returns the flags.
+static int fx_result(pwa_ctx *c, size_t count, double *out, int *flags)
+{
+    const int N = c->N;
+    CK(c, cudaMemcpyAsync(c->h_fx + 2 * N, c->d_fx + 2 * N, (1 + count) * sizeof(double),
+                          cudaMemcpyDeviceToHost, c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    *flags = *reinterpret_cast<const int *>(c->h_fx + 2 * N);
+    if (out)
+        memcpy(out, c->h_fx + 2 * N + 1, count * sizeof(double));
     return PWA_OK;
 }
 
@@ -598,6 +631,8 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
         return fail(c, PWA_EINVAL, "null V or H");
     if (!c->has_norm)
         return fail(c, PWA_ESTATE, "pwa_build_norm must come first");
+    if (c->n_lambda > 1)
+        return fail(c, PWA_ENOTSUP, "the Hessian takes coherent samples only");
     DeviceGuard g(c->device);
     double *dV, *dH, *dpart;
     int *ds;
@@ -607,9 +642,8 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
     CK(c, launch_hessian(c->data, dV, c->M, dpart, c->num_sms, ds, dH, c->stream));
     const int P = 2 * c->N;
     int flags = 0;
-    CK(c, cudaMemcpyAsync(H, dH, (size_t)P * P * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaMemcpyAsync(&flags, ds, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
+    if ((rc = fx_result(c, (size_t)P * P, H, &flags)))
+        return rc;
     return status_from_flags(c, flags);
 }
 
@@ -621,6 +655,8 @@ int pwa_mc_weights(pwa_ctx *c, const double *V, float *w)
         return fail(c, PWA_EINVAL, "null V or w");
     if (!c->loaded)
         return fail(c, PWA_ESTATE, "pwa_load_events must come first");
+    if (c->n_lambda > 1)
+        return fail(c, PWA_ENOTSUP, "projection weights take coherent samples only");
     DeviceGuard g(c->device);
     double *dV, *dout, *dpart;
     int *ds;
@@ -662,10 +698,8 @@ int pwa_fit_fractions(pwa_ctx *c, const double *V, double *F)
     if (rc)
         return rc;
     CK(c, launch_fit_fractions(c->M, dV, c->N, dF, c->stream));
-    CK(c, cudaMemcpyAsync(F, dF, (size_t)c->N * c->N * sizeof(double), cudaMemcpyDeviceToHost,
-                          c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    return PWA_OK;
+    int flags = 0;
+    return fx_result(c, (size_t)c->N * c->N, F, &flags);
 }
 
 int pwa_table_bytes(int n_waves, int64_t n_events, int64_t *bytes)
@@ -739,7 +773,8 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
         c->h_io = nullptr;
         return bail(fail(c, PWA_ENOMEM, "pinned host buffer"));
     }
-    size_t nwork = amp_partials_doubles(c->N, c->num_sms) + 8;
+    size_t nwork = std::max(amp_partials_doubles(c->N, c->num_sms),
+                            incoh_partials_doubles(c->N, c->num_sms)) + 8;
     if (forms & PWA_FORM_TABLE)
         nwork = std::max(nwork, table_scratch_bytes(c->N, c->num_sms) / sizeof(double) + 16);
     if (forms & PWA_FORM_TC)
@@ -775,6 +810,8 @@ int pwa_destroy(pwa_ctx *c)
     dev_free(c->d_io);
     dev_free(c->d_fx);
     dev_free(c->d_w);
+    if (c->h_fx)
+        cudaFreeHost(c->h_fx);
     dev_free(c->d_work);
     if (c->h_io)
         cudaFreeHost(c->h_io);
@@ -804,6 +841,7 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
     DeviceGuard g(c->device);
     cudaStreamSynchronize(c->stream);
     free_sample(c);
+    c->n_lambda = 1;
     int rc = load_planes(c, data_amp, n_data, amp_dtype, &c->data);
     if (!rc)
         rc = load_planes(c, mc_amp, n_mc_acc, amp_dtype, &c->mc);
@@ -872,6 +910,92 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
     return PWA_OK;
 }
 
+int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, int64_t n_data,
+                               const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
+                               int amp_dtype)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (n_lambda == 1)
+        return pwa_load_events(c, data_amp, n_data, mc_amp, n_mc_acc, n_mc_gen, amp_dtype);
+    if (n_lambda < 1 || n_lambda > incoh_max_components())
+        return fail(c, PWA_EINVAL, "n_lambda=%d outside [1, %d]", n_lambda, incoh_max_components());
+    if (!data_amp || !mc_amp)
+        return fail(c, PWA_EINVAL, "null amplitude pointer");
+    if (n_data < 1 || n_mc_acc < 1)
+        return fail(c, PWA_EINVAL, "n_data=%lld and n_mc_acc=%lld must be >= 1",
+                    (long long)n_data, (long long)n_mc_acc);
+    if (!(n_mc_gen >= (double)n_mc_acc))
+        return fail(c, PWA_EINVAL, "n_mc_gen=%g must be >= n_mc_acc=%lld", n_mc_gen,
+                    (long long)n_mc_acc);
+    if (amp_dtype != PWA_C64 && amp_dtype != PWA_C128)
+        return fail(c, PWA_EINVAL, "amp_dtype=%d is neither PWA_C64 nor PWA_C128", amp_dtype);
+    if (n_data > ((int64_t)1 << 31) - 1024 || n_mc_acc * n_lambda > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "samples are limited to 2^31 - 1024 events (MC: events x n_lambda)");
+    if (c->cfg.forms & PWA_FORM_TC)
+        return fail(c, PWA_ENOTSUP, "the tensor-core form takes coherent samples only");
+    if ((c->cfg.forms & PWA_FORM_AMP) && c->N > incoh_max_waves(n_lambda))
+        return fail(c, PWA_ENOTSUP, "the direct form takes up to %d waves at n_lambda=%d",
+                    incoh_max_waves(n_lambda), n_lambda);
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    free_sample(c);
+    const int N = c->N, L = n_lambda;
+    // data: [n][L][N] complex = n events of L N waves, plane 2 (l N + a) = Re A_a^l
+    Planes &d = c->data;
+    d.n = n_data;
+    d.n_waves = L * N;
+    d.pitch = round_up(n_data, 256);
+    int rc = dev_alloc(c, (void **)&d.ptr, (size_t)2 * L * N * d.pitch * sizeof(float), "planes");
+    if (!rc && cudaMemsetAsync(d.ptr, 0, (size_t)2 * L * N * d.pitch * sizeof(float), c->stream) !=
+                   cudaSuccess)
+        rc = fail(c, PWA_ECUDA, "memset");
+    if (!rc)
+        rc = pack_rows(c, data_amp, n_data, amp_dtype, L * N, d.ptr, d.pitch);
+    // MC: the same bytes read as n L pseudo-events of N waves, so that M sums
+    // the products over components as well as over events
+    if (!rc)
+        rc = load_planes(c, mc_amp, n_mc_acc * L, amp_dtype, &c->mc);
+    if (!rc && (c->cfg.forms & PWA_FORM_TABLE)) {
+        c->table_pitch = d.pitch;
+        rc = dev_alloc(c, (void **)&c->table, (size_t)N * N * c->table_pitch * sizeof(float),
+                       "table");
+        if (!rc)
+            rc = dev_alloc(c, (void **)&c->tmax, (size_t)N * N * sizeof(float), "tmax");
+        if (!rc) {
+            const int P = N * N;
+            cudaError_t e = launch_table_build_incoh(d, L, c->table, c->table_pitch, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(c->tmax, 0, P * sizeof(float), c->stream);
+            if (e == cudaSuccess)
+                e = launch_plane_absmax(c->table, c->table_pitch, n_data, P, c->tmax, c->stream);
+            if (e == cudaSuccess)
+                e = encode_planes_map(&c->table_map, c->table, n_data, c->table_pitch, P,
+                                      table_box_events(), table_box_rows(N));
+            if (e != cudaSuccess)
+                rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
+        }
+    }
+    if (!rc && cudaMemsetAsync(c->amax, 0, N * sizeof(float), c->stream) != cudaSuccess)
+        rc = fail(c, PWA_ECUDA, "memset");
+    if (!rc) {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "loading: %s", cudaGetErrorString(e));
+    }
+    if (rc) {
+        free_sample(c);
+        return rc;
+    }
+    c->n_lambda = L;
+    c->n_data = n_data;
+    c->n_mc = n_mc_acc;
+    c->n_gen = n_mc_gen;
+    c->loaded = true;
+    c->has_norm = false;
+    return PWA_OK;
+}
+
 int pwa_build_norm(pwa_ctx *c, double *M_out)
 {
     if (!c)
@@ -906,6 +1030,8 @@ int pwa_set_form(pwa_ctx *c, int form)
         return fail(c, PWA_EINVAL, "unknown form %d", form);
     if (!(c->cfg.forms & form))
         return fail(c, PWA_ESTATE, "form %d was not requested at pwa_create", form);
+    if (form == PWA_FORM_TC && c->n_lambda > 1)
+        return fail(c, PWA_ENOTSUP, "the tensor-core form takes coherent samples only");
     if (form != c->form) {
         // the two kernels lay out the shared scratch differently: start clean
         DeviceGuard g(c->device);
@@ -1325,7 +1451,9 @@ int pwa_autotune(pwa_ctx *c, const char *cache_path, char *choice, int choice_le
     std::string summary;
     char buf[256];
     if (c->loaded && c->has_norm) {
-        if (c->form == PWA_FORM_AMP) {
+        if (c->form == PWA_FORM_AMP && c->n_lambda > 1) {
+            summary += "incoherent direct form: one launch shape";
+        } else if (c->form == PWA_FORM_AMP) {
             const std::string key = tune_key(c, "amp-groups");
             int best = 0;
             double best_us = 0.0;

@@ -455,6 +455,19 @@ int res_max_free();
 size_t res_partials_doubles(int n_waves, int n_free, int grid);
 cudaError_t launch_nll_res(const ResArgs &a, int grid, cudaStream_t s);
 
+// k_nll_incoh.cu: direct form with an incoherent sum over n_lambda components;
+// d holds 2 n_lambda N planes (plane 2 (l N + a) = Re A_a^l). Same scratch,
+// ticket and outputs as the direct-form kernel (EvalArgs, one parameter set).
+int incoh_max_components();
+int incoh_max_waves(int n_lambda);  // largest N the direct kernel takes for n_lambda
+size_t incoh_partials_doubles(int n_waves, int grid);
+cudaError_t launch_nll_incoh(const Planes &d, int n_lambda, const EvalArgs &a, int grid,
+                             cudaStream_t s);
+// table of the incoherent sum: T[a][b] = sum_l A_a^l conj(A_b^l), layout as
+// launch_table_build, from planes of n_lambda * N waves
+cudaError_t launch_table_build_incoh(const Planes &amp, int n_lambda, float *table,
+                                     int64_t table_pitch, cudaStream_t s);
+
 // k_fit_extras.cu
 // FUMILI Hessian of the NLL over (Re V, Im V): H [2N][2N] doubles (device);
 // partials: hess_partials_doubles(n_waves, grid) doubles of scratch.
