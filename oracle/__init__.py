@@ -50,7 +50,7 @@ def _load():
         lib.oracle_nll_table.argtypes = [P, I64, I, P, P, I, P, P]
         lib.oracle_nll_table.restype = I
         lib.oracle_nll_res.argtypes = [I, I, P, P, P, I64, P, P, P, I64, D, P, P, P, P, P, P, P]
-        lib.oracle_hessian.argtypes = [P, I64, I, P, P, P]
+        lib.oracle_hessian.argtypes = [P, I64, I, P, P]
         lib.oracle_hessian.restype = I
         lib.oracle_mc_weights.argtypes = [P, I64, I, P, D, P]
         lib.oracle_fit_fractions.argtypes = [P, I, P, P]
@@ -177,13 +177,13 @@ def nll_res(m_d, Y_d, Afix_d, m_mc, Y_mc, Afix_mc, n_gen, V, mass, width):
     return nll.value, gV, gM, gW, bad
 
 
-def hessian(A, M, V):
-    """FUMILI Hessian of the NLL in p = (Re V, Im V): [2N, 2N] float64
-    (sum_i grad ln I_i grad ln I_i^T + d^2 V^H M V / dp^2), and n_bad."""
-    A, M, V = _c128(A), _c128(M), _c128(V)
+def hessian(A, V):
+    """FUMILI's approximation of the NLL Hessian in p = (Re V, Im V):
+    sum_i grad ln I_i grad ln I_i^T, [2N, 2N] float64; and n_bad."""
+    A, V = _c128(A), _c128(V)
     n, N = A.shape
     H = np.empty((2 * N, 2 * N))
-    bad = _load().oracle_hessian(_p(A), n, N, _p(M), _p(V), _p(H))
+    bad = _load().oracle_hessian(_p(A), n, N, _p(V), _p(H))
     return H, bad
 
 

@@ -27,10 +27,12 @@
  *   undefined: the call reports status 1, NLL = +inf and a zero gradient.
  *
  * Beyond the likelihood itself (the fitter's needs, Sec. 4 and 5):
- *   FUMILI's Hessian of the NLL in the real parameters p = (Re V, Im V):
- *     H = sum_i grad(ln I_i) grad(ln I_i)^T + d^2 (V^H M V) / dp^2,
- *   with grad(ln I_i) = 2 (Re, Im) of conj(A_a(i)) S_i / I_i per wave a and
- *   d^2 (V^H M V) = 2 [[Re M, -Im M], [Im M, Re M]];
+ *   FUMILI's approximation of the Hessian of the NLL in the real parameters
+ *   p = (Re V, Im V): the second derivatives of the intensity are dropped in
+ *   both terms of Eq. 3 (-sum_i d^2 I_i / I_i in the data term, d^2(V^H M V)
+ *   in the MC term; at the minimum they cancel in expectation), leaving
+ *     H = sum_i grad(ln I_i) grad(ln I_i)^T,
+ *   grad(ln I_i) = 2 (Re, Im) of conj(A_a(i)) S_i / I_i per wave a;
  *   per-MC-event weights w_j = I(Omega_j) / N_gen (their sum is V^H M V) for
  *   projections, and the fit fractions F_ab = Re(conj(V_a) M_ab V_b) / V^H M V.
  *
@@ -440,9 +442,10 @@ int oracle_nll_res(int N, int R,
 }
 
 /* ---- FUMILI Hessian (Sec. 4, 5) ---------------------------------------- */
-/* H[2N][2N] row-major in p = (Re V_0..Re V_{N-1}, Im V_0..Im V_{N-1}).
+/* H = sum_i grad ln I_i grad ln I_i^T, [2N][2N] row-major in
+ * p = (Re V_0..Re V_{N-1}, Im V_0..Im V_{N-1}).
  * Returns 1 (and leaves H zero) if an intensity is not positive and finite. */
-int oracle_hessian(const double *A, int64_t n, int N, const double *M, const double *V, double *H)
+int oracle_hessian(const double *A, int64_t n, int N, const double *V, double *H)
 {
     const int P = 2 * N;
     nsum *h = (nsum *)calloc((size_t)P * P, sizeof(nsum));
@@ -476,15 +479,6 @@ int oracle_hessian(const double *A, int64_t n, int N, const double *M, const dou
     for (int x = 0; x < P; ++x)
         for (int y = 0; y < P; ++y)
             H[x * P + y] = bad ? 0.0 : nval(&h[x * P + y]);
-    if (!bad)
-        for (int a = 0; a < N; ++a)
-            for (int b = 0; b < N; ++b) {
-                const double mr = M[(a * N + b) * 2], mi = M[(a * N + b) * 2 + 1];
-                H[a * P + b] += 2.0 * mr;              /* Re-Re block */
-                H[(N + a) * P + N + b] += 2.0 * mr;    /* Im-Im block */
-                H[a * P + N + b] += -2.0 * mi;         /* Re-Im block */
-                H[(N + a) * P + b] += 2.0 * mi;        /* Im-Re block */
-            }
     free(h);
     free(d);
     return bad;
