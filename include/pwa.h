@@ -208,20 +208,23 @@ int pwa_nll_grad_res(pwa_ctx *ctx, const double *V, const double *mass, const do
 
 /* ---- what the fitter and the plots take besides the NLL -------------------
  * FUMILI Hessian (Sec. 4 fits with FUMILI on analytic gradients and Hessian;
- * Sec. 5 returns the Hessian to the host each iteration). Over the real
- * parameters p = (Re V_0 .. Re V_{N-1}, Im V_0 .. Im V_{N-1}):
- *   H = sum_{i in data} d_i d_i^T + d^2(V^H M V)/dp^2,  d_i = grad_p ln I_i,
- *   (d_i)_a = 2 Re(conj(A_a(i)) S_i) / I_i,  (d_i)_{N+a} = 2 Im(...) / I_i,
- *   d^2(V^H M V)/dp^2 = 2 [[Re M, -Im M], [Im M, Re M]],
- * i.e. the exact second derivative of the normalisation term plus the
- * FUMILI (Gauss-Newton) approximation of the data term's, which drops
- * -sum_i d^2 I_i / I_i.
+ * Sec. 5 returns the Hessian to the host each iteration). FUMILI's
+ * approximation of the Hessian of Eq. 3 over the real parameters
+ * p = (Re V_0 .. Re V_{N-1}, Im V_0 .. Im V_{N-1}) drops the second
+ * derivatives of the intensity in both terms (-sum_i d^2 I_i / I_i in the data
+ * term, d^2(V^H M V) in the MC term; at the minimum they cancel in
+ * expectation), leaving
+ *   H = sum_{i in data} d_i d_i^T,  d_i = grad_p ln I_i,
+ *   (d_i)_a = 2 Re(conj(A_a(i)) S_i) / I_i,  (d_i)_{N+a} = 2 Im(...) / I_i.
+ * H is positive semi-definite with the global phase direction
+ * (-Im V, Re V) in its null space: fix one phase before solving with it.
  *   V: host [n_waves] complex128;  H: host [2 n_waves][2 n_waves] double,
  *   row-major, symmetric.
  * Uses the context's direct-form store (the data planes loaded by
  * pwa_load_events); any form may be current. Returns PWA_EDOMAIN (H all
  * zero) if a data intensity was not positive and finite; PWA_ESTATE before
- * pwa_build_norm; PWA_EINVAL for null pointers; PWA_ENOMEM, PWA_ECUDA. */
+ * pwa_load_events; PWA_EINVAL for null pointers; PWA_ENOTSUP for an
+ * incoherent sample; PWA_ENOMEM, PWA_ECUDA. */
 int pwa_hessian(pwa_ctx *ctx, const double *V, double *H);
 
 /* Projection weights (the "Plots" step of Table 1): the fitted intensity of

@@ -59,7 +59,9 @@ class Likelihood:
         return nll, g
 
     def hessian(self, V):
-        """FUMILI Hessian of the NLL over p = (Re V, Im V): [2N, 2N] float64."""
+        """FUMILI's approximation of the NLL Hessian over p = (Re V, Im V),
+        sum_i grad ln I_i grad ln I_i^T: [2N, 2N] float64 (singular along the
+        global phase direction)."""
         H, self.last_status = self._abi.pwa_hessian(self.ctx, V, self.n_waves)
         return H
 

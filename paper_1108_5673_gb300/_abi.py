@@ -291,8 +291,9 @@ def pwa_nll_grad_res(ctx, V, mass, width):
 
 
 def pwa_hessian(ctx, V, n_waves):
-    """FUMILI Hessian over (Re V, Im V): ([2N, 2N] float64, status); an
-    all-zero H with PWA_EDOMAIN when a data intensity was not positive."""
+    """FUMILI Hessian over (Re V, Im V), sum_i grad ln I_i grad ln I_i^T:
+    ([2N, 2N] float64, status); an all-zero H with PWA_EDOMAIN when a data
+    intensity was not positive."""
     V = np.ascontiguousarray(V, dtype=np.complex128)
     H = np.empty((2 * n_waves, 2 * n_waves))
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)

@@ -2,10 +2,11 @@
 // FUMILI needs the gradient and an approximation of the Hessian; plots of the
 // fit weight the accepted MC events with the fitted intensity).
 //
-// FUMILI Hessian in the real parameters p = (Re V_0..Re V_{N-1}, Im V_0..):
-//   H = sum_i d_i d_i^T + d^2(V^H M V)/dp^2,   d_i = grad_p ln I_i,
-//   d_i = 2 (Re, Im) of conj(A_a(i)) S_i / I_i per wave a,
-//   d^2(V^H M V)/dp^2 = 2 [[Re M, -Im M], [Im M, Re M]].
+// FUMILI's approximation of the NLL Hessian in the real parameters
+// p = (Re V_0..Re V_{N-1}, Im V_0..): the second derivatives of the intensity
+// are dropped in both terms of Eq. 3 (they cancel in expectation at the
+// minimum), leaving
+//   H = sum_i d_i d_i^T,   d_i = grad_p ln I_i = 2 (Re, Im) of conj(A_a(i)) S_i / I_i.
 // Each thread forms d_i of one event (S by a compensated dot product with V
 // as a float pair) into a shared-memory tile J of 256 events x 2NP columns
 // (Re parts at 0..NP-1, Im parts at NP..2NP-1, zero-padded). The upper
@@ -292,10 +293,10 @@ __global__ void __launch_bounds__(kHT, 1)
 }
 
 // H[r][c] over the real parameters (Re V at 0..N-1, Im V at N..2N-1): the sum
-// of the block partials in block order plus the MC block; zero when a data
-// intensity was not positive.
-__global__ void hess_finalize(const double *partials, int grid, int NP, int N, const double *M,
-                              const int *status, double *H)
+// of the block partials in block order; zero when a data intensity was not
+// positive.
+__global__ void hess_finalize(const double *partials, int grid, int NP, int N, const int *status,
+                              double *H)
 {
     const int B = NP / 2, NB = B * (B + 1) / 2, P = 2 * N;
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
@@ -314,13 +315,6 @@ __global__ void hess_finalize(const double *partials, int grid, int NP, int N, c
     double v = 0.0;
     for (int b = 0; b < grid; ++b)
         v += partials[b * stride + at];
-    // 2 [[Re M, -Im M], [Im M, Re M]]
-    const int a = r % N, bb = c % N;
-    const double mr = M[2 * (a * N + bb)], mi = M[2 * (a * N + bb) + 1];
-    if ((r < N) == (c < N))
-        v += 2.0 * mr;
-    else
-        v += r < N ? -2.0 * mi : 2.0 * mi;
     H[o] = dom ? 0.0 : v;
 }
 
@@ -375,7 +369,7 @@ __global__ void fit_fractions_kernel(const double *M, const double *V, int N, do
 
 template <int NP>
 cudaError_t hess_np(const Planes &d, const double *V, double *part, int grid, int *status,
-                    const double *M, double *H, cudaStream_t s)
+                    double *H, cudaStream_t s)
 {
     using C = HessCfg<NP>;
     cudaError_t e = cudaFuncSetAttribute(hess_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -386,7 +380,7 @@ cudaError_t hess_np(const Planes &d, const double *V, double *part, int grid, in
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     const int P = 2 * d.n_waves;
-    hess_finalize<<<(P * P + 255) / 256, 256, 0, s>>>(part, grid, NP, d.n_waves, M, status, H);
+    hess_finalize<<<(P * P + 255) / 256, 256, 0, s>>>(part, grid, NP, d.n_waves, status, H);
     return cudaGetLastError();
 }
 
@@ -414,19 +408,19 @@ size_t hess_partials_doubles(int n_waves, int grid)
     return (size_t)grid * (B * (B + 1) / 2) * 16;
 }
 
-cudaError_t launch_hessian(const Planes &d, const double *V, const double *M, double *partials,
-                           int grid, int *status, double *H, cudaStream_t s)
+cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, int grid, int *status,
+                           double *H, cudaStream_t s)
 {
     switch (pad_np(d.n_waves)) {
-    case 4: return hess_np<4>(d, V, partials, grid, status, M, H, s);
-    case 8: return hess_np<8>(d, V, partials, grid, status, M, H, s);
-    case 12: return hess_np<12>(d, V, partials, grid, status, M, H, s);
-    case 16: return hess_np<16>(d, V, partials, grid, status, M, H, s);
-    case 20: return hess_np<20>(d, V, partials, grid, status, M, H, s);
-    case 24: return hess_np<24>(d, V, partials, grid, status, M, H, s);
-    case 32: return hess_np<32>(d, V, partials, grid, status, M, H, s);
-    case 40: return hess_np<40>(d, V, partials, grid, status, M, H, s);
-    case 48: return hess_np<48>(d, V, partials, grid, status, M, H, s);
+    case 4: return hess_np<4>(d, V, partials, grid, status, H, s);
+    case 8: return hess_np<8>(d, V, partials, grid, status, H, s);
+    case 12: return hess_np<12>(d, V, partials, grid, status, H, s);
+    case 16: return hess_np<16>(d, V, partials, grid, status, H, s);
+    case 20: return hess_np<20>(d, V, partials, grid, status, H, s);
+    case 24: return hess_np<24>(d, V, partials, grid, status, H, s);
+    case 32: return hess_np<32>(d, V, partials, grid, status, H, s);
+    case 40: return hess_np<40>(d, V, partials, grid, status, H, s);
+    case 48: return hess_np<48>(d, V, partials, grid, status, H, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -12,7 +12,8 @@
 //
 // One event per thread, grid-stride, in two passes over the components: S^l
 // of every component first (the loads issued without branches), then the
-// gradient, re-reading each component from L1. S^l by the compensated dot product (Ogita,
+// gradient, re-reading each component from L1. Each warp prefetches the lines
+// of its next iteration into L1 while it computes the current one. S^l by the compensated dot product (Ogita,
 // Rump and Oishi, Dot2) with V as a float pair, packed (Re, Im) in FP32x2
 // registers, in four independent chains; ln I = e ln 2 + ln f with e summed
 // as an integer and ln f in float-float; gradients in FP32 per thread,
@@ -51,6 +52,11 @@ __device__ __forceinline__ void load_component(const float *__restrict__ pl, int
         ar[w] = w < N ? x : 0.f;
         ai[w] = w < N ? y : 0.f;
     }
+}
+
+__device__ __forceinline__ void prefetch_l1(const float *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
 }
 
 struct IncohShared {
@@ -96,8 +102,15 @@ __global__ void __launch_bounds__(kIT, 1)
     int eacc = 0;             // sum of exponents
     int bad = 0;
     const int64_t n = a.n_events;
-    for (int64_t i = (int64_t)blockIdx.x * kIT + threadIdx.x; i < n;
-         i += (int64_t)gridDim.x * kIT) {
+    const int64_t stride = (int64_t)gridDim.x * kIT;
+    for (int64_t i = (int64_t)blockIdx.x * kIT + threadIdx.x; i < n; i += stride) {
+        // The warp's events of the next iteration fill one 128-byte line per
+        // plane: lane k fetches the lines of planes k, k + 32, ... into L1,
+        // so the loads of that iteration find them there.
+        const int64_t nb = i - lane + stride;
+        if (nb < n)
+            for (int p = lane; p < 2 * L * N; p += 32)
+                prefetch_l1(pl + p * pitch + nb);
         // the component loops are not unrolled (the V coefficients are re-read
         // from shared memory per component instead of held in registers); S^l
         // stays in registers through the selects
@@ -260,6 +273,10 @@ cudaError_t launch_nl(const float *pl, int64_t pitch, const EvalArgs &a, int gri
     if constexpr (NP * L > kMaxLanes) {
         return cudaErrorInvalidValue;
     } else {
+        // shared memory is a few KB: leave the rest of the SM's array to L1,
+        // which holds the prefetched lines of the next iteration
+        cudaFuncSetAttribute(nll_incoh_kernel<NP, L>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             0);
         nll_incoh_kernel<NP, L><<<grid, kIT, 0, s>>>(pl, pitch, a);
         return cudaGetLastError();
     }

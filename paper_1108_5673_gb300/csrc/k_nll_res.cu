@@ -49,6 +49,11 @@ struct ResShared {
 
 __device__ __forceinline__ f2 splat(float v) { return pk2(v, v); }
 
+__device__ __forceinline__ void prefetch_l1(const float *p)
+{
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+}
+
 // Knuth's TwoSum on both halves: returns a + b rounded, err = the exact rest.
 __device__ __forceinline__ f2 two_sum2(f2 a, f2 b, f2 &err)
 {
@@ -115,14 +120,24 @@ __global__ void __launch_bounds__(res_threads(NP), 1) nll_res_kernel(const ResAr
             gm[r] = gw[r] = 0.f;
         dfloat acc = {0.f, 0.f};  // data: sum ln f; MC: sum I
         int eacc = 0;             // data: sum of exponents
-        for (int64_t i = (int64_t)blockIdx.x * kResThreads + threadIdx.x; i < n;
-             i += (int64_t)gridDim.x * kResThreads) {
+        const int64_t stride = (int64_t)gridDim.x * kResThreads;
+        for (int64_t i = (int64_t)blockIdx.x * kResThreads + threadIdx.x; i < n; i += stride) {
+            // the warp's events of the next iteration fill one 128-byte line per
+            // plane: lane k prefetches planes k, k + 32, ... into L1
+            const int64_t nb = i - lane + stride;
+            if (nb < n)
+                for (int p = lane; p < 1 + 2 * N; p += 32)
+                    prefetch_l1(base + p * pitch + nb);
             float ar[NP], ai[NP], br[RP], bi[RP];
             const float m = __ldg(base + i);
+            // unconditional loads (padded waves re-read wave 0, zeroed by a
+            // select), so that no branch separates them
 #pragma unroll
             for (int w = 0; w < NP; ++w) {
-                ar[w] = w < N ? __ldg(base + (1 + 2 * w) * pitch + i) : 0.f;
-                ai[w] = w < N ? __ldg(base + (2 + 2 * w) * pitch + i) : 0.f;
+                const int64_t o = (int64_t)(w < N ? 1 + 2 * w : 1) * pitch + i;
+                const float x = __ldg(base + o), y = __ldg(base + o + pitch);
+                ar[w] = w < N ? x : 0.f;
+                ai[w] = w < N ? y : 0.f;
             }
             // free waves: A = BW(m) Y
             const float mm = m * m;

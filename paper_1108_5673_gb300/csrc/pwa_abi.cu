@@ -629,8 +629,8 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
         return PWA_EINVAL;
     if (!V || !H)
         return fail(c, PWA_EINVAL, "null V or H");
-    if (!c->has_norm)
-        return fail(c, PWA_ESTATE, "pwa_build_norm must come first");
+    if (!c->loaded)
+        return fail(c, PWA_ESTATE, "pwa_load_events must come first");
     if (c->n_lambda > 1)
         return fail(c, PWA_ENOTSUP, "the Hessian takes coherent samples only");
     DeviceGuard g(c->device);
@@ -639,7 +639,7 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
     int rc = fx_buffer(c, V, &dV, &ds, &dH, &dpart);
     if (rc)
         return rc;
-    CK(c, launch_hessian(c->data, dV, c->M, dpart, c->num_sms, ds, dH, c->stream));
+    CK(c, launch_hessian(c->data, dV, dpart, c->num_sms, ds, dH, c->stream));
     const int P = 2 * c->N;
     int flags = 0;
     if ((rc = fx_result(c, (size_t)P * P, H, &flags)))

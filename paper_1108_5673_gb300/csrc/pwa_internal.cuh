@@ -469,11 +469,12 @@ cudaError_t launch_table_build_incoh(const Planes &amp, int n_lambda, float *tab
                                      int64_t table_pitch, cudaStream_t s);
 
 // k_fit_extras.cu
-// FUMILI Hessian of the NLL over (Re V, Im V): H [2N][2N] doubles (device);
-// partials: hess_partials_doubles(n_waves, grid) doubles of scratch.
+// FUMILI Hessian of the NLL over (Re V, Im V), sum_i grad ln I_i grad ln I_i^T:
+// H [2N][2N] doubles (device); partials: hess_partials_doubles(n_waves, grid)
+// doubles of scratch.
 size_t hess_partials_doubles(int n_waves, int grid);
-cudaError_t launch_hessian(const Planes &d, const double *V, const double *M, double *partials,
-                           int grid, int *status, double *H, cudaStream_t s);
+cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, int grid, int *status,
+                           double *H, cudaStream_t s);
 // w[j] = |sum_a V_a A_a(j)|^2 / n_gen for the accepted MC events (float, device).
 cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, float *w, int grid,
                               cudaStream_t s);
