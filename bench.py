@@ -57,11 +57,11 @@ WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M 
 TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "table": 1600.392e6 + 4.053504e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
-           "res": 1148.160e6 + 3.716096e6,
+           "res": 1148.450e6 + 3.265280e6,
            "models": None,
-           "hessian": None,
+           "hessian": 160.240896e6 + 3.188992e6,
            "weights": None,
-           "incoh": None,
+           "incoh": 320.140288e6 + 3.101952e6,
            "incoh_table": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
@@ -355,8 +355,7 @@ def job_fit_extra(pwa, torch, stream, local, rank, what):
         def cpu_baseline():
             import oracle
             sub = 20_000
-            Mo = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen)
-            dt, k = timed_oracle(lambda: oracle.hessian(wl.A_data[:sub], Mo, V), 10.0)
+            dt, k = timed_oracle(lambda: oracle.hessian(wl.A_data[:sub], V), 10.0)
             return {"value": 1.0 / (dt * N_DATA / sub), "unit": "Hessians/s", "cores": 1,
                     "kind": "oracle",
                     "sample": "%d FUMILI Hessians of the first 20k events (FP64 C oracle, "

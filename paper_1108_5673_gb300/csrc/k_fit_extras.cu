@@ -293,16 +293,16 @@ __global__ void __launch_bounds__(kHT, 1)
 }
 
 // H[r][c] over the real parameters (Re V at 0..N-1, Im V at N..2N-1): the sum
-// of the block partials in block order; zero when a data intensity was not
-// positive.
+// of the block partials, one warp per entry (lane k adds blocks k, k + 32, ...
+// in order, then a fixed shuffle tree), so the order is the same on every
+// run; zero when a data intensity was not positive.
 __global__ void hess_finalize(const double *partials, int grid, int NP, int N, const int *status,
                               double *H)
 {
     const int B = NP / 2, NB = B * (B + 1) / 2, P = 2 * N;
-    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (o >= P * P)
         return;
-    const bool dom = (*status & FLAG_DOMAIN) != 0;
     const int r = o / P, c = o % P;
     const int pr = r < N ? r : NP + (r - N), pc = c < N ? c : NP + (c - N);
     int x = pr >> 2, y = pc >> 2, ii = pr & 3, jj = pc & 3;
@@ -313,16 +313,20 @@ __global__ void hess_finalize(const double *partials, int grid, int NP, int N, c
     const int blk = x * B - x * (x - 1) / 2 + (y - x);
     const size_t stride = (size_t)NB * 16, at = (size_t)blk * 16 + ii * 4 + jj;
     double v = 0.0;
-    for (int b = 0; b < grid; ++b)
+    for (int b = lane; b < grid; b += 32)
         v += partials[b * stride + at];
-    H[o] = dom ? 0.0 : v;
+    v = warp_sum(v);
+    if (lane == 0)
+        H[o] = (*status & FLAG_DOMAIN) ? 0.0 : v;
 }
 
 // Blocks per SM the weights kernel is compiled for (the register cap that
 // gave no spills per size).
 constexpr int weights_min_blocks(int np) { return np == 16 ? 2 : np <= 24 ? 3 : 1; }
 
-// One event per thread and iteration; its 2N loads are issued together.
+// One event per thread and iteration; its 2N loads are issued together (an L1
+// prefetch of the next iteration's lines, as in the likelihood kernels, made
+// this kernel slower: 190 -> 242 us at 5M events, three CTAs per SM).
 template <int NP>
 __global__ void __launch_bounds__(256, weights_min_blocks(NP))
     mc_weights_kernel(const float *__restrict__ pl, int64_t pitch, int64_t n, int N,
@@ -380,7 +384,7 @@ cudaError_t hess_np(const Planes &d, const double *V, double *part, int grid, in
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     const int P = 2 * d.n_waves;
-    hess_finalize<<<(P * P + 255) / 256, 256, 0, s>>>(part, grid, NP, d.n_waves, status, H);
+    hess_finalize<<<(P * P + 7) / 8, 256, 0, s>>>(part, grid, NP, d.n_waves, status, H);
     return cudaGetLastError();
 }
 
