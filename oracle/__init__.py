@@ -55,6 +55,8 @@ def _load():
         lib.oracle_mc_weights.argtypes = [P, I64, I, P, D, P]
         lib.oracle_fit_fractions.argtypes = [P, I, P, P]
         lib.oracle_nll_res.restype = I
+        lib.oracle_amplitudes.argtypes = [P, I64, I, P, P, P, P, P]
+        lib.oracle_amplitudes.restype = I
         lib.oracle_norm_incoh.argtypes = [P, I64, I, I, D, P]
         lib.oracle_norm_incoh.restype = I
         lib.oracle_table_incoh.argtypes = [P, I64, I, I, P]
@@ -236,3 +238,20 @@ def nll_incoh(A, M, V, grad=True):
     if single:
         return nll[0], (g[0] if grad else None), bad
     return nll, g, bad
+
+
+def amplitudes(m, costh, phi, waves):
+    """A[i, a] = BW(m_i; M_a, G_a) Y_{l_a}^{m_a}(costh_i, phi_i), complex128
+    [n, N]; `waves` holds objects with mass, width, l, m (or 4-tuples)."""
+    kin = np.ascontiguousarray(np.stack([_f64(m), _f64(costh), _f64(phi)], axis=1))
+    w = [(x.mass, x.width, x.l, x.m) if hasattr(x, "mass") else tuple(x) for x in waves]
+    mass = _f64([x[0] for x in w])
+    width = _f64([x[1] for x in w])
+    ls = np.ascontiguousarray([x[2] for x in w], dtype=np.int32)
+    ms = np.ascontiguousarray([x[3] for x in w], dtype=np.int32)
+    A = np.empty((kin.shape[0], len(w)), dtype=np.complex128)
+    rc = _load().oracle_amplitudes(_p(kin), kin.shape[0], len(w), _p(mass), _p(width), _p(ls),
+                                   _p(ms), _p(A))
+    if rc:
+        raise ValueError("a wave has |m| > l or l < 0")
+    return A

@@ -43,6 +43,12 @@
  * conj(A_b^l), in the data term (the table) and in the MC bracket alike;
  * g_a = - sum_i sum_l conj(A_a^l(i)) S_i^l / I_i + (M V)_a.
  *
+ * The amplitude model the samples here use (the paper computes its amplitudes
+ * on the GPU, Sec. 4; its covariant tensor library is not given, so this is
+ * the model of the synthetic samples): A_a(Omega) = BW(m; M_a, G_a) Y_{l_a}^{m_a}
+ * (theta, phi) with BW(m; M, G) = 1 / (M^2 - m^2 - i M G) and Y_l^m the
+ * orthonormal spherical harmonic with the Condon-Shortley phase.
+ *
  * Layouts: complex numbers are interleaved (re, im) doubles.
  *   Amplitudes: event-major A[(i*N + a)*2 + {0,1}]; with L components
  *   A[((i*L + l)*N + a)*2 + {0,1}].
@@ -630,4 +636,74 @@ int oracle_nll_incoh(const double *A, int64_t n, int L, int N, const double *M,
     free(mv);
     free(s);
     return bad_sets;
+}
+
+/* ---- Amplitude model: Breit-Wigner x spherical harmonic ----------------- */
+/* Associated Legendre function P_l^m(x), 0 <= m <= l, with the Condon-Shortley
+ * phase: P_m^m = (-1)^m (2m - 1)!! (1 - x^2)^(m/2), P_{m+1}^m = x (2m + 1) P_m^m,
+ * (l - m) P_l^m = (2l - 1) x P_{l-1}^m - (l + m - 1) P_{l-2}^m. */
+static double legendre_p(int l, int m, double x)
+{
+    const double s = sqrt(fmax(0.0, 1.0 - x * x));
+    double pmm = 1.0;
+    for (int k = 1; k <= m; ++k)
+        pmm *= -(2.0 * k - 1.0) * s;
+    if (l == m)
+        return pmm;
+    double p1 = x * (2.0 * m + 1.0) * pmm;
+    if (l == m + 1)
+        return p1;
+    double p2 = pmm;
+    for (int ll = m + 2; ll <= l; ++ll) {
+        const double p = ((2.0 * ll - 1.0) * x * p1 - (ll + m - 1.0) * p2) / (ll - m);
+        p2 = p1;
+        p1 = p;
+    }
+    return p1;
+}
+
+/* Y_l^m(theta, phi) = sqrt((2l + 1)/(4 pi) (l - m)!/(l + m)!) P_l^m(cos theta)
+ * e^{i m phi} for m >= 0; Y_l^{-m} = (-1)^m conj(Y_l^m). */
+static void sph_harm(int l, int m, double costh, double phi, double *re, double *im)
+{
+    const int am = m < 0 ? -m : m;
+    double ratio = 1.0;  /* (l - am)! / (l + am)! */
+    for (int k = l - am + 1; k <= l + am; ++k)
+        ratio /= k;
+    const double pi = 3.14159265358979323846;
+    const double norm = sqrt((2.0 * l + 1.0) / (4.0 * pi) * ratio);
+    const double p = norm * legendre_p(l, am, costh);
+    double r = p * cos(am * phi), i = p * sin(am * phi);
+    if (m < 0) {
+        const double sign = (am & 1) ? -1.0 : 1.0;
+        r *= sign;
+        i *= -sign;
+    }
+    *re = r;
+    *im = i;
+}
+
+/* A[i][a] = BW(m_i; mass_a, width_a) Y_{l_a}^{mm_a}(costh_i, phi_i) for
+ * kin[i] = (m, cos theta, phi); BW = 1 / (M^2 - m^2 - i M G) written as
+ * (D + i M G) / (D^2 + (M G)^2) with D = M^2 - m^2. Returns -1 for a wave
+ * with |mm| > l or l < 0. */
+int oracle_amplitudes(const double *kin, int64_t n, int N, const double *mass, const double *width,
+                      const int *l, const int *mm, double *A)
+{
+    for (int a = 0; a < N; ++a)
+        if (l[a] < 0 || mm[a] > l[a] || -mm[a] > l[a])
+            return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        const double m = kin[3 * i], c = kin[3 * i + 1], ph = kin[3 * i + 2];
+        for (int a = 0; a < N; ++a) {
+            const double D = mass[a] * mass[a] - m * m, G = mass[a] * width[a];
+            const double den = D * D + G * G;
+            const double br = D / den, bi = G / den;
+            double yr, yi;
+            sph_harm(l[a], mm[a], c, ph, &yr, &yi);
+            A[(i * N + a) * 2] = br * yr - bi * yi;
+            A[(i * N + a) * 2 + 1] = br * yi + bi * yr;
+        }
+    }
+    return 0;
 }

@@ -556,3 +556,81 @@ def test_incoherent_euler_identity_and_phase():
     assert abs(vg.real - (nv - len(A))) < 1e-10 * len(A) and abs(vg.imag) < 1e-10 * len(A)
     n2, g2, _ = oracle.nll_incoh(A, M, V * np.exp(0.8j))
     assert abs(n2 - n) < 1e-12 * abs(n) and rel(g2, g * np.exp(0.8j)) < 1e-12
+
+
+# ---- the amplitude model: Breit-Wigner x spherical harmonic ---------------------
+
+def _grid(n=200, seed=21):
+    rng = np.random.Generator(np.random.Philox(seed))
+    return (rng.uniform(0.98, 3.0, n), rng.uniform(-1.0, 1.0, n), rng.uniform(0.0, 2 * math.pi, n))
+
+
+def test_amplitude_closed_forms():
+    """Y_0^0, Y_1^{0,1,-1}, Y_2^{0,1,2} and Y_3^3 written out, times the
+    Breit-Wigner 1 / (M^2 - m^2 - i M G)."""
+    m, c, p = _grid()
+    s = np.sqrt(1 - c * c)
+    e = np.exp(1j * p)
+    pi = math.pi
+    closed = {
+        (0, 0): np.full_like(c, 1 / math.sqrt(4 * pi)) + 0j,
+        (1, 0): math.sqrt(3 / (4 * pi)) * c + 0j,
+        (1, 1): -math.sqrt(3 / (8 * pi)) * s * e,
+        (1, -1): math.sqrt(3 / (8 * pi)) * s / e,
+        (2, 0): math.sqrt(5 / (16 * pi)) * (3 * c * c - 1) + 0j,
+        (2, 1): -math.sqrt(15 / (8 * pi)) * s * c * e,
+        (2, 2): math.sqrt(15 / (32 * pi)) * s * s * e ** 2,
+        (3, 3): -math.sqrt(35 / (64 * pi)) * s ** 3 * e ** 3,
+    }
+    waves = [(1.3, 0.2, l, mm) for (l, mm) in closed]
+    A = oracle.amplitudes(m, c, p, waves)
+    bw = 1.0 / (1.3 ** 2 - m ** 2 - 1j * 1.3 * 0.2)
+    for k, key in enumerate(closed):
+        assert np.max(np.abs(A[:, k] - bw * closed[key])) <= 1e-13 * np.max(np.abs(A[:, k])), key
+
+
+def test_amplitude_library_and_identities():
+    """Against scipy's spherical harmonics (Condon-Shortley phase) up to l = 6,
+    the conjugation rule Y_l^{-m} = (-1)^m conj(Y_l^m), the addition theorem
+    sum_m |Y_l^m|^2 = (2l + 1)/(4 pi), and |BW|^2 = 1/(M G)^2 at m = M."""
+    special = pytest.importorskip("scipy.special")
+    if not hasattr(special, "sph_harm_y"):
+        pytest.skip("scipy without sph_harm_y")
+    m, c, p = _grid(100, seed=22)
+    theta = np.arccos(c)
+    for l in range(7):
+        waves = [(2.0, 0.3, l, mm) for mm in range(-l, l + 1)]
+        A = oracle.amplitudes(np.full_like(m, 2.0), c, p, waves)
+        Y = A * (-1j * 2.0 * 0.3)       # BW(M; M, G) = 1 / (-i M G) = i / (M G)
+        for k, mm in enumerate(range(-l, l + 1)):
+            ref = special.sph_harm_y(l, mm, theta, p)
+            assert np.max(np.abs(Y[:, k] - ref)) <= 1e-12, (l, mm)
+            assert np.max(np.abs(Y[:, l - mm] - (-1) ** mm * np.conj(Y[:, k]))) <= 1e-14
+        assert np.max(np.abs((np.abs(Y) ** 2).sum(axis=1) - (2 * l + 1) / (4 * math.pi))) <= 1e-12
+    A = oracle.amplitudes([1.7], [0.3], [0.4], [(1.7, 0.11, 0, 0)])
+    assert abs(abs(A[0, 0]) ** 2 * 4 * math.pi - 1 / (1.7 * 0.11) ** 2) <= 1e-12 / (1.7 * 0.11) ** 2
+
+
+def test_amplitude_orthonormality_by_quadrature():
+    """int conj(Y_l^m) Y_l'^m' dOmega = delta_ll' delta_mm' (Gauss-Legendre in
+    cos theta, uniform in phi; exact for these degrees)."""
+    x, wx = np.polynomial.legendre.leggauss(12)
+    nphi = 16
+    ph = 2 * math.pi * np.arange(nphi) / nphi
+    C, P = np.meshgrid(x, ph, indexing="ij")
+    W = (wx[:, None] * np.full(nphi, 2 * math.pi / nphi)[None, :]).ravel()
+    keys = [(l, mm) for l in range(5) for mm in range(-l, l + 1)]
+    waves = [(2.0, 0.3, l, mm) for (l, mm) in keys]
+    Y = oracle.amplitudes(np.full(C.size, 2.0), C.ravel(), P.ravel(), waves) * (1j * 0.6)
+    G = (np.conj(Y) * W[:, None]).T @ Y
+    assert np.max(np.abs(G - np.eye(len(keys)))) <= 1e-12
+
+
+def test_amplitudes_match_the_sample_generator():
+    """The oracle's model and the seeded sample generator agree in FP64 (the
+    generator is what every other test feeds both sides)."""
+    m, c, p = _grid(300, seed=23)
+    waves = synth.waves_linear(13)
+    A = oracle.amplitudes(m, c, p, waves)
+    As = synth.amplitudes({"m": m, "costh": c, "phi": p}, waves, np.complex128)
+    assert np.max(np.abs(A - As)) <= 1e-13 * np.max(np.abs(As))
