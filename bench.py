@@ -22,9 +22,11 @@ Other workloads (one JSON line each, same keys):
           |sum_a V_a A_a^l|^2): 1M data events x 20 waves x 2, direct form
   incoh_table  the same sample in the table form (table bytes independent of
           the number of components)
+  ampgen  amplitudes BW x Y_l^m of 5M events x 20 waves generated on the
+          device from their kinematics (FP64, rounded to complex64)
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
-                  [--workload direct|table|tc|res|models|hessian|weights|incoh|incoh_table]
+                  [--workload direct|table|tc|res|models|hessian|weights|incoh|incoh_table|ampgen]
 
 `value` is device-timed (CUDA events on the launching stream; L2 flushed
 between steps where the inputs fit in it); `e2e` times the public host call
@@ -62,14 +64,17 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "hessian": 160.240896e6 + 3.188992e6,
            "weights": None,
            "incoh": 320.140288e6 + 3.101952e6,
-           "incoh_table": None}
+           "incoh_table": None,
+           "ampgen": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
            "models": "batched_kernel<F, 2> (all sizes)", "hessian": "hess_kernel<20>",
            "weights": "mc_weights_kernel<20>", "incoh": "nll_incoh_kernel<20, 2>",
-           "incoh_table": "nll_table_kernel<20>"}
+           "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel"}
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)
 DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,
-                 "hessian": 2000, "weights": 2000, "incoh": 1500, "incoh_table": 1000}
+                 "hessian": 2000, "weights": 2000, "incoh": 1500, "incoh_table": 1000,
+                 "ampgen": 100}
 
 
 def measured_peaks():
@@ -342,6 +347,48 @@ def job_incoh(pwa, torch, stream, local, rank, form="amp"):
         dtype="f32", h2d=16 * N_WAVES + 8, d2h=8 + 16 * N_WAVES + 8, cpu_baseline=cpu_baseline)
 
 
+def ampgen_flops(waves):
+    """FP64 operations per event of the generator as written: 6 per power of
+    e^{i phi} up to max |m|, and per wave 4 per step of P_m^m, 7 per step of
+    the recurrence in l, 20 for the normalisation, Breit-Wigner and complex
+    product (divisions and the one sincos counted as one operation each)."""
+    mx = max(abs(w.m) for w in waves)
+    return 6 * mx + 1 + sum(4 * abs(w.m) + 7 * max(0, w.l - abs(w.m) - 1) + 20 for w in waves)
+
+
+def job_ampgen(pwa, torch, stream, local, rank):
+    import synth
+    n = N_MC
+    waves = synth.waves_linear(N_WAVES)
+    ev, _ = synth.mc_sample(n, seed=synth.SEED_MC + rank)
+    kin_h = np.stack([ev["m"], ev["costh"], ev["phi"]], axis=1)
+    kin = torch.from_numpy(kin_h).cuda()
+    out = torch.empty(n, N_WAVES, dtype=torch.complex64, device="cuda")
+    L = pwa.Likelihood(N_WAVES, device=local, max_k=1, stream=stream.cuda_stream)
+
+    def cpu_baseline():
+        import oracle
+        sub = 200_000
+        dt, k = timed_oracle(lambda: oracle.amplitudes(ev["m"][:sub], ev["costh"][:sub],
+                                                       ev["phi"][:sub], waves), 10.0)
+        return {"value": 1.0 / (dt * n / sub), "unit": "passes/s", "cores": 1, "kind": "oracle",
+                "sample": "%d amplitude evaluations of the first 200k events x 20 waves (FP64 C "
+                          "oracle, 1 thread), scaled to 5M events" % k}
+
+    return Job(
+        name="ampgen", lib=L, step=lambda: L.amplitudes(waves, kin, out),
+        host_step=lambda: L.amplitudes(waves, kin_h), sync=lambda: L.last_status,
+        evals_per_step=1, launches_per_step=1, flush=False,
+        metric="amplitude-generation passes/s (5M events x 20 waves, BW x Y_l^m); % FP64 peak",
+        unit="passes/s",
+        workload="amplitudes BW x Y_l^m of 5M events x 20 waves from device-resident "
+                 "kinematics (FP64 arithmetic, complex64 out to a device buffer)",
+        config={"n_waves": N_WAVES, "n_events": n, "flops_per_event": ampgen_flops(waves)},
+        roof={"bound": "alu", "flops": float(ampgen_flops(waves)) * n},
+        dtype="f64", h2d=24 * n, d2h=8 * N_WAVES * n, cpu_baseline=cpu_baseline,
+        note="e2e passes host kinematics in (120 MB) and takes the amplitudes back (800 MB)")
+
+
 def job_fit_extra(pwa, torch, stream, local, rank, what):
     """FUMILI Hessian of the 1M-event sample, or the projection weights of its
     5M accepted MC events (host V in; H to the host, or w into a device buffer)."""
@@ -434,7 +481,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models", "hessian", "weights",
-                             "incoh", "incoh_table"])
+                             "incoh", "incoh_table", "ampgen"])
     ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
@@ -465,6 +512,8 @@ def main():
         job = job_tc(pwa, torch, stream, local, rank, args.precision)
     elif args.workload == "res":
         job = job_res(pwa, torch, stream, local, rank)
+    elif args.workload == "ampgen":
+        job = job_ampgen(pwa, torch, stream, local, rank)
     elif args.workload in ("incoh", "incoh_table"):
         job = job_incoh(pwa, torch, stream, local, rank, "table" if args.workload == "incoh_table" else "amp")
     elif args.workload in ("hessian", "weights"):
@@ -549,12 +598,19 @@ def main():
         achieved = job.roof["bytes"] / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm"], "algorithmic_bytes_per_launch": job.roof["bytes"]}
+    elif job.roof["bound"] == "alu":
+        achieved = job.roof["flops"] / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "algorithmic_flops_per_step": job.roof["flops"],
+                "peak_note": "nominal FP64 rate of the part (not measured); FP64 operations as "
+                             "counted per event in config.flops_per_event"}
     else:
         achieved = job.roof["flops"] / avg_s / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16"], "algorithmic_flops_per_step": job.roof["flops"],
                 "peak_note": "bf16 burst; the step time includes the small prep and final kernels"}
-    roof.update({"traffic": TRAFFIC[job.name], "peak_kind": peaks["kind"], "kernel": KERNELS[job.name]})
+    roof.update({"traffic": TRAFFIC[job.name], "kernel": KERNELS[job.name],
+                 "peak_kind": "nominal" if job.roof["bound"] == "alu" else peaks["kind"]})
     config = {"workload": job.workload}
     config.update(job.config)
     config.update({"l2": "flushed between timed steps (256 MB write + read back, untimed)"

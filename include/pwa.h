@@ -108,6 +108,41 @@ int pwa_load_events(pwa_ctx *ctx, const void *data_amp, int64_t n_data,
                     const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
                     int amp_dtype);
 
+/* ---- amplitudes on the device ---------------------------------------------
+ * The framework of the paper computes its amplitudes on the GPU (Sec. 4);
+ * its covariant-tensor amplitude library is not given, so these calls
+ * evaluate the amplitude model used throughout this library's samples:
+ *   A_a(Omega) = BW(m; M_a, G_a) Y_{l_a}^{m_a}(theta, phi),
+ *   BW(m; M, G) = 1 / (M^2 - m^2 - i M G)   (fixed-width Breit-Wigner),
+ *   Y_l^m the orthonormal spherical harmonic with the Condon-Shortley phase,
+ * in double precision, each amplitude rounded once to float. */
+typedef struct pwa_wave {
+    double mass;   /* M > 0 (GeV) */
+    double width;  /* G > 0 (GeV) */
+    int l;         /* 0 <= l <= 16 */
+    int m;         /* -l <= m <= l */
+} pwa_wave;
+
+/* Amplitudes of n events for the context's n_waves waves.
+ *   waves: host [n_waves];  kin: [n][3] doubles (m, cos theta, phi), host or
+ *   device pointer;  out: [n][n_waves] complex64 (float pairs), host or device.
+ * Does not touch the loaded sample. Errors: PWA_EINVAL (null pointer, n out
+ * of [1, 2^31 - 1024], a wave with |m| > l, l > 16, or a non-positive mass or
+ * width), PWA_ENOMEM, PWA_ECUDA. */
+int pwa_compute_amplitudes(pwa_ctx *ctx, const pwa_wave *waves, const double *kin, int64_t n,
+                           void *out);
+
+/* Load a data and an accepted-MC sample given by their kinematics: the
+ * amplitudes are generated on the device straight into the library's store
+ * (no host amplitude arrays, no amplitude transfer), then everything
+ * pwa_load_events does follows (table, tensor-core store as configured).
+ *   data_kin [n_data][3], mc_kin [n_mc_acc][3]: (m, cos theta, phi) doubles,
+ *   host or device pointers; n_mc_gen as in pwa_load_events.
+ * Errors as pwa_compute_amplitudes and pwa_load_events. */
+int pwa_load_events_generated(pwa_ctx *ctx, const pwa_wave *waves, const double *data_kin,
+                              int64_t n_data, const double *mc_kin, int64_t n_mc_acc,
+                              double n_mc_gen);
+
 /* Load a sample whose intensity is an incoherent sum over n_lambda
  * unobserved components per event (e.g. helicity states of an undetected
  * polarisation), I(Omega) = sum_l |sum_a V_a A_a^l(Omega)|^2. Eq. 3 keeps its

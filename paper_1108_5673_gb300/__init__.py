@@ -43,6 +43,18 @@ class Likelihood:
         self.n_mc = int(mc_amp.shape[0])
         return self
 
+    def load_generated(self, waves, data_kin, mc_kin, n_mc_gen):
+        """Load samples given by kinematics (m, cos theta, phi): the amplitudes
+        BW x Y_l^m of `waves` are computed on the device."""
+        self._abi.pwa_load_events_generated(self.ctx, waves, data_kin, mc_kin, n_mc_gen)
+        self.n_data = int(len(data_kin["m"]) if isinstance(data_kin, dict) else data_kin.shape[0])
+        self.n_mc = int(len(mc_kin["m"]) if isinstance(mc_kin, dict) else mc_kin.shape[0])
+        return self
+
+    def amplitudes(self, waves, kin, out=None):
+        """[n, N] complex64 amplitudes of `waves` at the events `kin`, on the device."""
+        return self._abi.pwa_compute_amplitudes(self.ctx, waves, kin, out)
+
     def build_norm(self):
         """Build M on the device; returns a host copy ([N, N] complex128)."""
         return self._abi.pwa_build_norm(self.ctx, self.n_waves)

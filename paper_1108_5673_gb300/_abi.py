@@ -90,6 +90,8 @@ def load(path=LIB_PATH):
         "pwa_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
         "pwa_hessian": ([P, P, P], I),
         "pwa_load_events_incoherent": ([P, I, P, I64, P, I64, D, I], I),
+        "pwa_compute_amplitudes": ([P, P, P, I64, P], I),
+        "pwa_load_events_generated": ([P, P, P, I64, P, I64, D], I),
         "pwa_mc_weights": ([P, P, P], I),
         "pwa_fit_fractions": ([P, P, P], I),
     }
@@ -186,6 +188,58 @@ def pwa_load_events_incoherent(ctx, data_amp, mc_amp, n_mc_gen):
     return _check(ctx, load().pwa_load_events_incoherent(
         ctx, int(data_amp.shape[1]), pd, int(data_amp.shape[0]), pm, int(mc_amp.shape[0]),
         float(n_mc_gen), kd))
+
+
+class pwa_wave(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("width", ctypes.c_double), ("l", ctypes.c_int),
+                ("m", ctypes.c_int)]
+
+
+def _waves(waves):
+    """A ctypes array of pwa_wave from objects with mass, width, l, m (or 4-tuples)."""
+    arr = (pwa_wave * len(waves))()
+    for k, w in enumerate(waves):
+        t = (w.mass, w.width, w.l, w.m) if hasattr(w, "mass") else tuple(w)
+        arr[k] = pwa_wave(float(t[0]), float(t[1]), int(t[2]), int(t[3]))
+    return arr
+
+
+def _kin(kin):
+    """(pointer, keepalive, n) for kinematics: a dict with m, costh, phi, an
+    [n, 3] float64 array, or an [n, 3] float64 CUDA tensor."""
+    if isinstance(kin, dict):
+        kin = np.stack([np.asarray(kin["m"], np.float64), np.asarray(kin["costh"], np.float64),
+                        np.asarray(kin["phi"], np.float64)], axis=1)
+    if getattr(kin, "is_cuda", False):
+        if "float64" not in str(kin.dtype) or tuple(kin.shape[1:]) != (3,):
+            raise ValueError("device kinematics must be [n, 3] float64")
+    else:
+        kin = np.ascontiguousarray(kin, dtype=np.float64)
+        if kin.ndim != 2 or kin.shape[1] != 3:
+            raise ValueError("kinematics must be [n, 3] (m, cos theta, phi)")
+    p, keep = _ptr(kin)
+    return p, keep, int(kin.shape[0])
+
+
+def pwa_compute_amplitudes(ctx, waves, kin, out=None):
+    """[n, n_waves] complex64 amplitudes BW x Y_l^m of the given events
+    (numpy, or into `out`: a numpy array or a CUDA tensor of that shape)."""
+    pk, keep, n = _kin(kin)
+    if out is None:
+        out = np.empty((n, len(waves)), dtype=np.complex64)
+    elif not getattr(out, "is_cuda", False) and not (
+            isinstance(out, np.ndarray) and out.dtype == np.complex64 and out.flags.c_contiguous):
+        raise ValueError("host output must be a contiguous complex64 numpy array")
+    po, keep_o = _ptr(out)
+    _check(ctx, load().pwa_compute_amplitudes(ctx, _waves(waves), pk, n, po))
+    return out
+
+
+def pwa_load_events_generated(ctx, waves, data_kin, mc_kin, n_mc_gen):
+    pd, kd, nd = _kin(data_kin)
+    pm, km, nm = _kin(mc_kin)
+    return _check(ctx, load().pwa_load_events_generated(ctx, _waves(waves), pd, nd, pm, nm,
+                                                        float(n_mc_gen)))
 
 
 def pwa_build_norm(ctx, n_waves):

@@ -18,6 +18,8 @@
 #include <string>
 #include <vector>
 
+#include <cmath>
+
 #include "pwa_internal.cuh"
 
 using namespace pwa;
@@ -446,6 +448,8 @@ cudaError_t encode_bf16_planes_map(CUtensorMap *map, const void *base, int64_t n
 
 extern "C" {
 
+static int finish_load(pwa_ctx *c, int rc, int64_t n_data, int64_t n_mc_acc, double n_mc_gen);
+
 int pwa_version(void) { return 100; }
 
 const char *pwa_last_error(const pwa_ctx *ctx) { return ctx ? ctx->err : g_create_err; }
@@ -845,6 +849,14 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
     int rc = load_planes(c, data_amp, n_data, amp_dtype, &c->data);
     if (!rc)
         rc = load_planes(c, mc_amp, n_mc_acc, amp_dtype, &c->mc);
+    return finish_load(c, rc, n_data, n_mc_acc, n_mc_gen);
+}
+
+// After the data and MC planes of a coherent sample are filled (rc = the
+// status so far): the table, the tensor-core store, the amplitude maxima and
+// the direct form's tensor map; then the sample is marked loaded.
+static int finish_load(pwa_ctx *c, int rc, int64_t n_data, int64_t n_mc_acc, double n_mc_gen)
+{
     if (!rc && (c->cfg.forms & PWA_FORM_TABLE)) {
         c->table_pitch = c->data.pitch;
         rc = dev_alloc(c, (void **)&c->table, (size_t)c->N * c->N * c->table_pitch * sizeof(float),
@@ -908,6 +920,154 @@ int pwa_load_events(pwa_ctx *c, const void *data_amp, int64_t n_data, const void
     c->loaded = true;
     c->has_norm = false;
     return PWA_OK;
+}
+
+// ---- amplitudes on the device --------------------------------------------
+
+// Checks the wave list and converts it (with N_lm) into the device table at
+// *d_waves (allocated here, freed by the caller); *max_m = max |m|.
+static int upload_waves(pwa_ctx *c, const pwa_wave *waves, GenWave **d_waves, int *max_m)
+{
+    *d_waves = nullptr;
+    if (!waves)
+        return fail(c, PWA_EINVAL, "null wave list");
+    std::vector<GenWave> h(c->N);
+    *max_m = 0;
+    for (int a = 0; a < c->N; ++a) {
+        const pwa_wave &w = waves[a];
+        const int am = w.m < 0 ? -w.m : w.m;
+        if (w.l < 0 || w.l > ampgen_max_l() || am > w.l)
+            return fail(c, PWA_EINVAL, "wave %d: (l, m) = (%d, %d) needs 0 <= |m| <= l <= %d", a, w.l,
+                        w.m, ampgen_max_l());
+        if (!(w.mass > 0) || !(w.width > 0) || !std::isfinite(w.mass) || !std::isfinite(w.width))
+            return fail(c, PWA_EINVAL, "wave %d: mass and width must be positive and finite", a);
+        double ratio = 1.0;  // (l - |m|)! / (l + |m|)!
+        for (int k = w.l - am + 1; k <= w.l + am; ++k)
+            ratio /= k;
+        h[a] = GenWave{w.mass, w.width, std::sqrt((2.0 * w.l + 1.0) / (4.0 * 3.14159265358979323846) * ratio),
+                       w.l, w.m};
+        *max_m = std::max(*max_m, am);
+    }
+    int rc = dev_alloc(c, (void **)d_waves, c->N * sizeof(GenWave), "wave table");
+    if (rc)
+        return rc;
+    CK(c, cudaMemcpyAsync(*d_waves, h.data(), c->N * sizeof(GenWave), cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PWA_OK;
+}
+
+// Generates the amplitudes of n events (kin host or device) into `out`
+// (device): SoA planes of `pitch` floats, or event-major complex64.
+static int generate(pwa_ctx *c, const GenWave *d_waves, int max_m, const double *kin, int64_t n,
+                    float *out, bool soa, int64_t pitch)
+{
+    const double *dk = kin;
+    double *staging = nullptr;
+    if (!is_device_pointer(kin)) {
+        int rc = dev_alloc(c, (void **)&staging, (size_t)n * 3 * sizeof(double), "kinematics");
+        if (rc)
+            return rc;
+        cudaError_t e = cudaMemcpyAsync(staging, kin, (size_t)n * 3 * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(staging);
+            return fail(c, PWA_ECUDA, "kinematics copy: %s", cudaGetErrorString(e));
+        }
+        dk = staging;
+    }
+    cudaError_t e = launch_amp_gen(dk, n, c->N, d_waves, max_m, out, soa, pitch, c->num_sms * 8,
+                                   c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (staging)
+        cudaFree(staging);
+    if (e == cudaSuccess)
+        e = e2;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "amplitude generation: %s", cudaGetErrorString(e));
+    }
+    return PWA_OK;
+}
+
+int pwa_compute_amplitudes(pwa_ctx *c, const pwa_wave *waves, const double *kin, int64_t n,
+                           void *out)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!kin || !out)
+        return fail(c, PWA_EINVAL, "null kinematics or output");
+    if (n < 1 || n > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "n=%lld outside [1, 2^31 - 1024]", (long long)n);
+    DeviceGuard g(c->device);
+    GenWave *dw;
+    int max_m;
+    int rc = upload_waves(c, waves, &dw, &max_m);
+    if (rc) {
+        dev_free(dw);
+        return rc;
+    }
+    const bool on_dev = is_device_pointer(out);
+    float *dout = static_cast<float *>(out);
+    if (!on_dev)
+        rc = dev_alloc(c, (void **)&dout, (size_t)n * c->N * 8, "amplitudes");
+    if (!rc)
+        rc = generate(c, dw, max_m, kin, n, dout, false, 0);
+    if (!rc && !on_dev) {
+        cudaError_t e = cudaMemcpy(out, dout, (size_t)n * c->N * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "amplitude copy: %s", cudaGetErrorString(e));
+    }
+    if (!on_dev)
+        dev_free(dout);
+    dev_free(dw);
+    return rc;
+}
+
+int pwa_load_events_generated(pwa_ctx *c, const pwa_wave *waves, const double *data_kin,
+                              int64_t n_data, const double *mc_kin, int64_t n_mc_acc,
+                              double n_mc_gen)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!data_kin || !mc_kin)
+        return fail(c, PWA_EINVAL, "null kinematics");
+    if (n_data < 1 || n_mc_acc < 1)
+        return fail(c, PWA_EINVAL, "n_data=%lld and n_mc_acc=%lld must be >= 1",
+                    (long long)n_data, (long long)n_mc_acc);
+    if (!(n_mc_gen >= (double)n_mc_acc))
+        return fail(c, PWA_EINVAL, "n_mc_gen=%g must be >= n_mc_acc=%lld", n_mc_gen,
+                    (long long)n_mc_acc);
+    if (n_data > ((int64_t)1 << 31) - 1024 || n_mc_acc > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "samples are limited to 2^31 - 1024 events");
+    DeviceGuard g(c->device);
+    cudaStreamSynchronize(c->stream);
+    GenWave *dw;
+    int max_m;
+    int rc = upload_waves(c, waves, &dw, &max_m);
+    if (rc) {
+        dev_free(dw);
+        return rc;
+    }
+    free_sample(c);
+    c->n_lambda = 1;
+    const int N = c->N;
+    for (int which = 0; which < 2 && !rc; ++which) {
+        Planes &p = which == 0 ? c->data : c->mc;
+        const int64_t n = which == 0 ? n_data : n_mc_acc;
+        p.n = n;
+        p.n_waves = N;
+        p.pitch = round_up(n, 256);
+        rc = dev_alloc(c, (void **)&p.ptr, (size_t)2 * N * p.pitch * sizeof(float), "planes");
+        if (!rc && cudaMemsetAsync(p.ptr, 0, (size_t)2 * N * p.pitch * sizeof(float), c->stream) !=
+                       cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "memset");
+        if (!rc)
+            rc = generate(c, dw, max_m, which == 0 ? data_kin : mc_kin, n, p.ptr, true, p.pitch);
+    }
+    dev_free(dw);
+    return finish_load(c, rc, n_data, n_mc_acc, n_mc_gen);
 }
 
 int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, int64_t n_data,

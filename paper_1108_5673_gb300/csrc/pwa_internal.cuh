@@ -455,6 +455,18 @@ int res_max_free();
 size_t res_partials_doubles(int n_waves, int n_free, int grid);
 cudaError_t launch_nll_res(const ResArgs &a, int grid, cudaStream_t s);
 
+// k_ampgen.cu: amplitudes BW(m; M, G) Y_l^m(theta, phi) from per-event
+// kinematics kin [n][3] = (m, cos theta, phi) (device), FP64, rounded to float;
+// out as SoA planes (Re A_a at plane 2a of `pitch` floats) or, soa = false,
+// event-major complex64 [n][N].
+struct GenWave {
+    double mass, width, norm;  // norm = sqrt((2l + 1)/(4 pi) (l - |m|)!/(l + |m|)!)
+    int l, m;
+};
+int ampgen_max_l();
+cudaError_t launch_amp_gen(const double *kin, int64_t n, int N, const GenWave *waves, int max_m,
+                           float *out, bool soa, int64_t pitch, int grid, cudaStream_t s);
+
 // k_nll_incoh.cu: direct form with an incoherent sum over n_lambda components;
 // d holds 2 n_lambda N planes (plane 2 (l N + a) = Re A_a^l). Same scratch,
 // ticket and outputs as the direct-form kernel (EvalArgs, one parameter set).
