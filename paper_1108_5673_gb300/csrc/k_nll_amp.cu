@@ -51,443 +51,11 @@
 #include <stdlib.h>
 
 #include "pwa_internal.cuh"
+#include "amp_kernel.cuh"
 
 namespace pwa {
 
 namespace {
-
-constexpr double kLn2 = 0.69314718055994530942;
-
-template <int N, int G>
-struct AmpCfg {
-    static constexpr int GROUPS = G;                   // consumer groups (tiles in turn)
-    static constexpr int GW = 4;                       // warps per group
-    static constexpr int CW = GROUPS * GW;             // consumer warps
-    static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
-    static constexpr int ROWS = 2 * N;
-    static constexpr uint32_t STAGE_BYTES = ROWS * TE * 4;
-    // Each group owns SPG stages of the ring, so a stage's successive uses
-    // always belong to the same group: a waiter can then never be a full
-    // barrier phase behind (parity waits only tell apart adjacent phases).
-    static constexpr int SPG_RAW = (200 * 1024) / (STAGE_BYTES * G);
-    static constexpr int SPG = SPG_RAW < 1 ? 1 : (SPG_RAW > 4 ? 4 : SPG_RAW);
-    static constexpr int STAGES = G * SPG;
-    static constexpr int THREADS = (CW + 2) * 32;      // + producer warp + helper warp
-    static constexpr int NF = 2 * N + 1;               // float partials: ln-fraction, gradient
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
-    // dynamic shared memory must leave room for the static arrays (< 16 KB)
-    static constexpr bool FITS = SMEM <= 210 * 1024;
-};
-
-// Layout of the per-launch scratch (EvalArgs::partials) for a grid of G CTAs:
-//   pi  [G][2] int64   per-CTA sum of round(2^23 ln f) and of exponents
-//   pf  [G][2N+1]      per-CTA float-float sums: ln-f remainders, gradient
-//   mv  [2 kMaxWaves + 1]  M V and then V^H M V (double), by CTA 0's helper warp
-//   flags              status bits of this launch (reset by the last CTA)
-struct AmpScratch {
-    long long *pi;
-    float2 *pf;
-    double *mv;
-    int *flags;
-};
-
-__host__ __device__ inline AmpScratch amp_scratch(void *base, int grid)
-{
-    char *p = static_cast<char *>(base);
-    AmpScratch s;
-    s.pi = reinterpret_cast<long long *>(p);
-    p += (size_t)grid * 2 * sizeof(long long);
-    s.pf = reinterpret_cast<float2 *>(p);
-    p += (size_t)grid * (2 * kMaxWaves + 1) * sizeof(float2);
-    s.mv = reinterpret_cast<double *>(p);
-    p += (2 * kMaxWaves + 2) * sizeof(double);
-    s.flags = reinterpret_cast<int *>(p);
-    return s;
-}
-
-
-
-// Per-wave coefficients, each duplicated into both halves of a packed pair.
-struct alignas(16) WaveCoef {
-    f2 vr, vi;  // Vhi
-    f2 lr, li;  // Vlo
-};
-
-__device__ __forceinline__ f2 lds2(const float *p) { return *reinterpret_cast<const f2 *>(p); }
-
-// Split c*a for both events of the pair (see the file comment): returns the
-// remainders and the bit patterns of t, whose sum gives the high parts.
-__device__ __forceinline__ f2 extract(f2 c, f2 a, f2 sg, unsigned &t0, unsigned &t1)
-{
-    const f2 t = fma2(c, a, sg);
-    float x0, x1;
-    upk2(t, x0, x1);
-    t0 = __float_as_uint(x0);
-    t1 = __float_as_uint(x1);
-    return fma2(c, a, sub2(sg, t));
-}
-
-template <int N, int G>
-__global__ void __launch_bounds__(AmpCfg<N, G>::THREADS, 1)
-    nll_amp_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs a, const int n_tiles,
-                   int *work_flags)
-{
-    using C = AmpCfg<N, G>;
-    constexpr int TE = C::TE, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
-    constexpr int GROUPS = C::GROUPS, GW = C::GW;
-    constexpr int NF = C::NF;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *tiles = reinterpret_cast<float *>(smem_raw);
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
-
-    __shared__ WaveCoef Vc[N];
-    __shared__ float s_sigma, s_unit;
-    __shared__ long long red_i[CW][2];
-    __shared__ float red_f[CW][NF];
-    __shared__ int s_flags;
-    __shared__ int s_last;
-    AmpScratch sc = amp_scratch(a.partials, gridDim.x);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...; tile j goes
-    // to group j % GROUPS and to that group's stage (j / GROUPS) % SPG
-    const int n_my =
-        (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    const uint32_t stage_tx = 2u * (uint32_t)a.n_waves * TE * 4u;
-    auto stage_of = [](int j) { return (j % GROUPS) * C::SPG + (j / GROUPS) % C::SPG; };
-    auto use_of = [](int j) { return (uint32_t)((j / GROUPS) / C::SPG); };
-    const int n_first = n_my < STAGES ? n_my : STAGES;  // first use of every stage
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], GW);
-        }
-        fence_barrier_init();
-        s_flags = 0;
-        // start streaming before the prologue below (its global loads take ~1 us)
-        for (int j = 0; j < n_first; ++j) {
-            mbar_arrive_expect_tx(&full[stage_of(j)], stage_tx);
-            tma_load_2d(tiles + (size_t)stage_of(j) * ROWS * TE, &map,
-                        ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[stage_of(j)]);
-        }
-    }
-    // Rows of padded waves (n_waves < N) are never written by TMA: zero them
-    // once so that they contribute nothing (their V is zero as well).
-    for (int s = 0; s < STAGES; ++s)
-        for (int i = 2 * a.n_waves * TE + threadIdx.x; i < ROWS * TE; i += blockDim.x)
-            tiles[(size_t)s * ROWS * TE + i] = 0.f;
-    if (threadIdx.x < N) {
-        const int w = threadIdx.x;
-        const bool on = w < a.n_waves;
-        const double dr = on ? a.V[2 * w] : 0.0, di = on ? a.V[2 * w + 1] : 0.0;
-        const float vr = __double2float_rn(dr), vi = __double2float_rn(di);
-        const float lr = __double2float_rn(dr - (double)vr), li = __double2float_rn(di - (double)vi);
-        Vc[w].vr = pk2(vr, vr);
-        Vc[w].vi = pk2(vi, vi);
-        Vc[w].lr = pk2(lr, lr);
-        Vc[w].li = pk2(li, li);
-    }
-    if (warp == 1) {
-        // 2^(k-1) >= 1.25 sum_a |V_a|_1 max_i |A_a(i)|_1 (margin for rounding)
-        float b = 0.f;
-        for (int w = lane; w < a.n_waves; w += 32) {
-            const float v1 = fabsf(__double2float_ru(fabs(a.V[2 * w]))) +
-                             fabsf(__double2float_ru(fabs(a.V[2 * w + 1])));
-            b = fmaf(v1, a.amax[w], b);
-        }
-        b = warp_sum(b);
-        if (lane == 0) {
-            const float target = 2.5f * b;
-            int k = -100;  // floor keeps u_k normal
-            if (target > 0.f)
-                k = max(k, ((__float_as_int(target) >> 23) & 0xff) - 126);  // target < 2^k
-            if (!(target < 1e30f))
-                k = 100;   // non-finite bound: the results will flag the domain error
-            s_sigma = 1.5f * ldexpf(1.0f, k);
-            s_unit = ldexpf(1.0f, k - 23);
-        }
-    }
-    __syncthreads();
-
-    int flags = 0;
-    long long l_int = 0;      // sum of round(2^23 ln f)
-    int eacc = 0;             // sum of exponents
-    float l_frac = 0.f;       // sum of the remainders (units of 2^-23)
-
-    if (warp == 0) {
-        if (lane == 0) {
-            // ---- producer: one thread issues the TMA copies ----------------
-            int j = n_first;
-            for (; j < n_my; ++j) {
-                const int s = stage_of(j);
-                const uint32_t u = use_of(j);
-                if (u > 0 && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
-                    flags |= FLAG_TIMEOUT;
-                    break;
-                }
-                mbar_arrive_expect_tx(&full[s], stage_tx);
-                tma_load_2d(tiles + (size_t)s * ROWS * TE, &map,
-                            ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[s]);
-            }
-            // no copy may still be landing in shared memory when the CTA exits
-            // (the last STAGES tiles issued are the latest use of every stage)
-            for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q) {
-                if (!mbar_wait(&full[stage_of(q)], use_of(q) & 1))
-                    flags |= FLAG_TIMEOUT;
-            }
-        }
-    } else if (warp <= CW) {
-        // ---- consumers: group grp takes tiles j = grp, grp + GROUPS, ... ---
-        const int cw = warp - 1;
-        const int grp = cw / GW;
-        const int ct = (cw % GW) * 32 + lane;  // thread within its group
-        const float sigma = s_sigma, unit = s_unit;
-        const f2 SG = pk2(sigma, sigma);
-        // bits(t) - bits(sigma) summed over the 2N terms of Im S: remove the offset once
-        const unsigned im_offset = 2u * (unsigned)N * __float_as_uint(sigma);
-        const f2 Z = 0ull;
-        float gs[2 * N];
-#pragma unroll
-        for (int c = 0; c < 2 * N; ++c)
-            gs[c] = 0.f;
-        int bad = 0;
-        for (int j = grp; j < n_my; j += GROUPS) {
-            const int s = stage_of(j);
-            const uint32_t u = use_of(j);
-            if (!mbar_wait(&full[s], u & 1)) {
-                flags |= FLAG_TIMEOUT;
-                break;
-            }
-            const float *T = tiles + (size_t)s * ROWS * TE + 2 * ct;
-            const int64_t ev0 = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * TE + 2 * ct;
-
-            // Re S = vr ar - vi ai ; Im S = vr ai + vi ar
-            unsigned hR0 = 0, hR1 = 0, hI0 = 0, hI1 = 0;  // high parts (units of u_k)
-            f2 lR = Z, lRm = Z, lI = Z;                    // remainders; lRm is subtracted
-#pragma unroll
-            for (int w = 0; w < N; ++w) {
-                const f2 ar = lds2(T + (2 * w) * TE), ai = lds2(T + (2 * w + 1) * TE);
-                const WaveCoef cf = Vc[w];
-                unsigned x0, x1;
-                lR = add2(lR, extract(cf.vr, ar, SG, x0, x1));
-                hR0 += x0;
-                hR1 += x1;
-                lRm = add2(lRm, extract(cf.vi, ai, SG, x0, x1));
-                hR0 -= x0;
-                hR1 -= x1;
-                lI = add2(lI, extract(cf.vr, ai, SG, x0, x1));
-                hI0 += x0;
-                hI1 += x1;
-                lI = add2(lI, extract(cf.vi, ar, SG, x0, x1));
-                hI0 += x0;
-                hI1 += x1;
-                lR = fma2(cf.lr, ar, lR);
-                lRm = fma2(cf.li, ai, lRm);
-                lI = fma2(cf.lr, ai, fma2(cf.li, ar, lI));
-            }
-            float Sr[2], Si[2], rr[2], ri[2];
-            {
-                const f2 hR = pk2((float)(int)hR0 * unit, (float)(int)hR1 * unit);
-                const f2 hI = pk2((float)(int)(hI0 - im_offset) * unit,
-                                  (float)(int)(hI1 - im_offset) * unit);
-                upk2(add2(hR, sub2(lR, lRm)), Sr[0], Sr[1]);
-                upk2(add2(hI, lI), Si[0], Si[1]);
-            }
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-                const float I = fmaf(Sr[e], Sr[e], Si[e] * Si[e]);
-                const bool in = (ev0 + e) < a.n_events;
-                const bool ok = (I > 0.f) && (I < INFINITY);
-                rr[e] = 0.f;
-                ri[e] = 0.f;
-                if (in) {
-                    if (ok) {
-                        int ex;
-                        const float f = split_exponent(I, ex);
-                        // 2^23 ln f = k + r exactly: k integer (|k| < 2^22), |r| <= 1/2
-                        const float y = logf(f) * 8388608.0f;
-                        const float t = y + 12582912.0f;  // 1.5 * 2^23: rounds y to an integer
-                        l_int += __float_as_int(t) - 0x4B400000;
-                        l_frac += y - (t - 12582912.0f);
-                        eacc += ex;
-                        const float rI = __frcp_rn(I);
-                        rr[e] = Sr[e] * rI;
-                        ri[e] = Si[e] * rI;
-                    } else {
-                        bad = 1;
-                    }
-                }
-            }
-#pragma unroll
-            for (int w = 0; w < N; ++w) {
-                float a0, a1, b0, b1;
-                upk2(lds2(T + (2 * w) * TE), a0, a1);
-                upk2(lds2(T + (2 * w + 1) * TE), b0, b1);
-                // conj(A) r = (ar rr + ai ri) + i (ar ri - ai rr)
-                gs[2 * w] = fmaf(a0, rr[0], fmaf(b0, ri[0], gs[2 * w]));
-                gs[2 * w] = fmaf(a1, rr[1], fmaf(b1, ri[1], gs[2 * w]));
-                gs[2 * w + 1] = fmaf(a0, ri[0], fmaf(-b0, rr[0], gs[2 * w + 1]));
-                gs[2 * w + 1] = fmaf(a1, ri[1], fmaf(-b1, rr[1], gs[2 * w + 1]));
-            }
-            __syncwarp();
-            if (lane == 0)
-                mbar_arrive(&empty[s]);
-        }
-        if (bad)
-            flags |= FLAG_DOMAIN;
-
-        // ---- per-warp reduction of this thread's sums (fixed order) ------
-        const long long li = warp_sum(l_int);
-        const long long ei = warp_sum((long long)eacc);
-        const float lf = warp_sum(l_frac);
-        if (lane == 0) {
-            red_i[cw][0] = li;
-            red_i[cw][1] = ei;
-            red_f[cw][0] = lf;
-        }
-#pragma unroll
-        for (int c = 0; c < 2 * N; ++c) {
-            const float v = warp_sum(gs[c]);
-            if (lane == 0)
-                red_f[cw][1 + c] = v;
-        }
-    } else if (warp == CW + 1 && blockIdx.x == 0) {
-        // ---- helper warp of CTA 0: M V and V^H M V in FP64 -------------
-        // One row per lane; this overlaps the streaming of the data.
-        const int Nw = a.n_waves;
-        double nv = 0.0;
-        for (int row = lane; row < Nw; row += 32) {
-            double re = 0.0, im = 0.0;
-            for (int b = 0; b < Nw; ++b) {
-                const double mr = a.M[2 * (row * Nw + b)], mi = a.M[2 * (row * Nw + b) + 1];
-                const double vr = a.V[2 * b], vi = a.V[2 * b + 1];
-                re = fma(mr, vr, fma(-mi, vi, re));
-                im = fma(mr, vi, fma(mi, vr, im));
-            }
-            sc.mv[2 * row] = re;
-            sc.mv[2 * row + 1] = im;
-            nv = fma(a.V[2 * row], re, fma(a.V[2 * row + 1], im, nv));  // Re(conj(V) (M V))
-        }
-        nv = warp_sum(nv);
-        if (lane == 0)
-            sc.mv[2 * kMaxWaves] = nv;
-    }
-    if (flags)
-        atomicOr(&s_flags, flags);
-    __syncthreads();
-
-    // ---- block partial, fixed order over warps -------------------------
-    if (threadIdx.x < 2) {
-        long long v = 0;
-        for (int w = 0; w < CW; ++w)
-            v += red_i[w][threadIdx.x];
-        sc.pi[2 * blockIdx.x + threadIdx.x] = v;
-    }
-    for (int c = threadIdx.x; c < NF; c += blockDim.x) {
-        dfloat v = {0.f, 0.f};
-        for (int w = 0; w < CW; ++w)
-            v = df_add(v, dfloat{red_f[w][c], 0.f});
-        sc.pf[(size_t)blockIdx.x * NF + c] = make_float2(v.hi, v.lo);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        if (s_flags)
-            atomicOr(work_flags, s_flags);
-        __threadfence();
-        const unsigned t = atomicAdd(a.ticket, 1u);
-        s_last = (t == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!s_last)
-        return;
-
-    // ---- last CTA: deterministic final sum + normalisation term ---------
-    // Each of the 2N+1 float components and the 2 integer ones is split into
-    // SUB interleaved sub-sums over the CTAs, one per thread, with all of a
-    // thread's loads issued before its adds (one L2 round trip); the
-    // sub-sums are then combined in a fixed order. (The partials are read
-    // with L2 loads after the ticket, so no further fence is needed.)
-    const int Nw = a.n_waves;
-    const int G_ = gridDim.x;
-    constexpr int SUB = 7, MAXB = 24;
-    dfloat *sub_f = reinterpret_cast<dfloat *>(tiles);                  // [NF][SUB]
-    long long *sub_i = reinterpret_cast<long long *>(sub_f + NF * SUB);  // [2][SUB]
-    double *smv = reinterpret_cast<double *>(sub_i + 2 * SUB);          // [2N] M V
-    for (int item = threadIdx.x; item < (NF + 2) * SUB; item += blockDim.x) {
-        const int c = item / SUB, k = item % SUB;
-        if (c < NF) {
-            dfloat v = {0.f, 0.f};
-            for (int b0 = k; b0 < G_; b0 += SUB * MAXB) {
-                float2 r[MAXB];
-#pragma unroll
-                for (int q = 0; q < MAXB; ++q) {
-                    const int b = b0 + q * SUB;
-                    r[q] = (b < G_) ? __ldcg(&sc.pf[(size_t)b * NF + c]) : make_float2(0.f, 0.f);
-                }
-#pragma unroll
-                for (int q = 0; q < MAXB; ++q)
-                    v = df_add(v, dfloat{r[q].x, r[q].y});
-            }
-            sub_f[c * SUB + k] = v;
-        } else {
-            const int ci = c - NF;
-            long long v = 0;
-            for (int b0 = k; b0 < G_; b0 += SUB * MAXB) {
-                long long r[MAXB];
-#pragma unroll
-                for (int q = 0; q < MAXB; ++q) {
-                    const int b = b0 + q * SUB;
-                    r[q] = (b < G_) ? __ldcg(&sc.pi[2 * b + ci]) : 0;
-                }
-#pragma unroll
-                for (int q = 0; q < MAXB; ++q)
-                    v += r[q];
-            }
-            sub_i[ci * SUB + k] = v;
-        }
-    }
-    for (int i = threadIdx.x; i < 2 * Nw; i += blockDim.x) {
-        smv[i] = __ldcg(&sc.mv[i]);
-    }
-    __syncthreads();
-    const int wf = __ldcg(work_flags);
-    const bool invalid = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) != 0;
-    for (int c = threadIdx.x; c < 2 * Nw + 1; c += blockDim.x) {  // padded waves excluded
-        dfloat v = sub_f[c * SUB];
-        for (int k = 1; k < SUB; ++k)
-            v = df_add(v, sub_f[c * SUB + k]);
-        if (c > 0) {
-            // gradient: - sum_i conj(A) S / I + (M V)
-            if (a.grad)
-                a.grad[c - 1] = invalid ? 0.0 : (smv[c - 1] - (double)v.hi) - (double)v.lo;
-        } else {
-            // ln sum: integer part and exponents are exact; the rest is small
-            long long li = 0, ei = 0;
-            for (int k = 0; k < SUB; ++k) {
-                li += sub_i[k];
-                ei += sub_i[SUB + k];
-            }
-            const double lnsum =
-                fma((double)ei, kLn2, ((double)li + ((double)v.hi + (double)v.lo)) * 0x1p-23);
-            double nll = __ldcg(&sc.mv[2 * kMaxWaves]) - lnsum;
-            if (wf & FLAG_DOMAIN)
-                nll = INFINITY;
-            if (wf & FLAG_TIMEOUT)
-                nll = NAN;
-            a.nll[0] = nll;
-            if (wf)
-                atomicOr(a.status, wf);
-            if (a.done)
-                atomicAdd(a.done, 1);
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        *work_flags = 0;
-        *a.ticket = 0u;
-    }
-}
 
 // The NLL-only call runs the same kernel and discards the gradient sums (the
 // extra FMAs hide under the HBM time).
@@ -520,13 +88,6 @@ int amp_groups()
     return g;
 }
 
-// The last CTA keeps its sub-sums in its (then idle) stage buffers.
-template <int N, int G>
-constexpr bool finalize_fits(int grid)
-{
-    (void)grid;
-    return (size_t)(2 * N + 3) * 7 * 8 + 32 * N <= AmpCfg<N, G>::SMEM;
-}
 
 template <int N>
 cudaError_t launch_n(const CUtensorMap *map, const EvalArgs &a, int grid, int n_tiles,

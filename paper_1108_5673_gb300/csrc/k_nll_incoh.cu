@@ -20,6 +20,7 @@
 // FP64 across warps and blocks. The last block (atomic ticket) adds the
 // block partials in block order and the normalisation term in FP64, so the
 // results are bitwise reproducible.
+#include "amp_kernel.cuh"
 #include "pwa_internal.cuh"
 
 namespace pwa {
@@ -303,7 +304,69 @@ int pad_np(int n)
     return 1 << 20;
 }
 
+// ---- TMA-fed path: the direct-form kernel with L components per event ------
+// (amp_kernel.cuh): tiles of 256 events x 2 L n rows streamed by TMA, the
+// products split exactly against sigma (bounded over all components) and
+// their high parts summed as integers, two events per thread in FP32x2. It
+// serves N_pad * L <= 48 (a stage of 2 L N_pad x 256 floats, one per
+// consumer group, in the 200 KB ring).
+template <int N, int L>
+cudaError_t launch_tma_nl(const CUtensorMap *map, const EvalArgs &a, int grid, cudaStream_t s)
+{
+    if constexpr (N * L > kMaxLanes || L < 2) {
+        return cudaErrorInvalidValue;
+    } else {
+        using C = AmpCfg<N, 2, L>;
+        static_assert(C::FITS, "one stage per consumer group must fit");
+        if (!finalize_fits<N, 2, L>(grid))
+            return cudaErrorInvalidConfiguration;
+        cudaError_t e = cudaFuncSetAttribute(nll_amp_kernel<N, 2, L>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+        if (e != cudaSuccess)
+            return e;
+        const int n_tiles = (int)((a.n_events + C::TE - 1) / C::TE);
+        int *work_flags = amp_scratch(a.partials, grid).flags;
+        nll_amp_kernel<N, 2, L><<<grid, C::THREADS, C::SMEM, s>>>(*map, a, n_tiles, work_flags);
+        return cudaGetLastError();
+    }
+}
+
+template <int N>
+cudaError_t launch_tma_n(const CUtensorMap *map, int L, const EvalArgs &a, int grid,
+                         cudaStream_t s)
+{
+    switch (L) {
+    case 2: return launch_tma_nl<N, 2>(map, a, grid, s);
+    case 3: return launch_tma_nl<N, 3>(map, a, grid, s);
+    case 4: return launch_tma_nl<N, 4>(map, a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
+
+bool incoh_tma_available(int n_waves, int n_lambda)
+{
+    return n_lambda >= 2 && n_lambda <= kMaxLambda && pad_np(n_waves) * n_lambda <= kMaxLanes;
+}
+
+int incoh_tma_box_events() { return AmpCfg<4, 2, 2>::TE; }
+
+cudaError_t launch_nll_incoh_tma(const CUtensorMap *map, int n_lambda, const EvalArgs &a, int grid,
+                                 cudaStream_t s)
+{
+    if (!incoh_tma_available(a.n_waves, n_lambda))
+        return cudaErrorInvalidValue;
+    switch (pad_np(a.n_waves)) {
+    case 4: return launch_tma_n<4>(map, n_lambda, a, grid, s);
+    case 8: return launch_tma_n<8>(map, n_lambda, a, grid, s);
+    case 12: return launch_tma_n<12>(map, n_lambda, a, grid, s);
+    case 16: return launch_tma_n<16>(map, n_lambda, a, grid, s);
+    case 20: return launch_tma_n<20>(map, n_lambda, a, grid, s);
+    case 24: return launch_tma_n<24>(map, n_lambda, a, grid, s);
+    }
+    return cudaErrorInvalidValue;
+}
 
 int incoh_max_components() { return kMaxLambda; }
 int incoh_max_waves(int n_lambda)

@@ -44,6 +44,7 @@ struct pwa_ctx {
     long long *xsum = nullptr;  // sum of the per-event exponents (inside xbf)
     int xs = 2;                 // BF16 slices of the amplitudes (tensor-core form)
     int n_lambda = 1;           // incoherent components per event (data planes hold L N waves)
+    bool incoh_tma = false;     // incoherent direct form through the TMA-fed kernel
     int tune_groups = 0;        // direct form: consumer groups (0 = default rule)
     int tune_res_cps = 1;       // free-resonance kernel: blocks per SM
     // free-resonance form
@@ -346,7 +347,9 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         a.nll = dnll + k;
         a.grad = dgrad ? dgrad + (size_t)2 * N * k : nullptr;
         cudaError_t e = cudaSuccess;
-        if (c->form == PWA_FORM_AMP && c->n_lambda > 1)
+        if (c->form == PWA_FORM_AMP && c->n_lambda > 1 && c->incoh_tma)
+            e = launch_nll_incoh_tma(&c->data_map, c->n_lambda, a, c->num_sms, c->stream);
+        else if (c->form == PWA_FORM_AMP && c->n_lambda > 1)
             e = launch_nll_incoh(c->data, c->n_lambda, a, c->num_sms, c->stream);
         else if (c->form == PWA_FORM_AMP)
             e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream, c->tune_groups);
@@ -1136,8 +1139,46 @@ int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, i
                 rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
         }
     }
+    // The TMA-fed kernel (N_pad L <= 48) bounds its exact product split by
+    // amax[a] = max over components and events of |Re A_a^l| + |Im A_a^l|; it
+    // reads all 2 L n planes as one box per tile. PWA_INCOH_KERNEL=generic
+    // selects the one-event-per-thread kernel instead.
+    const char *kv = getenv("PWA_INCOH_KERNEL");
+    const bool tma = (c->cfg.forms & PWA_FORM_AMP) && incoh_tma_available(N, L) &&
+                     !(kv && strcmp(kv, "generic") == 0);
     if (!rc && cudaMemsetAsync(c->amax, 0, N * sizeof(float), c->stream) != cudaSuccess)
         rc = fail(c, PWA_ECUDA, "memset");
+    if (!rc && tma) {
+        float *dmax = nullptr;
+        rc = dev_alloc(c, (void **)&dmax, (size_t)L * N * sizeof(float), "component maxima");
+        std::vector<float> hmax((size_t)L * N), amax(N, 0.f);
+        cudaError_t e = cudaSuccess;
+        if (!rc) {
+            e = cudaMemsetAsync(dmax, 0, (size_t)L * N * sizeof(float), c->stream);
+            if (e == cudaSuccess)
+                e = launch_amp_max(d, dmax, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(hmax.data(), dmax, (size_t)L * N * sizeof(float),
+                                    cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(c->stream);
+            for (int l = 0; l < L && e == cudaSuccess; ++l)
+                for (int a = 0; a < N; ++a)
+                    amax[a] = std::max(amax[a], hmax[(size_t)l * N + a]);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->amax, amax.data(), N * sizeof(float), cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = encode_planes_map(&c->data_map, d.ptr, n_data, d.pitch, 2 * L * N,
+                                      incoh_tma_box_events(), 2 * L * N);
+            if (e != cudaSuccess)
+                rc = fail(c, PWA_ECUDA, "incoherent direct-form set-up: %s", cudaGetErrorString(e));
+        }
+        if (dmax) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(dmax);
+        }
+    }
     if (!rc) {
         cudaError_t e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess)
@@ -1148,6 +1189,7 @@ int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, i
         return rc;
     }
     c->n_lambda = L;
+    c->incoh_tma = tma;
     c->n_data = n_data;
     c->n_mc = n_mc_acc;
     c->n_gen = n_mc_gen;

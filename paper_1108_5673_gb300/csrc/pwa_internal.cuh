@@ -475,6 +475,13 @@ int incoh_max_waves(int n_lambda);  // largest N the direct kernel takes for n_l
 size_t incoh_partials_doubles(int n_waves, int grid);
 cudaError_t launch_nll_incoh(const Planes &d, int n_lambda, const EvalArgs &a, int grid,
                              cudaStream_t s);
+// TMA-fed incoherent direct form (n_waves padded x n_lambda <= 48): map over
+// the 2 n_lambda n_waves planes with a box of incoh_tma_box_events() events x
+// all rows; a.amax[a] >= max over components and events of |Re| + |Im| of A_a.
+bool incoh_tma_available(int n_waves, int n_lambda);
+int incoh_tma_box_events();
+cudaError_t launch_nll_incoh_tma(const CUtensorMap *map, int n_lambda, const EvalArgs &a, int grid,
+                                 cudaStream_t s);
 // table of the incoherent sum: T[a][b] = sum_l A_a^l conj(A_b^l), layout as
 // launch_table_build, from planes of n_lambda * N waves
 cudaError_t launch_table_build_incoh(const Planes &amp, int n_lambda, float *table,

@@ -29,6 +29,17 @@ def pwa():
     return pkg
 
 
+@pytest.fixture(params=["tma", "generic"])
+def kernel(request, monkeypatch):
+    """Which direct-form kernel serves the incoherent sample: the TMA-fed one
+    (the default where it fits) or the one-event-per-thread one."""
+    if request.param == "generic":
+        monkeypatch.setenv("PWA_INCOH_KERNEL", "generic")
+    else:
+        monkeypatch.delenv("PWA_INCOH_KERNEL", raising=False)
+    return request.param
+
+
 def nll_tol(n):
     return max(1e-3 * math.sqrt(n / 1e6), 2e-6)
 
@@ -68,7 +79,7 @@ def run(pwa, wl, Vs, forms):
 
 @pytest.mark.parametrize("N,L", [(1, 2), (3, 2), (8, 2), (13, 2), (20, 2), (24, 2), (4, 3),
                                  (16, 3), (5, 4), (12, 4)])
-def test_incoherent_against_oracle(pwa, N, L):
+def test_incoherent_against_oracle(pwa, kernel, N, L):
     wl = case(N, L, 3000, 2500, seed=N * 7 + L)
     Vs = [wl.V_true, synth.random_V(N, 31 + N)]
     out = run(pwa, wl, Vs, pwa.PWA_FORM_AMP | pwa.PWA_FORM_TABLE)
@@ -80,7 +91,7 @@ def test_incoherent_against_oracle(pwa, N, L):
 
 
 @pytest.mark.parametrize("n_data", [1, 7, 255, 256, 257, 2049, 10007])
-def test_incoherent_ragged_event_counts(pwa, n_data):
+def test_incoherent_ragged_event_counts(pwa, kernel, n_data):
     wl = case(20, 2, n_data, 600, seed=n_data % 83)
     Vs = [synth.random_V(20, n_data)]
     out = run(pwa, wl, Vs, pwa.PWA_FORM_AMP)
@@ -102,7 +113,7 @@ def test_one_component_equals_coherent(pwa):
     assert np.array_equal(r0[0], r1[0]) and np.array_equal(r0[1], r1[1])
 
 
-def test_incoherent_deterministic_and_domain(pwa):
+def test_incoherent_deterministic_and_domain(pwa, kernel):
     wl = case(10, 3, 5000, 2000, seed=2)
     V = synth.random_V(10, 3)[None, :]
     with pwa.Likelihood(10) as L:
@@ -140,7 +151,7 @@ def test_incoherent_unsupported_paths(pwa):
 
 
 @pytest.mark.slow
-def test_incoherent_at_scale(pwa):
+def test_incoherent_at_scale(pwa, kernel):
     """1M events x 20 waves x 2 components (the bench workload) against the
     oracle, both forms."""
     wl = case(20, 2, 1_000_000, 1_000_000, seed=11)
