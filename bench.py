@@ -474,6 +474,25 @@ def run_reference(args):
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
+def max_over_ranks(dist, values, device):
+    """The per-rank timings [device ms, end-to-end s] reduced to their maximum
+    over ranks (the slowest replica sets the job's time), followed by a
+    barrier; values unchanged without a process group."""
+    if not dist:
+        return list(values)
+    import torch
+    t = torch.tensor(values, dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return [float(x) for x in t]
+
+
+def job_value(world, evals_per_step, steps, total_ms_max):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (weak scaling: every rank runs its own replica)."""
+    return world * evals_per_step * steps / (total_ms_max / 1e3)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -576,13 +595,7 @@ def main():
         sampler.terminate()
         sampler.wait()
 
-    total_ms_max = total_ms
-    e2e_max = e2e_s
-    if dist:
-        t = torch.tensor([total_ms, e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms_max, e2e_max = float(t[0]), float(t[1])
-        dist.barrier()
+    total_ms_max, e2e_max = max_over_ranks(dist, [total_ms, e2e_s], "cuda")
     if rank != 0:
         job.lib.close()
         if dist:
@@ -590,7 +603,7 @@ def main():
         return
 
     ev = job.evals_per_step
-    value = world * ev * args.steps / (total_ms_max / 1e3)
+    value = job_value(world, ev, args.steps, total_ms_max)
     e2e_value = world * ev * args.steps / e2e_max
     avg_s = total_ms / args.steps / 1e3
     peaks = measured_peaks()
