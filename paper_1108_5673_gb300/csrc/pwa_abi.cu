@@ -46,6 +46,18 @@ struct pwa_ctx {
     int n_lambda = 1;           // incoherent components per event (data planes hold L N waves)
     bool incoh_tma = false;     // incoherent direct form through the TMA-fed kernel
     int tune_groups = 0;        // direct form: consumer groups (0 = default rule)
+    // host evaluations replayed as CUDA graphs (copy in, kernels, copy out),
+    // one per (K, with gradient); stale once `epoch` moves (a new sample, form
+    // or launch shape)
+    struct EvalGraph {
+        int K;
+        bool grad;
+        unsigned epoch;
+        cudaGraphExec_t exec;
+    };
+    std::vector<EvalGraph> graphs;
+    unsigned epoch = 0;
+    bool graphs_off = false;
     int tune_res_cps = 1;       // free-resonance kernel: blocks per SM
     // free-resonance form
     float *res_data = nullptr, *res_mc = nullptr;
@@ -191,6 +203,7 @@ void free_sample(pwa_ctx *c)
     dev_free(c->xbf);
     c->loaded = c->has_norm = false;
     c->n_lambda = 1;
+    ++c->epoch;
 }
 
 // Copy n events of nw complex waves (event-major, host or device) into the
@@ -365,6 +378,72 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
     return PWA_OK;
 }
 
+// The copy of [status | V] in, the evaluation kernels and the copy of
+// [nll | grad | status] out, enqueued on the context's stream.
+int enqueue_host_eval(pwa_ctx *c, int K, bool with_grad)
+{
+    const size_t gK = (size_t)2 * c->N * K;
+    double *h_stat = c->h_io + K + gK, *d_stat = c->d_io + K + gK;
+    CK(c, cudaMemcpyAsync(d_stat, h_stat, (1 + gK) * sizeof(double), cudaMemcpyHostToDevice,
+                          c->stream));
+    int *ds = reinterpret_cast<int *>(d_stat);
+    int rc = enqueue_eval(c, d_stat + 1, K, c->d_io, with_grad ? c->d_io + K : nullptr, ds, ds + 1);
+    if (rc)
+        return rc;
+    CK(c, cudaMemcpyAsync(c->h_io, c->d_io, (K + gK + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                          c->stream));
+    return PWA_OK;
+}
+
+// The graph of enqueue_host_eval for (K, with_grad) at the current epoch,
+// captured on first use (null if capture is not possible here: the stream is
+// being captured by the caller, or PWA_EVAL_GRAPHS=0).
+cudaGraphExec_t eval_graph(pwa_ctx *c, int K, bool with_grad)
+{
+    const char *v = getenv("PWA_EVAL_GRAPHS");
+    if ((v && strcmp(v, "0") == 0) || c->graphs_off)
+        return nullptr;
+    for (size_t i = 0; i < c->graphs.size();) {
+        if (c->graphs[i].epoch != c->epoch) {
+            cudaGraphExecDestroy(c->graphs[i].exec);
+            c->graphs.erase(c->graphs.begin() + i);
+        } else if (c->graphs[i].K == K && c->graphs[i].grad == with_grad) {
+            return c->graphs[i].exec;
+        } else {
+            ++i;
+        }
+    }
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graphs_off = true;
+        return nullptr;
+    }
+    const int rc = enqueue_host_eval(c, K, with_grad);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->stream, &graph);
+    cudaGraphExec_t exec = nullptr;
+    if (rc == PWA_OK && e == cudaSuccess && graph &&
+        cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        if (c->graphs.size() >= 8) {
+            cudaGraphExecDestroy(c->graphs.front().exec);
+            c->graphs.erase(c->graphs.begin());
+        }
+        c->graphs.push_back({K, with_grad, c->epoch, exec});
+    } else {
+        cudaGetLastError();
+        c->graphs_off = true;   // fall back to direct enqueueing for this context
+        exec = nullptr;
+    }
+    if (graph)
+        cudaGraphDestroy(graph);
+    return exec;
+}
+
 int eval_host(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
 {
     int rc = check_eval_args(c, V, K, nll);
@@ -378,15 +457,11 @@ int eval_host(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
     hs[0] = 0;
     hs[1] = 0;
     memcpy(h_stat + 1, V, gK * sizeof(double));
-    double *d_stat = c->d_io + K + gK;
-    CK(c, cudaMemcpyAsync(d_stat, h_stat, (1 + gK) * sizeof(double), cudaMemcpyHostToDevice,
-                          c->stream));
-    int *ds = reinterpret_cast<int *>(d_stat);
-    rc = enqueue_eval(c, d_stat + 1, K, c->d_io, grad ? c->d_io + K : nullptr, ds, ds + 1);
-    if (rc)
+    if (cudaGraphExec_t ex = eval_graph(c, K, grad != nullptr)) {
+        CK(c, cudaGraphLaunch(ex, c->stream));
+    } else if ((rc = enqueue_host_eval(c, K, grad != nullptr))) {
         return rc;
-    CK(c, cudaMemcpyAsync(c->h_io, c->d_io, (K + gK + 1) * sizeof(double), cudaMemcpyDeviceToHost,
-                          c->stream));
+    }
     CK(c, cudaStreamSynchronize(c->stream));
     if (hs[1] != K)
         return fail(c, PWA_ETIMEOUT, "only %d of %d evaluations finished", hs[1], K);
@@ -810,6 +885,9 @@ int pwa_destroy(pwa_ctx *c)
     DeviceGuard g(c->device);
     if (c->stream)
         cudaStreamSynchronize(c->stream);
+    for (auto &g : c->graphs)
+        cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
     free_sample(c);
     free_res(c);
     dev_free(c->M);
@@ -1241,6 +1319,7 @@ int pwa_set_form(pwa_ctx *c, int form)
         CK(c, cudaStreamSynchronize(c->stream));
     }
     c->form = form;
+    ++c->epoch;
     return PWA_OK;
 }
 
@@ -1694,6 +1773,7 @@ int pwa_autotune(pwa_ctx *c, const char *cache_path, char *choice, int choice_le
                 snprintf(buf, sizeof buf, "direct form: %d consumer groups (cached)", best);
             }
             c->tune_groups = best;
+            ++c->epoch;
             summary += buf;
         } else {
             snprintf(buf, sizeof buf, "%s form: one launch shape",
