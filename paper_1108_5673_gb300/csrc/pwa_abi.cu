@@ -65,6 +65,9 @@ struct pwa_ctx {
     int res_R = 0;
     double res_ngen = 0.0;
     bool res_loaded = false;
+    bool res_tma = false;       // the TMA-fed free-resonance kernel serves this sample
+    CUtensorMap res_dmap, res_mmap;
+    float *res_amax = nullptr;  // [N] max over both samples of |Y_a|_1 or |A_a|_1
     double *d_res = nullptr;    // partials, ticket, io
     double *h_res = nullptr;    // pinned io mirror
     // Hessian, projection weights, fit fractions (allocated on first use)
@@ -188,10 +191,12 @@ void free_res(pwa_ctx *c)
     dev_free(c->res_data);
     dev_free(c->res_mc);
     dev_free(c->d_res);
+    dev_free(c->res_amax);
     if (c->h_res)
         cudaFreeHost(c->h_res);
     c->h_res = nullptr;
     c->res_loaded = false;
+    c->res_tma = false;
 }
 
 void free_sample(pwa_ctx *c)
@@ -577,12 +582,60 @@ int pwa_load_resonance_events(pwa_ctx *c, int n_free, const double *m_data, cons
         c->h_res = nullptr;
         rc = fail(c, PWA_ENOMEM, "pinned host buffer");
     }
+    // The TMA-fed kernel (PWA_RES_KERNEL=generic selects the per-event one):
+    // per-wave maxima over both samples bound its exact product split.
+    const char *kv = getenv("PWA_RES_KERNEL");
+    const bool tma = res_tma_available(N, n_free) && !(kv && strcmp(kv, "generic") == 0);
+    if (!rc && tma) {
+        float *tmp = nullptr;
+        rc = dev_alloc(c, (void **)&c->res_amax, N * sizeof(float), "resonance maxima");
+        if (!rc)
+            rc = dev_alloc(c, (void **)&tmp, N * sizeof(float), "resonance maxima");
+        cudaError_t e = cudaSuccess;
+        if (!rc) {
+            const Planes pd{c->res_data + c->res_data_pitch, c->res_data_pitch, n_data, N};
+            const Planes pm{c->res_mc + c->res_mc_pitch, c->res_mc_pitch, n_mc_acc, N};
+            e = cudaMemsetAsync(c->res_amax, 0, N * sizeof(float), c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemsetAsync(tmp, 0, N * sizeof(float), c->stream);
+            if (e == cudaSuccess)
+                e = launch_amp_max(pd, c->res_amax, c->stream);
+            if (e == cudaSuccess)
+                e = launch_amp_max(pm, tmp, c->stream);
+            std::vector<float> h1(N), h2(N);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h1.data(), c->res_amax, N * sizeof(float), cudaMemcpyDeviceToHost,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h2.data(), tmp, N * sizeof(float), cudaMemcpyDeviceToHost,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(c->stream);
+            for (int k = 0; k < N && e == cudaSuccess; ++k)
+                h1[k] = std::max(h1[k], h2[k]);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->res_amax, h1.data(), N * sizeof(float), cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = cudaStreamSynchronize(c->stream);
+            if (e == cudaSuccess)
+                e = encode_planes_map(&c->res_dmap, c->res_data, n_data, c->res_data_pitch, 1 + 2 * N,
+                                      res_tma_box_events(), 1 + 2 * N);
+            if (e == cudaSuccess)
+                e = encode_planes_map(&c->res_mmap, c->res_mc, n_mc_acc, c->res_mc_pitch, 1 + 2 * N,
+                                      res_tma_box_events(), 1 + 2 * N);
+            if (e != cudaSuccess)
+                rc = fail(c, PWA_ECUDA, "free-resonance set-up: %s", cudaGetErrorString(e));
+        }
+        dev_free(tmp);
+    }
     if (!rc && cudaStreamSynchronize(c->stream) != cudaSuccess)
         rc = fail(c, PWA_ECUDA, "loading the resonance samples");
     if (rc) {
         free_res(c);
         return rc;
     }
+    c->res_tma = tma;
     c->res_R = n_free;
     c->res_n_data = n_data;
     c->res_n_mc = n_mc_acc;
@@ -631,7 +684,10 @@ int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const doub
     a.status = ds;
     a.done = ds + 1;
     a.out = d_io + nin;
-    cudaError_t e = launch_nll_res(a, (int)res_grid(c), c->stream);
+    cudaError_t e = c->res_tma
+                        ? launch_nll_res_tma(&c->res_dmap, &c->res_mmap, a, c->res_amax, c->num_sms,
+                                             c->stream)
+                        : launch_nll_res(a, (int)res_grid(c), c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(c, PWA_ECUDA, "resonance kernel launch: %s", cudaGetErrorString(e));
@@ -1781,7 +1837,10 @@ int pwa_autotune(pwa_ctx *c, const char *cache_path, char *choice, int choice_le
             summary += buf;
         }
     }
-    if (c->res_loaded) {
+    if (c->res_loaded && c->res_tma) {
+        summary += summary.empty() ? "" : "; ";
+        summary += "free resonances: TMA-fed kernel, one launch shape";
+    } else if (c->res_loaded) {
         const std::string key = tune_key(c, "res-blocks-per-sm");
         int best = 0;
         double best_us = 0.0;

@@ -454,6 +454,14 @@ int res_max_waves();
 int res_max_free();
 size_t res_partials_doubles(int n_waves, int n_free, int grid);
 cudaError_t launch_nll_res(const ResArgs &a, int grid, cudaStream_t s);
+// k_nll_res_tma.cu: the same evaluation, TMA-fed (maps over the [1 + 2N]
+// planes of each sample with a box of res_tma_box_events() events x 1 + 2N
+// rows); amax[a] >= max over both samples of |Re| + |Im| of Y_a (free waves)
+// or A_a (fixed waves). Scratch as launch_nll_res with grid = one CTA per SM.
+int res_tma_box_events();
+bool res_tma_available(int n_waves, int n_free);
+cudaError_t launch_nll_res_tma(const CUtensorMap *dmap, const CUtensorMap *mmap, const ResArgs &a,
+                               const float *amax, int grid, cudaStream_t s);
 
 // k_ampgen.cu: amplitudes BW(m; M, G) Y_l^m(theta, phi) from per-event
 // kinematics kin [n][3] = (m, cos theta, phi) (device), FP64, rounded to float;

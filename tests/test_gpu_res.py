@@ -5,7 +5,10 @@ Identical inputs: m rounded to float32, Y and the fixed amplitudes complex64,
 promoted exactly for the oracle; V, masses and widths exact. Per event the
 kernel's errors are float roundings that vary from event to event (the
 Breit-Wigner denominator is formed from float pairs of M^2, M G and (M G)^2
-and the exact split of m^2; S is a compensated dot product), so they add as
+and the exact split of m^2; S is exact up to about one float rounding: by
+the direct form's exact product split in the TMA-fed kernel, by a
+compensated dot product in the per-event one; both kernels are tested), so
+they add as
 sqrt(n): |dNLL| <= 1e-3 sqrt(n_data / 1e6) + 1e-6 (n_mc / 1e6), the second term
 for the MC sum, whose (1/N_gen) sum I carries float-float sums of
 per-event float intensities. Gradients: ||dg|| / max(||g_data||, ||g_MC||)
@@ -31,6 +34,17 @@ def pwa():
     __graft_entry__.build()
     import paper_1108_5673_gb300 as pkg
     return pkg
+
+
+@pytest.fixture(params=["tma", "generic"])
+def kernel(request, monkeypatch):
+    """Which kernel serves the free-resonance sample: the TMA-fed one (the
+    default) or the one-event-per-thread one."""
+    if request.param == "generic":
+        monkeypatch.setenv("PWA_RES_KERNEL", "generic")
+    else:
+        monkeypatch.delenv("PWA_RES_KERNEL", raising=False)
+    return request.param
 
 
 def nll_tol(n_data, n_mc):
@@ -91,18 +105,18 @@ def params_for(wl, k=2, seed=0):
 
 @pytest.mark.parametrize("N,R", [(1, 1), (4, 2), (8, 4), (13, 5), (20, 4), (20, 8), (24, 3), (32, 4),
                                  (6, 6)])
-def test_waves_sweep(pwa, N, R):
+def test_waves_sweep(pwa, kernel, N, R):
     wl = case(N, R, 3000, 5000, seed=N + R)
     check(pwa, wl, params_for(wl, seed=N))
 
 
 @pytest.mark.parametrize("n_data", [1, 2, 255, 256, 257, 4097])
-def test_ragged_event_counts(pwa, n_data):
+def test_ragged_event_counts(pwa, kernel, n_data):
     wl = case(10, 3, n_data, 777, seed=n_data % 13)
     check(pwa, wl, params_for(wl, 1, seed=n_data))
 
 
-def test_at_generated_parameters_equals_fixed_form(pwa):
+def test_at_generated_parameters_equals_fixed_form(pwa, kernel):
     """At fixed masses and widths the free-resonance NLL is the direct form's
     (Sec. 2: the precomputation is valid then): both GPU paths on the same
     events agree up to the float rounding of the amplitudes BW * Y, which the
@@ -125,7 +139,7 @@ def test_at_generated_parameters_equals_fixed_form(pwa):
     assert np.linalg.norm(gV_r - g_d[0]) <= 1e-4 * np.linalg.norm(g_d[0]) + 1e-3
 
 
-def test_domain_error(pwa):
+def test_domain_error(pwa, kernel):
     wl = case(6, 2, 1000, 1000, seed=5)
     with pwa.Likelihood(6) as L:
         L.load_resonance_events(wl)
@@ -137,7 +151,7 @@ def test_domain_error(pwa):
         assert L.last_status == pwa.PWA_OK and np.isfinite(nll2)
 
 
-def test_gradient_by_finite_differences(pwa):
+def test_gradient_by_finite_differences(pwa, kernel):
     """Central differences (h = 1e-4) of the GPU NLL in mass and width. Near a
     narrow resonance the h^2 term of a central difference is not small (0.2%
     here), so the GPU difference is compared with the oracle's at the same h,
@@ -188,7 +202,7 @@ def test_autograd_function(pwa):
 
 
 @pytest.mark.slow
-def test_free_resonance_scale(pwa):
+def test_free_resonance_scale(pwa, kernel):
     """2M data events, 5M accepted MC, 20 waves, 4 free Breit-Wigners."""
     wl = synth.free_resonance_scale()
     check(pwa, wl, params_for(wl, 1, seed=2))

@@ -41,8 +41,14 @@ def test_direct_form_tuning_and_cache(pwa, tmp_path):
         assert abs(n[0] - no) <= 1e-3 * (200_000 / 1e6) ** 0.5 + 2e-6
 
 
-def test_resonance_tuning(pwa, tmp_path):
+def test_resonance_tuning(pwa, tmp_path, monkeypatch):
+    """The per-event free-resonance kernel has launch variants to time; the
+    TMA-fed one (the default) has one launch shape."""
     wl = synth.resonance_workload("t", synth.waves_linear(8), 3, 50_000, 80_000)
+    with pwa.Likelihood(8) as L:
+        L.load_resonance_events(wl)
+        assert "one launch shape" in L.autotune(None)
+    monkeypatch.setenv("PWA_RES_KERNEL", "generic")
     V = synth.random_V(8, 4)
     cache = str(tmp_path / "tune.json")
     with pwa.Likelihood(8) as L:
