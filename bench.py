@@ -59,7 +59,7 @@ WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M 
 TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "table": 1600.392e6 + 4.053504e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
-           "res": 1148.450e6 + 3.265280e6,
+           "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.240896e6 + 3.188992e6,
            "weights": None,
@@ -67,7 +67,7 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "incoh_table": None,
            "ampgen": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
-           "tc": "batched_kernel<64, 2>", "res": "nll_res_kernel<20, 4>",
+           "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
            "models": "batched_kernel<F, 2> (all models)", "hessian": "hess_kernel<20>",
            "weights": "mc_weights_kernel<20>", "incoh": "nll_amp_kernel<20, 2, 2>",
            "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel"}
@@ -246,17 +246,21 @@ def job_res(pwa, torch, stream, local, rank):
                           "250k MC events (FP64 C oracle, 1 thread), scaled to the full 2M + 5M "
                           "events" % k}
 
-    step = lambda: L.nll_grad_res(V, mass, width)
+    import torch as _t
+    dV = _t.from_numpy(np.ascontiguousarray(V)).cuda()
+    dm = _t.tensor(mass, dtype=_t.float64, device="cuda")
+    dw = _t.tensor(width, dtype=_t.float64, device="cuda")
+    dout = _t.empty(1 + 2 * N + 2 * R, dtype=_t.float64, device="cuda")
     return Job(
-        name="res", lib=L, step=step, host_step=step, sync=lambda: L.last_status,
+        name="res", lib=L, step=lambda: L.nll_grad_res_async(dV, dm, dw, dout),
+        host_step=lambda: L.nll_grad_res(V, mass, width), sync=L.sync,
         evals_per_step=1, launches_per_step=1, flush=False,
         workload="free masses and widths of 4 of 20 Breit-Wigner waves: 2M data + 5M accepted MC "
                  "events (m, Y of the free waves, fixed amplitudes; FP32), BW recomputed per call",
         config={"n_waves": N, "n_free": R, "n_data": n, "n_mc_acc": n_mc, "n_mc_gen": wl.n_gen,
                 "K": 1, "form": "res"},
         roof={"bound": "hbm", "bytes": 4.0 * (1 + 2 * N) * (n + n_mc)},
-        dtype="f32", h2d=16 * N + 16 * R + 8, d2h=8 + 16 * N + 16 * R, cpu_baseline=cpu_baseline,
-        note="value and e2e both time the host call (its copies are a few hundred bytes)")
+        dtype="f32", h2d=16 * N + 16 * R + 8, d2h=8 + 16 * N + 16 * R, cpu_baseline=cpu_baseline)
 
 
 def job_models(pwa, torch, stream, local, rank):
@@ -412,10 +416,12 @@ def job_fit_extra(pwa, torch, stream, local, rank, what):
                     "sample": "%d FUMILI Hessians of the first 20k events (FP64 C oracle, "
                               "1 thread), scaled to the 1M-event sample" % k}
 
-        step = lambda: L.hessian(V)
         P = 2 * N_WAVES
+        dV = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+        dH = torch.empty(P, P, dtype=torch.float64, device="cuda")
         return Job(
-            name="hessian", lib=L, step=step, host_step=step, sync=lambda: L.last_status,
+            name="hessian", lib=L, step=lambda: L.hessian_async(dV, dH),
+            host_step=lambda: L.hessian(V), sync=L.sync,
             evals_per_step=1, launches_per_step=2, flush=True,
             metric="FUMILI Hessian evals/s (1M events, 20 waves); % HBM roofline",
             unit="Hessians/s",
@@ -423,8 +429,7 @@ def job_fit_extra(pwa, torch, stream, local, rank, what):
                      "(FP32 amplitudes), M from 5M accepted MC",
             config={"n_waves": N_WAVES, "n_data": N_DATA, "n_mc_acc": N_MC, "K": 1},
             roof={"bound": "hbm", "bytes": 8.0 * N_WAVES * N_DATA},
-            dtype="f32", h2d=16 * N_WAVES, d2h=8 * P * P + 4, cpu_baseline=cpu_baseline,
-            note="value and e2e both time the host call (V in, the 12.8 KB Hessian out)")
+            dtype="f32", h2d=16 * N_WAVES, d2h=8 * P * P + 4, cpu_baseline=cpu_baseline)
 
     out = torch.empty(N_MC, dtype=torch.float32, device="cuda")
 

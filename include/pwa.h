@@ -241,6 +241,14 @@ int pwa_load_resonance_events(pwa_ctx *ctx, int n_free, const double *m_data, co
 int pwa_nll_grad_res(pwa_ctx *ctx, const double *V, const double *mass, const double *width,
                      double *nll, double *gV, double *gM, double *gW);
 
+/* pwa_nll_grad_res with device pointers, stream-ordered, returning after
+ * enqueueing: d_V [n_waves] complex128, d_mass and d_width [n_free] double in;
+ * d_out [1 + 2 n_waves + 2 n_free] double out: nll, dNLL/dV* (complex128),
+ * dNLL/dM, dNLL/dG (nll = +inf and gradients 0 on a domain error, reported by
+ * pwa_sync with the other asynchronous calls' status). */
+int pwa_nll_grad_res_async(pwa_ctx *ctx, const double *d_V, const double *d_mass,
+                           const double *d_width, double *d_out);
+
 /* ---- what the fitter and the plots take besides the NLL -------------------
  * FUMILI Hessian (Sec. 4 fits with FUMILI on analytic gradients and Hessian;
  * Sec. 5 returns the Hessian to the host each iteration). FUMILI's
@@ -261,6 +269,12 @@ int pwa_nll_grad_res(pwa_ctx *ctx, const double *V, const double *mass, const do
  * pwa_load_events; PWA_EINVAL for null pointers; PWA_ENOTSUP for an
  * incoherent sample; PWA_ENOMEM, PWA_ECUDA. */
 int pwa_hessian(pwa_ctx *ctx, const double *V, double *H);
+
+/* pwa_hessian with device pointers (d_V [n_waves] complex128, d_H
+ * [2 n_waves][2 n_waves] double), stream-ordered, returning after enqueueing;
+ * a domain error zeroes d_H and is reported, with the other asynchronous
+ * calls' status, by pwa_sync. Errors as pwa_hessian (before any work). */
+int pwa_hessian_async(pwa_ctx *ctx, const double *d_V, double *d_H);
 
 /* Projection weights (the "Plots" step of Table 1): the fitted intensity of
  * each accepted MC event divided by the number generated,

@@ -77,6 +77,10 @@ class Likelihood:
         H, self.last_status = self._abi.pwa_hessian(self.ctx, V, self.n_waves)
         return H
 
+    def hessian_async(self, d_V, d_H):
+        """Enqueue the Hessian with device tensors (see pwa_hessian_async)."""
+        self._abi.pwa_hessian_async(self.ctx, d_V, d_H)
+
     def mc_weights(self, V, out=None):
         """I(Omega_j) / n_mc_gen per accepted MC event, float32 (into `out`, a
         numpy array or CUDA tensor, when given)."""
@@ -104,6 +108,11 @@ class Likelihood:
         """(nll, dNLL/dV* [N] complex, dNLL/dM [R], dNLL/dGamma [R])."""
         nll, gV, gM, gW, self.last_status = self._abi.pwa_nll_grad_res(self.ctx, V, mass, width)
         return nll, gV, gM, gW
+
+    def nll_grad_res_async(self, d_V, d_mass, d_width, d_out):
+        """Enqueue the free-resonance evaluation with device tensors (see
+        pwa_nll_grad_res_async); results in d_out after sync()."""
+        self._abi.pwa_nll_grad_res_async(self.ctx, d_V, d_mass, d_width, d_out)
 
     def autotune(self, cache_path=None):
         """Pick the fastest launch variants on the loaded sample (see

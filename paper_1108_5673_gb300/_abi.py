@@ -89,6 +89,8 @@ def load(path=LIB_PATH):
         "pwa_batch_last_error": ([P], ctypes.c_char_p),
         "pwa_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
         "pwa_hessian": ([P, P, P], I),
+        "pwa_hessian_async": ([P, P, P], I),
+        "pwa_nll_grad_res_async": ([P, P, P, P, P], I),
         "pwa_load_events_incoherent": ([P, I, P, I64, P, I64, D, I], I),
         "pwa_compute_amplitudes": ([P, P, P, I64, P], I),
         "pwa_load_events_generated": ([P, P, P, I64, P, I64, D], I),
@@ -353,6 +355,20 @@ def pwa_hessian(ctx, V, n_waves):
     p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
     rc = _check(ctx, load().pwa_hessian(ctx, p(V), p(H)), allow=(PWA_EDOMAIN,))
     return H, rc
+
+
+def pwa_hessian_async(ctx, d_V, d_H):
+    """Device tensors: d_V [n_waves] complex128, d_H [2N, 2N] float64."""
+    pv, _a = _ptr(d_V)
+    ph, _b = _ptr(d_H)
+    return _check(ctx, load().pwa_hessian_async(ctx, pv, ph))
+
+
+def pwa_nll_grad_res_async(ctx, d_V, d_mass, d_width, d_out):
+    """Device tensors: d_V [N] complex128, d_mass/d_width [R] float64, d_out
+    [1 + 2N + 2R] float64 (nll, dNLL/dV* as (re, im) pairs, dNLL/dM, dNLL/dG)."""
+    ptrs = [_ptr(x) for x in (d_V, d_mass, d_width, d_out)]
+    return _check(ctx, load().pwa_nll_grad_res_async(ctx, *[p for p, _ in ptrs]))
 
 
 def pwa_mc_weights(ctx, V, w):

@@ -447,6 +447,20 @@ cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, f
     return cudaErrorInvalidValue;
 }
 
+namespace {
+__global__ void or_flags_kernel(const int *src, int *dst)
+{
+    if (*src)
+        atomicOr(dst, *src);
+}
+}  // namespace
+
+cudaError_t launch_or_flags(const int *src, int *dst, cudaStream_t s)
+{
+    or_flags_kernel<<<1, 1, 0, s>>>(src, dst);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fit_fractions(const double *M, const double *V, int N, double *F, cudaStream_t s)
 {
     fit_fractions_kernel<<<1, 256, 0, s>>>(M, V, N, F);

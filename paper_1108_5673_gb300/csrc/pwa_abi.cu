@@ -644,6 +644,55 @@ int pwa_load_resonance_events(pwa_ctx *c, int n_free, const double *m_data, cons
     return PWA_OK;
 }
 
+// The free-resonance evaluation with device pointers: V, mass, width in,
+// [nll | gV | gM | gW] out, status into `status`, `done` incremented (may be null).
+static int enqueue_res(pwa_ctx *c, const double *dV, const double *dmass, const double *dwidth,
+                       double *dout, int *status, int *done)
+{
+    const int N = c->N, R = c->res_R;
+    const size_t npart = res_partials_doubles(N, R, c->num_sms * kResMaxBlocksPerSm);
+    ResArgs a{};
+    a.n_waves = N;
+    a.n_free = R;
+    a.data = c->res_data;
+    a.data_pitch = c->res_data_pitch;
+    a.n_data = c->res_n_data;
+    a.mc = c->res_mc;
+    a.mc_pitch = c->res_mc_pitch;
+    a.n_mc = c->res_n_mc;
+    a.inv_ngen = 1.0 / c->res_ngen;
+    a.V = dV;
+    a.mass = dmass;
+    a.width = dwidth;
+    a.partials = c->d_res;
+    a.ticket = reinterpret_cast<unsigned *>(c->d_res + npart);
+    a.status = status;
+    a.done = done;
+    a.out = dout;
+    cudaError_t e = c->res_tma
+                        ? launch_nll_res_tma(&c->res_dmap, &c->res_mmap, a, c->res_amax, c->num_sms,
+                                             c->stream)
+                        : launch_nll_res(a, (int)res_grid(c), c->stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "resonance kernel launch: %s", cudaGetErrorString(e));
+    }
+    return PWA_OK;
+}
+
+int pwa_nll_grad_res_async(pwa_ctx *c, const double *d_V, const double *d_mass,
+                           const double *d_width, double *d_out)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!d_V || !d_mass || !d_width || !d_out)
+        return fail(c, PWA_EINVAL, "null V, mass, width or out");
+    if (!c->res_loaded)
+        return fail(c, PWA_ESTATE, "pwa_load_resonance_events must come first");
+    DeviceGuard g(c->device);
+    return enqueue_res(c, d_V, d_mass, d_width, d_out, c->async_status, nullptr);
+}
+
 int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const double *width,
                      double *nll, double *gV, double *gM, double *gW)
 {
@@ -665,33 +714,10 @@ int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const doub
     hs[0] = hs[1] = 0;
     const size_t nin = 2 * (size_t)N + 2 * R + 1, nout = 1 + 2 * (size_t)N + 2 * R;
     CK(c, cudaMemcpyAsync(d_io, h, nin * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    ResArgs a{};
-    a.n_waves = N;
-    a.n_free = R;
-    a.data = c->res_data;
-    a.data_pitch = c->res_data_pitch;
-    a.n_data = c->res_n_data;
-    a.mc = c->res_mc;
-    a.mc_pitch = c->res_mc_pitch;
-    a.n_mc = c->res_n_mc;
-    a.inv_ngen = 1.0 / c->res_ngen;
-    a.V = d_io;
-    a.mass = d_io + 2 * N;
-    a.width = d_io + 2 * N + R;
-    a.partials = c->d_res;
-    a.ticket = reinterpret_cast<unsigned *>(c->d_res + npart);
     int *ds = reinterpret_cast<int *>(d_io + 2 * N + 2 * R);
-    a.status = ds;
-    a.done = ds + 1;
-    a.out = d_io + nin;
-    cudaError_t e = c->res_tma
-                        ? launch_nll_res_tma(&c->res_dmap, &c->res_mmap, a, c->res_amax, c->num_sms,
-                                             c->stream)
-                        : launch_nll_res(a, (int)res_grid(c), c->stream);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, PWA_ECUDA, "resonance kernel launch: %s", cudaGetErrorString(e));
-    }
+    int rc = enqueue_res(c, d_io, d_io + 2 * N, d_io + 2 * N + R, d_io + nin, ds, ds + 1);
+    if (rc)
+        return rc;
     CK(c, cudaMemcpyAsync(h + 2 * N + 2 * R, d_io + 2 * N + 2 * R, (1 + nout) * sizeof(double),
                           cudaMemcpyDeviceToHost, c->stream));
     CK(c, cudaStreamSynchronize(c->stream));
@@ -712,8 +738,7 @@ int pwa_nll_grad_res(pwa_ctx *c, const double *V, const double *mass, const doub
 
 // Device scratch and its pinned host mirror for the Hessian, weight and
 // fraction calls; copies V in (through the mirror) and clears the status word.
-static int fx_buffer(pwa_ctx *c, const double *V, double **dV, int **dstat, double **dout,
-                     double **dpart)
+static int fx_alloc(pwa_ctx *c)
 {
     const int N = c->N;
     const size_t nio = 2 * (size_t)N + 1 + 4 * (size_t)N * N;
@@ -736,6 +761,16 @@ static int fx_buffer(pwa_ctx *c, const double *V, double **dV, int **dstat, doub
         }
         c->fx_bytes = bytes;
     }
+    return PWA_OK;
+}
+
+static int fx_buffer(pwa_ctx *c, const double *V, double **dV, int **dstat, double **dout,
+                     double **dpart)
+{
+    int rc = fx_alloc(c);
+    if (rc)
+        return rc;
+    const int N = c->N;
     *dV = c->d_fx;
     *dstat = reinterpret_cast<int *>(c->d_fx + 2 * N);
     *dout = c->d_fx + 2 * N + 1;
@@ -783,6 +818,29 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
     if ((rc = fx_result(c, (size_t)P * P, H, &flags)))
         return rc;
     return status_from_flags(c, flags);
+}
+
+int pwa_hessian_async(pwa_ctx *c, const double *d_V, double *d_H)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!d_V || !d_H)
+        return fail(c, PWA_EINVAL, "null V or H");
+    if (!c->loaded)
+        return fail(c, PWA_ESTATE, "pwa_load_events must come first");
+    if (c->n_lambda > 1)
+        return fail(c, PWA_ENOTSUP, "the Hessian takes coherent samples only");
+    DeviceGuard g(c->device);
+    int rc = fx_alloc(c);
+    if (rc)
+        return rc;
+    const int N = c->N;
+    int *ds = reinterpret_cast<int *>(c->d_fx + 2 * N);
+    double *dpart = c->d_fx + 2 * N + 1 + 4 * (size_t)N * N;
+    CK(c, cudaMemsetAsync(ds, 0, sizeof(double), c->stream));
+    CK(c, launch_hessian(c->data, d_V, dpart, c->num_sms, ds, d_H, c->stream));
+    CK(c, launch_or_flags(ds, c->async_status, c->stream));
+    return PWA_OK;
 }
 
 int pwa_mc_weights(pwa_ctx *c, const double *V, float *w)

@@ -505,6 +505,8 @@ cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, i
 // w[j] = |sum_a V_a A_a(j)|^2 / n_gen for the accepted MC events (float, device).
 cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, float *w, int grid,
                               cudaStream_t s);
+// *dst |= *src on the stream (status words)
+cudaError_t launch_or_flags(const int *src, int *dst, cudaStream_t s);
 // F[a][b] = Re(conj(V_a) M_ab V_b) / V^H M V (device doubles).
 cudaError_t launch_fit_fractions(const double *M, const double *V, int N, double *F, cudaStream_t s);
 // dst[i] = (float)src[i] (round to nearest)

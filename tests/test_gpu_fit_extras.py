@@ -166,3 +166,20 @@ def test_extras_need_state(pwa):
             L.hessian(np.ones(4, complex))
         with pytest.raises(pwa.PwaError):
             L.fit_fractions(np.ones(4, complex))
+
+
+def test_hessian_async_matches_host_call(pwa):
+    import torch
+    wl = case(9, 5000, 3000, seed=21)
+    V = synth.random_V(9, 22)
+    with pwa.Likelihood(9) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        H = L.hessian(V)
+        dH = torch.empty(18, 18, dtype=torch.float64, device="cuda")
+        L.hessian_async(torch.from_numpy(V).cuda(), dH)
+        assert L.sync() == pwa.PWA_OK
+        assert np.array_equal(dH.cpu().numpy(), H)
+        L.hessian_async(torch.zeros(9, dtype=torch.complex128, device="cuda"), dH)
+        assert L.sync() == pwa.PWA_EDOMAIN
+        assert not dH.cpu().numpy().any()

@@ -206,3 +206,20 @@ def test_free_resonance_scale(pwa, kernel):
     """2M data events, 5M accepted MC, 20 waves, 4 free Breit-Wigners."""
     wl = synth.free_resonance_scale()
     check(pwa, wl, params_for(wl, 1, seed=2))
+
+
+def test_async_matches_host_call(pwa, kernel):
+    import torch
+    wl = case(12, 3, 4000, 6000, seed=5)
+    V, mass, width = params_for(wl, k=1, seed=5)[0]
+    with pwa.Likelihood(12) as L:
+        L.load_resonance_events(wl)
+        nll, gV, gM, gW = L.nll_grad_res(V, mass, width)
+        dout = torch.empty(1 + 24 + 6, dtype=torch.float64, device="cuda")
+        L.nll_grad_res_async(torch.from_numpy(V).cuda(), torch.tensor(mass, device="cuda"),
+                             torch.tensor(width, device="cuda"), dout)
+        assert L.sync() == pwa.PWA_OK
+    o = dout.cpu().numpy()
+    assert o[0] == nll
+    assert np.array_equal(o[1:25].view(np.complex128), gV)
+    assert np.array_equal(o[25:28], gM) and np.array_equal(o[28:31], gW)
