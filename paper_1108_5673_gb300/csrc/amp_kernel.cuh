@@ -19,7 +19,10 @@ constexpr double kLn2 = 0.69314718055994530942;
 template <int N, int G, int L = 1>
 struct AmpCfg {
     static constexpr int GROUPS = G;                   // consumer groups (tiles in turn)
-    static constexpr int GW = 4;                       // warps per group
+    // warps per group: 4; 3 with several components, so that the CTA keeps to
+    // eight warps and the register cap of 255 (a larger CTA is allocated as
+    // twelve warps: 168 registers, and the per-component state spilled)
+    static constexpr int GW = L > 1 ? 3 : 4;
     static constexpr int CW = GROUPS * GW;             // consumer warps
     static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
     static constexpr int ROWS = 2 * N * L;
