@@ -27,22 +27,26 @@ namespace pwa {
 namespace {
 
 constexpr double kLn2 = 0.69314718055994530942;
-constexpr int kTE = 32;        // events per tile (one per lane)
 constexpr int kBoxRows = 256;  // TMA box height limit
 
+// Tiles of TE events: 64 (two per lane, packed in FP32x2 registers) where two
+// stages of them fit in shared memory (N <= 20), else 32 (one per lane).
 template <int N>
 struct TabCfg {
     static constexpr int P = N * N;
+    static constexpr int TE = N <= 20 ? 64 : 32;
+    static constexpr int EPL = TE / 32;                      // events per lane
     static constexpr int W = (P <= 256) ? 8 : 16;            // consumer warps
     static constexpr int RPW = (P + W - 1) / W;              // planes per warp
     static constexpr int BOXES = (P + kBoxRows - 1) / kBoxRows;
-    static constexpr uint32_t STAGE_BYTES = P * kTE * 4;
+    static constexpr uint32_t STAGE_BYTES = P * TE * 4;
     static constexpr int STAGES_RAW = (190 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
     static constexpr int THREADS = (W + 2) * 32;             // + producer warp + helper warp
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t) +
                                    (size_t)P * 3 * sizeof(float);  // w_hi, w_lo, |w|
-    static constexpr bool FITS = SMEM <= 200 * 1024;
+    // with the static arrays (part_hi/part_lo 2 W TE words each) inside 227 KB
+    static constexpr bool FITS = SMEM + (size_t)4 * W * TE * 4 + 4096 <= 227 * 1024;
 };
 
 // scratch: [G] int64 pairs (ln-integer part, exponents), [G][P + 1] float-float
@@ -89,9 +93,9 @@ __global__ void __launch_bounds__(TabCfg<N>::THREADS, 1)
     float *w_lo = w_hi + P;
     float *w_abs = w_lo + P;
 
-    __shared__ unsigned part_hi[W][kTE];
-    __shared__ float part_lo[W][kTE];
-    __shared__ float inv_I[kTE];
+    constexpr int TE = C::TE, EPL = C::EPL;
+    __shared__ unsigned part_hi[2][W][TE];  // double-buffered by tile parity
+    __shared__ float part_lo[2][W][TE];
     __shared__ float s_sigma, s_unit;
     __shared__ float red_g[W][C::RPW];
     __shared__ long long red_i[2];
@@ -106,16 +110,16 @@ __global__ void __launch_bounds__(TabCfg<N>::THREADS, 1)
         (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     // every box is counted in full (rows past Pw arrive zero-filled)
     const int rows_loaded = box_rows * n_boxes;
-    const uint32_t stage_tx = (uint32_t)rows_loaded * kTE * 4u;
+    const uint32_t stage_tx = (uint32_t)rows_loaded * TE * 4u;
     const int n_first = n_my < STAGES ? n_my : STAGES;
 
     auto issue = [&](int j) {
         const int s = j % STAGES;
-        float *dst = tiles + (size_t)s * P * kTE;
-        const int x = ((int)blockIdx.x + j * (int)gridDim.x) * kTE;
+        float *dst = tiles + (size_t)s * P * TE;
+        const int x = ((int)blockIdx.x + j * (int)gridDim.x) * TE;
         mbar_arrive_expect_tx(&full[s], stage_tx);
         for (int bx = 0; bx < n_boxes; ++bx)
-            tma_load_2d(dst + (size_t)bx * box_rows * kTE, &map, x, bx * box_rows, &full[s]);
+            tma_load_2d(dst + (size_t)bx * box_rows * TE, &map, x, bx * box_rows, &full[s]);
     };
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -131,8 +135,8 @@ __global__ void __launch_bounds__(TabCfg<N>::THREADS, 1)
     }
     // planes past the loaded boxes (padded waves) are never written: zero them once
     for (int s = 0; s < STAGES; ++s)
-        for (int i = rows_loaded * kTE + threadIdx.x; i < P * kTE; i += blockDim.x)
-            tiles[(size_t)s * P * kTE + i] = 0.f;
+        for (int i = rows_loaded * TE + threadIdx.x; i < P * TE; i += blockDim.x)
+            tiles[(size_t)s * P * TE + i] = 0.f;
     // coefficients w_p as float pairs, from V in FP64
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         double w = 0.0;
@@ -209,59 +213,108 @@ __global__ void __launch_bounds__(TabCfg<N>::THREADS, 1)
                 flags |= FLAG_TIMEOUT;
                 break;
             }
-            const float *T = tiles + (size_t)s * P * kTE + lane;
-            // intensity: this warp's share of sum_p w_p t_p, split exactly
-            unsigned hsum = 0;
-            float lsum = 0.f;
+            const float *T = tiles + (size_t)s * P * TE + EPL * lane;
+            // intensity: this warp's share of sum_p w_p t_p for the lane's EPL
+            // events, split exactly
+            unsigned hsum[EPL];
+            float lsum[EPL];
+            if constexpr (EPL == 2) {
+                const f2 SG = pk2(sigma, sigma);
+                unsigned h0 = 0, h1 = 0;
+                f2 l2 = 0ull;
 #pragma unroll
-            for (int r = 0; r < C::RPW; ++r) {
-                const int p = q + r * W;
-                if (p < P) {
-                    const float t = T[p * kTE];
-                    const float wh = w_hi[p];
-                    const float x = fmaf(wh, t, sigma);
-                    hsum += __float_as_uint(x);
-                    lsum += fmaf(wh, t, sigma - x);
-                    lsum = fmaf(w_lo[p], t, lsum);
+                for (int r = 0; r < C::RPW; ++r) {
+                    const int p = q + r * W;
+                    if (p < P) {
+                        const f2 t = *reinterpret_cast<const f2 *>(T + p * TE);
+                        const float wh = w_hi[p];
+                        const f2 W2 = pk2(wh, wh);
+                        const f2 x = fma2(W2, t, SG);
+                        float x0, x1;
+                        upk2(x, x0, x1);
+                        h0 += __float_as_uint(x0);
+                        h1 += __float_as_uint(x1);
+                        l2 = add2(l2, fma2(W2, t, sub2(SG, x)));
+                        const float wl = w_lo[p];
+                        l2 = fma2(pk2(wl, wl), t, l2);
+                    }
                 }
+                hsum[0] = h0;
+                hsum[1] = h1;
+                upk2(l2, lsum[0], lsum[1]);
+            } else {
+                unsigned h = 0;
+                float l = 0.f;
+#pragma unroll
+                for (int r = 0; r < C::RPW; ++r) {
+                    const int p = q + r * W;
+                    if (p < P) {
+                        const float t = T[p * TE];
+                        const float wh = w_hi[p];
+                        const float x = fmaf(wh, t, sigma);
+                        h += __float_as_uint(x);
+                        l += fmaf(wh, t, sigma - x);
+                        l = fmaf(w_lo[p], t, l);
+                    }
+                }
+                hsum[0] = h;
+                lsum[0] = l;
             }
-            part_hi[q][lane] = hsum;
-            part_lo[q][lane] = lsum;
+            // Every warp forms the TE intensities from the W partials (in the same
+            // order, so to the same bits); warp 0 alone accumulates the log sums.
+            // The partials are double-buffered by tile parity, so one barrier per
+            // tile suffices: a warp past tile j's barrier writes buffer (j+1)&1
+            // only after every warp has arrived there, i.e. finished reading it
+            // for tile j-1.
+            const int pb = j & 1;
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                part_hi[pb][q][EPL * lane + e] = hsum[e];
+                part_lo[pb][q][EPL * lane + e] = lsum[e];
+            }
             consumers_sync(W * 32);
-            if (q == 0) {
+            float iv[EPL];
+#pragma unroll
+            for (int e = 0; e < EPL; ++e) {
+                iv[e] = 0.f;
                 unsigned h = 0;
                 float l = 0.f;
 #pragma unroll
                 for (int k = 0; k < W; ++k) {
-                    h += part_hi[k][lane];
-                    l += part_lo[k][lane];
+                    h += part_hi[pb][k][EPL * lane + e];
+                    l += part_lo[pb][k][EPL * lane + e];
                 }
                 const float I = (float)(int)(h - offset) * unit + l;
-                const int64_t ev = (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * kTE + lane;
-                float inv = 0.f;
+                const int64_t ev =
+                    (int64_t)((int)blockIdx.x + j * (int)gridDim.x) * TE + EPL * lane + e;
                 if (ev < a.n_events) {
                     if (I > 0.f && I < INFINITY) {
-                        int ex;
-                        const float f = split_exponent(I, ex);
-                        const float y = logf(f) * 8388608.0f;
-                        const float tt = y + 12582912.0f;
-                        l_int += __float_as_int(tt) - 0x4B400000;
-                        l_frac += y - (tt - 12582912.0f);
-                        eacc += ex;
-                        inv = __frcp_rn(I);
+                        iv[e] = __frcp_rn(I);
+                        if (q == 0) {
+                            int ex;
+                            const float f = split_exponent(I, ex);
+                            const float y = logf(f) * 8388608.0f;
+                            const float tt = y + 12582912.0f;
+                            l_int += __float_as_int(tt) - 0x4B400000;
+                            l_frac += y - (tt - 12582912.0f);
+                            eacc += ex;
+                        }
                     } else {
                         bad = 1;
                     }
                 }
-                inv_I[lane] = inv;
             }
-            consumers_sync(W * 32);
-            const float iv = inv_I[lane];
 #pragma unroll
             for (int r = 0; r < C::RPW; ++r) {
                 const int p = q + r * W;
-                if (p < P)
-                    gacc[r] = fmaf(T[p * kTE], iv, gacc[r]);
+                if (p < P) {
+                    if constexpr (EPL == 2) {
+                        const float2 t = *reinterpret_cast<const float2 *>(T + p * TE);
+                        gacc[r] = fmaf(t.x, iv[0], fmaf(t.y, iv[1], gacc[r]));
+                    } else {
+                        gacc[r] = fmaf(T[p * TE], iv[0], gacc[r]);
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0)
@@ -427,9 +480,10 @@ cudaError_t configure_t()
 }
 
 template <int N>
-cudaError_t launch_t(const CUtensorMap *map, const EvalArgs &a, int grid, int n_tiles,
-                     const float *tmax, cudaStream_t s)
+cudaError_t launch_t(const CUtensorMap *map, const EvalArgs &a, int grid, const float *tmax,
+                     cudaStream_t s)
 {
+    const int n_tiles = (int)((a.n_events + TabCfg<N>::TE - 1) / TabCfg<N>::TE);
     const int Pw = a.n_waves * a.n_waves;
     const int n_boxes = (Pw + kBoxRows - 1) / kBoxRows;
     const int box_rows = (Pw + n_boxes - 1) / n_boxes;
@@ -442,8 +496,19 @@ cudaError_t launch_t(const CUtensorMap *map, const EvalArgs &a, int grid, int n_
 
 }  // namespace
 
-int table_max_waves() { return 24; }  // 32-event tiles of N^2 planes must fit two stages
-int table_box_events() { return kTE; }
+int table_max_waves() { return 24; }  // tiles of N^2 planes must fit two stages
+int table_box_events(int n_waves)
+{
+    switch (pad_waves_table(n_waves)) {
+    case 4: return TabCfg<4>::TE;
+    case 8: return TabCfg<8>::TE;
+    case 12: return TabCfg<12>::TE;
+    case 16: return TabCfg<16>::TE;
+    case 20: return TabCfg<20>::TE;
+    case 24: return TabCfg<24>::TE;
+    }
+    return 32;
+}
 int table_box_rows(int n_waves)
 {
     const int Pw = n_waves * n_waves;
@@ -471,14 +536,14 @@ cudaError_t table_configure()
 cudaError_t launch_nll_table(int64_t n_events, int n_waves, const CUtensorMap *map,
                              const EvalArgs &a, const float *tmax, int grid, cudaStream_t s)
 {
-    const int n_tiles = (int)((n_events + kTE - 1) / kTE);
+    (void)n_events;
     switch (pad_waves_table(n_waves)) {
-    case 4: return launch_t<4>(map, a, grid, n_tiles, tmax, s);
-    case 8: return launch_t<8>(map, a, grid, n_tiles, tmax, s);
-    case 12: return launch_t<12>(map, a, grid, n_tiles, tmax, s);
-    case 16: return launch_t<16>(map, a, grid, n_tiles, tmax, s);
-    case 20: return launch_t<20>(map, a, grid, n_tiles, tmax, s);
-    case 24: return launch_t<24>(map, a, grid, n_tiles, tmax, s);
+    case 4: return launch_t<4>(map, a, grid, tmax, s);
+    case 8: return launch_t<8>(map, a, grid, tmax, s);
+    case 12: return launch_t<12>(map, a, grid, tmax, s);
+    case 16: return launch_t<16>(map, a, grid, tmax, s);
+    case 20: return launch_t<20>(map, a, grid, tmax, s);
+    case 24: return launch_t<24>(map, a, grid, tmax, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -1067,7 +1067,7 @@ static int finish_load(pwa_ctx *c, int rc, int64_t n_data, int64_t n_mc_acc, dou
                 e = launch_plane_absmax(c->table, c->table_pitch, n_data, P, c->tmax, c->stream);
             if (e == cudaSuccess)
                 e = encode_planes_map(&c->table_map, c->table, n_data, c->table_pitch, P,
-                                      table_box_events(), table_box_rows(c->N));
+                                      table_box_events(c->N), table_box_rows(c->N));
             if (e != cudaSuccess)
                 rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
         }
@@ -1326,7 +1326,7 @@ int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, i
                 e = launch_plane_absmax(c->table, c->table_pitch, n_data, P, c->tmax, c->stream);
             if (e == cudaSuccess)
                 e = encode_planes_map(&c->table_map, c->table, n_data, c->table_pitch, P,
-                                      table_box_events(), table_box_rows(N));
+                                      table_box_events(N), table_box_rows(N));
             if (e != cudaSuccess)
                 rc = fail(c, PWA_ECUDA, "table build: %s", cudaGetErrorString(e));
         }

@@ -514,7 +514,7 @@ cudaError_t launch_to_float(const double *src, int64_t n, float *dst, cudaStream
 
 // k_nll_table.cu
 int table_max_waves();
-int table_box_events();
+int table_box_events(int n_waves);
 int table_box_rows(int n_waves);
 size_t table_scratch_bytes(int n_waves, int grid);
 cudaError_t table_configure();
