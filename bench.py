@@ -57,14 +57,14 @@ WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M 
 # DRAM bytes (read + write) per step of the timed kernel from one ncu
 # capture of the current kernel, or None where there is none.
 TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
-           "table": 1600.392e6 + 4.053504e6,
+           "table": 1600.119e6 + 3.221760e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.240896e6 + 3.188992e6,
            "weights": None,
-           "incoh": 321.553152e6 + 4.238336e6,
-           "incoh_table": None,
+           "incoh": 320.162304e6 + 3.733248e6,
+           "incoh_table": None,   # the table kernel's capture is of the coherent sample
            "ampgen": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
