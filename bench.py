@@ -69,7 +69,7 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
            "models": "batched_kernel<F, 2> (all models)", "hessian": "hess_kernel<20>",
-           "weights": "mc_weights_kernel<20>", "incoh": "nll_amp_kernel<20, 2, 2>",
+           "weights": "nll_amp_kernel<20, 2, 1, true> (weights mode)", "incoh": "nll_amp_kernel<20, 2, 2>",
            "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)
 DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,

@@ -88,11 +88,14 @@ __device__ __forceinline__ f2 extract(f2 c, f2 a, f2 sg, unsigned &t0, unsigned 
     return fma2(c, a, sub2(sg, t));
 }
 
-template <int N, int G, int L = 1>
+// WEIGHTS: instead of the NLL, write I / N_gen of every event to a.weights
+// (the projection weights of the accepted MC events; L = 1), with no sums.
+template <int N, int G, int L = 1, bool WEIGHTS = false>
 __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     nll_amp_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs a, const int n_tiles,
                    int *work_flags)
 {
+    static_assert(!WEIGHTS || L == 1, "projection weights of a coherent sample");
     using C = AmpCfg<N, G, L>;
     constexpr int TE = C::TE, ROWS = C::ROWS, STAGES = C::STAGES, CW = C::CW;
     constexpr int GROUPS = C::GROUPS, GW = C::GW;
@@ -292,6 +295,18 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
                         }
                 }
             }
+            if constexpr (WEIGHTS) {
+                const float w0 = fmaf(Sr[0][0], Sr[0][0], Si[0][0] * Si[0][0]) * a.inv_ngen;
+                const float w1 = fmaf(Sr[0][1], Sr[0][1], Si[0][1] * Si[0][1]) * a.inv_ngen;
+                if (ev0 + 1 < a.n_events)
+                    *reinterpret_cast<float2 *>(a.weights + ev0) = make_float2(w0, w1);
+                else if (ev0 < a.n_events)
+                    a.weights[ev0] = w0;
+                __syncwarp();
+                if (lane == 0)
+                    mbar_arrive(&empty[s]);
+                continue;
+            }
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 float I = fmaf(Sr[0][e], Sr[0][e], Si[0][e] * Si[0][e]);
@@ -365,7 +380,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
             if (lane == 0)
                 red_f[cw][1 + c] = v;
         }
-    } else if (warp == CW + 1 && blockIdx.x == 0) {
+    } else if (warp == CW + 1 && blockIdx.x == 0 && !WEIGHTS) {
         // ---- helper warp of CTA 0: M V and V^H M V in FP64 -------------
         // One row per lane; this overlaps the streaming of the data.
         const int Nw = a.n_waves;
@@ -385,6 +400,11 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         nv = warp_sum(nv);
         if (lane == 0)
             sc.mv[2 * kMaxWaves] = nv;
+    }
+    if constexpr (WEIGHTS) {
+        if (flags)
+            atomicOr(a.status, flags);
+        return;
     }
     if (flags)
         atomicOr(&s_flags, flags);

@@ -17,6 +17,7 @@
 //
 // Projection weights: w_j = I(Omega_j) / N_gen per accepted MC event (their
 // sum is V^H M V), and fit fractions F_ab = Re(conj(V_a) M_ab V_b) / V^H M V.
+#include "amp_kernel.cuh"
 #include "pwa_internal.cuh"
 
 namespace pwa {
@@ -459,6 +460,50 @@ cudaError_t launch_or_flags(const int *src, int *dst, cudaStream_t s)
 {
     or_flags_kernel<<<1, 1, 0, s>>>(src, dst);
     return cudaGetLastError();
+}
+
+namespace {
+template <int N>
+cudaError_t weights_tma_n(const CUtensorMap *map, const EvalArgs &a, int grid, cudaStream_t s)
+{
+    using C = AmpCfg<N, 2>;
+    cudaError_t e = cudaFuncSetAttribute(nll_amp_kernel<N, 2, 1, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
+    if (e != cudaSuccess)
+        return e;
+    const int n_tiles = (int)((a.n_events + C::TE - 1) / C::TE);
+    nll_amp_kernel<N, 2, 1, true><<<grid, C::THREADS, C::SMEM, s>>>(*map, a, n_tiles, nullptr);
+    return cudaGetLastError();
+}
+}  // namespace
+
+// Projection weights through the TMA-fed direct-form kernel (its weights
+// mode): map over the MC planes as for the data (box of 256 events x 2n
+// rows), amax over the MC sample; S by the exact product split.
+cudaError_t launch_mc_weights_tma(const CUtensorMap *map, const Planes &mc, const double *V,
+                                  const float *amax, double n_gen, float *w, int *status, int grid,
+                                  cudaStream_t s)
+{
+    EvalArgs a{};
+    a.n_waves = mc.n_waves;
+    a.n_events = mc.n;
+    a.V = V;
+    a.amax = amax;
+    a.status = status;
+    a.weights = w;
+    a.inv_ngen = (float)(1.0 / n_gen);
+    switch (pad_np(mc.n_waves)) {
+    case 4: return weights_tma_n<4>(map, a, grid, s);
+    case 8: return weights_tma_n<8>(map, a, grid, s);
+    case 12: return weights_tma_n<12>(map, a, grid, s);
+    case 16: return weights_tma_n<16>(map, a, grid, s);
+    case 20: return weights_tma_n<20>(map, a, grid, s);
+    case 24: return weights_tma_n<24>(map, a, grid, s);
+    case 32: return weights_tma_n<32>(map, a, grid, s);
+    case 40: return weights_tma_n<40>(map, a, grid, s);
+    case 48: return weights_tma_n<48>(map, a, grid, s);
+    }
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fit_fractions(const double *M, const double *V, int N, double *F, cudaStream_t s)

@@ -81,6 +81,8 @@ struct pwa_ctx {
     bool loaded = false, has_norm = false;
     double *M = nullptr;     // [N][N] complex
     float *amax = nullptr;   // [N] max over data events of |Re A_a| + |Im A_a|
+    float *mc_amax = nullptr;  // [N] the same over the accepted MC events (projection weights)
+    CUtensorMap mc_map;        // over the MC planes, as data_map over the data
 
     // per-call buffers
     double *d_io = nullptr;  // [nll K | grad 2NK | status,done | V 2NK]
@@ -871,12 +873,20 @@ int pwa_mc_weights(pwa_ctx *c, const double *V, float *w)
         }
         dw = c->d_w;
     }
-    CK(c, launch_mc_weights(c->mc, dV, c->n_gen, dw, c->num_sms * 8, c->stream));
+    const char *kv = getenv("PWA_WEIGHTS_KERNEL");
+    if (kv && strcmp(kv, "generic") == 0) {
+        CK(c, launch_mc_weights(c->mc, dV, c->n_gen, dw, c->num_sms * 8, c->stream));
+    } else {
+        CK(c, launch_mc_weights_tma(&c->mc_map, c->mc, dV, c->mc_amax, c->n_gen, dw, ds, c->num_sms,
+                                    c->stream));
+    }
     if (!on_dev)
         CK(c, cudaMemcpyAsync(w, dw, (size_t)c->n_mc * sizeof(float), cudaMemcpyDeviceToHost,
                               c->stream));
-    CK(c, cudaStreamSynchronize(c->stream));
-    return PWA_OK;
+    int flags = 0;
+    if ((rc = fx_result(c, 0, nullptr, &flags)))
+        return rc;
+    return status_from_flags(c, flags);
 }
 
 int pwa_fit_fractions(pwa_ctx *c, const double *V, double *F)
@@ -988,6 +998,8 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
         return bail(rc);
     if ((rc = dev_alloc(c, (void **)&c->amax, (size_t)c->N * sizeof(float), "amax")))
         return bail(rc);
+    if ((rc = dev_alloc(c, (void **)&c->mc_amax, (size_t)c->N * sizeof(float), "MC amax")))
+        return bail(rc);
     *out = c;
     return PWA_OK;
 }
@@ -1005,6 +1017,7 @@ int pwa_destroy(pwa_ctx *c)
     free_sample(c);
     free_res(c);
     dev_free(c->M);
+    dev_free(c->mc_amax);
     dev_free(c->amax);
     dev_free(c->d_io);
     dev_free(c->d_fx);
@@ -1097,6 +1110,14 @@ static int finish_load(pwa_ctx *c, int rc, int64_t n_data, int64_t n_mc_acc, dou
     if (!rc) {
         cudaError_t e = encode_planes_map(&c->data_map, c->data.ptr, c->data.n, c->data.pitch,
                                           2 * c->N, amp_box_events(c->N), amp_box_rows(c->N));
+        // the MC sample's map and maxima serve the projection weights
+        if (e == cudaSuccess)
+            e = encode_planes_map(&c->mc_map, c->mc.ptr, c->mc.n, c->mc.pitch, 2 * c->N,
+                                  amp_box_events(c->N), amp_box_rows(c->N));
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(c->mc_amax, 0, c->N * sizeof(float), c->stream);
+        if (e == cudaSuccess)
+            e = launch_amp_max(c->mc, c->mc_amax, c->stream);
         if (e != cudaSuccess)
             rc = fail(c, PWA_ECUDA, "tensor map encode failed");
     }

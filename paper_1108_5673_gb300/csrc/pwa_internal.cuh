@@ -388,6 +388,8 @@ struct EvalArgs {
     int *done;         // incremented by the last block (may be null)
     double *nll;       // [1] output
     double *grad;      // [n_waves] complex output (null: NLL only)
+    float *weights;    // projection weights I / N_gen per event (the weights mode)
+    float inv_ngen;    // 1 / N_gen (the weights mode)
 };
 
 // Structure-of-arrays store: plane 2a holds Re A_a, plane 2a+1 holds Im A_a,
@@ -505,6 +507,12 @@ cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, i
 // w[j] = |sum_a V_a A_a(j)|^2 / n_gen for the accepted MC events (float, device).
 cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, float *w, int grid,
                               cudaStream_t s);
+// w[j] = |S_j|^2 / n_gen through the TMA-fed kernel: map over the MC planes
+// (box amp_box_events() x 2 n_waves rows), amax[a] >= max over the MC sample
+// of |Re A_a| + |Im A_a|; a timeout is OR-ed into *status.
+cudaError_t launch_mc_weights_tma(const CUtensorMap *map, const Planes &mc, const double *V,
+                                  const float *amax, double n_gen, float *w, int *status, int grid,
+                                  cudaStream_t s);
 // *dst |= *src on the stream (status words)
 cudaError_t launch_or_flags(const int *src, int *dst, cudaStream_t s);
 // F[a][b] = Re(conj(V_a) M_ab V_b) / V^H M V (device doubles).

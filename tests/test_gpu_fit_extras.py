@@ -125,8 +125,16 @@ def test_hessian_homogeneity_at_scale(pwa):
 
 @pytest.mark.parametrize("N", [1, 3, 8, 20, 33, 48])
 @pytest.mark.parametrize("where", ["host", "device"])
-def test_mc_weights(pwa, N, where):
+@pytest.mark.parametrize("kernel", ["tma", "generic"])
+def test_mc_weights(pwa, monkeypatch, N, where, kernel):
+    """The TMA-fed weights mode of the direct-form kernel (S by the exact
+    product split) and the per-event kernel (plain FP32 dot product) both
+    meet the plain kernel's rounding bound."""
     import torch
+    if kernel == "generic":
+        monkeypatch.setenv("PWA_WEIGHTS_KERNEL", "generic")
+    else:
+        monkeypatch.delenv("PWA_WEIGHTS_KERNEL", raising=False)
     wl = case(N, 100, 5003, seed=N + 40)
     V = synth.random_V(N, N + 41)
     with pwa.Likelihood(N) as L:
