@@ -61,14 +61,14 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
-           "hessian": 160.240896e6 + 3.188992e6,
+           "hessian": None,       # the tensor-core kernel is not yet captured
            "weights": None,
            "incoh": 320.162304e6 + 3.733248e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
            "ampgen": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
-           "models": "batched_kernel<F, 2> (all models)", "hessian": "hess_kernel<20>",
+           "models": "batched_kernel<F, 2> (all models)", "hessian": "hess_tc_kernel<20>",
            "weights": "nll_amp_kernel<20, 2, 1, true> (weights mode)", "incoh": "nll_amp_kernel<20, 2, 2>",
            "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)

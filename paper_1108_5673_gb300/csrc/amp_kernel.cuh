@@ -88,6 +88,84 @@ __device__ __forceinline__ f2 extract(f2 c, f2 a, f2 sg, unsigned &t0, unsigned 
     return fma2(c, a, sub2(sg, t));
 }
 
+// S = sum_w V_w A_w of two events, exact up to its final rounding (see the
+// file comment); amp(w, ar, ai) gives wave w's amplitudes of both events.
+// SG = (sigma, sigma), unit = u_k, im_offset = 2 N bits(sigma).
+template <int N, class AmpOf>
+__device__ __forceinline__ void exact_sum2(AmpOf amp, const WaveCoef *Vc, f2 SG, float unit,
+                                           unsigned im_offset, float (&sr)[2], float (&si)[2])
+{
+    // Re S = vr ar - vi ai ; Im S = vr ai + vi ar
+    unsigned hR0 = 0, hR1 = 0, hI0 = 0, hI1 = 0;  // high parts (units of u_k)
+    const f2 Z = 0ull;
+    f2 lR = Z, lRm = Z, lI = Z;                    // remainders; lRm is subtracted
+#pragma unroll
+    for (int w = 0; w < N; ++w) {
+        f2 ar, ai;
+        amp(w, ar, ai);
+        const WaveCoef cf = Vc[w];
+        unsigned x0, x1;
+        lR = add2(lR, extract(cf.vr, ar, SG, x0, x1));
+        hR0 += x0;
+        hR1 += x1;
+        lRm = add2(lRm, extract(cf.vi, ai, SG, x0, x1));
+        hR0 -= x0;
+        hR1 -= x1;
+        lI = add2(lI, extract(cf.vr, ai, SG, x0, x1));
+        hI0 += x0;
+        hI1 += x1;
+        lI = add2(lI, extract(cf.vi, ar, SG, x0, x1));
+        hI0 += x0;
+        hI1 += x1;
+        lR = fma2(cf.lr, ar, lR);
+        lRm = fma2(cf.li, ai, lRm);
+        lI = fma2(cf.lr, ai, fma2(cf.li, ar, lI));
+    }
+    const f2 hR = pk2((float)(int)hR0 * unit, (float)(int)hR1 * unit);
+    const f2 hI = pk2((float)(int)(hI0 - im_offset) * unit, (float)(int)(hI1 - im_offset) * unit);
+    upk2(add2(hR, sub2(lR, lRm)), sr[0], sr[1]);
+    upk2(add2(hI, lI), si[0], si[1]);
+}
+
+// V as float pairs Vhi + Vlo, duplicated for packed use; waves w >= n_waves
+// (padding) get V = 0. One thread per wave.
+__device__ __forceinline__ void wave_coef(const double *V, int n_waves, int w, WaveCoef &c)
+{
+    const bool on = w < n_waves;
+    const double dr = on ? V[2 * w] : 0.0, di = on ? V[2 * w + 1] : 0.0;
+    const float vr = __double2float_rn(dr), vi = __double2float_rn(di);
+    const float lr = __double2float_rn(dr - (double)vr), li = __double2float_rn(di - (double)vi);
+    c.vr = pk2(vr, vr);
+    c.vi = pk2(vi, vi);
+    c.lr = pk2(lr, lr);
+    c.li = pk2(li, li);
+}
+
+// sigma = 1.5 2^k and u_k = 2^(k-23) with 2^(k-1) >= 1.25 sum_a |V_a|_1
+// max_i |A_a(i)|_1 (margin for rounding); called by one whole warp, lane 0
+// writes the results.
+__device__ __forceinline__ void exact_scale(const double *V, const float *amax, int n_waves,
+                                            int lane, float *sigma, float *unit)
+{
+    float b = 0.f;
+    for (int w = lane; w < n_waves; w += 32) {
+        const float v1 = fabsf(__double2float_ru(fabs(V[2 * w]))) +
+                         fabsf(__double2float_ru(fabs(V[2 * w + 1])));
+        b = fmaf(v1, amax[w], b);
+    }
+    b = warp_sum(b);
+    if (lane == 0) {
+        const float target = 2.5f * b;
+        int k = -100;  // floor keeps u_k normal
+        if (target > 0.f)
+            k = max(k, ((__float_as_int(target) >> 23) & 0xff) - 126);  // target < 2^k
+        if (!(target < 1e30f))
+            k = 100;   // non-finite bound: the results will flag the domain error
+        *sigma = 1.5f * ldexpf(1.0f, k);
+        *unit = ldexpf(1.0f, k - 23);
+    }
+}
+
 // WEIGHTS: instead of the NLL, write I / N_gen of every event to a.weights
 // (the projection weights of the accepted MC events; L = 1), with no sums.
 template <int N, int G, int L = 1, bool WEIGHTS = false>
@@ -141,37 +219,10 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     for (int s = 0; s < STAGES; ++s)
         for (int i = 2 * a.n_waves * L * TE + threadIdx.x; i < ROWS * TE; i += blockDim.x)
             tiles[(size_t)s * ROWS * TE + i] = 0.f;
-    if (threadIdx.x < N) {
-        const int w = threadIdx.x;
-        const bool on = w < a.n_waves;
-        const double dr = on ? a.V[2 * w] : 0.0, di = on ? a.V[2 * w + 1] : 0.0;
-        const float vr = __double2float_rn(dr), vi = __double2float_rn(di);
-        const float lr = __double2float_rn(dr - (double)vr), li = __double2float_rn(di - (double)vi);
-        Vc[w].vr = pk2(vr, vr);
-        Vc[w].vi = pk2(vi, vi);
-        Vc[w].lr = pk2(lr, lr);
-        Vc[w].li = pk2(li, li);
-    }
-    if (warp == 1) {
-        // 2^(k-1) >= 1.25 sum_a |V_a|_1 max_i |A_a(i)|_1 (margin for rounding)
-        float b = 0.f;
-        for (int w = lane; w < a.n_waves; w += 32) {
-            const float v1 = fabsf(__double2float_ru(fabs(a.V[2 * w]))) +
-                             fabsf(__double2float_ru(fabs(a.V[2 * w + 1])));
-            b = fmaf(v1, a.amax[w], b);
-        }
-        b = warp_sum(b);
-        if (lane == 0) {
-            const float target = 2.5f * b;
-            int k = -100;  // floor keeps u_k normal
-            if (target > 0.f)
-                k = max(k, ((__float_as_int(target) >> 23) & 0xff) - 126);  // target < 2^k
-            if (!(target < 1e30f))
-                k = 100;   // non-finite bound: the results will flag the domain error
-            s_sigma = 1.5f * ldexpf(1.0f, k);
-            s_unit = ldexpf(1.0f, k - 23);
-        }
-    }
+    if (threadIdx.x < N)
+        wave_coef(a.V, a.n_waves, threadIdx.x, Vc[threadIdx.x]);
+    if (warp == 1)
+        exact_scale(a.V, a.amax, a.n_waves, lane, &s_sigma, &s_unit);
     __syncthreads();
 
     int flags = 0;
@@ -210,7 +261,6 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         const f2 SG = pk2(sigma, sigma);
         // bits(t) - bits(sigma) summed over the 2N terms of Im S: remove the offset once
         const unsigned im_offset = 2u * (unsigned)N * __float_as_uint(sigma);
-        const f2 Z = 0ull;
         float gs[2 * N];
 #pragma unroll
         for (int c = 0; c < 2 * N; ++c)
@@ -231,35 +281,12 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
             const int comp_rows = 2 * a.n_waves * TE;
             // S of the two events of this thread for the component at Tl
             auto component_sum = [&](const float *Tl, float (&sr)[2], float (&si)[2]) {
-                // Re S = vr ar - vi ai ; Im S = vr ai + vi ar
-                unsigned hR0 = 0, hR1 = 0, hI0 = 0, hI1 = 0;  // high parts (units of u_k)
-                f2 lR = Z, lRm = Z, lI = Z;                    // remainders; lRm is subtracted
-#pragma unroll
-                for (int w = 0; w < N; ++w) {
-                    const f2 ar = lds2(Tl + (2 * w) * TE), ai = lds2(Tl + (2 * w + 1) * TE);
-                    const WaveCoef cf = Vc[w];
-                    unsigned x0, x1;
-                    lR = add2(lR, extract(cf.vr, ar, SG, x0, x1));
-                    hR0 += x0;
-                    hR1 += x1;
-                    lRm = add2(lRm, extract(cf.vi, ai, SG, x0, x1));
-                    hR0 -= x0;
-                    hR1 -= x1;
-                    lI = add2(lI, extract(cf.vr, ai, SG, x0, x1));
-                    hI0 += x0;
-                    hI1 += x1;
-                    lI = add2(lI, extract(cf.vi, ar, SG, x0, x1));
-                    hI0 += x0;
-                    hI1 += x1;
-                    lR = fma2(cf.lr, ar, lR);
-                    lRm = fma2(cf.li, ai, lRm);
-                    lI = fma2(cf.lr, ai, fma2(cf.li, ar, lI));
-                }
-                const f2 hR = pk2((float)(int)hR0 * unit, (float)(int)hR1 * unit);
-                const f2 hI = pk2((float)(int)(hI0 - im_offset) * unit,
-                                  (float)(int)(hI1 - im_offset) * unit);
-                upk2(add2(hR, sub2(lR, lRm)), sr[0], sr[1]);
-                upk2(add2(hI, lI), si[0], si[1]);
+                exact_sum2<N>(
+                    [&](int w, f2 &ar, f2 &ai) {
+                        ar = lds2(Tl + (2 * w) * TE);
+                        ai = lds2(Tl + (2 * w + 1) * TE);
+                    },
+                    Vc, SG, unit, im_offset, sr, si);
             };
             // gs += conj(A) r for the component at Tl, r = S / I of the two events
             auto component_grad = [&](const float *Tl, float r0, float r1, float i0, float i1) {

@@ -83,6 +83,8 @@ struct pwa_ctx {
     float *amax = nullptr;   // [N] max over data events of |Re A_a| + |Im A_a|
     float *mc_amax = nullptr;  // [N] the same over the accepted MC events (projection weights)
     CUtensorMap mc_map;        // over the MC planes, as data_map over the data
+    CUtensorMap hess_map;      // over the data planes, tiles of the tensor-core Hessian
+    bool hess_tc = false;      // hess_map is set: the tensor-core Hessian serves this sample
 
     // per-call buffers
     double *d_io = nullptr;  // [nll K | grad 2NK | status,done | V 2NK]
@@ -209,6 +211,7 @@ void free_sample(pwa_ctx *c)
     dev_free(c->tmax);
     dev_free(c->xbf);
     c->loaded = c->has_norm = false;
+    c->hess_tc = false;
     c->n_lambda = 1;
     ++c->epoch;
 }
@@ -744,7 +747,8 @@ static int fx_alloc(pwa_ctx *c)
 {
     const int N = c->N;
     const size_t nio = 2 * (size_t)N + 1 + 4 * (size_t)N * N;
-    const size_t npart = hess_partials_doubles(N, c->num_sms);
+    const size_t npart = std::max(hess_partials_doubles(N, c->num_sms),
+                                  hess_tc_partials_doubles(N, c->num_sms));
     const size_t bytes = (nio + npart) * sizeof(double);
     if (c->fx_bytes < bytes) {
         dev_free(c->d_fx);
@@ -798,6 +802,17 @@ static int fx_result(pwa_ctx *c, size_t count, double *out, int *flags)
     return PWA_OK;
 }
 
+// The tensor-core kernel where it serves the sample (PWA_HESS_KERNEL=generic
+// selects the CUDA-core kernel), else the CUDA-core one.
+static cudaError_t enqueue_hessian(pwa_ctx *c, const double *dV, double *dpart, int *ds, double *dH)
+{
+    const char *kv = getenv("PWA_HESS_KERNEL");
+    if (c->hess_tc && !(kv && strcmp(kv, "generic") == 0))
+        return launch_hessian_tc(&c->hess_map, c->data, dV, c->amax, dpart, c->num_sms, ds, dH,
+                                 c->stream);
+    return launch_hessian(c->data, dV, dpart, c->num_sms, ds, dH, c->stream);
+}
+
 int pwa_hessian(pwa_ctx *c, const double *V, double *H)
 {
     if (!c)
@@ -814,7 +829,7 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
     int rc = fx_buffer(c, V, &dV, &ds, &dH, &dpart);
     if (rc)
         return rc;
-    CK(c, launch_hessian(c->data, dV, dpart, c->num_sms, ds, dH, c->stream));
+    CK(c, enqueue_hessian(c, dV, dpart, ds, dH));
     const int P = 2 * c->N;
     int flags = 0;
     if ((rc = fx_result(c, (size_t)P * P, H, &flags)))
@@ -840,7 +855,7 @@ int pwa_hessian_async(pwa_ctx *c, const double *d_V, double *d_H)
     int *ds = reinterpret_cast<int *>(c->d_fx + 2 * N);
     double *dpart = c->d_fx + 2 * N + 1 + 4 * (size_t)N * N;
     CK(c, cudaMemsetAsync(ds, 0, sizeof(double), c->stream));
-    CK(c, launch_hessian(c->data, d_V, dpart, c->num_sms, ds, d_H, c->stream));
+    CK(c, enqueue_hessian(c, d_V, dpart, ds, d_H));
     CK(c, launch_or_flags(ds, c->async_status, c->stream));
     return PWA_OK;
 }
@@ -1114,6 +1129,12 @@ static int finish_load(pwa_ctx *c, int rc, int64_t n_data, int64_t n_mc_acc, dou
         if (e == cudaSuccess)
             e = encode_planes_map(&c->mc_map, c->mc.ptr, c->mc.n, c->mc.pitch, 2 * c->N,
                                   amp_box_events(c->N), amp_box_rows(c->N));
+        c->hess_tc = false;
+        if (e == cudaSuccess && hess_tc_available(c->N)) {
+            e = encode_planes_map(&c->hess_map, c->data.ptr, c->data.n, c->data.pitch, 2 * c->N,
+                                  hess_tc_box_events(), 2 * c->N);
+            c->hess_tc = e == cudaSuccess;
+        }
         if (e == cudaSuccess)
             e = cudaMemsetAsync(c->mc_amax, 0, c->N * sizeof(float), c->stream);
         if (e == cudaSuccess)

@@ -504,6 +504,17 @@ cudaError_t launch_table_build_incoh(const Planes &amp, int n_lambda, float *tab
 size_t hess_partials_doubles(int n_waves, int grid);
 cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, int grid, int *status,
                            double *H, cudaStream_t s);
+// k_hess_tc.cu
+// The same Hessian on the tensor cores (n_waves <= 20): map over the data
+// planes with box hess_tc_box_events() x 2 n_waves rows, amax[a] >= max over
+// the data of |Re A_a| + |Im A_a|, partials: hess_tc_partials_doubles(n_waves,
+// grid) doubles. Returns cudaErrorNotSupported for more waves.
+bool hess_tc_available(int n_waves);
+int hess_tc_box_events();
+size_t hess_tc_partials_doubles(int n_waves, int grid);
+cudaError_t launch_hessian_tc(const CUtensorMap *map, const Planes &d, const double *V,
+                              const float *amax, double *partials, int grid, int *status, double *H,
+                              cudaStream_t s);
 // w[j] = |sum_a V_a A_a(j)|^2 / n_gen for the accepted MC events (float, device).
 cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, float *w, int grid,
                               cudaStream_t s);

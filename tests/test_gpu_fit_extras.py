@@ -4,7 +4,10 @@ fractions against the FP64 oracle.
 Hessian (FUMILI's sum_i grad ln I_i grad ln I_i^T): per-event gradients d_i
 of ln I in FP32, so each d_i carries a few
 units of 2^-24 relative to |A|/|S|; the products are summed in FP32 over runs
-of a few hundred events and in float-float / FP64 beyond. Bound: max
+of a few hundred events and in float-float / FP64 beyond. The tensor-core
+kernel (up to 20 waves) splits d_i into three BF16 terms (exact but for the
+last bits of the third) and drops the products below 2^-23 |d_p d_q|; its
+FP32 sums in tensor memory span 128 events. Bound, both kernels: max
 |H - H_oracle| <= 3e-6 max |H_oracle|, and exactly symmetric. Weights: S in
 FP32 by four FMA chains of ceil(N/4) waves joined pairwise, so per component
 |dS| <= (gamma_k + u) sqrt(2) T with k = 2 ceil(N/4) + 2, u = 2^-24 (the +u
@@ -34,6 +37,17 @@ def pwa():
     return pkg
 
 
+@pytest.fixture(params=["tc", "generic"])
+def hess_kernel(request, monkeypatch):
+    """Which Hessian kernel serves the sample: the tensor-core one (the
+    default up to 20 waves; more waves take the other) or the CUDA-core one."""
+    if request.param == "generic":
+        monkeypatch.setenv("PWA_HESS_KERNEL", "generic")
+    else:
+        monkeypatch.delenv("PWA_HESS_KERNEL", raising=False)
+    return request.param
+
+
 def case(N, n_data, n_mc, seed=0):
     waves = synth.waves_linear(N)
     return synth.mixture_workload("h", waves, n_data, n_mc, seed_data=400 + seed,
@@ -57,7 +71,7 @@ def check_hessian(L, wl, V):
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 8, 13, 20, 24, 25, 32, 40, 48])
-def test_hessian_waves_sweep(pwa, N):
+def test_hessian_waves_sweep(pwa, hess_kernel, N):
     wl = case(N, 3000, 4000, seed=N)
     with pwa.Likelihood(N) as L:
         L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
@@ -67,7 +81,7 @@ def test_hessian_waves_sweep(pwa, N):
 
 
 @pytest.mark.parametrize("n_data", [1, 7, 255, 256, 257, 2049, 10007])
-def test_hessian_ragged_event_counts(pwa, n_data):
+def test_hessian_ragged_event_counts(pwa, hess_kernel, n_data):
     wl = case(20, n_data, 700, seed=n_data % 89)
     with pwa.Likelihood(20) as L:
         L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
@@ -75,7 +89,7 @@ def test_hessian_ragged_event_counts(pwa, n_data):
         check_hessian(L, wl, synth.random_V(20, n_data))
 
 
-def test_hessian_any_form_current(pwa):
+def test_hessian_any_form_current(pwa, hess_kernel):
     """The Hessian reads the direct-form store whichever form evaluates the NLL."""
     wl = case(12, 5000, 3000, seed=3)
     V = synth.random_V(12, 5)
@@ -87,7 +101,7 @@ def test_hessian_any_form_current(pwa):
         assert np.array_equal(L.hessian(V), H0)
 
 
-def test_hessian_domain_error(pwa):
+def test_hessian_domain_error(pwa, hess_kernel):
     wl = case(6, 500, 500, seed=9)
     with pwa.Likelihood(6) as L:
         L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
@@ -99,7 +113,7 @@ def test_hessian_domain_error(pwa):
         check_hessian(L, wl, wl.V_true)
 
 
-def test_hessian_homogeneity_at_scale(pwa):
+def test_hessian_homogeneity_at_scale(pwa, hess_kernel):
     """At a million events (the bench workload): H p = -2 grad NLL + 2 grad N
     with the GPU's own gradient (ln I_i is homogeneous of degree 2 in p, so
     H p = 2 sum_i grad ln I_i), the global phase direction (-Im V, Re V) is a
@@ -121,6 +135,19 @@ def test_hessian_homogeneity_at_scale(pwa):
     assert np.linalg.norm(H @ Jp) <= 1e-5 * np.linalg.norm(H, 2) * np.linalg.norm(Jp)
     ev = np.linalg.eigvalsh(H)
     assert ev.min() >= -1e-6 * ev.max() and ev[1] > 0
+
+
+@pytest.mark.slow
+def test_hessian_against_oracle_at_scale(pwa, hess_kernel):
+    """The bench workload (1M data events x 20 waves) against the FP64 oracle,
+    at the fitted scale and at a random V."""
+    N, n = 20, 1_000_000
+    wl = case(N, n, 1000, seed=2)
+    with pwa.Likelihood(N) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        for V in (wl.V_true, synth.random_V(N, 77)):
+            check_hessian(L, wl, V)
 
 
 @pytest.mark.parametrize("N", [1, 3, 8, 20, 33, 48])
@@ -176,7 +203,7 @@ def test_extras_need_state(pwa):
             L.fit_fractions(np.ones(4, complex))
 
 
-def test_hessian_async_matches_host_call(pwa):
+def test_hessian_async_matches_host_call(pwa, hess_kernel):
     import torch
     wl = case(9, 5000, 3000, seed=21)
     V = synth.random_V(9, 22)
