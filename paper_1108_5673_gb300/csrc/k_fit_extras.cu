@@ -296,10 +296,13 @@ __global__ void __launch_bounds__(kHT, 1)
 // H[r][c] over the real parameters (Re V at 0..N-1, Im V at N..2N-1): the sum
 // of the block partials, one warp per entry (lane k adds blocks k, k + 32, ...
 // in order, then a fixed shuffle tree), so the order is the same on every
-// run; zero when a data intensity was not positive.
+// run; zero when a data intensity was not positive. With async_or set, the
+// status bits of the call are also OR-ed into *async_or.
 __global__ void hess_finalize(const double *partials, int grid, int NP, int N, const int *status,
-                              double *H)
+                              double *H, int *async_or)
 {
+    if (async_or && blockIdx.x == 0 && threadIdx.x == 0 && *status)
+        atomicOr(async_or, *status);
     const int B = NP / 2, NB = B * (B + 1) / 2, P = 2 * N;
     const int o = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
     if (o >= P * P)
@@ -374,7 +377,7 @@ __global__ void fit_fractions_kernel(const double *M, const double *V, int N, do
 
 template <int NP>
 cudaError_t hess_np(const Planes &d, const double *V, double *part, int grid, int *status,
-                    double *H, cudaStream_t s)
+                    double *H, int *async_or, cudaStream_t s)
 {
     using C = HessCfg<NP>;
     cudaError_t e = cudaFuncSetAttribute(hess_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -385,7 +388,7 @@ cudaError_t hess_np(const Planes &d, const double *V, double *part, int grid, in
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     const int P = 2 * d.n_waves;
-    hess_finalize<<<(P * P + 7) / 8, 256, 0, s>>>(part, grid, NP, d.n_waves, status, H);
+    hess_finalize<<<(P * P + 7) / 8, 256, 0, s>>>(part, grid, NP, d.n_waves, status, H, async_or);
     return cudaGetLastError();
 }
 
@@ -414,18 +417,18 @@ size_t hess_partials_doubles(int n_waves, int grid)
 }
 
 cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, int grid, int *status,
-                           double *H, cudaStream_t s)
+                           double *H, int *async_or, cudaStream_t s)
 {
     switch (pad_np(d.n_waves)) {
-    case 4: return hess_np<4>(d, V, partials, grid, status, H, s);
-    case 8: return hess_np<8>(d, V, partials, grid, status, H, s);
-    case 12: return hess_np<12>(d, V, partials, grid, status, H, s);
-    case 16: return hess_np<16>(d, V, partials, grid, status, H, s);
-    case 20: return hess_np<20>(d, V, partials, grid, status, H, s);
-    case 24: return hess_np<24>(d, V, partials, grid, status, H, s);
-    case 32: return hess_np<32>(d, V, partials, grid, status, H, s);
-    case 40: return hess_np<40>(d, V, partials, grid, status, H, s);
-    case 48: return hess_np<48>(d, V, partials, grid, status, H, s);
+    case 4: return hess_np<4>(d, V, partials, grid, status, H, async_or, s);
+    case 8: return hess_np<8>(d, V, partials, grid, status, H, async_or, s);
+    case 12: return hess_np<12>(d, V, partials, grid, status, H, async_or, s);
+    case 16: return hess_np<16>(d, V, partials, grid, status, H, async_or, s);
+    case 20: return hess_np<20>(d, V, partials, grid, status, H, async_or, s);
+    case 24: return hess_np<24>(d, V, partials, grid, status, H, async_or, s);
+    case 32: return hess_np<32>(d, V, partials, grid, status, H, async_or, s);
+    case 40: return hess_np<40>(d, V, partials, grid, status, H, async_or, s);
+    case 48: return hess_np<48>(d, V, partials, grid, status, H, async_or, s);
     }
     return cudaErrorInvalidValue;
 }

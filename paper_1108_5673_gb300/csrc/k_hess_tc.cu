@@ -25,6 +25,14 @@
 // sums per CTA; the tensor core's FP32 sums thus span 128 events. A second
 // kernel adds the CTAs' sums in FP64 in a fixed order and assembles H.
 //
+// Buffers: the TMA stages belong to the consumer groups (two per group), so
+// that a stage's successive uses are one group's tiles in order; the J
+// buffers (two) are shared by the groups in tile order, tile j in buffer
+// j % 2. A group may write tile j's J once the products of tile j - 2 are
+// done: a drain warp publishes the count of finished tiles in shared memory
+// (a count, unlike a barrier phase, cannot be mistaken for an older one when
+// a group runs ahead).
+//
 // Padded waves (n_waves < NW) have zero rows in the tile (never written by
 // TMA) and V = 0, hence d = 0. Events past the sample read the TMA fill value
 // zero and get d = 0.
@@ -44,6 +52,7 @@ constexpr int kHFirstCons = kHFirstDrain + kHDrain;
 constexpr int kHThreads = (kHFirstCons + kHGroups * kHGW) * 32;
 constexpr uint32_t kHAccCols = 128;                        // column of the second accumulator
 constexpr uint32_t kHTmemCols = 256;
+constexpr int kHJB = 2;                                    // J buffers (tile j: j % kHJB)
 
 template <int NW>
 struct HessTcCfg {
@@ -55,17 +64,22 @@ struct HessTcCfg {
     // reads from the second atom (A has 128 rows)
     static constexpr uint32_t JBYTES = 2 * KA + (128 - AROWS) * 128;
     static constexpr uint32_t STAGE_BYTES = 2 * NW * kHTE * 4;
-    // TMA stages per consumer group (a stage's successive uses belong to one group)
-    static constexpr int SPG =
-        (kHGroups * (2 * STAGE_BYTES + JBYTES) + 1024 <= 210 * 1024) ? 2 : 1;
+    // TMA stages per consumer group, as many as fit beside the J buffers (up
+    // to three)
+    static constexpr size_t smem_for(int spg)
+    {
+        return (size_t)kHGroups * spg * STAGE_BYTES + (size_t)kHJB * JBYTES + 1024;
+    }
+    static constexpr size_t kMax = 223 * 1024;
+    static constexpr int SPG = smem_for(3) <= kMax ? 3 : smem_for(2) <= kMax ? 2 : 1;
     static constexpr int STAGES = kHGroups * SPG;
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + (size_t)kHGroups * JBYTES + 1024;
+    static constexpr size_t SMEM = smem_for(SPG);
     static_assert(AROWS <= 128, "three BF16 terms of the parameters exceed M = 128");
     static_assert(NMMA % 16 == 0 && NMMA <= 128, "N of the MMA");
     static_assert(R % 8 == 0, "drain in 8-column steps");
     static_assert(KA % 1024 == 0 && STAGE_BYTES % 1024 == 0 && JBYTES % 1024 == 0,
                   "swizzle atoms must stay 1 KB aligned");
-    static_assert(SMEM <= 220 * 1024, "shared memory");
+    static_assert(SMEM <= kMax, "shared memory");
 };
 
 // Byte offset of (row, byte b of the row) in a K-major operand with 128-byte
@@ -114,12 +128,33 @@ __device__ __forceinline__ void store_split(uint32_t atom, int row, uint32_t cb,
     sts32(atom + sw128_off(2 * R + row, cb), bf16x2_rn(x0, x1));
 }
 
-__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x)
+// (hi, lo) += x for two float-float sums at once (TwoSum of Knuth).
+__device__ __forceinline__ void two_sum_acc2(f2 &hi, f2 &lo, f2 x)
 {
-    const float s = hi + x;
-    const float bb = s - hi;
-    lo += (hi - (s - bb)) + (x - bb);
+    const f2 s = add2(hi, x);
+    const f2 bb = sub2(s, hi);
+    lo = add2(lo, add2(sub2(hi, sub2(s, bb)), sub2(x, bb)));
     hi = s;
+}
+
+// Wait until *count >= target (a count written by one thread of the CTA with
+// release semantics); gives up after kWaitLimitNs and returns false.
+__device__ __forceinline__ bool wait_count(const int *count, int target)
+{
+    const uint32_t a = smem_u32(count);
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    if (v >= target)
+        return true;
+    const unsigned long long t0 = global_timer_ns();
+    for (;;) {
+        __nanosleep(64);
+        asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+        if (v >= target)
+            return true;
+        if (global_timer_ns() - t0 > kWaitLimitNs)
+            return false;
+    }
 }
 
 template <int NW>
@@ -134,16 +169,17 @@ __global__ void __launch_bounds__(kHThreads, 1)
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
     float *tiles = reinterpret_cast<float *>(base);
     const uint32_t jbase = smem_u32(base) + (uint32_t)STAGES * C::STAGE_BYTES;
-    __shared__ uint64_t full[STAGES], empty[STAGES], jfull[kHGroups], jempty[kHGroups];
+    __shared__ uint64_t full[STAGES], empty[STAGES], jfull[kHJB];
     __shared__ uint64_t accfull[2], accempty[2], g_done;
     __shared__ WaveCoef Vc[NW];
     __shared__ float s_sigma, s_unit;
     __shared__ uint32_t tmem_base;
     __shared__ int s_flags;
+    __shared__ int s_done;    // tiles whose products are complete
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // tiles of this CTA: blockIdx.x + j gridDim.x, j = 0 .. n_my - 1; tile j
-    // goes to group j % kHGroups, to that group's stage and to its J buffer
+    // goes to group j % kHGroups, to that group's stage and to J buffer j % kHJB
     const int n_my =
         (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t stage_tx = 2u * (uint32_t)n_waves * kHTE * 4u;
@@ -155,10 +191,8 @@ __global__ void __launch_bounds__(kHThreads, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], kHGW);
         }
-        for (int g = 0; g < kHGroups; ++g) {
-            mbar_init(&jfull[g], kHGW);
-            mbar_init(&jempty[g], 1);
-        }
+        for (int b = 0; b < kHJB; ++b)
+            mbar_init(&jfull[b], kHGW);
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull[b], 1);
             mbar_init(&accempty[b], kHDrain);
@@ -166,6 +200,7 @@ __global__ void __launch_bounds__(kHThreads, 1)
         mbar_init(&g_done, 1);
         fence_barrier_init();
         s_flags = 0;
+        s_done = 0;
         for (int j = 0; j < n_first; ++j) {
             mbar_arrive_expect_tx(&full[stage_of(j)], stage_tx);
             tma_load_2d(tiles + (size_t)stage_of(j) * (C::STAGE_BYTES / 4), &map,
@@ -215,8 +250,8 @@ __global__ void __launch_bounds__(kHThreads, 1)
             const uint64_t dK = umma_desc_sw128(0, 16, 1024);
             bool ok = true;
             for (int j = 0; j < n_my; ++j) {
-                const int g = j % kHGroups, ab = j & 1;
-                if (!mbar_wait(&jfull[g], (uint32_t)(j / kHGroups) & 1)) {
+                const int b = j % kHJB, ab = j & 1;
+                if (!mbar_wait(&jfull[b], (uint32_t)(j / kHJB) & 1)) {
                     ok = false;
                     break;
                 }
@@ -226,7 +261,7 @@ __global__ void __launch_bounds__(kHThreads, 1)
                     break;
                 }
                 tc_fence_after();
-                const uint32_t jb = jbase + (uint32_t)g * C::JBYTES;
+                const uint32_t jb = jbase + (uint32_t)b * C::JBYTES;
 #pragma unroll
                 for (int ks = 0; ks < kHTE / 16; ++ks) {
                     // 16 events (32 bytes) per step, four steps per K-atom
@@ -234,7 +269,7 @@ __global__ void __launch_bounds__(kHThreads, 1)
                     umma_bf16(tmem + (uint32_t)ab * kHAccCols, dK + (a >> 4), dK + (a >> 4), idesc,
                               ks > 0 ? 1u : 0u);
                 }
-                umma_commit(&jempty[g]);
+                // on completion tile j's J buffer is free and its accumulator full
                 umma_commit(&accfull[ab]);
             }
             umma_commit(&g_done);
@@ -248,16 +283,20 @@ __global__ void __launch_bounds__(kHThreads, 1)
         // ---- drain: lane quarter q of tensor memory, rows m = 32 q + lane ---
         const int q = warp & 3, m = q * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
-        float hi[R], lo[R];
+        f2 hi[R / 2], lo[R / 2];
 #pragma unroll
-        for (int c = 0; c < R; ++c)
-            hi[c] = lo[c] = 0.f;
+        for (int c = 0; c < R / 2; ++c)
+            hi[c] = lo[c] = 0ull;
         for (int j = 0; j < n_my; ++j) {
             const int ab = j & 1;
             if (!mbar_wait(&accfull[ab], (uint32_t)(j >> 1) & 1)) {
                 flags |= FLAG_TIMEOUT;
                 break;
             }
+            if (warp == kHFirstDrain && lane == 0)  // tile j's J buffer may be rewritten
+                asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_done)),
+                             "r"(j + 1)
+                             : "memory");
             tc_fence_after();
             const uint32_t acc = tmem + lane_addr + (uint32_t)ab * kHAccCols;
 #pragma unroll
@@ -274,17 +313,24 @@ __global__ void __launch_bounds__(kHThreads, 1)
                         mbar_arrive(&accempty[ab]);
                 }
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float x1 = __uint_as_float(v1[i]), x2 = __uint_as_float(v2[i]);
-                    two_sum_acc(hi[c0 + i], lo[c0 + i], m < 2 * R ? x1 + x2 : x1);
+                for (int i = 0; i < 4; ++i) {
+                    f2 x = pk2(__uint_as_float(v1[2 * i]), __uint_as_float(v1[2 * i + 1]));
+                    if (m < 2 * R)
+                        x = add2(x, pk2(__uint_as_float(v2[2 * i]), __uint_as_float(v2[2 * i + 1])));
+                    two_sum_acc2(hi[c0 / 2 + i], lo[c0 / 2 + i], x);
                 }
             }
         }
         if (m < C::AROWS) {
             float2 *out = part + ((size_t)blockIdx.x * C::AROWS + m) * R;
 #pragma unroll
-            for (int c = 0; c < R; ++c)
-                out[c] = make_float2(hi[c], lo[c]);
+            for (int c = 0; c < R / 2; ++c) {
+                float h0, h1, l0, l1;
+                upk2(hi[c], h0, h1);
+                upk2(lo[c], l0, l1);
+                out[2 * c] = make_float2(h0, l0);
+                out[2 * c + 1] = make_float2(h1, l1);
+            }
         }
     } else {
         // ---- consumers: group grp takes tiles j = grp, grp + kHGroups, ... --
@@ -293,8 +339,8 @@ __global__ void __launch_bounds__(kHThreads, 1)
         const float sigma = s_sigma, unit = s_unit;
         const f2 SG = pk2(sigma, sigma);
         const unsigned im_offset = 2u * (unsigned)NW * __float_as_uint(sigma);
-        // this warp's K-atom of the group's J buffer, this lane's 4 bytes of a row
-        const uint32_t atom = jbase + (uint32_t)grp * C::JBYTES + (uint32_t)wg * C::KA;
+        // this warp's K-atom of a J buffer, this lane's 4 bytes of a row
+        const uint32_t atom0 = jbase + (uint32_t)wg * C::KA;
         const uint32_t cb = (uint32_t)lane * 4;
         int bad = 0;
         for (int j = grp; j < n_my; j += kHGroups) {
@@ -337,12 +383,12 @@ __global__ void __launch_bounds__(kHThreads, 1)
                 }
             }
             const f2 rr = pk2(r[0], r[1]), ri = pk2(im[0], im[1]), nrr = pk2(-r[0], -r[1]);
-            // the group's J buffer is free once the MMAs of its previous tile are done
-            const uint32_t ju = (uint32_t)(j / kHGroups);
-            if (ju > 0 && !mbar_wait(&jempty[grp], (ju - 1) & 1)) {
+            // J buffer j % kHJB is free once the products of tile j - kHJB are done
+            if (j >= kHJB && !wait_count(&s_done, j - kHJB + 1)) {
                 flags |= FLAG_TIMEOUT;
                 break;
             }
+            const uint32_t atom = atom0 + (uint32_t)(j % kHJB) * C::JBYTES;
 #pragma unroll
             for (int w = 0; w < NW; ++w) {
                 // 2 conj(A) S / I = (ar rr + ai ri) + i (ar ri - ai rr), rr + i ri = 2 S / I
@@ -353,7 +399,7 @@ __global__ void __launch_bounds__(kHThreads, 1)
             fence_async_smem();
             __syncwarp();
             if (lane == 0)
-                mbar_arrive(&jfull[grp]);
+                mbar_arrive(&jfull[j % kHJB]);
         }
         if (bad)
             flags |= FLAG_DOMAIN;
@@ -370,48 +416,75 @@ __global__ void __launch_bounds__(kHThreads, 1)
     }
 }
 
-// H[r][c] over the real parameters (Re V at 0..N-1, Im V at N..2N-1): one
-// warp per entry, lane k adding the CTAs k, k + 32, ... in order, then a
-// fixed shuffle tree. Entries (r, c) and (c, r) take the same terms (the pair
-// ordered), so H is exactly symmetric; zero when a data intensity was not
-// positive.
+// H[r][c] over the real parameters (Re V at 0..N-1, Im V at N..2N-1), one
+// warp per entry of the upper triangle, written to both (r, c) and (c, r):
+// lane k adds the CTAs k, k + 32, ... in order (all of its loads issued
+// before the adds), then a fixed shuffle tree; zero when a data intensity
+// was not positive. With async_or set, the status bits of the call are also
+// OR-ed into *async_or.
+constexpr int kFinMaxRounds = 8;   // CTAs up to 32 x 8
+
 __global__ void hess_tc_finalize(const float2 *__restrict__ part, int grid, int NW, int N,
-                                 const int *status, double *H)
+                                 const int *status, double *H, int *async_or)
 {
+    if (async_or && blockIdx.x == 0 && threadIdx.x == 0 && *status)
+        atomicOr(async_or, *status);
     const int R = 2 * NW, AR = 3 * R, P = 2 * N;
-    const int o = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
-    if (o >= P * P)
+    int o = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (o >= P * (P + 1) / 2)
         return;
-    int r = o / P, c = o % P;
-    if (r > c) {
-        const int t = r;
-        r = c;
-        c = t;
+    // o -> (r, c), r <= c, row by row
+    int r = 0;
+    while (o >= P - r) {
+        o -= P - r;
+        ++r;
     }
+    const int c = r + o;
     const int jp = r < N ? r : NW + (r - N), jq = c < N ? c : NW + (c - N);
     const size_t stride = (size_t)AR * R;
     const size_t i1 = (size_t)jp * R + jq, i2 = (size_t)(R + jp) * R + jq;
     const size_t i3 = (size_t)(2 * R + jp) * R + jq, i4 = (size_t)(2 * R + jq) * R + jp;
-    double v = 0.0;
-    for (int b = lane; b < grid; b += 32) {
-        const float2 *pb = part + (size_t)b * stride;
-        const float2 x1 = pb[i1], x2 = pb[i2], x3 = pb[i3], x4 = pb[i4];
-        v += (((double)x1.x + x1.y) + ((double)x2.x + x2.y)) +
-             (((double)x3.x + x3.y) + ((double)x4.x + x4.y));
+    float2 x[kFinMaxRounds][4];
+#pragma unroll
+    for (int k = 0; k < kFinMaxRounds; ++k) {
+        const int b = lane + 32 * k;
+        if (b < grid) {
+            const float2 *pb = part + (size_t)b * stride;
+            x[k][0] = pb[i1];
+            x[k][1] = pb[i2];
+            x[k][2] = pb[i3];
+            x[k][3] = pb[i4];
+        } else {
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                x[k][t] = make_float2(0.f, 0.f);
+        }
     }
+    double v = 0.0;
+#pragma unroll
+    for (int k = 0; k < kFinMaxRounds; ++k)
+        v += (((double)x[k][0].x + x[k][0].y) + ((double)x[k][1].x + x[k][1].y)) +
+             (((double)x[k][2].x + x[k][2].y) + ((double)x[k][3].x + x[k][3].y));
     v = warp_sum(v);
-    if (lane == 0)
-        H[o] = (*status & FLAG_DOMAIN) ? 0.0 : v;
+    if (lane == 0) {
+        const double h = (*status & FLAG_DOMAIN) ? 0.0 : v;
+        H[(size_t)r * P + c] = h;
+        H[(size_t)c * P + r] = h;
+    }
 }
 
 template <int NW>
 cudaError_t hess_tc_nw(const CUtensorMap *map, const Planes &d, const double *V, const float *amax,
-                       double *partials, int grid, int *status, double *H, cudaStream_t s)
+                       double *partials, int grid, int *status, double *H, int *async_or,
+                       cudaStream_t s)
 {
     using C = HessTcCfg<NW>;
     const int n_tiles = (int)((d.n + kHTE - 1) / kHTE);
     if (grid > n_tiles)
         grid = n_tiles;
+    if (grid > 32 * kFinMaxRounds)
+        grid = 32 * kFinMaxRounds;
     cudaError_t e = cudaFuncSetAttribute(hess_tc_kernel<NW>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess)
@@ -421,8 +494,9 @@ cudaError_t hess_tc_nw(const CUtensorMap *map, const Planes &d, const double *V,
                                                         part, status);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
-    const int P = 2 * d.n_waves;
-    hess_tc_finalize<<<(P * P + 7) / 8, 256, 0, s>>>(part, grid, NW, d.n_waves, status, H);
+    const int P = 2 * d.n_waves, entries = P * (P + 1) / 2;
+    hess_tc_finalize<<<(entries + 7) / 8, 256, 0, s>>>(part, grid, NW, d.n_waves, status, H,
+                                                       async_or);
     return cudaGetLastError();
 }
 
@@ -448,16 +522,16 @@ size_t hess_tc_partials_doubles(int n_waves, int grid)
 
 cudaError_t launch_hessian_tc(const CUtensorMap *map, const Planes &d, const double *V,
                               const float *amax, double *partials, int grid, int *status, double *H,
-                              cudaStream_t s)
+                              int *async_or, cudaStream_t s)
 {
     if (d.n < 1)
         return cudaErrorInvalidValue;
     switch (hess_tc_nw_of(d.n_waves)) {
-    case 4: return hess_tc_nw<4>(map, d, V, amax, partials, grid, status, H, s);
-    case 8: return hess_tc_nw<8>(map, d, V, amax, partials, grid, status, H, s);
-    case 12: return hess_tc_nw<12>(map, d, V, amax, partials, grid, status, H, s);
-    case 16: return hess_tc_nw<16>(map, d, V, amax, partials, grid, status, H, s);
-    case 20: return hess_tc_nw<20>(map, d, V, amax, partials, grid, status, H, s);
+    case 4: return hess_tc_nw<4>(map, d, V, amax, partials, grid, status, H, async_or, s);
+    case 8: return hess_tc_nw<8>(map, d, V, amax, partials, grid, status, H, async_or, s);
+    case 12: return hess_tc_nw<12>(map, d, V, amax, partials, grid, status, H, async_or, s);
+    case 16: return hess_tc_nw<16>(map, d, V, amax, partials, grid, status, H, async_or, s);
+    case 20: return hess_tc_nw<20>(map, d, V, amax, partials, grid, status, H, async_or, s);
     default: return cudaErrorNotSupported;
     }
 }

@@ -804,13 +804,14 @@ static int fx_result(pwa_ctx *c, size_t count, double *out, int *flags)
 
 // The tensor-core kernel where it serves the sample (PWA_HESS_KERNEL=generic
 // selects the CUDA-core kernel), else the CUDA-core one.
-static cudaError_t enqueue_hessian(pwa_ctx *c, const double *dV, double *dpart, int *ds, double *dH)
+static cudaError_t enqueue_hessian(pwa_ctx *c, const double *dV, double *dpart, int *ds, double *dH,
+                                   int *async_or)
 {
     const char *kv = getenv("PWA_HESS_KERNEL");
     if (c->hess_tc && !(kv && strcmp(kv, "generic") == 0))
         return launch_hessian_tc(&c->hess_map, c->data, dV, c->amax, dpart, c->num_sms, ds, dH,
-                                 c->stream);
-    return launch_hessian(c->data, dV, dpart, c->num_sms, ds, dH, c->stream);
+                                 async_or, c->stream);
+    return launch_hessian(c->data, dV, dpart, c->num_sms, ds, dH, async_or, c->stream);
 }
 
 int pwa_hessian(pwa_ctx *c, const double *V, double *H)
@@ -829,7 +830,7 @@ int pwa_hessian(pwa_ctx *c, const double *V, double *H)
     int rc = fx_buffer(c, V, &dV, &ds, &dH, &dpart);
     if (rc)
         return rc;
-    CK(c, enqueue_hessian(c, dV, dpart, ds, dH));
+    CK(c, enqueue_hessian(c, dV, dpart, ds, dH, nullptr));
     const int P = 2 * c->N;
     int flags = 0;
     if ((rc = fx_result(c, (size_t)P * P, H, &flags)))
@@ -855,8 +856,7 @@ int pwa_hessian_async(pwa_ctx *c, const double *d_V, double *d_H)
     int *ds = reinterpret_cast<int *>(c->d_fx + 2 * N);
     double *dpart = c->d_fx + 2 * N + 1 + 4 * (size_t)N * N;
     CK(c, cudaMemsetAsync(ds, 0, sizeof(double), c->stream));
-    CK(c, enqueue_hessian(c, d_V, dpart, ds, d_H));
-    CK(c, launch_or_flags(ds, c->async_status, c->stream));
+    CK(c, enqueue_hessian(c, d_V, dpart, ds, d_H, c->async_status));
     return PWA_OK;
 }
 

@@ -502,8 +502,9 @@ cudaError_t launch_table_build_incoh(const Planes &amp, int n_lambda, float *tab
 // H [2N][2N] doubles (device); partials: hess_partials_doubles(n_waves, grid)
 // doubles of scratch.
 size_t hess_partials_doubles(int n_waves, int grid);
+// async_or (may be null): the call's status bits are OR-ed into it as well.
 cudaError_t launch_hessian(const Planes &d, const double *V, double *partials, int grid, int *status,
-                           double *H, cudaStream_t s);
+                           double *H, int *async_or, cudaStream_t s);
 // k_hess_tc.cu
 // The same Hessian on the tensor cores (n_waves <= 20): map over the data
 // planes with box hess_tc_box_events() x 2 n_waves rows, amax[a] >= max over
@@ -514,7 +515,7 @@ int hess_tc_box_events();
 size_t hess_tc_partials_doubles(int n_waves, int grid);
 cudaError_t launch_hessian_tc(const CUtensorMap *map, const Planes &d, const double *V,
                               const float *amax, double *partials, int grid, int *status, double *H,
-                              cudaStream_t s);
+                              int *async_or, cudaStream_t s);
 // w[j] = |sum_a V_a A_a(j)|^2 / n_gen for the accepted MC events (float, device).
 cudaError_t launch_mc_weights(const Planes &mc, const double *V, double n_gen, float *w, int grid,
                               cudaStream_t s);
