@@ -161,9 +161,11 @@ template <int NW>
 __global__ void __launch_bounds__(kHThreads, 1)
     hess_tc_kernel(const __grid_constant__ CUtensorMap map, const float *__restrict__ amax,
                    const double *__restrict__ V, int n_waves, int64_t n_events, int n_tiles,
-                   float2 *__restrict__ part, int *status)
+                   double *__restrict__ part, int *status)
 {
     using C = HessTcCfg<NW>;
+    static_assert((size_t)C::AROWS * (C::R + 1) * 8 <= (size_t)kHJB * C::JBYTES,
+                  "the CTA's sums fit in the J buffers");
     constexpr int R = C::R, STAGES = C::STAGES, SPG = C::SPG;
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base = smem_raw + ((1024 - (smem_u32(smem_raw) & 1023)) & 1023);
@@ -321,16 +323,38 @@ __global__ void __launch_bounds__(kHThreads, 1)
                 }
             }
         }
+        // ---- this CTA's share of H -------------------------------------
+        // The rows T[m] go through shared memory (the J buffers are free once
+        // the last tile is drained), then every entry p <= q of H takes its
+        // four terms: T[p][q] + T[R + p][q] + T[2R + p][q] + T[2R + q][p]
+        // (row indices of the J layout), summed in FP64 and stored with the
+        // CTA index innermost.
+        double *Td = reinterpret_cast<double *>(base + (size_t)STAGES * C::STAGE_BYTES);
+        constexpr int RP = R + 1;  // padded row stride: rows in different banks
         if (m < C::AROWS) {
-            float2 *out = part + ((size_t)blockIdx.x * C::AROWS + m) * R;
 #pragma unroll
             for (int c = 0; c < R / 2; ++c) {
                 float h0, h1, l0, l1;
                 upk2(hi[c], h0, h1);
                 upk2(lo[c], l0, l1);
-                out[2 * c] = make_float2(h0, l0);
-                out[2 * c + 1] = make_float2(h1, l1);
+                Td[m * RP + 2 * c] = (double)h0 + (double)l0;
+                Td[m * RP + 2 * c + 1] = (double)h1 + (double)l1;
             }
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(kHDrain * 32) : "memory");
+        const int P = 2 * n_waves, E = P * (P + 1) / 2;
+        for (int e = (warp - kHFirstDrain) * 32 + lane; e < E; e += kHDrain * 32) {
+            int o = e, r = 0;
+            while (o >= P - r) {
+                o -= P - r;
+                ++r;
+            }
+            const int c = r + o;
+            const int jp = r < n_waves ? r : NW + (r - n_waves);
+            const int jq = c < n_waves ? c : NW + (c - n_waves);
+            part[(size_t)e * gridDim.x + blockIdx.x] =
+                (Td[jp * RP + jq] + Td[(R + jp) * RP + jq]) +
+                (Td[(2 * R + jp) * RP + jq] + Td[(2 * R + jq) * RP + jp]);
         }
     } else {
         // ---- consumers: group grp takes tiles j = grp, grp + kHGroups, ... --
@@ -424,48 +448,32 @@ __global__ void __launch_bounds__(kHThreads, 1)
 // OR-ed into *async_or.
 constexpr int kFinMaxRounds = 8;   // CTAs up to 32 x 8
 
-__global__ void hess_tc_finalize(const float2 *__restrict__ part, int grid, int NW, int N,
-                                 const int *status, double *H, int *async_or)
+__global__ void hess_tc_finalize(const double *__restrict__ part, int grid, int N, const int *status,
+                                 double *H, int *async_or)
 {
     if (async_or && blockIdx.x == 0 && threadIdx.x == 0 && *status)
         atomicOr(async_or, *status);
-    const int R = 2 * NW, AR = 3 * R, P = 2 * N;
-    int o = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (o >= P * (P + 1) / 2)
+    const int P = 2 * N;
+    const int e = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (e >= P * (P + 1) / 2)
         return;
-    // o -> (r, c), r <= c, row by row
-    int r = 0;
+    int o = e, r = 0;
     while (o >= P - r) {
         o -= P - r;
         ++r;
     }
     const int c = r + o;
-    const int jp = r < N ? r : NW + (r - N), jq = c < N ? c : NW + (c - N);
-    const size_t stride = (size_t)AR * R;
-    const size_t i1 = (size_t)jp * R + jq, i2 = (size_t)(R + jp) * R + jq;
-    const size_t i3 = (size_t)(2 * R + jp) * R + jq, i4 = (size_t)(2 * R + jq) * R + jp;
-    float2 x[kFinMaxRounds][4];
+    const double *pe = part + (size_t)e * grid;
+    double x[kFinMaxRounds];
 #pragma unroll
     for (int k = 0; k < kFinMaxRounds; ++k) {
         const int b = lane + 32 * k;
-        if (b < grid) {
-            const float2 *pb = part + (size_t)b * stride;
-            x[k][0] = pb[i1];
-            x[k][1] = pb[i2];
-            x[k][2] = pb[i3];
-            x[k][3] = pb[i4];
-        } else {
-#pragma unroll
-            for (int t = 0; t < 4; ++t)
-                x[k][t] = make_float2(0.f, 0.f);
-        }
+        x[k] = b < grid ? pe[b] : 0.0;
     }
     double v = 0.0;
 #pragma unroll
     for (int k = 0; k < kFinMaxRounds; ++k)
-        v += (((double)x[k][0].x + x[k][0].y) + ((double)x[k][1].x + x[k][1].y)) +
-             (((double)x[k][2].x + x[k][2].y) + ((double)x[k][3].x + x[k][3].y));
+        v += x[k];
     v = warp_sum(v);
     if (lane == 0) {
         const double h = (*status & FLAG_DOMAIN) ? 0.0 : v;
@@ -489,13 +497,12 @@ cudaError_t hess_tc_nw(const CUtensorMap *map, const Planes &d, const double *V,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM);
     if (e != cudaSuccess)
         return e;
-    float2 *part = reinterpret_cast<float2 *>(partials);
     hess_tc_kernel<NW><<<grid, kHThreads, C::SMEM, s>>>(*map, amax, V, d.n_waves, d.n, n_tiles,
-                                                        part, status);
+                                                        partials, status);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     const int P = 2 * d.n_waves, entries = P * (P + 1) / 2;
-    hess_tc_finalize<<<(entries + 7) / 8, 256, 0, s>>>(part, grid, NW, d.n_waves, status, H,
+    hess_tc_finalize<<<(entries + 7) / 8, 256, 0, s>>>(partials, grid, d.n_waves, status, H,
                                                        async_or);
     return cudaGetLastError();
 }
@@ -516,8 +523,8 @@ int hess_tc_box_events() { return kHTE; }
 
 size_t hess_tc_partials_doubles(int n_waves, int grid)
 {
-    const int NW = hess_tc_nw_of(n_waves);
-    return NW > 0 ? (size_t)grid * (6 * NW) * (2 * NW) : 0;
+    const int P = 2 * n_waves;
+    return hess_tc_nw_of(n_waves) > 0 ? (size_t)grid * (P * (P + 1) / 2) : 0;
 }
 
 cudaError_t launch_hessian_tc(const CUtensorMap *map, const Planes &d, const double *V,
