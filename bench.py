@@ -61,7 +61,7 @@ TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
-           "hessian": None,       # the tensor-core kernel is not yet captured
+           "hessian": 160.091648e6 + 3.346944e6,
            "weights": None,
            "incoh": 320.162304e6 + 3.733248e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample

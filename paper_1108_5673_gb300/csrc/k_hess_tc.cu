@@ -342,14 +342,12 @@ __global__ void __launch_bounds__(kHThreads, 1)
             }
         }
         asm volatile("bar.sync 1, %0;" ::"r"(kHDrain * 32) : "memory");
-        const int P = 2 * n_waves, E = P * (P + 1) / 2;
-        for (int e = (warp - kHFirstDrain) * 32 + lane; e < E; e += kHDrain * 32) {
-            int o = e, r = 0;
-            while (o >= P - r) {
-                o -= P - r;
-                ++r;
-            }
-            const int c = r + o;
+        const int P = 2 * n_waves;
+        for (int rc = (warp - kHFirstDrain) * 32 + lane; rc < P * P; rc += kHDrain * 32) {
+            const int r = rc / P, c = rc % P;
+            if (r > c)
+                continue;
+            const int e = r * P - r * (r - 1) / 2 + (c - r);  // row-major upper triangle
             const int jp = r < n_waves ? r : NW + (r - n_waves);
             const int jq = c < n_waves ? c : NW + (c - n_waves);
             part[(size_t)e * gridDim.x + blockIdx.x] =
