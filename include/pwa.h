@@ -264,7 +264,12 @@ int pwa_nll_grad_res_async(pwa_ctx *ctx, const double *d_V, const double *d_mass
  *   V: host [n_waves] complex128;  H: host [2 n_waves][2 n_waves] double,
  *   row-major, symmetric.
  * Uses the context's direct-form store (the data planes loaded by
- * pwa_load_events); any form may be current. Returns PWA_EDOMAIN (H all
+ * pwa_load_events); any form may be current. Up to 20 waves the sum runs on
+ * the tensor cores (each d_i split into three BF16 terms, FP32 sums over
+ * 128-event tiles, float-float and FP64 beyond), otherwise (or with the
+ * environment variable PWA_HESS_KERNEL=generic) on the FP32 pipe; either way
+ * max |H - H_exact| <= 3e-6 max |H_exact|, and the result of a given sample
+ * and V is the same on every call. Returns PWA_EDOMAIN (H all
  * zero) if a data intensity was not positive and finite; PWA_ESTATE before
  * pwa_load_events; PWA_EINVAL for null pointers; PWA_ENOTSUP for an
  * incoherent sample; PWA_ENOMEM, PWA_ECUDA. */
