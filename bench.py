@@ -56,13 +56,13 @@ N_WAVES, N_DATA, N_MC = 20, 1_000_000, 5_000_000
 WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M accepted MC, K=1 per evaluation"
 # DRAM bytes (read + write) per step of the timed kernel from one ncu
 # capture of the current kernel, or None where there is none.
-TRAFFIC = {"direct": 160.138240e6 + 3.847168e6,
+TRAFFIC = {"direct": 160.139008e6 + 3.103744e6,
            "table": 1600.119e6 + 3.221760e6,
            "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.091648e6 + 3.346944e6,
-           "weights": None,
+           "weights": 800.148224e6 + 21.018112e6,
            "incoh": 320.162304e6 + 3.733248e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
            "ampgen": None}
