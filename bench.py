@@ -65,7 +65,7 @@ TRAFFIC = {"direct": 160.139008e6 + 3.103744e6,
            "weights": 800.148224e6 + 21.018112e6,
            "incoh": 320.162304e6 + 3.733248e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
-           "ampgen": None}
+           "ampgen": 278.9e6 + 962.9e6}   # FP64-bound; DRAM bytes for reference
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
            "models": "batched_kernel<F, 2> (all models)", "hessian": "hess_tc_kernel<20>",
