@@ -56,6 +56,25 @@ def test_twenty_waves(pwa, where):
     assert check_rounding(A, ev, waves) >= 0.999
 
 
+@pytest.mark.slow
+def test_amplitudes_at_scale(pwa):
+    """The bench configuration (5M events x 20 waves, kinematics and
+    amplitudes on the device): a random sample of 200k events against the
+    oracle, one by one."""
+    import torch
+    waves = synth.waves_linear(20)
+    ev, _ = synth.mc_sample(5_000_000)
+    n = ev["m"].shape[0]
+    kin = torch.from_numpy(np.stack([ev["m"], ev["costh"], ev["phi"]], 1)).cuda()
+    out = torch.empty(n, 20, dtype=torch.complex64, device="cuda")
+    with pwa.Likelihood(20) as L:
+        L.amplitudes(waves, kin, out)
+    idx = np.sort(np.random.Generator(np.random.Philox(5)).choice(n, 200_000, replace=False))
+    A = out[torch.from_numpy(idx).cuda()].cpu().numpy()
+    sample = {k: np.ascontiguousarray(ev[k][idx]) for k in ("m", "costh", "phi")}
+    assert check_rounding(A, sample, waves) >= 0.999
+
+
 def test_all_l_and_m_up_to_sixteen(pwa):
     waves = [(0.9 + 0.1 * l, 0.02 + 0.03 * ((l + m) % 5), l, m)
              for l in (0, 1, 3, 7, 12, 16) for m in sorted({-l, -(l // 2), 0, l // 2, l})]

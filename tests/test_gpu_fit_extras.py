@@ -181,6 +181,40 @@ def test_mc_weights(pwa, monkeypatch, N, where, kernel):
     assert abs(w.astype(np.float64).sum() - nv) <= 1e-6 * nv
 
 
+@pytest.fixture(scope="module")
+def paper_sample():
+    """The bench workload: 1M data and 5M accepted MC events x 20 waves."""
+    return synth.paper_scale()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("kernel", ["tma", "generic"])
+def test_mc_weights_at_scale(pwa, monkeypatch, paper_sample, kernel):
+    """The bench configuration (5M accepted MC x 20 waves, weights into a
+    device buffer): every weight within the bound of test_mc_weights, and
+    their sum equal to V^H M V."""
+    import torch
+    if kernel == "generic":
+        monkeypatch.setenv("PWA_WEIGHTS_KERNEL", "generic")
+    else:
+        monkeypatch.delenv("PWA_WEIGHTS_KERNEL", raising=False)
+    wl = paper_sample
+    V = synth.start_points(20, 1)[0]
+    with pwa.Likelihood(20) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        M = L.build_norm()
+        out = torch.empty(wl.A_mc.shape[0], dtype=torch.float32, device="cuda:0")
+        w = L.mc_weights(V, out).cpu().numpy()
+    wo = oracle.mc_weights(wl.A_mc, V, wl.n_gen)
+    k = 2 * math.ceil(20 / 4) + 2
+    for lo in range(0, wl.A_mc.shape[0], 1 << 20):
+        A = wl.A_mc[lo:lo + (1 << 20)].astype(np.complex128)
+        T2 = (np.abs(A) * np.abs(V)[None, :]).sum(axis=1) ** 2 / wl.n_gen
+        assert np.all(np.abs(w[lo:lo + len(A)] - wo[lo:lo + len(A)]) <= (4 * k + 10) * 2.0 ** -24 * T2)
+    nv = oracle.norm_term(M, V)[0]
+    assert abs(w.astype(np.float64).sum() - nv) <= 1e-6 * nv
+
+
 @pytest.mark.parametrize("N", [1, 2, 7, 20, 48])
 def test_fit_fractions(pwa, N):
     wl = case(N, 100, 4000, seed=N + 80)
