@@ -170,6 +170,15 @@ def test_multistart_scale(pwa, p):
 
 
 @pytest.mark.slow
+def test_bench_configuration(pwa):
+    """The bench configuration: 4M events x 32 waves, 256 parameter sets in
+    one call (BFP16); five of the sets against the oracle."""
+    wl = synth.multistart_scale(n_mc_acc=1_000_000)
+    Vs = synth.start_points(32, 256) * 2.0
+    check(pwa, wl, Vs, pwa.PWA_PREC_BFP16, idx=[0, 1, 127, 128, 255])
+
+
+@pytest.mark.slow
 def test_paper_scale_one_million(pwa):
     """1M events, 20 waves (the headline sample), 64 parameter sets."""
     wl = synth.paper_scale(n_mc_acc=300_000)
