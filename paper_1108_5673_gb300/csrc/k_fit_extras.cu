@@ -13,7 +13,9 @@
 // triangle of J^T J is cut into 4x4 blocks; each thread owns one to three
 // (block, event group) items and accumulates 16 products per pair of float4
 // loads. FP32 within a run of tiles, float-float across runs, FP64 across
-// event groups and blocks, summed in a fixed order.
+// event groups and blocks, summed in a fixed order. This kernel serves
+// samples of more than 20 waves (and PWA_HESS_KERNEL=generic); up to 20
+// waves the tensor-core kernel of k_hess_tc.cu forms the same sum.
 //
 // Projection weights: w_j = I(Omega_j) / N_gen per accepted MC event (their
 // sum is V^H M V), and fit fractions F_ab = Re(conj(V_a) M_ab V_b) / V^H M V.
