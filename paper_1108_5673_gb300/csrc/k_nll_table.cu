@@ -38,7 +38,6 @@ struct TabCfg {
     static constexpr int EPL = TE / 32;                      // events per lane
     static constexpr int W = (P <= 256) ? 8 : 16;            // consumer warps
     static constexpr int RPW = (P + W - 1) / W;              // planes per warp
-    static constexpr int BOXES = (P + kBoxRows - 1) / kBoxRows;
     static constexpr uint32_t STAGE_BYTES = P * TE * 4;
     static constexpr int STAGES_RAW = (190 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW < 2 ? 2 : (STAGES_RAW > 6 ? 6 : STAGES_RAW);
