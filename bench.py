@@ -43,6 +43,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -564,8 +565,9 @@ def main():
     torch.cuda.synchronize()
     assert job.sync() in (pwa.PWA_OK,), "warm-up status"
 
-    clock_path = os.path.join(ROOT, "gpurun_out" if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                              else ".", "bench_clocks_rank%d.csv" % rank)
+    # raw nvidia-smi samples of the timed region (summarised into the line)
+    clock_path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
+                              "bench_clocks_rank%d.csv" % rank)
     sampler = start_clock_sampler(clock_path) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
