@@ -61,9 +61,14 @@ extern "C" {
 /* ---- amplitude encoding of the tensor-core form (pwa_config.precision) --- */
 #define PWA_PREC_DEFAULT 0 /* PWA_PREC_BFP16 */
 #define PWA_PREC_BFP16 1   /* A = 2^(E-8) (x0 + x1/256), |x0| <= 256, |x1| <= 128 integers:
-                              16 bits below the event's largest component */
+                              16 bits below the event's largest component. Against
+                              FP64 amplitudes (1M events x 20 waves) this moves the
+                              NLL by ~0.04 and a fitted V by < 0.01 of its error */
 #define PWA_PREC_BFP8 2    /* A = 2^(E-8) x0: 8 bits below the event's largest
-                              component; about half the tensor-core work */
+                              component; about half the tensor-core work. A coarser
+                              sample: the NLL moves by ~500 and a fitted V by tens of
+                              its errors at the same size, so it ranks starting
+                              points; a final fit takes an FP32 form */
 
 /* ---- amplitude element types ------------------------------------------- */
 #define PWA_C64 1  /* float pairs: used as given */
