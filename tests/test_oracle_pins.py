@@ -475,6 +475,14 @@ def test_mc_weights_and_fit_fractions():
     assert abs(F.sum() - 1.0) <= 1e-12                    # fractions + interference = 1
     for a in range(5):
         assert abs(F[a, a] - abs(V[a]) ** 2 * Mm[a, a].real / nv) <= 1e-13
+    # every entry from the events themselves (no M): the MC average of the
+    # interference of waves a and b, Re(conj(V_a A_a) V_b A_b) / N_gen
+    # (F is symmetric: F_ab + F_ba is the pair's interference fraction)
+    VA = Am * V[None, :]
+    for a in range(5):
+        for b in range(5):
+            Fb = np.sum((np.conj(VA[:, a]) * VA[:, b]).real) / n_gen / nv
+            assert abs(F[a, b] - Fb) <= 1e-12, (a, b)
 
 
 # ---- incoherent sums over unobserved components --------------------------------
