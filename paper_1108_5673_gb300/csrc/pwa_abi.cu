@@ -1382,6 +1382,11 @@ int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, i
                      !(kv && strcmp(kv, "generic") == 0);
     if (!rc && cudaMemsetAsync(c->amax, 0, N * sizeof(float), c->stream) != cudaSuccess)
         rc = fail(c, PWA_ECUDA, "memset");
+    // the MC planes hold n_mc_acc L pseudo-events of N waves: their maxima
+    // scale the tensor-core build of M
+    if (!rc && (cudaMemsetAsync(c->mc_amax, 0, N * sizeof(float), c->stream) != cudaSuccess ||
+                launch_amp_max(c->mc, c->mc_amax, c->stream) != cudaSuccess))
+        rc = fail(c, PWA_ECUDA, "MC amplitude maxima");
     if (!rc && tma) {
         float *dmax = nullptr;
         rc = dev_alloc(c, (void **)&dmax, (size_t)L * N * sizeof(float), "component maxima");
@@ -1439,17 +1444,58 @@ int pwa_build_norm(pwa_ctx *c, double *M_out)
     if (!c->loaded)
         return fail(c, PWA_ESTATE, "pwa_load_events must come first");
     DeviceGuard g(c->device);
-    double *scratch = nullptr;
-    int rc = dev_alloc(c, (void **)&scratch, norm_scratch_bytes(c->N, c->num_sms), "norm scratch");
-    if (rc)
-        return rc;
-    cudaError_t e = launch_build_norm(c->mc, c->n_gen, c->M, scratch, c->num_sms, c->stream);
-    if (e == cudaSuccess)
-        e = cudaStreamSynchronize(c->stream);
-    cudaFree(scratch);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(c, PWA_ECUDA, "build_norm: %s", cudaGetErrorString(e));
+    // The tensor-core kernel serves up to 20 waves when every wave's scale is
+    // in its range; the FP64 kernel everything else (or PWA_NORM_KERNEL=fp64).
+    bool tc = norm_tc_available(c->N);
+    if (const char *v = getenv("PWA_NORM_KERNEL"))
+        if (strcmp(v, "fp64") == 0)
+            tc = false;
+    if (tc) {
+        std::vector<float> am(c->N);
+        CK(c, cudaMemcpy(am.data(), c->mc_amax, c->N * sizeof(float), cudaMemcpyDeviceToHost));
+        for (float x : am)
+            tc = tc && norm_tc_scale_ok(x);
+    }
+    if (tc) {
+        CUtensorMap map;
+        CK(c, encode_planes_map(&map, c->mc.ptr, c->mc.n, c->mc.pitch, 2 * c->N,
+                                norm_tc_box_events(), 2 * c->N));
+        const int grid = c->num_sms;
+        const size_t nd = norm_tc_partials_doubles(c->N, grid);
+        double *scratch = nullptr;
+        int rc = dev_alloc(c, (void **)&scratch, (nd + 1) * sizeof(double), "norm scratch");
+        if (rc)
+            return rc;
+        int *dstat = reinterpret_cast<int *>(scratch + nd);
+        int flags = 0;
+        cudaError_t e = cudaMemsetAsync(dstat, 0, sizeof(int), c->stream);
+        if (e == cudaSuccess)
+            e = launch_build_norm_tc(&map, c->mc, c->mc_amax, c->n_gen, scratch, grid, dstat, c->M,
+                                     c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&flags, dstat, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        cudaFree(scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PWA_ECUDA, "build_norm: %s", cudaGetErrorString(e));
+        }
+        if (flags & FLAG_TIMEOUT)
+            return fail(c, PWA_ETIMEOUT, "build_norm: a device-side wait timed out");
+    } else {
+        double *scratch = nullptr;
+        int rc = dev_alloc(c, (void **)&scratch, norm_scratch_bytes(c->N, c->num_sms), "norm scratch");
+        if (rc)
+            return rc;
+        cudaError_t e = launch_build_norm(c->mc, c->n_gen, c->M, scratch, c->num_sms, c->stream);
+        if (e == cudaSuccess)
+            e = cudaStreamSynchronize(c->stream);
+        cudaFree(scratch);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PWA_ECUDA, "build_norm: %s", cudaGetErrorString(e));
+        }
     }
     if (M_out)
         CK(c, cudaMemcpy(M_out, c->M, (size_t)2 * c->N * c->N * sizeof(double),

@@ -545,6 +545,19 @@ cudaError_t launch_nll_table(int64_t n_events, int n_waves, const CUtensorMap *m
 size_t norm_scratch_bytes(int n_waves, int num_sms);
 cudaError_t launch_build_norm(const Planes &mc, double n_gen, double *M, double *scratch,
                               int num_sms, cudaStream_t s);
+// k_norm_tc.cu: the same M on the tensor cores (n_waves <= 20) from exact
+// fixed-point digits of the amplitudes. map: over the MC planes with a box of
+// norm_tc_box_events() events x 2 n_waves rows; amax[a] = max over the MC of
+// |Re A_a| + |Im A_a| (each must pass norm_tc_scale_ok); partials:
+// norm_tc_partials_doubles(n_waves, grid) doubles; a timeout is OR-ed into
+// *status (zero on entry) and M is then NaN.
+bool norm_tc_available(int n_waves);
+int norm_tc_box_events();
+bool norm_tc_scale_ok(float amax);
+size_t norm_tc_partials_doubles(int n_waves, int grid);
+cudaError_t launch_build_norm_tc(const CUtensorMap *map, const Planes &mc, const float *amax,
+                                 double n_gen, double *partials, int grid, int *status, double *M,
+                                 cudaStream_t s);
 
 // k_nll_amp.cu
 int amp_grid(int n_waves, int num_sms);

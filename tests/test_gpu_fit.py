@@ -92,7 +92,10 @@ def test_fumili_fit_matches_lbfgs(pwa):
         Vl, fl, _ = fit.fit_lbfgs(L, V0, grad_tol=1e-6, change_tol=1e-13)
         Vf, ff, info = fit.fit_fumili(L, V0, grad_tol=1e-6)
     assert info["iterations"] <= 12, info
-    assert abs(ff - fl) < 1e-5, (ff, fl)
+    # both minima agree within the FP32 evaluation noise of the NLL: per-event
+    # roundings of ~1e-7 in ln I add up as sqrt(n), the GPU tolerance
+    # 1e-3 sqrt(n / 1e6) against the oracle (1e-4 at these 10k events)
+    assert abs(ff - fl) < 1e-3 * math.sqrt(len(A) / 1e6), (ff, fl)
     assert np.max(np.abs(fit.phase_fixed(Vf) - fit.phase_fixed(Vl))) < 1e-4 * np.abs(Vl).max()
 
 
