@@ -40,9 +40,10 @@ struct AmpCfg {
     static constexpr bool FITS = SMEM <= 210 * 1024;
 };
 
-// Layout of the per-launch scratch (EvalArgs::partials) for a grid of G CTAs:
-//   pi  [G][2] int64   per-CTA sum of round(2^23 ln f) and of exponents
-//   pf  [G][2N+1]      per-CTA float-float sums: ln-f remainders, gradient
+// Layout of the per-launch scratch (EvalArgs::partials) for a grid of G CTAs
+// (component-major, so that the final sum reads each component coalesced):
+//   pi  [2][G] int64   per-CTA sum of round(2^23 ln f) and of exponents
+//   pf  [2N+1][G]      per-CTA float-float sums: ln-f remainders, gradient
 //   mv  [2 kMaxWaves + 1]  M V and then V^H M V (double), by CTA 0's helper warp
 //   flags              status bits of this launch (reset by the last CTA)
 struct AmpScratch {
@@ -127,6 +128,35 @@ __device__ __forceinline__ void exact_sum2(AmpOf amp, const WaveCoef *Vc, f2 SG,
     upk2(add2(hI, lI), si[0], si[1]);
 }
 
+// Sums of P values over the 32 lanes of a warp, every lane ending with the
+// total of value `lane` of each block of 32 (x[32 b + lane]); the rest of x
+// is left undefined. At each of the five levels a lane keeps one half of its
+// remaining values, sends the other half to its partner and adds what it
+// receives: 31 shuffles per 32 values instead of 5 per value.
+template <int P>
+__device__ __forceinline__ void warp_transpose_sum(float (&x)[P], int lane)
+{
+    constexpr int B = (P + 31) / 32;
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        float v[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i)
+            v[i] = (32 * b + i < P) ? x[32 * b + i] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const bool upper = (lane & o) != 0;
+#pragma unroll
+            for (int i = 0; i < o; ++i) {
+                const float send = upper ? v[i] : v[i + o];
+                const float keep = upper ? v[i + o] : v[i];
+                v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+            }
+        }
+        x[32 * b] = v[0];
+    }
+}
+
 // V as float pairs Vhi + Vlo, duplicated for packed use; waves w >= n_waves
 // (padding) get V = 0. One thread per wave.
 __device__ __forceinline__ void wave_coef(const double *V, int n_waves, int w, WaveCoef &c)
@@ -184,6 +214,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     uint64_t *empty = full + STAGES;
 
     __shared__ WaveCoef Vc[N];
+    __shared__ double sV[2 * N];   // the helper warp's copy of V
     __shared__ float s_sigma, s_unit;
     __shared__ long long red_i[CW][2];
     __shared__ float red_f[CW][NF];
@@ -219,6 +250,8 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     for (int s = 0; s < STAGES; ++s)
         for (int i = 2 * a.n_waves * L * TE + threadIdx.x; i < ROWS * TE; i += blockDim.x)
             tiles[(size_t)s * ROWS * TE + i] = 0.f;
+    // V may sit in host memory: these reads and those of the helper warp are
+    // its only ones (one round trip each, concurrent with the first tiles)
     if (threadIdx.x < N)
         wave_coef(a.V, a.n_waves, threadIdx.x, Vc[threadIdx.x]);
     if (warp == 1)
@@ -395,34 +428,39 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         // ---- per-warp reduction of this thread's sums (fixed order) ------
         const long long li = warp_sum(l_int);
         const long long ei = warp_sum((long long)eacc);
-        const float lf = warp_sum(l_frac);
         if (lane == 0) {
             red_i[cw][0] = li;
             red_i[cw][1] = ei;
-            red_f[cw][0] = lf;
         }
+        float fv[NF];
+        fv[0] = l_frac;
 #pragma unroll
-        for (int c = 0; c < 2 * N; ++c) {
-            const float v = warp_sum(gs[c]);
-            if (lane == 0)
-                red_f[cw][1 + c] = v;
-        }
+        for (int c = 0; c < 2 * N; ++c)
+            fv[1 + c] = gs[c];
+        warp_transpose_sum<NF>(fv, lane);
+#pragma unroll
+        for (int b = 0; b < (NF + 31) / 32; ++b)
+            if (32 * b + lane < NF)
+                red_f[cw][32 * b + lane] = fv[32 * b];
     } else if (warp == CW + 1 && blockIdx.x == 0 && !WEIGHTS) {
         // ---- helper warp of CTA 0: M V and V^H M V in FP64 -------------
         // One row per lane; this overlaps the streaming of the data.
         const int Nw = a.n_waves;
+        for (int i = lane; i < 2 * Nw; i += 32)
+            sV[i] = a.V[i];
+        __syncwarp();
         double nv = 0.0;
         for (int row = lane; row < Nw; row += 32) {
             double re = 0.0, im = 0.0;
             for (int b = 0; b < Nw; ++b) {
                 const double mr = a.M[2 * (row * Nw + b)], mi = a.M[2 * (row * Nw + b) + 1];
-                const double vr = a.V[2 * b], vi = a.V[2 * b + 1];
+                const double vr = sV[2 * b], vi = sV[2 * b + 1];
                 re = fma(mr, vr, fma(-mi, vi, re));
                 im = fma(mr, vi, fma(mi, vr, im));
             }
             sc.mv[2 * row] = re;
             sc.mv[2 * row + 1] = im;
-            nv = fma(a.V[2 * row], re, fma(a.V[2 * row + 1], im, nv));  // Re(conj(V) (M V))
+            nv = fma(sV[2 * row], re, fma(sV[2 * row + 1], im, nv));  // Re(conj(V) (M V))
         }
         nv = warp_sum(nv);
         if (lane == 0)
@@ -442,13 +480,13 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         long long v = 0;
         for (int w = 0; w < CW; ++w)
             v += red_i[w][threadIdx.x];
-        sc.pi[2 * blockIdx.x + threadIdx.x] = v;
+        sc.pi[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = v;
     }
     for (int c = threadIdx.x; c < NF; c += blockDim.x) {
         dfloat v = {0.f, 0.f};
         for (int w = 0; w < CW; ++w)
             v = df_add(v, dfloat{red_f[w][c], 0.f});
-        sc.pf[(size_t)blockIdx.x * NF + c] = make_float2(v.hi, v.lo);
+        sc.pf[(size_t)c * gridDim.x + blockIdx.x] = make_float2(v.hi, v.lo);
     }
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -463,74 +501,92 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         return;
 
     // ---- last CTA: deterministic final sum + normalisation term ---------
-    // Each of the 2N+1 float components and the 2 integer ones is split into
-    // SUB interleaved sub-sums over the CTAs, one per thread, with all of a
-    // thread's loads issued before its adds (one L2 round trip); the
-    // sub-sums are then combined in a fixed order. (The partials are read
-    // with L2 loads after the ticket, so no further fence is needed.)
+    // One warp per component (2N+1 float-float ones, then the 2 integer
+    // ones): lane l adds CTAs l, l + 32, ... (coalesced loads, all issued
+    // before the adds, with M V and the launch's flags: one L2 round trip),
+    // then a fixed shuffle tree. (The partials are read with L2 loads after
+    // the ticket, so no further fence is needed.)
     const int Nw = a.n_waves;
     const int G_ = gridDim.x;
-    constexpr int SUB = 7, MAXB = 24;
-    dfloat *sub_f = reinterpret_cast<dfloat *>(tiles);                  // [NF][SUB]
-    long long *sub_i = reinterpret_cast<long long *>(sub_f + NF * SUB);  // [2][SUB]
-    double *smv = reinterpret_cast<double *>(sub_i + 2 * SUB);          // [2N] M V
-    for (int item = threadIdx.x; item < (NF + 2) * SUB; item += blockDim.x) {
-        const int c = item / SUB, k = item % SUB;
-        if (c < NF) {
-            dfloat v = {0.f, 0.f};
-            for (int b0 = k; b0 < G_; b0 += SUB * MAXB) {
-                float2 r[MAXB];
+    constexpr int NWARPS = C::THREADS / 32;
+    constexpr int CPW = (NF + 2 + NWARPS - 1) / NWARPS;  // components per warp
+    constexpr int QB = 5;                                 // loads per lane and component in flight
+    dfloat *tot_f = reinterpret_cast<dfloat *>(tiles);                  // [NF]
+    long long *tot_i = reinterpret_cast<long long *>(tot_f + NF);       // [2]
+    double *smv = reinterpret_cast<double *>(tot_i + 2);                // [2N] M V, V^H M V
+    const double mv_i = threadIdx.x < 2 * Nw ? __ldcg(&sc.mv[threadIdx.x])
+                                             : threadIdx.x == 2 * Nw ? __ldcg(&sc.mv[2 * kMaxWaves])
+                                                                      : 0.0;
+    const int wf = __ldcg(work_flags);
+    {
+        // a partial is 8 bytes either way: a float pair (hi in the low word)
+        // or an integer
+        const unsigned long long *pf64 = reinterpret_cast<const unsigned long long *>(sc.pf);
+        const unsigned long long *pi64 = reinterpret_cast<const unsigned long long *>(sc.pi);
+        dfloat acc[CPW];
+        long long iacc[CPW];
 #pragma unroll
-                for (int q = 0; q < MAXB; ++q) {
-                    const int b = b0 + q * SUB;
-                    r[q] = (b < G_) ? __ldcg(&sc.pf[(size_t)b * NF + c]) : make_float2(0.f, 0.f);
+        for (int k = 0; k < CPW; ++k) {
+            acc[k] = dfloat{0.f, 0.f};
+            iacc[k] = 0;
+        }
+        for (int b0 = 0; b0 < G_; b0 += 32 * QB) {
+            unsigned long long r[CPW][QB];
+#pragma unroll
+            for (int k = 0; k < CPW; ++k) {
+                const int comp = warp + k * NWARPS;
+                const unsigned long long *src =
+                    comp < NF ? pf64 + (size_t)comp * G_ : pi64 + (size_t)(comp - NF) * G_;
+#pragma unroll
+                for (int q = 0; q < QB; ++q) {
+                    const int b = b0 + lane + 32 * q;
+                    r[k][q] = (b < G_ && comp < NF + 2) ? __ldcg(src + b) : 0ull;
                 }
-#pragma unroll
-                for (int q = 0; q < MAXB; ++q)
-                    v = df_add(v, dfloat{r[q].x, r[q].y});
             }
-            sub_f[c * SUB + k] = v;
-        } else {
-            const int ci = c - NF;
-            long long v = 0;
-            for (int b0 = k; b0 < G_; b0 += SUB * MAXB) {
-                long long r[MAXB];
 #pragma unroll
-                for (int q = 0; q < MAXB; ++q) {
-                    const int b = b0 + q * SUB;
-                    r[q] = (b < G_) ? __ldcg(&sc.pi[2 * b + ci]) : 0;
+            for (int k = 0; k < CPW; ++k) {
+                if (warp + k * NWARPS < NF) {
+#pragma unroll
+                    for (int q = 0; q < QB; ++q)
+                        acc[k] = df_add(acc[k], dfloat{__uint_as_float((unsigned)r[k][q]),
+                                                       __uint_as_float((unsigned)(r[k][q] >> 32))});
+                } else {
+#pragma unroll
+                    for (int q = 0; q < QB; ++q)
+                        iacc[k] += (long long)r[k][q];
                 }
-#pragma unroll
-                for (int q = 0; q < MAXB; ++q)
-                    v += r[q];
             }
-            sub_i[ci * SUB + k] = v;
+        }
+#pragma unroll
+        for (int k = 0; k < CPW; ++k) {
+            const int comp = warp + k * NWARPS;
+            if (comp < NF) {
+                const dfloat v = warp_sum(acc[k]);
+                if (lane == 0)
+                    tot_f[comp] = v;
+            } else if (comp < NF + 2) {
+                const long long v = warp_sum(iacc[k]);
+                if (lane == 0)
+                    tot_i[comp - NF] = v;
+            }
         }
     }
-    for (int i = threadIdx.x; i < 2 * Nw; i += blockDim.x) {
-        smv[i] = __ldcg(&sc.mv[i]);
-    }
+    if (threadIdx.x <= 2 * Nw)
+        smv[threadIdx.x] = mv_i;
     __syncthreads();
-    const int wf = __ldcg(work_flags);
     const bool invalid = (wf & (FLAG_DOMAIN | FLAG_TIMEOUT)) != 0;
     for (int c = threadIdx.x; c < 2 * Nw + 1; c += blockDim.x) {  // padded waves excluded
-        dfloat v = sub_f[c * SUB];
-        for (int k = 1; k < SUB; ++k)
-            v = df_add(v, sub_f[c * SUB + k]);
+        const dfloat v = tot_f[c];
         if (c > 0) {
             // gradient: - sum_i conj(A) S / I + (M V)
             if (a.grad)
                 a.grad[c - 1] = invalid ? 0.0 : (smv[c - 1] - (double)v.hi) - (double)v.lo;
         } else {
             // ln sum: integer part and exponents are exact; the rest is small
-            long long li = 0, ei = 0;
-            for (int k = 0; k < SUB; ++k) {
-                li += sub_i[k];
-                ei += sub_i[SUB + k];
-            }
+            const long long li = tot_i[0], ei = tot_i[1];
             const double lnsum =
                 fma((double)ei, kLn2, ((double)li + ((double)v.hi + (double)v.lo)) * 0x1p-23);
-            double nll = __ldcg(&sc.mv[2 * kMaxWaves]) - lnsum;
+            double nll = smv[2 * Nw] - lnsum;
             if (wf & FLAG_DOMAIN)
                 nll = INFINITY;
             if (wf & FLAG_TIMEOUT)
@@ -542,10 +598,15 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
                 atomicAdd(a.done, 1);
         }
     }
+    if (a.host_flag)
+        __threadfence_system();  // this thread's results reach the host before the flag
     __syncthreads();
     if (threadIdx.x == 0) {
         *work_flags = 0;
         *a.ticket = 0u;
+        if (a.host_flag)
+            *reinterpret_cast<volatile unsigned long long *>(a.host_flag) =
+                ((unsigned long long)a.seq << 32) | (unsigned)wf;
     }
 }
 
@@ -554,7 +615,8 @@ template <int N, int G, int L = 1>
 constexpr bool finalize_fits(int grid)
 {
     (void)grid;
-    return (size_t)(2 * N + 3) * 7 * 8 + 32 * N <= AmpCfg<N, G, L>::SMEM;
+    return (size_t)(2 * N + 3) * 8 + 8 * (2 * N + 1) <= AmpCfg<N, G, L>::SMEM &&
+           AmpCfg<N, G, L>::THREADS > 2 * N;
 }
 
 }  // namespace

@@ -88,7 +88,10 @@ struct pwa_ctx {
 
     // per-call buffers
     double *d_io = nullptr;  // [nll K | grad 2NK | status,done | V 2NK]
-    double *h_io = nullptr;  // pinned mirror
+    double *h_io = nullptr;  // pinned mirror (and, at io_flags_at, max_k result flags)
+    double *h_io_dev = nullptr;  // h_io as a device address (null: not mapped)
+    int *zc_status = nullptr;    // device word the zero-copy launches OR their status into
+    unsigned zc_seq = 0;         // sequence number of the last zero-copy call
     double *d_work = nullptr;  // partials + work flag, then ticket and async status
     unsigned *ticket = nullptr;
     int *async_status = nullptr;
@@ -188,7 +191,9 @@ bool is_device_pointer(const void *p)
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-size_t io_doubles(int N, int max_k) { return (size_t)max_k * (1 + 4 * (size_t)N) + 1; }
+// [nll K | grad 2NK | status,done | V 2NK] for K <= max_k, then max_k flags
+size_t io_flags_at(int N, int max_k) { return (size_t)max_k * (1 + 4 * (size_t)N) + 1; }
+size_t io_doubles(int N, int max_k) { return io_flags_at(N, max_k) + max_k; }
 
 void free_res(pwa_ctx *c)
 {
@@ -454,12 +459,92 @@ cudaGraphExec_t eval_graph(pwa_ctx *c, int K, bool with_grad)
     return exec;
 }
 
+// The direct form's host call without copies: the kernels read V from the
+// pinned buffer and write nll, grad and a flag (sequence number, status
+// bits) straight back into it, and the host spins on the flags instead of
+// synchronising the stream. Used for coherent samples in the direct form
+// unless PWA_ZERO_COPY=0.
+bool zero_copy_ok(const pwa_ctx *c)
+{
+    static const bool off = [] {
+        const char *v = getenv("PWA_ZERO_COPY");
+        return v && strcmp(v, "0") == 0;
+    }();
+    return !off && c->h_io_dev && c->form == PWA_FORM_AMP && c->n_lambda == 1;
+}
+
+int eval_host_zc(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
+{
+    const int N = c->N;
+    const size_t gK = (size_t)2 * N * K;
+    double *h_stat = c->h_io + K + gK;
+    const ptrdiff_t to_dev = reinterpret_cast<char *>(c->h_io_dev) - reinterpret_cast<char *>(c->h_io);
+    auto dev = [&](void *p) { return reinterpret_cast<char *>(p) + to_dev; };
+    unsigned long long *flags =
+        reinterpret_cast<unsigned long long *>(c->h_io + io_flags_at(N, c->cfg.max_k));
+    memcpy(h_stat + 1, V, gK * sizeof(double));
+    const unsigned seq = ++c->zc_seq;
+    std::atomic_thread_fence(std::memory_order_seq_cst);  // V is in memory before the launch
+    for (int k = 0; k < K; ++k) {
+        EvalArgs a{};
+        a.n_waves = N;
+        a.n_events = c->n_data;
+        a.V = reinterpret_cast<const double *>(dev(h_stat + 1 + (size_t)2 * N * k));
+        a.M = c->M;
+        a.amax = c->amax;
+        a.partials = c->d_work;
+        a.ticket = c->ticket;
+        a.status = c->zc_status;
+        a.nll = reinterpret_cast<double *>(dev(c->h_io + k));
+        a.grad = grad ? reinterpret_cast<double *>(dev(c->h_io + K + (size_t)2 * N * k)) : nullptr;
+        a.host_flag = reinterpret_cast<unsigned long long *>(dev(flags + k));
+        a.seq = seq;
+        const cudaError_t e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream,
+                                             c->tune_groups);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PWA_ECUDA, "kernel launch: %s", cudaGetErrorString(e));
+        }
+    }
+    // spin on the flags; look at the stream now and then, so that a failed
+    // launch or a kernel that ended without its flag cannot hold the caller
+    int status = 0;
+    for (int k = 0; k < K; ++k) {
+        unsigned long long f;
+        for (long it = 0;; ++it) {
+            f = __atomic_load_n(&flags[k], __ATOMIC_ACQUIRE);
+            if ((unsigned)(f >> 32) == seq)
+                break;
+            if ((it & 1023) == 1023) {
+                const cudaError_t q = cudaStreamQuery(c->stream);
+                if (q == cudaSuccess) {
+                    f = __atomic_load_n(&flags[k], __ATOMIC_ACQUIRE);
+                    if ((unsigned)(f >> 32) == seq)
+                        break;
+                    return fail(c, PWA_ETIMEOUT, "evaluation %d of %d ended without its result", k, K);
+                }
+                if (q != cudaErrorNotReady) {
+                    cudaGetLastError();
+                    return fail(c, PWA_ECUDA, "evaluation: %s", cudaGetErrorString(q));
+                }
+            }
+        }
+        status |= (int)(unsigned)(f & 0xffffffffu);
+    }
+    memcpy(nll, c->h_io, K * sizeof(double));
+    if (grad)
+        memcpy(grad, c->h_io + K, gK * sizeof(double));
+    return status_from_flags(c, status);
+}
+
 int eval_host(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
 {
     int rc = check_eval_args(c, V, K, nll);
     if (rc)
         return rc;
     DeviceGuard g(c->device);
+    if (zero_copy_ok(c))
+        return eval_host_zc(c, V, K, nll, grad);
     const int N = c->N;
     const size_t gK = (size_t)2 * N * K;
     double *h_stat = c->h_io + K + gK;
@@ -989,10 +1074,16 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
     const size_t nio = io_doubles(c->N, cfg->max_k);
     if ((rc = dev_alloc(c, (void **)&c->d_io, nio * sizeof(double), "io")))
         return bail(rc);
-    if (cudaMallocHost((void **)&c->h_io, nio * sizeof(double)) != cudaSuccess) {
+    if (cudaHostAlloc((void **)&c->h_io, nio * sizeof(double), cudaHostAllocMapped) != cudaSuccess) {
         cudaGetLastError();
         c->h_io = nullptr;
         return bail(fail(c, PWA_ENOMEM, "pinned host buffer"));
+    }
+    memset(c->h_io, 0, nio * sizeof(double));
+    // the device address of the pinned buffer, for the zero-copy host call
+    if (cudaHostGetDevicePointer((void **)&c->h_io_dev, c->h_io, 0) != cudaSuccess) {
+        cudaGetLastError();
+        c->h_io_dev = nullptr;
     }
     size_t nwork = std::max(amp_partials_doubles(c->N, c->num_sms),
                             incoh_partials_doubles(c->N, c->num_sms)) + 8;
@@ -1009,6 +1100,7 @@ int pwa_create(pwa_ctx **out, int device, const pwa_config *cfg)
         return bail(fail(c, PWA_ECUDA, "memset"));
     c->ticket = reinterpret_cast<unsigned *>(c->d_work + nwork - 4);
     c->async_status = reinterpret_cast<int *>(c->d_work + nwork - 2);
+    c->zc_status = reinterpret_cast<int *>(c->d_work + nwork - 6);
     if ((rc = dev_alloc(c, (void **)&c->M, (size_t)2 * c->N * c->N * sizeof(double), "M")))
         return bail(rc);
     if ((rc = dev_alloc(c, (void **)&c->amax, (size_t)c->N * sizeof(float), "amax")))

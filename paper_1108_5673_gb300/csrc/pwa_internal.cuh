@@ -390,6 +390,11 @@ struct EvalArgs {
     double *grad;      // [n_waves] complex output (null: NLL only)
     float *weights;    // projection weights I / N_gen per event (the weights mode)
     float inv_ngen;    // 1 / N_gen (the weights mode)
+    // Results straight to (mapped, pinned) host memory: when set, nll, grad
+    // and V may be host addresses, and the last CTA, once every result is
+    // visible to the host, stores (seq << 32) | status bits here.
+    unsigned long long *host_flag;
+    unsigned seq;
 };
 
 // Structure-of-arrays store: plane 2a holds Re A_a, plane 2a+1 holds Im A_a,
