@@ -230,7 +230,10 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     const uint32_t stage_tx = 2u * (uint32_t)a.n_waves * L * TE * 4u;
     auto stage_of = [](int j) { return (j % GROUPS) * C::SPG + (j / GROUPS) % C::SPG; };
     auto use_of = [](int j) { return (uint32_t)((j / GROUPS) / C::SPG); };
-    const int n_first = n_my < STAGES ? n_my : STAGES;  // first use of every stage
+    // tiles the producer issues (none when the timeout path is being tested)
+    const int n_issue = a.stall_ns ? 0 : n_my;
+    const unsigned long long wait_ns = a.stall_ns ? a.stall_ns : kWaitLimitNs;
+    const int n_first = n_issue < STAGES ? n_issue : STAGES;  // first use of every stage
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -267,7 +270,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         if (lane == 0) {
             // ---- producer: one thread issues the TMA copies ----------------
             int j = n_first;
-            for (; j < n_my; ++j) {
+            for (; j < n_issue; ++j) {
                 const int s = stage_of(j);
                 const uint32_t u = use_of(j);
                 if (u > 0 && !mbar_wait(&empty[s], (u & 1) ^ 1)) {
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         for (int j = grp; j < n_my; j += GROUPS) {
             const int s = stage_of(j);
             const uint32_t u = use_of(j);
-            if (!mbar_wait(&full[s], u & 1)) {
+            if (!mbar_wait(&full[s], u & 1, wait_ns)) {
                 flags |= FLAG_TIMEOUT;
                 break;
             }

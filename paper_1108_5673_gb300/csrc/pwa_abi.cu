@@ -339,6 +339,15 @@ int check_eval_args(pwa_ctx *c, const void *V, int K, const void *nll)
     return PWA_OK;
 }
 
+// PWA_TEST_TIMEOUT_NS=<ns> (tests of the timeout path): the direct form's
+// copies are not issued and its consumers give up after <ns>, so that the
+// call reports PWA_ETIMEOUT without anything left in flight. Read per call.
+unsigned long long test_stall_ns()
+{
+    const char *v = getenv("PWA_TEST_TIMEOUT_NS");
+    return v ? strtoull(v, nullptr, 10) : 0ull;
+}
+
 // Enqueue the evaluation of K parameter sets (device pointers).
 int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgrad, int *status,
                  int *done)
@@ -374,6 +383,7 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         a.done = done;
         a.nll = dnll + k;
         a.grad = dgrad ? dgrad + (size_t)2 * N * k : nullptr;
+        a.stall_ns = test_stall_ns();
         cudaError_t e = cudaSuccess;
         if (c->form == PWA_FORM_AMP && c->n_lambda > 1 && c->incoh_tma)
             e = launch_nll_incoh_tma(&c->data_map, c->n_lambda, a, c->num_sms, c->stream);
@@ -499,6 +509,7 @@ int eval_host_zc(pwa_ctx *c, const double *V, int K, double *nll, double *grad)
         a.grad = grad ? reinterpret_cast<double *>(dev(c->h_io + K + (size_t)2 * N * k)) : nullptr;
         a.host_flag = reinterpret_cast<unsigned long long *>(dev(flags + k));
         a.seq = seq;
+        a.stall_ns = test_stall_ns();
         const cudaError_t e = launch_nll_amp(c->data, &c->data_map, a, c->num_sms, c->stream,
                                              c->tune_groups);
         if (e != cudaSuccess) {

@@ -93,8 +93,10 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
 }
 
 // Wait for the phase with the given parity to complete; gives up after
-// kWaitLimitNs and returns false (the caller records FLAG_TIMEOUT).
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+// limit_ns (default kWaitLimitNs) and returns false (the caller records
+// FLAG_TIMEOUT).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
+                                          unsigned long long limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity))
         return true;
@@ -103,7 +105,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
         for (int i = 0; i < 4; ++i)
             if (mbar_try_wait(bar, parity))
                 return true;
-        if (global_timer_ns() - t0 > kWaitLimitNs)
+        if (global_timer_ns() - t0 > limit_ns)
             return false;
     }
 }
@@ -395,6 +397,11 @@ struct EvalArgs {
     // visible to the host, stores (seq << 32) | status bits here.
     unsigned long long *host_flag;
     unsigned seq;
+    // Test of the timeout path (direct form): with stall_ns > 0 the producer
+    // issues no copies and the consumers wait at most stall_ns for a tile, so
+    // their waits run out with nothing in flight and the call reports
+    // FLAG_TIMEOUT. Zero in normal use.
+    unsigned long long stall_ns;
 };
 
 // Structure-of-arrays store: plane 2a holds Re A_a, plane 2a+1 holds Im A_a,

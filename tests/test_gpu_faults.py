@@ -81,3 +81,49 @@ def test_allocation_failures_reported_and_recoverable(built):
         assert code == _abi.PWA_ENOMEM and "ENOMEM" in msg, (n, out)
         failed += 1
     assert failed >= 3
+
+
+def test_bounded_wait_runs_out_and_context_recovers(built):
+    """The device-side waits are bounded: with PWA_TEST_TIMEOUT_NS the
+    direct-form producer issues no copies, so every consumer's wait for its
+    first tile runs out (after 1 ms) with nothing in flight. The call reports
+    PWA_ETIMEOUT (host call and async call with pwa_sync), the NLL is NaN and
+    the gradient zero; the next normal call on the same context gives the
+    results of a call made before."""
+    import numpy as np
+    import torch
+    import paper_1108_5673_gb300 as pwa
+    import synth
+    from paper_1108_5673_gb300 import _abi
+
+    wl = synth.mixture_workload("t", synth.waves_linear(12), 50_000, 20_000, seed_data=8,
+                                seed_mc=9, seed_v=10)
+    V = synth.random_V(12, 11)
+    old = os.environ.pop("PWA_TEST_TIMEOUT_NS", None)
+    try:
+        with pwa.Likelihood(12) as L:
+            L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+            L.build_norm()
+            n0, g0 = L.nll_grad(V[None, :])
+            dV = torch.from_numpy(V[None, :].copy()).cuda()
+            dn = torch.zeros(1, dtype=torch.float64, device="cuda")
+            dg = torch.ones(1, 12, dtype=torch.complex128, device="cuda")
+            os.environ["PWA_TEST_TIMEOUT_NS"] = "1000000"
+            with pytest.raises(pwa.PwaError) as e:
+                L.nll_grad(V[None, :])
+            assert e.value.code == _abi.PWA_ETIMEOUT
+            L.nll_grad_async(dV, dn, dg)
+            with pytest.raises(pwa.PwaError) as e:
+                L.sync()
+            assert e.value.code == _abi.PWA_ETIMEOUT
+            assert np.isnan(float(dn.item())) and bool((dg == 0).all())
+            del os.environ["PWA_TEST_TIMEOUT_NS"]
+            n1, g1 = L.nll_grad(V[None, :])
+            assert n1[0] == n0[0] and np.array_equal(g1, g0)
+            L.nll_grad_async(dV, dn, dg)
+            assert L.sync() == _abi.PWA_OK
+            assert float(dn.item()) == n0[0]
+    finally:
+        os.environ.pop("PWA_TEST_TIMEOUT_NS", None)
+        if old is not None:
+            os.environ["PWA_TEST_TIMEOUT_NS"] = old

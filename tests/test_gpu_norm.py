@@ -62,7 +62,7 @@ def digit_bound(A_mc, n_gen):
     X[:, 0::2] = A.real
     X[:, 1::2] = A.imag
     amax = (np.abs(A.real) + np.abs(A.imag)).max(axis=0).astype(np.float32)
-    r = np.where(amax > 0, np.floor(np.log2(np.maximum(amax, 1e-300))) + 2, 0)
+    r = np.where(amax > 0, np.floor(np.log2(np.maximum(amax, np.float32(1e-38)))) + 2, 0)
     r = np.repeat(np.maximum(r, -35), 2)
     s = 2.0 ** r
     ax = np.abs(X)

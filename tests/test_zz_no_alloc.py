@@ -7,6 +7,7 @@ library. This file is collected last on purpose, so that a run stopping at
 the first failure has already run every other test; it also passes alone.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -44,6 +45,9 @@ def test_noalloc_matches_context_entry_point_twice():
     d_nll = torch.empty(1, dtype=torch.float64, device="cuda")
     d_grad = torch.empty(N, dtype=torch.complex128, device="cuda")
     d_status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    # the same kernel and grid as the context call (no launch-shape overrides):
+    # the results are then bitwise those of the context entry point
+    same_shape = not any(os.environ.get(v) for v in ("PWA_AMP_GROUPS", "PWA_AMP_GRID"))
     for V, (n_ref, g_ref) in zip(Vs, ref):          # two calls in a row
         d_V = torch.from_numpy(V).cuda()
         _abi.pwa_nll_grad_noalloc(d_planes, pitch, n, N, d_amax, d_M, d_V, d_nll, d_grad,
@@ -53,6 +57,22 @@ def test_noalloc_matches_context_entry_point_twice():
         assert int(d_status.item()) == 0
         assert abs(nll - n_ref[0]) <= max(1e-3 * math.sqrt(n / 1e6), 2e-6)
         assert np.linalg.norm(g - g_ref[0]) <= 1e-5 * np.linalg.norm(g_ref[0])
+        if same_shape:
+            assert nll == n_ref[0] and np.array_equal(g, g_ref[0])
+
+    # without a status word (the library's own word in the array takes the
+    # bits) and without a gradient (the NLL alone; the buffer is not touched)
+    d_V = torch.from_numpy(Vs[0]).cuda()
+    d_grad.fill_(7.0)
+    _abi.pwa_nll_grad_noalloc(d_planes, pitch, n, N, d_amax, d_M, d_V, d_nll, None, None)
+    torch.cuda.synchronize()
+    assert abs(float(d_nll.item()) - ref[0][0][0]) <= max(1e-3 * math.sqrt(n / 1e6), 2e-6)
+    if same_shape:
+        assert float(d_nll.item()) == ref[0][0][0]
+    assert bool((d_grad == 7.0).all())
+    _abi.pwa_nll_grad_noalloc(d_planes, pitch, n, N, d_amax, d_M, d_V, d_nll, d_grad, None)
+    torch.cuda.synchronize()
+    assert np.linalg.norm(d_grad.cpu().numpy() - ref[0][1][0]) <= 1e-5 * np.linalg.norm(ref[0][1][0])
 
     # sizes beyond the limits are refused before anything runs
     with pytest.raises(_abi.PwaError):
