@@ -31,6 +31,7 @@ class Likelihood:
         self.max_k = max_k
         self.ctx = _abi.pwa_create(device, n_waves, forms, precision, max_k, stream)
         self.last_status = PWA_OK
+        self.M = None
 
     def load_events(self, data_amp, mc_amp, n_mc_gen):
         """[n, N] amplitudes (coherent sum, Eq. 1), or [n, n_lambda, N] for an
@@ -39,6 +40,7 @@ class Likelihood:
             self._abi.pwa_load_events_incoherent(self.ctx, data_amp, mc_amp, n_mc_gen)
         else:
             self._abi.pwa_load_events(self.ctx, data_amp, mc_amp, n_mc_gen)
+        self.M = None
         self.n_data = int(data_amp.shape[0])
         self.n_mc = int(mc_amp.shape[0])
         return self
@@ -47,6 +49,7 @@ class Likelihood:
         """Load samples given by kinematics (m, cos theta, phi): the amplitudes
         BW x Y_l^m of `waves` are computed on the device."""
         self._abi.pwa_load_events_generated(self.ctx, waves, data_kin, mc_kin, n_mc_gen)
+        self.M = None
         self.n_data = int(len(data_kin["m"]) if isinstance(data_kin, dict) else data_kin.shape[0])
         self.n_mc = int(len(mc_kin["m"]) if isinstance(mc_kin, dict) else mc_kin.shape[0])
         return self
@@ -56,8 +59,10 @@ class Likelihood:
         return self._abi.pwa_compute_amplitudes(self.ctx, waves, kin, out)
 
     def build_norm(self):
-        """Build M on the device; returns a host copy ([N, N] complex128)."""
-        return self._abi.pwa_build_norm(self.ctx, self.n_waves)
+        """Build M on the device; returns a host copy ([N, N] complex128),
+        also kept as self.M (the fit drivers scale their variables by it)."""
+        self.M = self._abi.pwa_build_norm(self.ctx, self.n_waves)
+        return self.M
 
     def set_form(self, form):
         self._abi.pwa_set_form(self.ctx, form)
