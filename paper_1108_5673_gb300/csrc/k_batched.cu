@@ -60,6 +60,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "pwa_internal.cuh"
 
@@ -70,7 +73,8 @@ namespace {
 constexpr int kBM = 128;        // events per tile
 constexpr int kKC = 64;         // parameter sets per chunk (GEMM 2: M = 2 kKC = 128)
 constexpr int kHS = 32;         // parameter sets per half chunk (one GEMM 1 / epilogue step)
-constexpr int kXS = 2;          // X stages
+constexpr int kXSMax = 6;       // X stages at most (as many as shared memory takes, at least 2)
+constexpr int kMaxSmem = 226 * 1024;
 constexpr int kMaxChunks = 4;
 constexpr int kEpiWarps = 16;
 constexpr int kThreads = (kEpiWarps + 3) * 32;
@@ -116,19 +120,37 @@ struct BatchArgs {
 
 struct Smem {
     uint32_t w_off, x_off, r_off, w_bytes, bytes;
+    int nxs;   // X stages
 };
 
-__host__ __device__ inline Smem batch_smem(int F, int xs, int n_chunks)
+// Bytes of the W image of n_chunks chunks (both halves of each), as built in
+// global memory by the prep kernel.
+__host__ __device__ inline uint32_t w_image_bytes(int F, int n_chunks)
+{
+    return (uint32_t)n_chunks * 2 * kWSlices * ((F + 63) / 64) * kWBlock;
+}
+
+// Shared memory of a launch for K sets: the W image of the hpt half chunks
+// that hold sets (its first part), then as many X stages as fit (2..kXSMax),
+// then R'. Small K leave room for a deeper X pipeline, which their short
+// per-tile work needs to hide the loads.
+__host__ __device__ inline Smem batch_smem(int F, int xs, int hpt)
 {
     const int kb = (F + 63) / 64;
     Smem s;
-    s.w_bytes = (uint32_t)n_chunks * 2 * kWSlices * kb * kWBlock;
+    s.w_bytes = (uint32_t)hpt * kWSlices * kb * kWBlock;
+    const uint32_t stage = 2u * xs * F * 128;
+    const int64_t room = (int64_t)kMaxSmem - 1024 - kRBytes - (int64_t)s.w_bytes;
+    const int fit = room > 0 ? (int)(room / stage) : 0;
+    s.nxs = fit < 2 ? 2 : (fit > kXSMax ? kXSMax : fit);
     s.w_off = 0;
     s.x_off = s.w_bytes;
-    s.r_off = s.x_off + (uint32_t)kXS * 2 * xs * F * 128;
+    s.r_off = s.x_off + (uint32_t)s.nxs * stage;
     s.bytes = s.r_off + kRBytes + 1024;  // + alignment slack
     return s;
 }
+
+__host__ __device__ inline int batch_hpt(int K) { return (K + kHS - 1) / kHS; }
 
 __host__ __device__ inline uint32_t sw128(int row, int byte_in_row)
 {
@@ -162,11 +184,16 @@ __device__ __forceinline__ f2 log2_fixed2(f2 z)
     return fma2(p, z, pk2(12582912.0f, 12582912.0f));
 }
 
+// A work item of the model batch: tiles [tile0, tile0 + n_tiles) of a model,
+// partial sums at `slot` among that model's.
+struct BatchItem {
+    int model, tile0, n_tiles, slot;
+};
+
 // ---- per-call preparation: W image and set exponents ------------------------
 // One block per (chunk, half, slice).
-__global__ void batched_prep(const BatchArgs a)
+__device__ __forceinline__ void batched_prep_block(const BatchArgs &a, const int blk)
 {
-    const int blk = blockIdx.x;
     const int p = blk % kWSlices, h = (blk / kWSlices) & 1, c = blk / (2 * kWSlices);
     const int Nw = a.n_waves, KB = (a.F + 63) / 64;
     __shared__ int s_T[kHS];
@@ -211,37 +238,64 @@ __global__ void batched_prep(const BatchArgs a)
     }
 }
 
+__global__ void batched_prep(const BatchArgs a) { batched_prep_block(a, blockIdx.x); }
+
+// The preparation of every model of a batch: blocks_per_model blocks each.
+__global__ void batched_items_prep(const BatchArgs *__restrict__ models, int blocks_per_model)
+{
+    batched_prep_block(models[blockIdx.x / blocks_per_model], blockIdx.x % blocks_per_model);
+}
+
 // ---- main kernel ----------------------------------------------------------------
+// The CTA's share of one launch: tiles tile0 + j stride for j < n_tiles of
+// one sample, with its partial sums at `slot` of the sample's scratch; the
+// helper warp forms M V for the sets mv_k0, mv_k0 + mv_kstride, ...
+struct TileRange {
+    int tile0, n_tiles, stride, slot;
+    int mv_k0, mv_kstride;
+};
+
+// The CTA's barriers and small state (declared once per kernel, so that the
+// several instantiations of the body in one kernel share them).
+struct BatchShared {
+    uint64_t w_full, x_full[kXSMax], x_empty[kXSMax], s_full, s_free, r_full, r_free, g_done;
+    uint32_t tmem_base;
+    int s_flags;
+    unsigned s_kflags[2 * kMaxChunks];
+};
+
 template <int F, int XS>
-__global__ void __launch_bounds__(kThreads, 1)
-    batched_kernel(const __grid_constant__ CUtensorMap xmap, const BatchArgs a, const int n_tiles)
+__device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const BatchArgs &a,
+                                             const TileRange &tr, unsigned char *smem_dyn,
+                                             BatchShared &sh)
 {
     constexpr int KB = (F + 63) / 64;
     constexpr int kGCol = s_cols(XS);
     constexpr uint32_t kXBlk = XS * F * 128;    // one 64-event block: x0 (and x1) rows
     constexpr uint32_t kXBytes = 2 * kXBlk;     // one stage
-    extern __shared__ unsigned char smem_dyn[];
-    __shared__ uint64_t w_full, x_full[kXS], x_empty[kXS], s_full, s_free, r_full, r_free, g_done;
-    __shared__ uint32_t tmem_base;
-    __shared__ int s_flags;
-    __shared__ unsigned s_kflags[2 * kMaxChunks];
+    uint64_t &w_full = sh.w_full, &s_full = sh.s_full, &s_free = sh.s_free, &r_full = sh.r_full,
+             &r_free = sh.r_free, &g_done = sh.g_done;
+    uint64_t *x_full = sh.x_full, *x_empty = sh.x_empty;
+    uint32_t &tmem_base = sh.tmem_base;
+    int &s_flags = sh.s_flags;
+    unsigned *s_kflags = sh.s_kflags;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int NCH = a.n_chunks;
-    const Smem L = batch_smem(F, XS, NCH);
+    // half chunks per tile that hold parameter sets (a last half past K is skipped)
+    const int HPT = batch_hpt(a.K);
+    const Smem L = batch_smem(F, XS, HPT);
+    const int NXS = L.nxs;
     unsigned char *base = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     unsigned char *sW = base + L.w_off;
     unsigned char *sX = base + L.x_off;
     unsigned char *sR = base + L.r_off;
-    const int n_my =
-        (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-    // half chunks per tile that hold parameter sets (a last half past K is skipped)
-    const int HPT = (a.K + kHS - 1) / kHS;
+    const int n_my = tr.n_tiles;
     const int steps = n_my * HPT;
 
     if (threadIdx.x == 0) {
         mbar_init(&w_full, 1);
-        for (int s = 0; s < kXS; ++s) {
+        for (int s = 0; s < NXS; ++s) {
             mbar_init(&x_full[s], 1);
             mbar_init(&x_empty[s], 1);
         }
@@ -270,20 +324,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             bulk_load(sW, a.wimg, L.w_bytes, &w_full);
             int j = 0;
             for (; j < n_my; ++j) {
-                const int s = j % kXS;
-                const uint32_t u = j / kXS;
+                const int s = j % NXS;
+                const uint32_t u = j / NXS;
                 if (u > 0 && !mbar_wait(&x_empty[s], (u & 1) ^ 1)) {
                     flags |= FLAG_TIMEOUT;
                     break;
                 }
-                const int e0 = ((int)blockIdx.x + j * (int)gridDim.x) * kBM;
+                const int e0 = (tr.tile0 + j * tr.stride) * kBM;
                 mbar_arrive_expect_tx(&x_full[s], kXBytes);
-                tma_load_2d(sX + (size_t)s * kXBytes, &xmap, e0, 0, &x_full[s]);
-                tma_load_2d(sX + (size_t)s * kXBytes + kXBlk, &xmap, e0 + 64, 0, &x_full[s]);
+                tma_load_2d(sX + (size_t)s * kXBytes, xmap_p, e0, 0, &x_full[s]);
+                tma_load_2d(sX + (size_t)s * kXBytes + kXBlk, xmap_p, e0 + 64, 0, &x_full[s]);
             }
             // copies still in flight complete before the block may exit
-            for (int q = (j > kXS ? j - kXS : 0); q < j; ++q)
-                if (!mbar_wait(&x_full[q % kXS], (q / kXS) & 1))
+            for (int q = (j > NXS ? j - NXS : 0); q < j; ++q)
+                if (!mbar_wait(&x_full[q % NXS], (q / NXS) & 1))
                     flags |= FLAG_TIMEOUT;
             if (!mbar_wait(&w_full, 0))
                 flags |= FLAG_TIMEOUT;
@@ -302,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint64_t dK = umma_desc_sw128(0, 16, 1024);         // K-major operands
             // GEMM 2 of chunk step cq (pipelined behind GEMM 1 of the next step)
             auto gemm2 = [&](int cq) -> bool {
-                const int j = cq / NCH, c = cq % NCH, s = j % kXS;
+                const int j = cq / NCH, c = cq % NCH, s = j % NXS;
                 if (!mbar_wait(&r_full, cq & 1))
                     return false;
                 tc_fence_after();
@@ -321,8 +375,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             };
             bool ok = mbar_wait(&w_full, 0);
             for (int q = 0; q < steps && ok; ++q) {
-                const int j = q / HPT, ch = q % HPT, c = ch >> 1, h = ch & 1, s = j % kXS;
-                if (ch == 0 && !mbar_wait(&x_full[s], (j / kXS) & 1)) {
+                const int j = q / HPT, ch = q % HPT, c = ch >> 1, h = ch & 1, s = j % NXS;
+                if (ch == 0 && !mbar_wait(&x_full[s], (j / NXS) & 1)) {
                     ok = false;
                     break;
                 }
@@ -370,9 +424,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // per-thread constants: R' store offsets, the atomic partials of this lane
         const uint32_t st0 = sw128(e, 32 * sg), st1 = sw128(e, 32 * sg + 16);
         unsigned long long *lp = reinterpret_cast<unsigned long long *>(
-            a.lpart + ((size_t)blockIdx.x * 4 + qq) * (NCH * kKC) + 8 * sg + lane);
-        int64_t ev = (int64_t)blockIdx.x * kBM + e;       // this thread's event in tile j
-        const int64_t ev_step = (int64_t)gridDim.x * kBM;
+            a.lpart + ((size_t)tr.slot * 4 + qq) * (NCH * kKC) + 8 * sg + lane);
+        int64_t ev = (int64_t)tr.tile0 * kBM + e;          // this thread's event in tile j
+        const int64_t ev_step = (int64_t)tr.stride * kBM;
         bool ok = true;
         int j = 0, ch = 0;                                 // tile, half chunk (q = j HPT + ch)
         for (int q = 0; q < steps && ok; ++q) {
@@ -383,9 +437,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 break;
             }
             tc_fence_after();
+            // a warp whose 8 sets all lie past K (padding of the last half
+            // chunk) keeps to the barriers and does no work: its rows of R'
+            // feed only the G^T rows of those sets, which are never read
+            const bool idle = a.K - (ch >> 1) * kKC - h * kHS - 8 * sg <= 0;
             // Q of this warp's 8 sets: acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8
             float qr[8], qi[8];
-            {
+            if (!idle) {
                 uint32_t v0[16], v1[16], v2[16], v3[16];
                 tmem_ld16(tmem + lane_addr + 16 * sg, v0);
                 tmem_ld16(tmem + lane_addr + 64 + 16 * sg, v1);
@@ -413,7 +471,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_arrive(&s_free);
             uint32_t rpk[8];
             int l[8];
-            if (ev < a.n_events) {
+            if (!idle && ev < a.n_events) {
                 float Iv[8], z[8];
                 int kx[8];
                 unsigned mn = 0xffffffffu;
@@ -451,22 +509,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             // fixed-point log2 sums over the warp's 32 events; lane s keeps set s
-            int mine = 0;
+            if (!idle) {
+                int mine = 0;
 #pragma unroll
-            for (int s = 0; s < 8; ++s) {
-                const int t = __reduce_add_sync(0xffffffffu, l[s]);
-                mine = lane == s ? t : mine;
+                for (int s = 0; s < 8; ++s) {
+                    const int t = __reduce_add_sync(0xffffffffu, l[s]);
+                    mine = lane == s ? t : mine;
+                }
+                if (lane < 8)  // no return value: a fire-and-forget reduction
+                    atomicAdd(lp + ch * kHS, (unsigned long long)(long long)mine);
             }
-            if (lane < 8)  // no return value: a fire-and-forget reduction
-                atomicAdd(lp + ch * kHS, (unsigned long long)(long long)mine);
             // R' may be overwritten once GEMM 2 of the previous chunk step is done
             if (h == 0 && cq >= 1 && !mbar_wait(&r_free, (cq - 1) & 1)) {
                 ok = false;
                 break;
             }
             unsigned char *rrow = sR + h * (128 * 128);
-            *reinterpret_cast<uint4 *>(rrow + st0) = make_uint4(rpk[0], rpk[1], rpk[2], rpk[3]);
-            *reinterpret_cast<uint4 *>(rrow + st1) = make_uint4(rpk[4], rpk[5], rpk[6], rpk[7]);
+            if (!idle) {
+                *reinterpret_cast<uint4 *>(rrow + st0) = make_uint4(rpk[0], rpk[1], rpk[2], rpk[3]);
+                *reinterpret_cast<uint4 *>(rrow + st1) = make_uint4(rpk[4], rpk[5], rpk[6], rpk[7]);
+            }
             if (last_half) {
                 fence_async_smem();
                 __syncwarp();
@@ -503,7 +565,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         gv[i] = XS == 2 ? fmaf(__uint_as_float(g1[i]), 1.0f / 256.0f, __uint_as_float(g[i]))
                                         : __uint_as_float(g[i]);
                     float4 *dst = reinterpret_cast<float4 *>(
-                        a.gpart + (((size_t)blockIdx.x * NCH + c) * 128 + e) * F + c0);
+                        a.gpart + (((size_t)tr.slot * NCH + c) * 128 + e) * F + c0);
                     dst[0] = make_float4(gv[0], gv[1], gv[2], gv[3]);
                     dst[1] = make_float4(gv[4], gv[5], gv[6], gv[7]);
                 }
@@ -512,9 +574,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             flags |= FLAG_TIMEOUT;
         }
     } else if (warp == kEpiWarps + 2) {
-        // ---- helper: M V and V^H M V for the sets k = blockIdx.x, + grid, ... --
+        // ---- helper: M V and V^H M V for the sets mv_k0, + mv_kstride, ... --
         const int Nw = a.n_waves;
-        for (int k = blockIdx.x; k < a.K; k += gridDim.x) {
+        for (int k = tr.mv_k0; k < a.K; k += tr.mv_kstride) {
             const double *V = a.V + 2 * (size_t)k * Nw;
             double nv = 0.0;
             for (int row = lane; row < Nw; row += 32) {
@@ -547,11 +609,65 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
-// Final sums over CTAs (fixed order), M V, the first-order correction for
-// V - V_r; one block per parameter set.
-__global__ void batched_finalize(const BatchArgs a, int grid, int *done, double *nll, double *grad)
+// One sample, a persistent grid: CTA b takes tiles b, b + grid, ...
+template <int F, int XS>
+__global__ void __launch_bounds__(kThreads, 1)
+    batched_kernel(const __grid_constant__ CUtensorMap xmap, const BatchArgs a, const int n_tiles)
 {
-    const int k = blockIdx.x, Nw = a.n_waves, F = a.F, NCH = a.n_chunks;
+    extern __shared__ unsigned char smem_dyn[];
+    __shared__ BatchShared sh;
+    TileRange tr;
+    tr.tile0 = blockIdx.x;
+    tr.stride = gridDim.x;
+    tr.n_tiles = (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    tr.slot = blockIdx.x;
+    tr.mv_k0 = blockIdx.x;
+    tr.mv_kstride = gridDim.x;
+    batched_body<F, XS>(&xmap, a, tr, smem_dyn, sh);
+}
+
+// Many samples (the uneven model batch) in one launch: CTA b is the work item
+// items[b], a contiguous range of one model's tiles; its partials go to the
+// item's slot among the model's, and the model's first item forms M V. The
+// hardware starts an item's CTA as an SM frees up; the items and the order
+// in which the final kernel adds their partials are fixed, so the results
+// do not depend on that schedule. The body is instantiated per feature
+// count F (the tile shape of each wave-count bucket).
+template <int XS>
+__global__ void __launch_bounds__(kThreads, 1)
+    batched_items_kernel(const BatchItem *__restrict__ items, const BatchArgs *__restrict__ models,
+                         const CUtensorMap *__restrict__ maps)
+{
+    extern __shared__ unsigned char smem_dyn[];
+    __shared__ BatchShared sh;
+    const BatchItem it = items[blockIdx.x];
+    const BatchArgs &a = models[it.model];
+    TileRange tr;
+    tr.tile0 = it.tile0;
+    tr.n_tiles = it.n_tiles;
+    tr.stride = 1;
+    tr.slot = it.slot;
+    tr.mv_k0 = it.slot == 0 ? 0 : a.K;    // the model's first item forms M V
+    tr.mv_kstride = 1;
+    const CUtensorMap *m = maps + it.model;
+    switch (a.F) {
+    case 16: batched_body<16, XS>(m, a, tr, smem_dyn, sh); break;
+    case 32: batched_body<32, XS>(m, a, tr, smem_dyn, sh); break;
+    case 48: batched_body<48, XS>(m, a, tr, smem_dyn, sh); break;
+    case 64: batched_body<64, XS>(m, a, tr, smem_dyn, sh); break;
+    case 80: batched_body<80, XS>(m, a, tr, smem_dyn, sh); break;
+    case 96: batched_body<96, XS>(m, a, tr, smem_dyn, sh); break;
+    default: break;
+    }
+}
+
+// Final sums over the n_slots partial slots of a sample (fixed order), M V,
+// the first-order correction for V - V_r; one block per parameter set.
+__device__ __forceinline__ void batched_finalize_set(const BatchArgs &a, int k, int n_slots,
+                                                     int *done, double *nll, double *grad)
+{
+    const int grid = n_slots;
+    const int Nw = a.n_waves, F = a.F, NCH = a.n_chunks;
     const int c = k / kKC, kl = k % kKC;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     __shared__ double s_corr[2];
@@ -620,6 +736,20 @@ __global__ void batched_finalize(const BatchArgs a, int grid, int *done, double 
     }
 }
 
+__global__ void batched_finalize(const BatchArgs a, int grid, int *done, double *nll, double *grad)
+{
+    batched_finalize_set(a, blockIdx.x, grid, done, nll, grad);
+}
+
+// The final sums of every model of a batch: block b is set b % K of model b / K.
+__global__ void batched_items_finalize(const BatchArgs *__restrict__ models, const int *n_slots,
+                                       int K, int *const *done, double *const *nll,
+                                       double *const *grad)
+{
+    const int m = blockIdx.x / K, k = blockIdx.x % K;
+    batched_finalize_set(models[m], k, n_slots[m], done[m], nll[m], grad[m]);
+}
+
 // ---- block-floating-point encoding of the data (once per load) ---------------
 // One thread per event: shared exponent E = exponent of the largest |feature|
 // (max = m 2^E, m in [1/2, 1)), slices x0 = rint(A 2^(8-E)) and, for XS = 2,
@@ -666,8 +796,6 @@ __global__ void batched_encode_kernel(const float *__restrict__ planes, int64_t 
     }
 }
 
-constexpr int kMaxSmem = 226 * 1024;
-
 template <int F, int XS>
 cudaError_t configure_f()
 {
@@ -680,7 +808,10 @@ cudaError_t configure_xs()
 {
     cudaError_t e = cudaSuccess;
     for (cudaError_t r : {configure_f<16, XS>(), configure_f<32, XS>(), configure_f<48, XS>(),
-                          configure_f<64, XS>(), configure_f<80, XS>(), configure_f<96, XS>()})
+                          configure_f<64, XS>(), configure_f<80, XS>(), configure_f<96, XS>(),
+                          cudaFuncSetAttribute(batched_items_kernel<XS>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               kMaxSmem)})
         if (r != cudaSuccess)
             e = r;
     return e;
@@ -712,7 +843,7 @@ ScratchLayout scratch_layout(int F, int xs, int n_waves, int K, int grid)
     auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
     ScratchLayout s;
     s.wimg = 0;
-    s.gpart = up(s.wimg + batch_smem(F, xs, nch).w_bytes);
+    s.gpart = up(s.wimg + w_image_bytes(F, nch));
     s.lpart = up(s.gpart + (size_t)grid * nch * 128 * F * 4);
     s.mv = up(s.lpart + (size_t)grid * 4 * nch * kKC * 8);
     s.T = up(s.mv + (size_t)K * (2 * n_waves + 1) * 8);
@@ -730,7 +861,8 @@ int batched_max_k(int n_waves, int xs)
     const int F = batched_features(n_waves);
     int nch = kMaxChunks;
     while (nch > 0 &&
-           (s_cols(xs) + nch * xs * F > 512 || (int)batch_smem(F, xs, nch).bytes > kMaxSmem))
+           (s_cols(xs) + nch * xs * F > 512 ||
+            (int)batch_smem(F, xs, batch_hpt(nch * kKC)).bytes > kMaxSmem))
         --nch;
     return nch * kKC;
 }
@@ -799,12 +931,195 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
     if (e != cudaSuccess)
         return e;
     const int n_tiles = (int)((n_events + kBM - 1) / kBM);
-    const uint32_t smem = batch_smem(F, xs, nch).bytes;
+    const uint32_t smem = batch_smem(F, xs, batch_hpt(K)).bytes;
     e = xs == 2 ? launch_main<2>(F, grid, smem, s, xmap, a, n_tiles)
                 : launch_main<1>(F, grid, smem, s, xmap, a, n_tiles);
     if (e != cudaSuccess)
         return e;
     batched_finalize<<<K, 64, 0, s>>>(a, grid, done, nll, grad);
+    return cudaGetLastError();
+}
+
+// ---- the uneven model batch in one launch -------------------------------------
+// Plan buffer (device, one allocation), in this order: BatchArgs[n_models],
+// CUtensorMap[n_models] (64-byte aligned), BatchItem[n_items], int
+// n_slots[n_models], the per-model output pointers (done, nll, grad), then
+// per model its scratch: W image, G^T partials, log partials, M V, set
+// exponents, domain flags. The log partials and domain flags of all models
+// are contiguous, so one memset clears them per call.
+namespace {
+
+struct PlanLayout {
+    size_t args, maps, items, nslots, pdone, pnll, pgrad, zero, zero_bytes, scratch, total;
+    std::vector<size_t> wimg, gpart, lpart, mv, T, kflags;
+    std::vector<BatchItem> items_h;
+    std::vector<int> slots;
+};
+
+size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+PlanLayout plan_layout(const BatchModelDesc *m, int n_models, int xs, int K, int num_sms,
+                       int items_per_sm)
+{
+    PlanLayout p;
+    const int nch = (K + kKC - 1) / kKC;
+    // work items: about num_sms * items_per_sm in all, of equal estimated
+    // cost (tiles x (F + 32): the MMAs grow with F, the epilogue does not)
+    std::vector<double> cost(n_models);
+    double total = 0.0;
+    for (int i = 0; i < n_models; ++i) {
+        const int64_t tiles = (m[i].n_events + kBM - 1) / kBM;
+        cost[i] = (double)tiles * (batched_features(m[i].n_waves) + 32);
+        total += cost[i];
+    }
+    const double target = total / std::max(1, num_sms * items_per_sm);
+    p.slots.resize(n_models);
+    for (int i = 0; i < n_models; ++i) {
+        const int tiles = (int)((m[i].n_events + kBM - 1) / kBM);
+        int n_it = (int)std::lround(cost[i] / target);
+        n_it = std::max(1, std::min(n_it, tiles));
+        p.slots[i] = n_it;
+        for (int k = 0; k < n_it; ++k) {
+            const int t0 = (int)((int64_t)tiles * k / n_it), t1 = (int)((int64_t)tiles * (k + 1) / n_it);
+            p.items_h.push_back({i, t0, t1 - t0, k});
+        }
+    }
+    // largest items first: the hardware hands out CTAs in block order
+    std::stable_sort(p.items_h.begin(), p.items_h.end(), [&](const BatchItem &x, const BatchItem &y) {
+        return (double)x.n_tiles * (batched_features(m[x.model].n_waves) + 32) >
+               (double)y.n_tiles * (batched_features(m[y.model].n_waves) + 32);
+    });
+    size_t o = 0;
+    p.args = o;
+    o = up256(o + sizeof(BatchArgs) * n_models);
+    p.maps = o;
+    o = up256(o + sizeof(CUtensorMap) * n_models);
+    p.items = o;
+    o = up256(o + sizeof(BatchItem) * p.items_h.size());
+    p.nslots = o;
+    o = up256(o + sizeof(int) * n_models);
+    p.pdone = o;
+    o = up256(o + sizeof(void *) * n_models);
+    p.pnll = o;
+    o = up256(o + sizeof(void *) * n_models);
+    p.pgrad = o;
+    o = up256(o + sizeof(void *) * n_models);
+    p.zero = o;
+    p.lpart.resize(n_models);
+    p.kflags.resize(n_models);
+    for (int i = 0; i < n_models; ++i) {
+        p.lpart[i] = o;
+        o = up256(o + (size_t)p.slots[i] * 4 * nch * kKC * 8);
+        p.kflags[i] = o;
+        o = up256(o + (size_t)nch * 2 * 4);
+    }
+    p.zero_bytes = o - p.zero;
+    p.scratch = o;
+    p.wimg.resize(n_models);
+    p.gpart.resize(n_models);
+    p.mv.resize(n_models);
+    p.T.resize(n_models);
+    for (int i = 0; i < n_models; ++i) {
+        const int F = batched_features(m[i].n_waves);
+        p.wimg[i] = o;
+        o = up256(o + w_image_bytes(F, nch));
+        p.gpart[i] = o;
+        o = up256(o + (size_t)p.slots[i] * nch * 128 * F * 4);
+        p.mv[i] = o;
+        o = up256(o + (size_t)K * (2 * m[i].n_waves + 1) * 8);
+        p.T[i] = o;
+        o = up256(o + (size_t)K * 4);
+    }
+    p.total = o;
+    return p;
+}
+
+}  // namespace
+
+size_t batched_plan_bytes(const BatchModelDesc *models, int n_models, int xs, int K, int num_sms,
+                          int items_per_sm, int *n_items)
+{
+    const PlanLayout p = plan_layout(models, n_models, xs, K, num_sms, items_per_sm);
+    if (n_items)
+        *n_items = (int)p.items_h.size();
+    return p.total;
+}
+
+cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_models, int xs,
+                               int K, int num_sms, int items_per_sm, cudaStream_t s)
+{
+    if ((xs != 1 && xs != 2) || K < 1 || n_models < 1)
+        return cudaErrorInvalidValue;
+    const PlanLayout p = plan_layout(models, n_models, xs, K, num_sms, items_per_sm);
+    char *d = static_cast<char *>(plan);
+    std::vector<char> h(p.scratch, 0);
+    const int nch = (K + kKC - 1) / kKC;
+    for (int i = 0; i < n_models; ++i) {
+        const BatchModelDesc &m = models[i];
+        if (K > batched_max_k(m.n_waves, xs))
+            return cudaErrorInvalidValue;
+        BatchArgs a{};
+        a.n_waves = m.n_waves;
+        a.F = batched_features(m.n_waves);
+        a.XS = xs;
+        a.K = K;
+        a.n_chunks = nch;
+        a.n_events = m.n_events;
+        a.V = m.V;
+        a.M = m.M;
+        a.sum_e = m.sum_e;
+        a.wimg = reinterpret_cast<unsigned char *>(d + p.wimg[i]);
+        a.gpart = reinterpret_cast<float *>(d + p.gpart[i]);
+        a.lpart = reinterpret_cast<long long *>(d + p.lpart[i]);
+        a.mv = reinterpret_cast<double *>(d + p.mv[i]);
+        a.T = reinterpret_cast<int *>(d + p.T[i]);
+        a.kflags = reinterpret_cast<unsigned *>(d + p.kflags[i]);
+        a.status = m.status;
+        memcpy(&h[p.args + i * sizeof(BatchArgs)], &a, sizeof a);
+        memcpy(&h[p.maps + i * sizeof(CUtensorMap)], &m.xmap, sizeof(CUtensorMap));
+        memcpy(&h[p.nslots + i * sizeof(int)], &p.slots[i], sizeof(int));
+        memcpy(&h[p.pdone + i * sizeof(void *)], &m.done, sizeof(void *));
+        memcpy(&h[p.pnll + i * sizeof(void *)], &m.nll, sizeof(void *));
+        memcpy(&h[p.pgrad + i * sizeof(void *)], &m.grad, sizeof(void *));
+    }
+    memcpy(&h[p.items], p.items_h.data(), p.items_h.size() * sizeof(BatchItem));
+    // the host vector is staged through a synchronous copy: it goes away here
+    cudaError_t e = cudaMemcpyAsync(d, h.data(), p.scratch, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(s);
+    return e;
+}
+
+cudaError_t launch_batched_items(void *plan, const BatchModelDesc *models, int n_models, int xs,
+                                 int K, int num_sms, int items_per_sm, cudaStream_t s)
+{
+    const PlanLayout p = plan_layout(models, n_models, xs, K, num_sms, items_per_sm);
+    char *d = static_cast<char *>(plan);
+    const int nch = (K + kKC - 1) / kKC;
+    uint32_t smem = 0;
+    for (int i = 0; i < n_models; ++i)
+        smem = std::max(smem, batch_smem(batched_features(models[i].n_waves), xs, batch_hpt(K)).bytes);
+    cudaError_t e = cudaMemsetAsync(d + p.zero, 0, p.zero_bytes, s);
+    if (e != cudaSuccess)
+        return e;
+    const BatchArgs *args = reinterpret_cast<const BatchArgs *>(d + p.args);
+    const int bpm = nch * 2 * kWSlices;
+    batched_items_prep<<<n_models * bpm, 256, 0, s>>>(args, bpm);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    const BatchItem *items = reinterpret_cast<const BatchItem *>(d + p.items);
+    const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(d + p.maps);
+    const int n_items = (int)p.items_h.size();
+    if (xs == 2)
+        batched_items_kernel<2><<<n_items, kThreads, smem, s>>>(items, args, maps);
+    else
+        batched_items_kernel<1><<<n_items, kThreads, smem, s>>>(items, args, maps);
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return e;
+    batched_items_finalize<<<n_models * K, 64, 0, s>>>(
+        args, reinterpret_cast<const int *>(d + p.nslots), K,
+        reinterpret_cast<int *const *>(d + p.pdone), reinterpret_cast<double *const *>(d + p.pnll),
+        reinterpret_cast<double *const *>(d + p.pgrad));
     return cudaGetLastError();
 }
 

@@ -1683,6 +1683,13 @@ struct pwa_batch {
     double *d_buf = nullptr, *h_buf = nullptr;  // V | nll | grad | status
     cudaGraphExec_t exec = nullptr;
     int graph_k = 0;
+    // one launch over work items of every model (the default), or, with
+    // PWA_BATCH_MODE=graph, a graph of per-model launches
+    bool per_model = false;
+    void *plan = nullptr;        // device plan of the one-launch form (for graph_k)
+    size_t plan_bytes = 0;
+    int items_per_sm = 4;        // work granularity (pwa_batch_autotune picks it)
+    int num_sms = 0;
     char err[512] = {0};
 };
 
@@ -1704,6 +1711,36 @@ static void batch_drop_graph(pwa_batch *b)
         cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
     b->graph_k = 0;
+    if (b->plan)
+        cudaFree(b->plan);
+    b->plan = nullptr;
+    b->plan_bytes = 0;
+}
+
+// The models as the one-launch form sees them, for K sets per model.
+static std::vector<BatchModelDesc> batch_descs(pwa_batch *b, int K)
+{
+    const int nm = (int)b->models.size();
+    const size_t nv = 2 * (size_t)K * b->sum_n;
+    double *dV = b->d_buf, *dN = dV + nv, *dG = dN + (size_t)nm * K;
+    int *dS = reinterpret_cast<int *>(dG + nv);
+    std::vector<BatchModelDesc> d(nm);
+    size_t off = 0;
+    for (int m = 0; m < nm; ++m) {
+        const pwa_ctx *c = b->models[m];
+        d[m].xmap = c->xbf_map;
+        d[m].n_events = c->n_data;
+        d[m].n_waves = c->N;
+        d[m].sum_e = c->xsum;
+        d[m].M = c->M;
+        d[m].V = dV + off;
+        d[m].nll = dN + (size_t)m * K;
+        d[m].grad = dG + off;
+        d[m].status = dS + 2 * m;
+        d[m].done = dS + 2 * m + 1;
+        off += 2 * (size_t)K * b->n_waves[m];
+    }
+    return d;
 }
 
 int pwa_batch_destroy(pwa_batch *b)
@@ -1759,6 +1796,12 @@ int pwa_batch_create(pwa_batch **out, int device, int n_models, const int *n_wav
     pwa_batch *b = new pwa_batch();
     b->device = device;
     b->max_k = max_k;
+    if (const char *v = getenv("PWA_BATCH_MODE"))
+        b->per_model = strcmp(v, "graph") == 0;
+    if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        b->num_sms = 1;
+    }
     b->n_waves.assign(n_waves, n_waves + n_models);
     b->sum_n = std::accumulate(b->n_waves.begin(), b->n_waves.end(), 0);
     auto bail = [&](int code) {
@@ -1851,16 +1894,38 @@ int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, do
         off[m] = off[m - 1] + 2 * (size_t)K * b->n_waves[m - 1];
     if (!b->exec || b->graph_k != K) {
         batch_drop_graph(b);
+        std::vector<BatchModelDesc> descs;
+        const int xs = b->models[0]->xs;
+        if (!b->per_model) {
+            // the plan of the one-launch form: arguments, maps and work items
+            descs = batch_descs(b, K);
+            b->plan_bytes = batched_plan_bytes(descs.data(), nm, xs, K, b->num_sms,
+                                               b->items_per_sm, nullptr);
+            if (cudaMalloc(&b->plan, b->plan_bytes) != cudaSuccess) {
+                cudaGetLastError();
+                b->plan = nullptr;
+                return bfail(b, PWA_ENOMEM, "batch plan (%zu bytes)", b->plan_bytes);
+            }
+            const cudaError_t pe = batched_plan_build(b->plan, descs.data(), nm, xs, K, b->num_sms,
+                                                      b->items_per_sm, b->stream);
+            if (pe != cudaSuccess) {
+                cudaGetLastError();
+                return bfail(b, PWA_ECUDA, "batch plan: %s", cudaGetErrorString(pe));
+            }
+        }
         cudaGraph_t graph = nullptr;
         cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
         int rc = PWA_OK;
         if (e == cudaSuccess)
             e = cudaMemsetAsync(dS, 0, (size_t)nm * 2 * sizeof(int), b->stream);
-        if (e == cudaSuccess)
+        if (e == cudaSuccess && !b->per_model)
+            e = launch_batched_items(b->plan, descs.data(), nm, xs, K, b->num_sms, b->items_per_sm,
+                                     b->stream);
+        if (e == cudaSuccess && b->per_model)
             e = cudaEventRecord(b->ev_fork, b->stream);
-        for (int s = 0; s < kBatchStreams && e == cudaSuccess; ++s)
+        for (int s = 0; s < kBatchStreams && e == cudaSuccess && b->per_model; ++s)
             e = cudaStreamWaitEvent(b->side[s], b->ev_fork, 0);
-        for (int i = 0; i < nm && e == cudaSuccess && !rc; ++i) {
+        for (int i = 0; i < nm && e == cudaSuccess && !rc && b->per_model; ++i) {
             const int m = b->order[i];
             pwa_ctx *c = b->models[m];
             c->stream = b->side[i % kBatchStreams];
@@ -1869,7 +1934,7 @@ int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, do
             if (rc)
                 bfail(b, rc, "model %d: %s", m, c->err);
         }
-        for (int s = 0; s < kBatchStreams && e == cudaSuccess; ++s) {
+        for (int s = 0; s < kBatchStreams && e == cudaSuccess && b->per_model; ++s) {
             e = cudaEventRecord(b->ev_join[s], b->side[s]);
             if (e == cudaSuccess)
                 e = cudaStreamWaitEvent(b->stream, b->ev_join[s], 0);

@@ -449,6 +449,34 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
                            void *scratch, int grid, int *status, int *done, double *nll,
                            double *grad, cudaStream_t s);
 
+// The uneven model batch in one launch (k_batched.cu): work items, each a
+// contiguous range of one model's 128-event tiles, about num_sms *
+// items_per_sm in all with equal estimated cost; one kernel takes them all
+// (one CTA per item), a prep kernel and a final kernel serve every model.
+struct BatchModelDesc {
+    CUtensorMap xmap;          // the model's BF16 slices (encode_bf16_planes_map)
+    int64_t n_events;
+    int n_waves;
+    const long long *sum_e;    // the sum of its event exponents
+    const double *M;           // [N][N] complex
+    const double *V;           // [K][N] complex, device
+    double *nll;               // [K]
+    double *grad;              // [K][N] complex, may be null
+    int *status;               // status bits OR-ed here
+    int *done;                 // incremented once per set, may be null
+};
+// Bytes of the plan (device buffer) and its number of work items.
+size_t batched_plan_bytes(const BatchModelDesc *models, int n_models, int xs, int K, int num_sms,
+                          int items_per_sm, int *n_items);
+// Writes the plan (arguments, tensor maps, items, output pointers) into the
+// device buffer `plan`; synchronises the stream. Each model: K <= its
+// batched_max_k.
+cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_models, int xs,
+                               int K, int num_sms, int items_per_sm, cudaStream_t s);
+// One evaluation of every model (the plan built for the same arguments).
+cudaError_t launch_batched_items(void *plan, const BatchModelDesc *models, int n_models, int xs,
+                                 int K, int num_sms, int items_per_sm, cudaStream_t s);
+
 // k_nll_res.cu: free Breit-Wigner masses and widths
 struct ResArgs {
     int n_waves, n_free, pstride;
