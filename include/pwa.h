@@ -379,18 +379,34 @@ int pwa_nll_grad_noalloc(const float *d_planes, int64_t plane_pitch, int64_t n_e
  * loaded sample (a few evaluations of a fixed parameter set each, CUDA events
  * on the context's stream), and of the free-resonance kernel if resonance
  * samples are loaded; applies the fastest; records each choice in a JSON
- * cache file, one line per key (device name, SM count, form, n_waves), and
- * applies a cached choice instead of timing when the key is present. The
- * variants: the direct form's consumer groups per block (2 or 3 groups of
- * four warps, where both fit), the free-resonance kernel's blocks per SM
- * (1 to 3). The table and tensor-core forms have one launch shape each (set
- * by their shared- and tensor-memory budgets) and are reported as such.
+ * cache file, one line per key (device name, SM count, form, n_waves, and
+ * for the tensor-core form max_k and the precision), and applies a cached
+ * choice instead of timing when the key is present. The variants: the
+ * direct form's consumer groups per block (2 or 3 groups of four warps,
+ * where both fit); the tensor-core form's tile parameters for max_k sets per
+ * call, the sets per launch (multiples of 64 up to the launch's tensor- and
+ * shared-memory limit) and the X pipeline stages (2 up to what shared memory
+ * takes); the free-resonance kernel's blocks per SM (1 to 3). The table
+ * form has one launch shape (set by its shared-memory budget) and is
+ * reported as such.
  *   cache_path  file to read and update (NULL: time every call, no file)
  *   choice      receives a one-line summary (may be NULL), choice_len bytes
  * Results of the evaluation calls do not depend on the choice beyond float
  * summation order. Errors: PWA_ESTATE (nothing loaded), PWA_ECUDA, PWA_EINVAL
  * (an unreadable or unwritable cache file). */
 int pwa_autotune(pwa_ctx *ctx, const char *cache_path, char *choice, int choice_len);
+
+/* Launch-shape autotuner of a model batch (the one-launch form; Sec. 2: many
+ * trial models are fitted to one data set): times the batch's evaluation for
+ * max_k sets with 1, 2, 4 or 8 work items per SM and 2 up to the most X
+ * pipeline stages shared memory takes, applies the fastest and records it
+ * in the JSON cache (cache_path as for pwa_autotune; a cached key is applied
+ * without timing). The key holds the device name, SM count, number of
+ * models, total waves and events, max_k and the precision. Results do not
+ * depend on the choice beyond float summation order. With
+ * PWA_BATCH_MODE=graph (per-model launches) there is nothing to tune.
+ * Errors: PWA_ESTATE (a model not loaded), PWA_ECUDA, PWA_EINVAL (cache). */
+int pwa_batch_autotune(pwa_batch *b, const char *cache_path, char *choice, int choice_len);
 
 /* Message describing the last error on ctx ("" if none); valid until the
  * next call on ctx. A NULL ctx gives the message of the last failed

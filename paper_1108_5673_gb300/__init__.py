@@ -164,6 +164,11 @@ class ModelBatch:
     def load_model(self, m, data_amp, mc_amp, n_mc_gen):
         self._abi.pwa_batch_load_model(self.b, m, data_amp, mc_amp, n_mc_gen)
 
+    def autotune(self, cache_path=None):
+        """Time the batch's launch shapes (work items per SM, X stages) and
+        apply the fastest (pwa_batch_autotune); returns a one-line summary."""
+        return self._abi.pwa_batch_autotune(self.b, cache_path)
+
     def nll_grad(self, Vs):
         """Vs: list over models of [K, n_waves[m]] complex arrays. Returns
         (nll [n_models, K], list of [K, n_waves[m]] gradients)."""

@@ -88,6 +88,7 @@ def load(path=LIB_PATH):
         "pwa_batch_nll_grad": ([P, P, I, P, P], I),
         "pwa_batch_last_error": ([P], ctypes.c_char_p),
         "pwa_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
+        "pwa_batch_autotune": ([P, ctypes.c_char_p, ctypes.c_char_p, I], I),
         "pwa_hessian": ([P, P, P], I),
         "pwa_hessian_async": ([P, P, P], I),
         "pwa_nll_grad_res_async": ([P, P, P, P, P], I),
@@ -444,6 +445,13 @@ def pwa_autotune(ctx, cache_path=None):
     """Returns the one-line summary of the choices applied."""
     buf = ctypes.create_string_buffer(512)
     _check(ctx, load().pwa_autotune(ctx, cache_path.encode() if cache_path else None, buf, 512))
+    return buf.value.decode()
+
+
+def pwa_batch_autotune(b, cache_path=None):
+    """Returns the one-line summary of the choice applied to the model batch."""
+    buf = ctypes.create_string_buffer(512)
+    _bcheck(b, load().pwa_batch_autotune(b, cache_path.encode() if cache_path else None, buf, 512))
     return buf.value.decode()
 
 

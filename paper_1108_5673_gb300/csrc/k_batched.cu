@@ -1,7 +1,7 @@
 // Batched evaluation of NLL and gradient for K parameter sets on the
 // tensor cores (tcgen05, BF16 operands, FP32 accumulation in tensor memory).
 //
-// The paper runs thousands of fits from different starting parameters and
+// The paper runs a great many fits from different starting parameters and
 // models (Sec. 2); evaluating K parameter sets against the same events turns
 // the direct form into two chained products per tile of 128 events:
 //   S[e][(k,re/im)] = sum_f A[e][f] W[(k,re/im)][f]            (GEMM 1)
@@ -116,6 +116,7 @@ struct BatchArgs {
     unsigned *kflags;           // [n_chunks * 2] domain bits per half chunk
     double *mv;                 // [K][2N + 1]: M V and V^H M V
     int *status;
+    int nxs_req;                // X stages asked for (0: as many as fit)
 };
 
 struct Smem {
@@ -134,7 +135,7 @@ __host__ __device__ inline uint32_t w_image_bytes(int F, int n_chunks)
 // that hold sets (its first part), then as many X stages as fit (2..kXSMax),
 // then R'. Small K leave room for a deeper X pipeline, which their short
 // per-tile work needs to hide the loads.
-__host__ __device__ inline Smem batch_smem(int F, int xs, int hpt)
+__host__ __device__ inline Smem batch_smem(int F, int xs, int hpt, int nxs_req = 0)
 {
     const int kb = (F + 63) / 64;
     Smem s;
@@ -143,6 +144,8 @@ __host__ __device__ inline Smem batch_smem(int F, int xs, int hpt)
     const int64_t room = (int64_t)kMaxSmem - 1024 - kRBytes - (int64_t)s.w_bytes;
     const int fit = room > 0 ? (int)(room / stage) : 0;
     s.nxs = fit < 2 ? 2 : (fit > kXSMax ? kXSMax : fit);
+    if (nxs_req >= 2 && nxs_req < s.nxs)
+        s.nxs = nxs_req;
     s.w_off = 0;
     s.x_off = s.w_bytes;
     s.r_off = s.x_off + (uint32_t)s.nxs * stage;
@@ -284,7 +287,7 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
     const int NCH = a.n_chunks;
     // half chunks per tile that hold parameter sets (a last half past K is skipped)
     const int HPT = batch_hpt(a.K);
-    const Smem L = batch_smem(F, XS, HPT);
+    const Smem L = batch_smem(F, XS, HPT, a.nxs_req);
     const int NXS = L.nxs;
     unsigned char *base = smem_dyn + ((1024 - (smem_u32(smem_dyn) & 1023)) & 1023);
     unsigned char *sW = base + L.w_off;
@@ -867,6 +870,11 @@ int batched_max_k(int n_waves, int xs)
     return nch * kKC;
 }
 
+int batched_max_x_stages(int n_waves, int xs, int K)
+{
+    return batch_smem(batched_features(n_waves), xs, batch_hpt(K)).nxs;
+}
+
 size_t batched_scratch_bytes(int n_waves, int xs, int K, int grid)
 {
     return scratch_layout(batched_features(n_waves), xs, n_waves, K, grid).total;
@@ -897,7 +905,7 @@ cudaError_t launch_batched_encode(const float *planes, int64_t pitch, int64_t n,
 cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, int xs,
                            const long long *sum_e, const double *V, int K, const double *M,
                            void *scratch, int grid, int *status, int *done, double *nll,
-                           double *grad, cudaStream_t s)
+                           double *grad, cudaStream_t s, int nxs)
 {
     const int F = batched_features(n_waves), nch = (K + kKC - 1) / kKC;
     if ((xs != 1 && xs != 2) || K < 1 || K > batched_max_k(n_waves, xs) || grid < 1)
@@ -921,6 +929,7 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
     a.T = reinterpret_cast<int *>(p + sl.T);
     a.kflags = reinterpret_cast<unsigned *>(p + sl.kflags);
     a.status = status;
+    a.nxs_req = nxs;
     cudaError_t e = cudaMemsetAsync(a.kflags, 0, nch * 2 * 4, s);
     if (e == cudaSuccess)
         e = cudaMemsetAsync(a.lpart, 0, (size_t)grid * 4 * nch * kKC * 8, s);
@@ -931,7 +940,7 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
     if (e != cudaSuccess)
         return e;
     const int n_tiles = (int)((n_events + kBM - 1) / kBM);
-    const uint32_t smem = batch_smem(F, xs, batch_hpt(K)).bytes;
+    const uint32_t smem = batch_smem(F, xs, batch_hpt(K), nxs).bytes;
     e = xs == 2 ? launch_main<2>(F, grid, smem, s, xmap, a, n_tiles)
                 : launch_main<1>(F, grid, smem, s, xmap, a, n_tiles);
     if (e != cudaSuccess)
@@ -1046,7 +1055,7 @@ size_t batched_plan_bytes(const BatchModelDesc *models, int n_models, int xs, in
 }
 
 cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_models, int xs,
-                               int K, int num_sms, int items_per_sm, cudaStream_t s)
+                               int K, int num_sms, int items_per_sm, int nxs, cudaStream_t s)
 {
     if ((xs != 1 && xs != 2) || K < 1 || n_models < 1)
         return cudaErrorInvalidValue;
@@ -1075,6 +1084,7 @@ cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_m
         a.T = reinterpret_cast<int *>(d + p.T[i]);
         a.kflags = reinterpret_cast<unsigned *>(d + p.kflags[i]);
         a.status = m.status;
+        a.nxs_req = nxs;
         memcpy(&h[p.args + i * sizeof(BatchArgs)], &a, sizeof a);
         memcpy(&h[p.maps + i * sizeof(CUtensorMap)], &m.xmap, sizeof(CUtensorMap));
         memcpy(&h[p.nslots + i * sizeof(int)], &p.slots[i], sizeof(int));
@@ -1091,14 +1101,15 @@ cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_m
 }
 
 cudaError_t launch_batched_items(void *plan, const BatchModelDesc *models, int n_models, int xs,
-                                 int K, int num_sms, int items_per_sm, cudaStream_t s)
+                                 int K, int num_sms, int items_per_sm, int nxs, cudaStream_t s)
 {
     const PlanLayout p = plan_layout(models, n_models, xs, K, num_sms, items_per_sm);
     char *d = static_cast<char *>(plan);
     const int nch = (K + kKC - 1) / kKC;
     uint32_t smem = 0;
     for (int i = 0; i < n_models; ++i)
-        smem = std::max(smem, batch_smem(batched_features(models[i].n_waves), xs, batch_hpt(K)).bytes);
+        smem = std::max(smem,
+                        batch_smem(batched_features(models[i].n_waves), xs, batch_hpt(K), nxs).bytes);
     cudaError_t e = cudaMemsetAsync(d + p.zero, 0, p.zero_bytes, s);
     if (e != cudaSuccess)
         return e;

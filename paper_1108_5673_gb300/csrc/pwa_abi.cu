@@ -46,6 +46,8 @@ struct pwa_ctx {
     int n_lambda = 1;           // incoherent components per event (data planes hold L N waves)
     bool incoh_tma = false;     // incoherent direct form through the TMA-fed kernel
     int tune_groups = 0;        // direct form: consumer groups (0 = default rule)
+    int tune_tc_nxs = 0;        // tensor-core form: X stages (0 = as many as fit)
+    int tune_tc_per = 0;        // tensor-core form: sets per launch (0 = the even split)
     // host evaluations replayed as CUDA graphs (copy in, kernels, copy out),
     // one per (K, with gradient); stale once `epoch` moves (a new sample, form
     // or launch shape)
@@ -357,12 +359,15 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         // launches of near-equal size (multiples of 64 sets): each launch reads the data once
         const int kmax = batched_max_k(N, c->xs);
         const int nl = (K + kmax - 1) / kmax;
-        const int per = ((K + nl - 1) / nl + 63) / 64 * 64;
+        int per = ((K + nl - 1) / nl + 63) / 64 * 64;
+        if (c->tune_tc_per > 0)
+            per = std::min(c->tune_tc_per, kmax);
         for (int k0 = 0; k0 < K; k0 += per) {
             const int kk = std::min(per, K - k0);
             cudaError_t e = launch_batched(&c->xbf_map, c->n_data, N, c->xs, c->xsum, dV + (size_t)2 * N * k0,
                                            kk, c->M, c->d_work, c->num_sms, status, done, dnll + k0,
-                                           dgrad ? dgrad + (size_t)2 * N * k0 : nullptr, c->stream);
+                                           dgrad ? dgrad + (size_t)2 * N * k0 : nullptr, c->stream,
+                                           c->tune_tc_nxs);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(c, PWA_ECUDA, "batched launch: %s", cudaGetErrorString(e));
@@ -1689,6 +1694,7 @@ struct pwa_batch {
     void *plan = nullptr;        // device plan of the one-launch form (for graph_k)
     size_t plan_bytes = 0;
     int items_per_sm = 4;        // work granularity (pwa_batch_autotune picks it)
+    int tune_nxs = 0;            // X stages of the tensor-core kernel (0 = as many as fit)
     int num_sms = 0;
     char err[512] = {0};
 };
@@ -1873,19 +1879,12 @@ int pwa_batch_load_model(pwa_batch *b, int model, const void *data_amp, int64_t 
     return PWA_OK;
 }
 
-int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, double *grad)
+// The graph of one evaluation of every model for K sets (and, in the
+// one-launch form, its plan), built on first use for K and kept until a
+// model is reloaded or the launch shape changes.
+static int batch_prepare(pwa_batch *b, int K)
 {
-    if (!b)
-        return PWA_EINVAL;
-    if (!V_all || !nll)
-        return bfail(b, PWA_EINVAL, "null V_all or nll");
-    if (K < 1 || K > b->max_k)
-        return bfail(b, PWA_EINVAL, "K=%d outside [1, max_k=%d]", K, b->max_k);
     const int nm = (int)b->models.size();
-    for (int m = 0; m < nm; ++m)
-        if (!b->models[m]->loaded || !b->models[m]->has_norm)
-            return bfail(b, PWA_ESTATE, "model %d has no samples (pwa_batch_load_model)", m);
-    DeviceGuard g(b->device);
     const size_t nv = 2 * (size_t)K * b->sum_n;  // doubles of V (and of grad)
     double *dV = b->d_buf, *dN = dV + nv, *dG = dN + (size_t)nm * K;
     int *dS = reinterpret_cast<int *>(dG + nv);  // [nm][2]: flags, done
@@ -1907,7 +1906,7 @@ int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, do
                 return bfail(b, PWA_ENOMEM, "batch plan (%zu bytes)", b->plan_bytes);
             }
             const cudaError_t pe = batched_plan_build(b->plan, descs.data(), nm, xs, K, b->num_sms,
-                                                      b->items_per_sm, b->stream);
+                                                      b->items_per_sm, b->tune_nxs, b->stream);
             if (pe != cudaSuccess) {
                 cudaGetLastError();
                 return bfail(b, PWA_ECUDA, "batch plan: %s", cudaGetErrorString(pe));
@@ -1920,7 +1919,7 @@ int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, do
             e = cudaMemsetAsync(dS, 0, (size_t)nm * 2 * sizeof(int), b->stream);
         if (e == cudaSuccess && !b->per_model)
             e = launch_batched_items(b->plan, descs.data(), nm, xs, K, b->num_sms, b->items_per_sm,
-                                     b->stream);
+                                     b->tune_nxs, b->stream);
         if (e == cudaSuccess && b->per_model)
             e = cudaEventRecord(b->ev_fork, b->stream);
         for (int s = 0; s < kBatchStreams && e == cudaSuccess && b->per_model; ++s)
@@ -1953,6 +1952,28 @@ int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, do
         }
         b->graph_k = K;
     }
+    return PWA_OK;
+}
+
+int pwa_batch_nll_grad(pwa_batch *b, const double *V_all, int K, double *nll, double *grad)
+{
+    if (!b)
+        return PWA_EINVAL;
+    if (!V_all || !nll)
+        return bfail(b, PWA_EINVAL, "null V_all or nll");
+    if (K < 1 || K > b->max_k)
+        return bfail(b, PWA_EINVAL, "K=%d outside [1, max_k=%d]", K, b->max_k);
+    const int nm = (int)b->models.size();
+    for (int m = 0; m < nm; ++m)
+        if (!b->models[m]->loaded || !b->models[m]->has_norm)
+            return bfail(b, PWA_ESTATE, "model %d has no samples (pwa_batch_load_model)", m);
+    DeviceGuard g(b->device);
+    const size_t nv = 2 * (size_t)K * b->sum_n;  // doubles of V (and of grad)
+    double *dV = b->d_buf, *dN = dV + nv, *dG = dN + (size_t)nm * K;
+    int *dS = reinterpret_cast<int *>(dG + nv);  // [nm][2]: flags, done
+    int rc = batch_prepare(b, K);
+    if (rc)
+        return rc;
     double *h = b->h_buf;
     memcpy(h, V_all, nv * sizeof(double));
     cudaError_t e = cudaMemcpyAsync(dV, h, nv * sizeof(double), cudaMemcpyHostToDevice, b->stream);
@@ -2145,10 +2166,59 @@ int pwa_autotune(pwa_ctx *c, const char *cache_path, char *choice, int choice_le
             c->tune_groups = best;
             ++c->epoch;
             summary += buf;
-        } else {
-            snprintf(buf, sizeof buf, "%s form: one launch shape",
-                     c->form == PWA_FORM_TABLE ? "table" : "tensor-core");
+        } else if (c->form == PWA_FORM_TC) {
+            // tile parameters of the tensor-core form for K = max_k sets: sets
+            // per launch (multiples of 64 up to the launch limit) and X
+            // pipeline stages (2 up to what shared memory takes)
+            const int N = c->N, K = c->cfg.max_k;
+            char what[64];
+            snprintf(what, sizeof what, "tc-tiles|K%d|xs%d", K, c->xs);
+            const std::string key = tune_key(c, what);
+            int best = 0;
+            double best_us = 0.0;
+            if (!cache_lookup(cache_path, key, &best)) {
+                const size_t gK = (size_t)2 * N * K;
+                std::vector<double> V(gK, 0.0);
+                for (size_t i = 0; i < gK; i += 2)
+                    V[i] = 1.0;
+                double *dV = c->d_io + K + gK + 1;
+                int *ds = reinterpret_cast<int *>(c->d_io + K + gK);
+                CK(c, cudaMemcpyAsync(dV, V.data(), gK * sizeof(double), cudaMemcpyHostToDevice,
+                                      c->stream));
+                const int kmax = batched_max_k(N, c->xs);
+                for (int per = 64; per <= std::max(64, std::min(kmax, ((K + 63) / 64) * 64)); per += 64) {
+                    const int top = batched_max_x_stages(N, c->xs, std::min(per, K));
+                    for (int nxs = 2; nxs <= top; ++nxs) {
+                        c->tune_tc_per = per;
+                        c->tune_tc_nxs = nxs;
+                        double us = 0.0;
+                        const int rc = time_variant(
+                            c, [&] { return enqueue_eval(c, dV, K, c->d_io, c->d_io + K, ds, ds + 1); },
+                            2, 5, &us);
+                        if (rc)
+                            return rc;
+                        if (!best || us < best_us) {
+                            best = nxs * 10000 + per;
+                            best_us = us;
+                        }
+                    }
+                }
+                CK(c, cudaStreamSynchronize(c->stream));
+                if (cache_path && !cache_store(cache_path, key, best, best_us))
+                    return fail(c, PWA_EINVAL, "cannot write the tuning cache %s", cache_path);
+                snprintf(buf, sizeof buf,
+                         "tensor-core form: %d sets per launch, %d X stages (%.1f us for %d sets, timed)",
+                         best % 10000, best / 10000, best_us, K);
+            } else {
+                snprintf(buf, sizeof buf, "tensor-core form: %d sets per launch, %d X stages (cached)",
+                         best % 10000, best / 10000);
+            }
+            c->tune_tc_per = best % 10000;
+            c->tune_tc_nxs = best / 10000;
+            ++c->epoch;
             summary += buf;
+        } else {
+            summary += "table form: one launch shape";
         }
     }
     if (c->res_loaded && c->res_tma) {
@@ -2221,6 +2291,103 @@ int pwa_autotune(pwa_ctx *c, const char *cache_path, char *choice, int choice_le
     }
     if (choice && choice_len > 0)
         snprintf(choice, (size_t)choice_len, "%s", summary.c_str());
+    return PWA_OK;
+}
+
+int pwa_batch_autotune(pwa_batch *b, const char *cache_path, char *choice, int choice_len)
+{
+    if (!b)
+        return PWA_EINVAL;
+    const int nm = (int)b->models.size();
+    for (int m = 0; m < nm; ++m)
+        if (!b->models[m]->loaded || !b->models[m]->has_norm)
+            return bfail(b, PWA_ESTATE, "model %d has no samples (pwa_batch_load_model)", m);
+    char buf[256];
+    if (b->per_model) {
+        snprintf(buf, sizeof buf, "model batch: per-model graph, the models' own launch shapes");
+        if (choice && choice_len > 0)
+            snprintf(choice, (size_t)choice_len, "%s", buf);
+        return PWA_OK;
+    }
+    DeviceGuard g(b->device);
+    const int K = b->max_k, xs = b->models[0]->xs;
+    // the key: device, models (count, total waves and events), K, precision
+    int64_t n_events = 0;
+    for (pwa_ctx *c : b->models)
+        n_events += c->n_data;
+    char what[128];
+    snprintf(what, sizeof what, "batch|M%d|W%d|E%lld|K%d|xs%d", nm, b->sum_n, (long long)n_events,
+             K, xs);
+    const std::string key = tune_key(b->models[0], what);
+    int best = 0;
+    double best_us = 0.0;
+    if (!cache_lookup(cache_path, key, &best)) {
+        // V_a = 1 for every set of every model
+        const size_t nv = 2 * (size_t)K * b->sum_n;
+        std::vector<double> V(nv, 0.0);
+        for (size_t i = 0; i < nv; i += 2)
+            V[i] = 1.0;
+        if (cudaMemcpy(b->d_buf, V.data(), nv * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, PWA_ECUDA, "autotune: copy of V failed");
+        }
+        int top = 2;
+        for (int m = 0; m < nm; ++m)
+            top = std::max(top, batched_max_x_stages(b->n_waves[m], xs, K));
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+            cudaGetLastError();
+            return bfail(b, PWA_ECUDA, "autotune: event creation failed");
+        }
+        int rc = PWA_OK;
+        for (int ips : {1, 2, 4, 8}) {
+            for (int nxs = 2; nxs <= top && !rc; ++nxs) {
+                b->items_per_sm = ips;
+                b->tune_nxs = nxs;
+                batch_drop_graph(b);
+                if ((rc = batch_prepare(b, K)))
+                    break;
+                float ms = 0.f;
+                cudaError_t e = cudaGraphLaunch(b->exec, b->stream);   // warm-up
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(e0, b->stream);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r)
+                    e = cudaGraphLaunch(b->exec, b->stream);
+                if (e == cudaSuccess)
+                    e = cudaEventRecord(e1, b->stream);
+                if (e == cudaSuccess)
+                    e = cudaEventSynchronize(e1);
+                if (e == cudaSuccess)
+                    e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    rc = bfail(b, PWA_ECUDA, "autotune: %s", cudaGetErrorString(e));
+                    break;
+                }
+                const double us = 1e3 * ms / 3;
+                if (!best || us < best_us) {
+                    best = nxs * 100 + ips;
+                    best_us = us;
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc)
+            return rc;
+        if (cache_path && !cache_store(cache_path, key, best, best_us))
+            return bfail(b, PWA_EINVAL, "cannot write the tuning cache %s", cache_path);
+        snprintf(buf, sizeof buf, "model batch: %d work items per SM, %d X stages (%.1f us for %d sets, timed)",
+                 best % 100, best / 100, best_us, K);
+    } else {
+        snprintf(buf, sizeof buf, "model batch: %d work items per SM, %d X stages (cached)", best % 100,
+                 best / 100);
+    }
+    b->items_per_sm = best % 100;
+    b->tune_nxs = best / 100;
+    batch_drop_graph(b);
+    if (choice && choice_len > 0)
+        snprintf(choice, (size_t)choice_len, "%s", buf);
     return PWA_OK;
 }
 

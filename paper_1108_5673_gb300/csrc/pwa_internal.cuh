@@ -444,10 +444,13 @@ cudaError_t batched_configure();
 // the sum over events of the event exponents.
 cudaError_t launch_batched_encode(const float *planes, int64_t pitch, int64_t n, int n_waves, int xs,
                                   void *out, long long *sum_e, cudaStream_t s);
+// nxs: X pipeline stages (0: as many as shared memory takes; the autotuner
+// may ask for fewer, from 2 up to batched_max_x_stages)
 cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, int xs,
                            const long long *sum_e, const double *V, int K, const double *M,
                            void *scratch, int grid, int *status, int *done, double *nll,
-                           double *grad, cudaStream_t s);
+                           double *grad, cudaStream_t s, int nxs = 0);
+int batched_max_x_stages(int n_waves, int xs, int K);
 
 // The uneven model batch in one launch (k_batched.cu): work items, each a
 // contiguous range of one model's 128-event tiles, about num_sms *
@@ -472,10 +475,10 @@ size_t batched_plan_bytes(const BatchModelDesc *models, int n_models, int xs, in
 // device buffer `plan`; synchronises the stream. Each model: K <= its
 // batched_max_k.
 cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_models, int xs,
-                               int K, int num_sms, int items_per_sm, cudaStream_t s);
+                               int K, int num_sms, int items_per_sm, int nxs, cudaStream_t s);
 // One evaluation of every model (the plan built for the same arguments).
 cudaError_t launch_batched_items(void *plan, const BatchModelDesc *models, int n_models, int xs,
-                                 int K, int num_sms, int items_per_sm, cudaStream_t s);
+                                 int K, int num_sms, int items_per_sm, int nxs, cudaStream_t s);
 
 // k_nll_res.cu: free Breit-Wigner masses and widths
 struct ResArgs {

@@ -68,3 +68,59 @@ def test_no_cache_file(pwa):
         L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
         L.build_norm()
         assert "timed" in L.autotune(None)
+
+
+def test_tensor_core_tile_tuning(pwa, tmp_path):
+    """The tensor-core form's tile parameters (sets per launch, X stages):
+    timed, cached, applied; the results agree with the default shape to
+    float summation order and with the oracle on the BFP16 inputs."""
+    from test_gpu_batched import bfp_amplitudes, nll_tol
+    wl = synth.mixture_workload("t", synth.waves_linear(16), 100_000, 20_000)
+    K = 128
+    Vs = synth.start_points(16, K, seed=9)
+    cache = str(tmp_path / "tune.json")
+    with pwa.Likelihood(16, forms=pwa.PWA_FORM_TC, max_k=K) as L:
+        L.load_events(wl.A_data, wl.A_mc, wl.n_gen)
+        L.build_norm()
+        L.set_form(pwa.PWA_FORM_TC)
+        n0, g0 = L.nll_grad(Vs)
+        s1 = L.autotune(cache)
+        assert "tensor-core form" in s1 and "timed" in s1
+        n1, g1 = L.nll_grad(Vs)
+        assert "cached" in L.autotune(cache)
+    rows = json.load(open(cache))
+    (key, row), = rows.items()
+    assert "tc-tiles|K128" in key and row["choice"] % 10000 in (64, 128)
+    assert 2 <= row["choice"] // 10000 <= 6
+    assert np.max(np.abs(n1 - n0) / np.abs(n0)) <= 1e-12
+    assert np.linalg.norm(g1 - g0) <= 1e-6 * np.linalg.norm(g0)
+    M = oracle.norm_matrix(wl.A_mc, wl.n_gen)
+    no, _, _ = oracle.nll_amp(bfp_amplitudes(wl.A_data, 2), M, Vs[0])
+    assert abs(n1[0] - no) <= nll_tol(100_000)
+
+
+def test_model_batch_tuning(pwa, tmp_path):
+    """The model batch's launch shape (work items per SM, X stages): timed,
+    cached and applied; results agree with the untuned batch to float
+    summation order."""
+    spec = [(8, 20_000), (20, 30_000), (33, 10_000)]
+    wls = [synth.mixture_workload("b%d" % j, synth.waves_linear(N), n, 2 * n, seed_data=70 + j)
+           for j, (N, n) in enumerate(spec)]
+    K = 16
+    Vs = [synth.start_points(N, K, seed=80 + j) for j, (N, _) in enumerate(spec)]
+    cache = str(tmp_path / "tune.json")
+    with pwa.ModelBatch([N for N, _ in spec], K) as B:
+        for j, w in enumerate(wls):
+            B.load_model(j, w.A_data, w.A_mc, w.n_gen)
+        n0, g0 = B.nll_grad(Vs)
+        s1 = B.autotune(cache)
+        assert "model batch" in s1 and "timed" in s1
+        n1, g1 = B.nll_grad(Vs)
+        assert "cached" in B.autotune(cache)
+        n2, g2 = B.nll_grad(Vs)
+    (key, row), = json.load(open(cache)).items()
+    assert "batch|M3" in key and row["choice"] % 100 in (1, 2, 4, 8)
+    assert np.array_equal(n1, n2)
+    assert np.max(np.abs(n1 - n0) / np.abs(n0)) <= 1e-12
+    for a, b in zip(g0, g1):
+        assert np.linalg.norm(a - b) <= 1e-6 * np.linalg.norm(a)
