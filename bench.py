@@ -33,6 +33,13 @@ between steps where the inputs fit in it); `e2e` times the public host call
 (inputs from host memory, results back) with a wall clock. With N > 1
 (torchrun) every rank runs an independent replica on its own GPU (weak
 scaling, no collective on the data path); rank 0 prints.
+
+The default line also carries, timed in the same run on the same GPU with
+fewer steps, `secondary`: the table form of the headline sample and K = 256
+sets on the tensor cores (4M events x 32 waves, generated on the device),
+each with its own roofline and clocks (--no-secondary skips them); and next
+to `cpu_baseline` (the oracle on one thread) `cpu_baseline_all_cores` (the
+unchanged oracle on one chunk of events per host core, spawned processes).
 """
 from __future__ import annotations
 
@@ -132,6 +139,50 @@ def timed_oracle(fn, budget_s):
     return (time.perf_counter() - t0) / n, n
 
 
+_CHUNK = {}
+
+
+def _oracle_chunk_init(shm_name, shape, M, V):
+    from multiprocessing import shared_memory
+    _CHUNK["shm"] = shared_memory.SharedMemory(name=shm_name)
+    _CHUNK["A"] = np.ndarray(shape, dtype=np.complex128, buffer=_CHUNK["shm"].buf)
+    _CHUNK["M"], _CHUNK["V"] = M, V
+
+
+def _oracle_chunk_eval(bounds):
+    import oracle
+    lo, hi = bounds
+    return oracle.nll_amp(_CHUNK["A"][lo:hi], _CHUNK["M"], _CHUNK["V"])[0]
+
+
+def oracle_all_cores(A, M, V, budget_s):
+    """The oracle as it stands on all host cores: the events split into one
+    contiguous chunk per core, each evaluated by oracle.nll_amp in its own
+    spawned process (the MC term is added per chunk; its cost is O(N^2)).
+    Returns (seconds per full evaluation, steps timed, processes)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    P = os.cpu_count() or 1
+    A = np.ascontiguousarray(A, dtype=np.complex128)
+    shm = shared_memory.SharedMemory(create=True, size=A.nbytes)
+    try:
+        np.ndarray(A.shape, dtype=np.complex128, buffer=shm.buf)[:] = A
+        n = A.shape[0]
+        bounds = [(n * k // P, n * (k + 1) // P) for k in range(P)]
+        with mp.get_context("spawn").Pool(P, initializer=_oracle_chunk_init,
+                                          initargs=(shm.name, A.shape, M, V)) as pool:
+            pool.map(_oracle_chunk_eval, bounds)          # warm-up (imports, library load)
+            t0, k = time.perf_counter(), 0
+            while time.perf_counter() - t0 < budget_s or k < 2:
+                pool.map(_oracle_chunk_eval, bounds)
+                k += 1
+            dt = (time.perf_counter() - t0) / k
+    finally:
+        shm.close()
+        shm.unlink()
+    return dt, k, P
+
+
 # ---- workloads: each sets up the library and returns a Job ---------------------
 
 class Job:
@@ -174,6 +225,15 @@ def job_direct(pwa, torch, stream, local, rank, form="amp"):
                 "sample": "%d full NLL+grad evaluations of the same 1M-event, 20-wave sample "
                           "(M precomputed), FP64 C oracle, 1 thread" % k}
 
+    def cpu_baseline_all():
+        import oracle
+        Mo = oracle.norm_matrix_blas(wl.A_mc, wl.n_gen)
+        dt, k, P = oracle_all_cores(wl.A_data, Mo, V, 8.0)
+        return {"value": 1.0 / dt, "unit": UNIT, "cores": P, "kind": "oracle",
+                "sample": "%d full NLL+grad evaluations of the same sample, the 1M events split "
+                          "into %d chunks evaluated by the unchanged FP64 C oracle in %d spawned "
+                          "processes" % (k, P, P)}
+
     table = form == "table"
     return Job(
         name=form if table else "direct", lib=L,
@@ -184,13 +244,22 @@ def job_direct(pwa, torch, stream, local, rank, form="amp"):
         config={"n_waves": N_WAVES, "n_data": N_DATA, "n_mc_acc": N_MC, "n_mc_gen": wl.n_gen,
                 "K": 1, "form": form, "build_norm_s": build_norm_s},
         roof={"bound": "hbm", "bytes": (4.0 * N_WAVES ** 2 if table else 8.0 * N_WAVES) * N_DATA},
-        dtype="f32", h2d=16 * N_WAVES + 8, d2h=8 + 16 * N_WAVES + 8, cpu_baseline=cpu_baseline)
+        dtype="f32", h2d=16 * N_WAVES + 8, d2h=8 + 16 * N_WAVES + 8, cpu_baseline=cpu_baseline,
+        cpu_baseline_all=None if table else cpu_baseline_all)
 
 
-def job_tc(pwa, torch, stream, local, rank, precision="bfp16"):
+def job_tc(pwa, torch, stream, local, rank, precision="bfp16", gen="numpy"):
     import synth
     N, n, n_mc, K = 32, 4_000_000, 10_000_000, 256
-    wl = synth.multistart_scale()
+    if gen == "torch":
+        # the same sample shape from the torch generator on the device (the
+        # host generator takes ~40 s for these 14M events)
+        A_d, A_m, n_gen = synth.torch_mixture_workload(synth.waves_linear(N), n, n_mc,
+                                                       synth.SEED_DATA + rank)
+        wl = synth.Workload("pwa_4M_events_32_waves", synth.waves_linear(N), A_d, A_m, n_gen,
+                            synth.random_V(N, synth.SEED_DATA + rank))
+    else:
+        wl = synth.multistart_scale()
     Vs = synth.start_points(N, K, seed=synth.SEED_STARTS + rank) * 2.0
     prec = pwa.PWA_PREC_BFP8 if precision == "bfp8" else pwa.PWA_PREC_BFP16
     L = pwa.Likelihood(N, device=local, forms=pwa.PWA_FORM_TC, max_k=K, stream=stream.cuda_stream,
@@ -478,7 +547,8 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n_waves": N_WAVES,
-                                        "n_data": N_DATA, "n_mc_acc": N_MC},
+                                        "n_data": N_DATA, "n_mc_acc": N_MC, "n_mc_gen": wl.n_gen,
+                                        "K": 1, "form": "amp"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": "each step one full NLL+grad evaluation of the 1M-event sample"},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
@@ -513,6 +583,8 @@ def main():
                              "incoh", "incoh_table", "ampgen"])
     ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the table and tensor-core forms in the default line")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = DEFAULT_STEPS[args.workload] if args.impl == "gb300" else 3
@@ -558,7 +630,84 @@ def main():
         flush.fill_(float(i & 0xff))
         return flush.sum()
 
-    for i in range(args.warmup):
+    peaks = measured_peaks()
+    m = measure(job, args.steps, args.warmup, evict_l2, stream, dist, rank, local, pwa, torch)
+    total_ms_max, e2e_max = max_over_ranks(dist, [m["total_ms"], m["e2e_s"]], "cuda")
+    if rank != 0:
+        job.lib.close()
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    ev = job.evals_per_step
+    value = job_value(world, ev, args.steps, total_ms_max)
+    e2e_value = world * ev * args.steps / e2e_max
+    config = {"workload": job.workload}
+    config.update(job.config)
+    config.update({"l2": "flushed between timed steps (256 MB write + read back, untimed)"
+                   if job.flush else "inputs larger than L2 (129 MB), no flush",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "ms_per_step_back_to_back": m["b2b_ms"]})
+    if getattr(job, "note", None):
+        config["note"] = job.note
+    out = {
+        "metric": getattr(job, "metric", METRIC), "value": value,
+        "unit": getattr(job, "unit", UNIT), "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": job.dtype, "data": "synthetic",
+        "config": config, "roofline": roofline(job, m["total_ms"] / args.steps / 1e3, peaks),
+        "e2e": {"value": e2e_value, "unit": getattr(job, "unit", UNIT), "h2d_bytes_per_step": job.h2d,
+                "d2h_bytes_per_step": job.d2h},
+        "gpu_launches": job.launches_per_step * args.steps,
+        "status": m["status"],
+    }
+    if m["clocks"] is not None:
+        out["clocks"] = m["clocks"]
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = job.cpu_baseline()
+        if getattr(job, "cpu_baseline_all", None):
+            out["cpu_baseline_all_cores"] = job.cpu_baseline_all()
+    job.lib.close()
+    # The other forms of the method, timed in the same run on the same GPU
+    # (fewer steps): the table form of the same sample and K = 256 sets on
+    # the tensor cores (4M events x 32 waves).
+    if args.workload == "direct" and world == 1 and not args.no_secondary:
+        sec = {}
+        for name, make, steps in (
+                ("table", lambda: job_direct(pwa, torch, stream, local, rank, form="table"), 300),
+                ("tc", lambda: job_tc(pwa, torch, stream, local, rank, args.precision, gen="torch"), 40)):
+            j = make()
+            ms = measure(j, steps, 3, evict_l2, stream, None, rank, local, pwa, torch)
+            sec[name] = {
+                "workload": j.workload, "metric": getattr(j, "metric", METRIC),
+                "value": j.evals_per_step * steps / (ms["total_ms"] / 1e3),
+                "unit": getattr(j, "unit", UNIT), "steps": steps, "warmup": 3,
+                "ms_per_step": ms["total_ms"] / steps, "dtype": j.dtype,
+                "roofline": roofline(j, ms["total_ms"] / steps / 1e3, peaks),
+                "e2e": {"value": j.evals_per_step * steps / ms["e2e_s"],
+                        "unit": getattr(j, "unit", UNIT), "h2d_bytes_per_step": j.h2d,
+                        "d2h_bytes_per_step": j.d2h},
+                "gpu_launches": j.launches_per_step * steps, "status": ms["status"],
+                "config": dict(j.config, l2="flushed between timed steps" if j.flush
+                               else "inputs larger than L2 (129 MB), no flush",
+                               ms_per_step_back_to_back=ms["b2b_ms"])}
+            if ms["clocks"] is not None:
+                sec[name]["clocks"] = ms["clocks"]
+            out["gpu_launches"] += j.launches_per_step * steps
+            j.lib.close()
+            del j
+            torch.cuda.empty_cache()
+        out["secondary"] = sec
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+
+
+def measure(job, steps, warmup, evict_l2, stream, dist, rank, local, pwa, torch):
+    """Device-timed steps (CUDA events on the launching stream, L2 flushed
+    before each where the job asks), back-to-back steps, and end-to-end host
+    calls, with the clocks sampled during the timed steps."""
+    for i in range(warmup):
         if job.flush:
             evict_l2(i)
         job.step()
@@ -567,15 +716,15 @@ def main():
 
     # raw nvidia-smi samples of the timed region (summarised into the line)
     clock_path = os.path.join(os.environ.get("BENCH_CLOCKS_DIR", tempfile.gettempdir()),
-                              "bench_clocks_rank%d.csv" % rank)
+                              "bench_clocks_rank%d_%s.csv" % (rank, job.name))
     sampler = start_clock_sampler(clock_path) if rank == 0 else None
     time.sleep(0.3 if sampler else 0)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         if job.flush:
             evict_l2(i)                  # untimed
         starts[i].record(stream)
@@ -583,11 +732,10 @@ def main():
         ends[i].record(stream)
     torch.cuda.synchronize()
     status = job.sync()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     # back-to-back (no flush), for reference only
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nb = max(3, args.steps // 2)
+    nb = max(3, steps // 2)
     e0.record(stream)
     for _ in range(nb):
         job.step()
@@ -599,25 +747,20 @@ def main():
         job.host_step()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         job.host_step()
     e2e_s = time.perf_counter() - t0
+    clocks = None
     if sampler:
         sampler.terminate()
         sampler.wait()
+        clocks = summarise_clocks(clock_path, local)
+    return {"total_ms": total_ms, "b2b_ms": b2b_ms, "e2e_s": e2e_s, "status": status,
+            "clocks": clocks}
 
-    total_ms_max, e2e_max = max_over_ranks(dist, [total_ms, e2e_s], "cuda")
-    if rank != 0:
-        job.lib.close()
-        if dist:
-            dist.destroy_process_group()
-        return
 
-    ev = job.evals_per_step
-    value = job_value(world, ev, args.steps, total_ms_max)
-    e2e_value = world * ev * args.steps / e2e_max
-    avg_s = total_ms / args.steps / 1e3
-    peaks = measured_peaks()
+def roofline(job, avg_s, peaks):
+    """The dominant kernel against its roofline, from the average step time."""
     if job.roof["bound"] == "hbm":
         achieved = job.roof["bytes"] / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
@@ -638,34 +781,7 @@ def main():
                 "peak_note": "bf16 burst; the step time includes the small prep and final kernels"}
     roof.update({"traffic": TRAFFIC[job.name], "kernel": KERNELS[job.name],
                  "peak_kind": "nominal" if job.roof["bound"] == "alu" else peaks["kind"]})
-    config = {"workload": job.workload}
-    config.update(job.config)
-    config.update({"l2": "flushed between timed steps (256 MB write + read back, untimed)"
-                   if job.flush else "inputs larger than L2 (129 MB), no flush",
-                   "parallelism": "replicas" if world > 1 else "single",
-                   "ms_per_step_back_to_back": b2b_ms})
-    if getattr(job, "note", None):
-        config["note"] = job.note
-    out = {
-        "metric": getattr(job, "metric", METRIC), "value": value,
-        "unit": getattr(job, "unit", UNIT), "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": job.dtype, "data": "synthetic",
-        "config": config, "roofline": roof,
-        "e2e": {"value": e2e_value, "unit": getattr(job, "unit", UNIT), "h2d_bytes_per_step": job.h2d,
-                "d2h_bytes_per_step": job.d2h},
-        "gpu_launches": job.launches_per_step * args.steps,
-        "status": status,
-    }
-    if sampler:
-        out["clocks"] = summarise_clocks(clock_path, local)
-    if not args.no_cpu_baseline:
-        out["cpu_baseline"] = job.cpu_baseline()
-    print(json.dumps(out))
-    job.lib.close()
-    if dist:
-        dist.destroy_process_group()
-
+    return roof
 
 if __name__ == "__main__":
     main()
