@@ -62,6 +62,8 @@ def _load():
         lib.oracle_table_incoh.argtypes = [P, I64, I, I, P]
         lib.oracle_nll_incoh.argtypes = [P, I64, I, I, P, P, I, P, P]
         lib.oracle_nll_incoh.restype = I
+        lib.oracle_cov_amplitudes.argtypes = [P, I64, I, P, P, P, P]
+        lib.oracle_cov_amplitudes.restype = I
         _lib = lib
     return _lib
 
@@ -255,3 +257,21 @@ def amplitudes(m, costh, phi, waves):
     if rc:
         raise ValueError("a wave has |m| > l or l < 0")
     return A
+
+
+def covariant_amplitudes(p3, waves):
+    """Covariant tensor amplitudes of J/psi -> gamma X, X -> K+ K- (see
+    oracle_cov_amplitudes in pwa_oracle.c): p3 [n, 9] = 3-momenta (GeV) of the
+    photon, K+ and K- in the J/psi rest frame; `waves` holds (mass, width,
+    spin) with spin 0 or 2. Returns [n, 4, N] complex128: component l = 2 m +
+    p for J/psi helicity (+1, -1)[m] and photon polarization p."""
+    p3 = np.ascontiguousarray(p3, dtype=np.float64)
+    w = [(x.mass, x.width, x.spin) if hasattr(x, "spin") else tuple(x) for x in waves]
+    mass = _f64([x[0] for x in w])
+    width = _f64([x[1] for x in w])
+    spin = np.ascontiguousarray([x[2] for x in w], dtype=np.int32)
+    out = np.empty((p3.shape[0], 4, len(w)), dtype=np.complex128)
+    if _load().oracle_cov_amplitudes(_p(p3), p3.shape[0], len(w), _p(mass), _p(width), _p(spin),
+                                     _p(out)):
+        raise ValueError("a wave's spin is not 0 or 2")
+    return out

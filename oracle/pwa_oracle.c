@@ -707,3 +707,113 @@ int oracle_amplitudes(const double *kin, int64_t n, int N, const double *mass, c
     }
     return 0;
 }
+
+/* ---- Covariant tensor amplitudes: J/psi -> gamma X, X -> K+ K- -------------
+ * Paper Sec. 4: the framework builds its amplitudes on the GPU in the
+ * covariant tensor formalism. Written here from that formalism: 4-vectors in
+ * the J/psi rest frame, metric (+,-,-,-), a.b = a0 b0 - a.b(3).
+ *   p3[i] = (q, k1, k2): 3-momenta (GeV) of the photon, K+ and K-.
+ *   q = (|q|, q), k = (sqrt(mK^2 + |k|^2), k), p = k1 + k2, m^2 = p.p,
+ *   r = k1 - k2, rt = r - (r.p / p.p) p  (the relative momentum orthogonal to p).
+ * Unobserved: the J/psi helicity M = +1, -1 along the beam (z) axis,
+ *   psi(+1) = (0, -1, -i, 0)/sqrt2, psi(-1) = (0, 1, -i, 0)/sqrt2,
+ * and the photon's linear polarization lam = 1, 2, real and transverse,
+ *   e1 = (0, z x q / |z x q|) (x when q is along z), e2 = (0, q/|q| x e1).
+ * Component l = 2 (M index) + (lam index), M index 0 for +1.
+ * Wave a (mass M_a, width G_a, spin s_a):
+ *   s = 0: A = BW(m^2) psi.e
+ *   s = 2: A = BW(m^2) B2(Q) t(psi, e),
+ *          t(u, w) = (u.rt)(w.rt) - (1/3)(rt.rt)(u.w - (u.p)(w.p)/p.p),
+ *          the contraction of psi and e with the symmetric, traceless tensor
+ *          of rank 2 orthogonal to p built from rt;
+ *          Q^2 = m^2/4 - mK^2, B2 = sqrt(13 / (Q^4 + 3 Q^2 Q0^2 + 9 Q0^4)),
+ *          Q0 = 0.197327 GeV (an interaction radius of 1 fm);
+ *   BW(m^2) = 1 / (M^2 - m^2 - i M G).
+ * out[((i * 4 + l) * N + a) * 2 + {0, 1}]. Returns -1 for a spin other than
+ * 0 or 2. */
+static double mdot(const double *a, const double *b)
+{
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+}
+
+int oracle_cov_amplitudes(const double *p3, int64_t n, int N, const double *mass,
+                          const double *width, const int *spin, double *out)
+{
+    const double mK = 0.493677, Q0 = 0.197327, isq2 = 0.70710678118654752440;
+    for (int a = 0; a < N; ++a)
+        if (spin[a] != 0 && spin[a] != 2)
+            return -1;
+    for (int64_t i = 0; i < n; ++i) {
+        const double *v = p3 + 9 * i;
+        double q[4], k1[4], k2[4], p[4], r[4], rt[4];
+        const double qq = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        q[0] = qq;
+        k1[0] = sqrt(mK * mK + v[3] * v[3] + v[4] * v[4] + v[5] * v[5]);
+        k2[0] = sqrt(mK * mK + v[6] * v[6] + v[7] * v[7] + v[8] * v[8]);
+        for (int c = 0; c < 3; ++c) {
+            q[c + 1] = v[c];
+            k1[c + 1] = v[3 + c];
+            k2[c + 1] = v[6 + c];
+        }
+        for (int c = 0; c < 4; ++c) {
+            p[c] = k1[c] + k2[c];
+            r[c] = k1[c] - k2[c];
+        }
+        const double pp = mdot(p, p), rp = mdot(r, p);
+        for (int c = 0; c < 4; ++c)
+            rt[c] = r[c] - rp / pp * p[c];
+        const double rr = mdot(rt, rt);
+        const double Q2 = pp / 4.0 - mK * mK;
+        const double b2 = sqrt(13.0 / (Q2 * Q2 + 3.0 * Q2 * Q0 * Q0 + 9.0 * Q0 * Q0 * Q0 * Q0));
+        /* photon polarizations */
+        double e[2][4];
+        double ux = -q[2], uy = q[1];           /* z x q */
+        double un = sqrt(ux * ux + uy * uy);
+        if (un > 1e-12 * qq) {
+            e[0][1] = ux / un;
+            e[0][2] = uy / un;
+        } else {
+            e[0][1] = 1.0;
+            e[0][2] = 0.0;
+        }
+        e[0][0] = 0.0;
+        e[0][3] = 0.0;
+        const double qh[3] = {q[1] / qq, q[2] / qq, q[3] / qq};
+        e[1][0] = 0.0;
+        e[1][1] = qh[1] * e[0][3] - qh[2] * e[0][2];
+        e[1][2] = qh[2] * e[0][1] - qh[0] * e[0][3];
+        e[1][3] = qh[0] * e[0][2] - qh[1] * e[0][1];
+        /* psi polarizations: real and imaginary parts */
+        const double psr[2][4] = {{0.0, -isq2, 0.0, 0.0}, {0.0, isq2, 0.0, 0.0}};
+        const double psi[2][4] = {{0.0, 0.0, -isq2, 0.0}, {0.0, 0.0, -isq2, 0.0}};
+        for (int im = 0; im < 2; ++im)
+            for (int il = 0; il < 2; ++il) {
+                const int l = 2 * im + il;
+                const double *w = e[il];
+                /* the contractions are linear in psi: real and imaginary parts apart */
+                const double s0r = mdot(psr[im], w), s0i = mdot(psi[im], w);
+                const double prw = mdot(w, rt), pwp = mdot(w, p);
+                const double ar = mdot(psr[im], rt), ai = mdot(psi[im], rt);
+                const double apr = mdot(psr[im], p), api = mdot(psi[im], p);
+                const double t_r = ar * prw - rr / 3.0 * (s0r - apr * pwp / pp);
+                const double t_i = ai * prw - rr / 3.0 * (s0i - api * pwp / pp);
+                for (int a = 0; a < N; ++a) {
+                    const double D = mass[a] * mass[a] - pp, G = mass[a] * width[a];
+                    const double den = D * D + G * G;
+                    const double br = D / den, bi = G / den;
+                    double cr, ci;
+                    if (spin[a] == 0) {
+                        cr = s0r;
+                        ci = s0i;
+                    } else {
+                        cr = b2 * t_r;
+                        ci = b2 * t_i;
+                    }
+                    double *o = out + ((i * 4 + l) * N + a) * 2;
+                    o[0] = br * cr - bi * ci;
+                    o[1] = br * ci + bi * cr;
+                }
+            }
+    }
+    return 0;
+}

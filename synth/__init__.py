@@ -420,3 +420,78 @@ def model_batch_spec(n_models=64, n_lo=8, n_hi=48, d_lo=100_000, d_hi=2_000_000,
     nw = rng.integers(n_lo, n_hi + 1, n_models)
     nd = rng.integers(d_lo, d_hi + 1, n_models)
     return [(int(a), int(b), seed + 1000 * (j + 1)) for j, (a, b) in enumerate(zip(nw, nd))]
+
+
+# ---- radiative decay kinematics for the covariant tensor amplitudes --------
+M_PSI = 3.0969    # J/psi mass (GeV)
+M_K = 0.493677    # charged kaon mass (GeV)
+
+
+@dataclass(frozen=True)
+class CovWave:
+    """A wave of J/psi -> gamma X, X -> K+ K-: X's Breit-Wigner and spin (0, 2)."""
+    mass: float
+    width: float
+    spin: int
+
+
+def cov_waves(n):
+    """n waves, spins alternating 0, 2, masses and widths as waves_linear."""
+    base = waves_linear(n)
+    return [CovWave(w.mass, w.width, 2 * (a % 2)) for a, w in enumerate(base)]
+
+
+def radiative_kinematics(m, cos_g, phi_g, cos_k, phi_k):
+    """3-momenta (photon, K+, K-) in the J/psi rest frame, [n, 9] float64:
+    the photon at polar angles (cos_g, phi_g) about the beam (z) axis, X of
+    mass m recoiling against it, K+ at (cos_k, phi_k) in the X rest frame
+    (axes parallel to the J/psi frame's)."""
+    m, cos_g, phi_g, cos_k, phi_k = (np.asarray(x, dtype=np.float64) for x in
+                                     (m, cos_g, phi_g, cos_k, phi_k))
+    sg, sk = np.sqrt(1 - cos_g ** 2), np.sqrt(1 - cos_k ** 2)
+    qhat = np.stack([sg * np.cos(phi_g), sg * np.sin(phi_g), cos_g], axis=1)
+    Eg = (M_PSI ** 2 - m ** 2) / (2 * M_PSI)
+    q = Eg[:, None] * qhat
+    EX = M_PSI - Eg
+    beta = -q / EX[:, None]                       # X's velocity
+    gam = EX / m
+    kstar = np.sqrt(m ** 2 / 4 - M_K ** 2)
+    ks = kstar[:, None] * np.stack([sk * np.cos(phi_k), sk * np.sin(phi_k), cos_k], axis=1)
+    b2 = np.sum(beta ** 2, axis=1)
+
+    def boost(k3, E):
+        bk = np.sum(beta * k3, axis=1)
+        coef = np.where(b2 > 0, (gam - 1) * bk / np.where(b2 > 0, b2, 1), 0.0)
+        return k3 + coef[:, None] * beta + (gam * E)[:, None] * beta
+
+    k1 = boost(ks, m / 2)
+    k2 = boost(-ks, m / 2)
+    return np.concatenate([q, k1, k2], axis=1)
+
+
+def radiative_events(n, rng, accept=False):
+    """n radiative events uniform in (m, cos_g, phi_g, cos_k, phi_k); with
+    accept, kept with probability 0.6 + 0.3 cos_g (returns the candidates
+    drawn as well)."""
+    out, drawn, got = [], 0, 0
+    while got < n:
+        k = max(1024, 2 * (n - got))
+        m = rng.uniform(M_LO, M_HI, k)
+        cg = rng.uniform(-1.0, 1.0, k)
+        pg = rng.uniform(0.0, 2 * math.pi, k)
+        ck = rng.uniform(-1.0, 1.0, k)
+        pk = rng.uniform(0.0, 2 * math.pi, k)
+        if accept:
+            keep = rng.uniform(0.0, 1.0, k) < 0.6 + 0.3 * cg
+            idx = np.nonzero(keep)[0]
+            if idx.size > n - got:
+                drawn += int(idx[n - got - 1]) + 1
+                idx = idx[:n - got]
+            else:
+                drawn += k
+        else:
+            idx = np.arange(min(k, n - got))
+            drawn += idx.size
+        out.append(radiative_kinematics(m[idx], cg[idx], pg[idx], ck[idx], pk[idx]))
+        got += idx.size
+    return np.concatenate(out)[:n], drawn
