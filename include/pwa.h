@@ -114,9 +114,11 @@ int pwa_load_events(pwa_ctx *ctx, const void *data_amp, int64_t n_data,
                     int amp_dtype);
 
 /* ---- amplitudes on the device ---------------------------------------------
- * The framework of the paper computes its amplitudes on the GPU (Sec. 4);
- * its covariant-tensor amplitude library is not given, so these calls
- * evaluate the amplitude model used throughout this library's samples:
+ * The framework of the paper computes its amplitudes on the GPU (Sec. 4).
+ * Two amplitude models: the covariant tensor amplitudes of the radiative
+ * decay J/psi -> gamma X, X -> K+ K- (pwa_compute_covariant_amplitudes,
+ * pwa_load_events_covariant, below the incoherent loader), and a model with
+ * one angle pair that serves the coherent samples:
  *   A_a(Omega) = BW(m; M_a, G_a) Y_{l_a}^{m_a}(theta, phi),
  *   BW(m; M, G) = 1 / (M^2 - m^2 - i M G)   (fixed-width Breit-Wigner),
  *   Y_l^m the orthonormal spherical harmonic with the Condon-Shortley phase,
@@ -172,6 +174,54 @@ int pwa_load_events_generated(pwa_ctx *ctx, const pwa_wave *waves, const double 
 int pwa_load_events_incoherent(pwa_ctx *ctx, int n_lambda, const void *data_amp, int64_t n_data,
                                const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
                                int amp_dtype);
+
+/* Covariant tensor amplitudes of J/psi -> gamma X, X -> K+ K- (Sec. 4: the
+ * amplitudes are built on the GPU in the covariant tensor formalism), per
+ * event four unobserved components l = 2 iM + ie: the J/psi helicity
+ * M = +1 (iM = 0) or -1 (iM = 1) along z, and the photon's linear
+ * polarization e1 (ie = 0) or e2 (ie = 1) (the photon and the J/psi spin
+ * states are not observed, so the intensity is the incoherent sum over
+ * them, pwa_load_events_incoherent with n_lambda = 4). In the J/psi rest
+ * frame, metric (+,-,-,-), mK = 0.493677 GeV:
+ *   q the photon, k1 = K+, k2 = K-, p = k1 + k2, r = k1 - k2,
+ *   rt = r - (r.p / p.p) p;
+ *   psi(+1) = (0, -1, -i, 0)/sqrt2, psi(-1) = (0, 1, -i, 0)/sqrt2;
+ *   e1 = (0, z x q / |z x q|) (the x axis when q is along z),
+ *   e2 = (0, q/|q| x e1);
+ *   spin 0: A = BW(p.p) (psi.e);
+ *   spin 2: A = BW(p.p) B2(Q) [(psi.rt)(e.rt) - (1/3)(rt.rt)(psi.e - (psi.p)(e.p)/p.p)]
+ *     with Q^2 = p.p/4 - mK^2, B2(Q) = sqrt(13 / (Q^4 + 3 Q^2 Q0^2 + 9 Q0^4)),
+ *     Q0 = 0.197327 GeV (the spin-2 Blatt-Weisskopf barrier);
+ *   BW(s) = 1 / (M^2 - s - i M G).
+ * Evaluated in double precision, each amplitude rounded once to float. */
+typedef struct pwa_cov_wave {
+    double mass;   /* M > 0 (GeV) */
+    double width;  /* G > 0 (GeV) */
+    int spin;      /* 0 or 2 */
+} pwa_cov_wave;
+
+/* Covariant amplitudes of n events for the context's n_waves waves.
+ *   waves: host [n_waves];  p3: [n][9] doubles, the 3-momenta (GeV) of the
+ *   photon, the K+ and the K- in the J/psi rest frame, host or device
+ *   pointer;  out: [n][4][n_waves] complex64 (component l, then wave), host
+ *   or device pointer.
+ * Does not touch the loaded sample. Errors: PWA_EINVAL (null pointer, n out
+ * of [1, 2^31 - 1024], a spin other than 0 or 2, a non-positive mass or
+ * width), PWA_ENOMEM, PWA_ECUDA. */
+int pwa_compute_covariant_amplitudes(pwa_ctx *ctx, const pwa_cov_wave *waves, const double *p3,
+                                     int64_t n, void *out);
+
+/* Load a data and an accepted-MC sample of J/psi -> gamma K+ K- events given
+ * by their 3-momenta: the covariant amplitudes are generated on the device
+ * (as pwa_compute_covariant_amplitudes) and loaded as an incoherent sample
+ * with n_lambda = 4, without host amplitude arrays.
+ *   data_p3 [n_data][9], mc_p3 [n_mc_acc][9], host or device pointers;
+ *   n_mc_gen as in pwa_load_events.
+ * Errors as pwa_compute_covariant_amplitudes and pwa_load_events_incoherent
+ * (the direct form takes up to 12 waves at n_lambda = 4). */
+int pwa_load_events_covariant(pwa_ctx *ctx, const pwa_cov_wave *waves, const double *data_p3,
+                              int64_t n_data, const double *mc_p3, int64_t n_mc_acc,
+                              double n_mc_gen);
 
 /* Build the MC normalisation matrix M (the inner bracket of the second term
  * of Eq. 3), once per loaded sample. If M_out is not NULL it receives M as

@@ -54,6 +54,22 @@ class Likelihood:
         self.n_mc = int(len(mc_kin["m"]) if isinstance(mc_kin, dict) else mc_kin.shape[0])
         return self
 
+    def load_covariant(self, waves, data_p3, mc_p3, n_mc_gen):
+        """Load J/psi -> gamma K+ K- samples given by their 3-momenta ([n, 9]:
+        photon, K+, K-): the covariant amplitudes of `waves` (mass, width,
+        spin 0 or 2) are computed on the device and loaded as an incoherent
+        sample over the 4 unobserved components."""
+        self._abi.pwa_load_events_covariant(self.ctx, waves, data_p3, mc_p3, n_mc_gen)
+        self.M = None
+        self.n_data = int(data_p3.shape[0])
+        self.n_mc = int(mc_p3.shape[0])
+        return self
+
+    def covariant_amplitudes(self, waves, p3, out=None):
+        """[n, 4, N] complex64 covariant amplitudes of `waves` at the events
+        `p3`, on the device."""
+        return self._abi.pwa_compute_covariant_amplitudes(self.ctx, waves, p3, out)
+
     def amplitudes(self, waves, kin, out=None):
         """[n, N] complex64 amplitudes of `waves` at the events `kin`, on the device."""
         return self._abi.pwa_compute_amplitudes(self.ctx, waves, kin, out)

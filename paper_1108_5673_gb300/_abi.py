@@ -95,6 +95,8 @@ def load(path=LIB_PATH):
         "pwa_load_events_incoherent": ([P, I, P, I64, P, I64, D, I], I),
         "pwa_compute_amplitudes": ([P, P, P, I64, P], I),
         "pwa_load_events_generated": ([P, P, P, I64, P, I64, D], I),
+        "pwa_compute_covariant_amplitudes": ([P, P, P, I64, P], I),
+        "pwa_load_events_covariant": ([P, P, P, I64, P, I64, D], I),
         "pwa_mc_weights": ([P, P, P], I),
         "pwa_fit_fractions": ([P, P, P], I),
     }
@@ -242,6 +244,55 @@ def pwa_load_events_generated(ctx, waves, data_kin, mc_kin, n_mc_gen):
     pd, kd, nd = _kin(data_kin)
     pm, km, nm = _kin(mc_kin)
     return _check(ctx, load().pwa_load_events_generated(ctx, _waves(waves), pd, nd, pm, nm,
+                                                        float(n_mc_gen)))
+
+
+class pwa_cov_wave(ctypes.Structure):
+    _fields_ = [("mass", ctypes.c_double), ("width", ctypes.c_double), ("spin", ctypes.c_int)]
+
+
+def _cov_waves(waves):
+    """A ctypes array of pwa_cov_wave from objects with mass, width, spin (or 3-tuples)."""
+    arr = (pwa_cov_wave * len(waves))()
+    for k, w in enumerate(waves):
+        t = (w.mass, w.width, w.spin) if hasattr(w, "mass") else tuple(w)
+        arr[k] = pwa_cov_wave(float(t[0]), float(t[1]), int(t[2]))
+    return arr
+
+
+def _p3(p3):
+    """(pointer, keepalive, n) for [n, 9] float64 momenta (photon, K+, K-),
+    a numpy array or a CUDA tensor."""
+    if getattr(p3, "is_cuda", False):
+        if "float64" not in str(p3.dtype) or tuple(p3.shape[1:]) != (9,) or not p3.is_contiguous():
+            raise ValueError("device momenta must be a contiguous [n, 9] float64 tensor")
+    else:
+        p3 = np.ascontiguousarray(p3, dtype=np.float64)
+        if p3.ndim != 2 or p3.shape[1] != 9:
+            raise ValueError("momenta must be [n, 9] (photon, K+, K- 3-momenta)")
+    p, keep = _ptr(p3)
+    return p, keep, int(p3.shape[0])
+
+
+def pwa_compute_covariant_amplitudes(ctx, waves, p3, out=None):
+    """[n, 4, n_waves] complex64 covariant amplitudes of J/psi -> gamma X,
+    X -> K+ K- (numpy, or into `out`: a numpy array or a CUDA tensor of that
+    shape)."""
+    pk, keep, n = _p3(p3)
+    if out is None:
+        out = np.empty((n, 4, len(waves)), dtype=np.complex64)
+    elif not getattr(out, "is_cuda", False) and not (
+            isinstance(out, np.ndarray) and out.dtype == np.complex64 and out.flags.c_contiguous):
+        raise ValueError("host output must be a contiguous complex64 numpy array")
+    po, keep_o = _ptr(out)
+    _check(ctx, load().pwa_compute_covariant_amplitudes(ctx, _cov_waves(waves), pk, n, po))
+    return out
+
+
+def pwa_load_events_covariant(ctx, waves, data_p3, mc_p3, n_mc_gen):
+    pd, kd, nd = _p3(data_p3)
+    pm, km, nm = _p3(mc_p3)
+    return _check(ctx, load().pwa_load_events_covariant(ctx, _cov_waves(waves), pd, nd, pm, nm,
                                                         float(n_mc_gen)))
 
 

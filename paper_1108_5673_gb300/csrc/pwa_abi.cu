@@ -1415,6 +1415,133 @@ int pwa_load_events_generated(pwa_ctx *c, const pwa_wave *waves, const double *d
     return finish_load(c, rc, n_data, n_mc_acc, n_mc_gen);
 }
 
+// ---- covariant amplitudes ------------------------------------------------
+
+// Checks the covariant wave list and uploads it to *d_waves (freed by the caller).
+static int upload_cov_waves(pwa_ctx *c, const pwa_cov_wave *waves, CovWave **d_waves)
+{
+    *d_waves = nullptr;
+    if (!waves)
+        return fail(c, PWA_EINVAL, "null wave list");
+    std::vector<CovWave> h(c->N);
+    for (int a = 0; a < c->N; ++a) {
+        const pwa_cov_wave &w = waves[a];
+        if (w.spin != 0 && w.spin != 2)
+            return fail(c, PWA_EINVAL, "wave %d: spin %d is neither 0 nor 2", a, w.spin);
+        if (!(w.mass > 0) || !(w.width > 0) || !std::isfinite(w.mass) || !std::isfinite(w.width))
+            return fail(c, PWA_EINVAL, "wave %d: mass and width must be positive and finite", a);
+        h[a] = CovWave{w.mass, w.width, w.spin};
+    }
+    int rc = dev_alloc(c, (void **)d_waves, c->N * sizeof(CovWave), "wave table");
+    if (rc)
+        return rc;
+    CK(c, cudaMemcpyAsync(*d_waves, h.data(), c->N * sizeof(CovWave), cudaMemcpyHostToDevice,
+                          c->stream));
+    CK(c, cudaStreamSynchronize(c->stream));
+    return PWA_OK;
+}
+
+// Covariant amplitudes of n events (p3 host or device) into `out` (device,
+// event-major [n][4][N] complex64).
+static int generate_cov(pwa_ctx *c, const CovWave *d_waves, const double *p3, int64_t n, float *out)
+{
+    const double *dk = p3;
+    double *staging = nullptr;
+    if (!is_device_pointer(p3)) {
+        int rc = dev_alloc(c, (void **)&staging, (size_t)n * 9 * sizeof(double), "momenta");
+        if (rc)
+            return rc;
+        cudaError_t e = cudaMemcpyAsync(staging, p3, (size_t)n * 9 * sizeof(double),
+                                        cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(staging);
+            return fail(c, PWA_ECUDA, "momenta copy: %s", cudaGetErrorString(e));
+        }
+        dk = staging;
+    }
+    cudaError_t e = launch_cov_amp_gen(dk, n, c->N, d_waves, out, false, 0, c->num_sms * 8, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    if (staging)
+        cudaFree(staging);
+    if (e == cudaSuccess)
+        e = e2;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "covariant amplitudes: %s", cudaGetErrorString(e));
+    }
+    return PWA_OK;
+}
+
+int pwa_compute_covariant_amplitudes(pwa_ctx *c, const pwa_cov_wave *waves, const double *p3,
+                                     int64_t n, void *out)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!p3 || !out)
+        return fail(c, PWA_EINVAL, "null momenta or output");
+    if (n < 1 || n > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "n=%lld outside [1, 2^31 - 1024]", (long long)n);
+    DeviceGuard g(c->device);
+    CovWave *dw;
+    int rc = upload_cov_waves(c, waves, &dw);
+    if (rc) {
+        dev_free(dw);
+        return rc;
+    }
+    const size_t bytes = (size_t)n * 4 * c->N * 8;
+    const bool on_dev = is_device_pointer(out);
+    float *dout = static_cast<float *>(out);
+    if (!on_dev)
+        rc = dev_alloc(c, (void **)&dout, bytes, "amplitudes");
+    if (!rc)
+        rc = generate_cov(c, dw, p3, n, dout);
+    if (!rc && !on_dev) {
+        cudaError_t e = cudaMemcpy(out, dout, bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess)
+            rc = fail(c, PWA_ECUDA, "amplitude copy: %s", cudaGetErrorString(e));
+    }
+    if (!on_dev)
+        dev_free(dout);
+    dev_free(dw);
+    return rc;
+}
+
+// The amplitudes of both samples go through device buffers of this call into
+// the incoherent loader (which copies them into its planes), so that every
+// check and store that loader makes applies unchanged.
+int pwa_load_events_covariant(pwa_ctx *c, const pwa_cov_wave *waves, const double *data_p3,
+                              int64_t n_data, const double *mc_p3, int64_t n_mc_acc,
+                              double n_mc_gen)
+{
+    if (!c)
+        return PWA_EINVAL;
+    if (!data_p3 || !mc_p3)
+        return fail(c, PWA_EINVAL, "null momenta");
+    if (n_data < 1 || n_mc_acc < 1)
+        return fail(c, PWA_EINVAL, "n_data=%lld and n_mc_acc=%lld must be >= 1",
+                    (long long)n_data, (long long)n_mc_acc);
+    if (n_data > ((int64_t)1 << 31) - 1024 || n_mc_acc * 4 > ((int64_t)1 << 31) - 1024)
+        return fail(c, PWA_EINVAL, "samples are limited to 2^31 - 1024 events (MC: 4 x events)");
+    DeviceGuard g(c->device);
+    CovWave *dw;
+    int rc = upload_cov_waves(c, waves, &dw);
+    float *amp[2] = {nullptr, nullptr};
+    const int64_t n[2] = {n_data, n_mc_acc};
+    for (int k = 0; k < 2 && !rc; ++k) {
+        rc = dev_alloc(c, (void **)&amp[k], (size_t)n[k] * 4 * c->N * 8, "amplitudes");
+        if (!rc)
+            rc = generate_cov(c, dw, k == 0 ? data_p3 : mc_p3, n[k], amp[k]);
+    }
+    dev_free(dw);
+    if (!rc)
+        rc = pwa_load_events_incoherent(c, 4, amp[0], n_data, amp[1], n_mc_acc, n_mc_gen, PWA_C64);
+    cudaStreamSynchronize(c->stream);
+    dev_free(amp[0]);
+    dev_free(amp[1]);
+    return rc;
+}
+
 int pwa_load_events_incoherent(pwa_ctx *c, int n_lambda, const void *data_amp, int64_t n_data,
                                const void *mc_amp, int64_t n_mc_acc, double n_mc_gen,
                                int amp_dtype)

@@ -520,6 +520,17 @@ int ampgen_max_l();
 cudaError_t launch_amp_gen(const double *kin, int64_t n, int N, const GenWave *waves, int max_m,
                            float *out, bool soa, int64_t pitch, int grid, cudaStream_t s);
 
+// k_ampgen_cov.cu: covariant tensor amplitudes of J/psi -> gamma X, X -> K+ K-
+// from p3 [n][9] (photon, K+, K- 3-momenta, device), 4 incoherent components
+// per event; out as event-major [n][4][N] complex64 or, soa, the planes of an
+// incoherent sample (plane 2 (l N + a) = Re A_a^l of `pitch` floats).
+struct CovWave {
+    double mass, width;
+    int spin;  // 0 or 2
+};
+cudaError_t launch_cov_amp_gen(const double *p3, int64_t n, int N, const CovWave *waves, float *out,
+                               bool soa, int64_t pitch, int grid, cudaStream_t s);
+
 // k_nll_incoh.cu: direct form with an incoherent sum over n_lambda components;
 // d holds 2 n_lambda N planes (plane 2 (l N + a) = Re A_a^l). Same scratch,
 // ticket and outputs as the direct-form kernel (EvalArgs, one parameter set).

@@ -469,14 +469,20 @@ def radiative_kinematics(m, cos_g, phi_g, cos_k, phi_k):
     return np.concatenate([q, k1, k2], axis=1)
 
 
+# K+ K- mass range of the radiative samples: from just above the threshold
+# 2 mK = 0.98735 GeV to 3.0 GeV (below M_PSI)
+M_KK_LO, M_KK_HI = 0.99, 3.0
+
+
 def radiative_events(n, rng, accept=False):
-    """n radiative events uniform in (m, cos_g, phi_g, cos_k, phi_k); with
+    """n radiative events uniform in (m, cos_g, phi_g, cos_k, phi_k), m in
+    [M_KK_LO, M_KK_HI]; with
     accept, kept with probability 0.6 + 0.3 cos_g (returns the candidates
     drawn as well)."""
     out, drawn, got = [], 0, 0
     while got < n:
         k = max(1024, 2 * (n - got))
-        m = rng.uniform(M_LO, M_HI, k)
+        m = rng.uniform(M_KK_LO, M_KK_HI, k)
         cg = rng.uniform(-1.0, 1.0, k)
         pg = rng.uniform(0.0, 2 * math.pi, k)
         ck = rng.uniform(-1.0, 1.0, k)

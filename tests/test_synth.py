@@ -51,3 +51,17 @@ def test_seeded_and_reproducible():
     b = synth.mixture_workload("t", synth.waves_linear(5), 1000, 2000)
     assert np.array_equal(a.A_data, b.A_data) and np.array_equal(a.A_mc, b.A_mc)
     assert a.n_gen == b.n_gen and a.A_data.dtype == np.complex64
+
+
+def test_radiative_events_physical():
+    """Every radiative event lies above the K+ K- threshold, conserves the
+    J/psi's momentum, and has the kaons and X on shell."""
+    p3, drawn = synth.radiative_events(20_000, np.random.default_rng(3), accept=True)
+    assert np.all(np.isfinite(p3)) and drawn >= 20_000
+    q, k1, k2 = p3[:, 0:3], p3[:, 3:6], p3[:, 6:9]
+    assert np.abs(q + k1 + k2).max() < 1e-12
+    E = (np.linalg.norm(q, axis=1) + np.sqrt(synth.M_K ** 2 + np.sum(k1 ** 2, 1))
+         + np.sqrt(synth.M_K ** 2 + np.sum(k2 ** 2, 1)))
+    assert np.abs(E - synth.M_PSI).max() < 1e-12
+    m2 = (E - np.linalg.norm(q, axis=1)) ** 2 - np.sum((k1 + k2) ** 2, 1)
+    assert np.sqrt(m2).min() > 2 * synth.M_K
