@@ -64,9 +64,9 @@ N_WAVES, N_DATA, N_MC = 20, 1_000_000, 5_000_000
 WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M accepted MC, K=1 per evaluation"
 # DRAM bytes (read + write) per step of the timed kernel from one ncu
 # capture of the current kernel, or None where there is none.
-TRAFFIC = {"direct": 160.139008e6 + 3.103744e6,
+TRAFFIC = {"direct": 160.153856e6 + 3.591936e6,
            "table": 1600.119e6 + 3.221760e6,
-           "tc": 2 * (1024.851e6 + 3.764992e6),        # a step is two launches of 128 sets
+           "tc": 2 * (1024.867e6 + 3.751680e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.091648e6 + 3.346944e6,
@@ -76,7 +76,7 @@ TRAFFIC = {"direct": 160.139008e6 + 3.103744e6,
            "ampgen": 278.9e6 + 962.9e6}   # FP64-bound; DRAM bytes for reference
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
-           "models": "batched_kernel<F, 2> (all models)", "hessian": "hess_tc_kernel<20>",
+           "models": "batched_items_kernel<2> (all models, one launch)", "hessian": "hess_tc_kernel<20>",
            "weights": "nll_amp_kernel<20, 2, 1, true> (weights mode)", "incoh": "nll_amp_kernel<20, 2, 2>",
            "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)
@@ -363,10 +363,11 @@ def job_models(pwa, torch, stream, local, rank):
 
     return Job(
         name="models", lib=B, step=lambda: B.nll_grad(Vs), host_step=lambda: B.nll_grad(Vs),
-        sync=lambda: B.last_status, evals_per_step=64 * K, launches_per_step=64 * 3,
+        sync=lambda: B.last_status, evals_per_step=64 * K, launches_per_step=3,
         flush=False,
         workload="64 trial models (n_waves 8..48, 100k..2M data events each, MC 2x data, 63.4M "
-                 "data events in all), K=16 parameter sets per model, one CUDA-graph launch",
+                 "data events in all), K=16 parameter sets per model, one persistent launch over "
+                 "(model, tile range) work items",
         config={"n_models": 64, "K": K, "n_data_total": sum(s[1] for s in spec),
                 "n_waves_mean": float(np.mean([s[0] for s in spec])), "form": "tc",
                 "precision": "bfp16", "load_and_norm_s": load_s},

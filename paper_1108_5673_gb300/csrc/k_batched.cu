@@ -357,11 +357,9 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
             const uint64_t dA = umma_desc_sw128(0, kXBlk, 1024);      // X, MN-major
             const uint64_t dR = umma_desc_sw128(0, 128 * 128, 1024);  // R', MN-major
             const uint64_t dK = umma_desc_sw128(0, 16, 1024);         // K-major operands
-            // GEMM 2 of chunk step cq (pipelined behind GEMM 1 of the next step)
-            auto gemm2 = [&](int cq) -> bool {
+            // GEMM 2 of chunk step cq (its R' complete: r_full phase cq)
+            auto gemm2 = [&](int cq) {
                 const int j = cq / NCH, c = cq % NCH, s = j % NXS;
-                if (!mbar_wait(&r_full, cq & 1))
-                    return false;
                 tc_fence_after();
                 const uint32_t xs = xbase + s * kXBytes;
 #pragma unroll
@@ -374,16 +372,42 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
                 umma_commit(&r_free);
                 if (c == NCH - 1)
                     umma_commit(&x_empty[s]);
-                return true;
+            };
+            // GEMM 2 does not wait in line behind GEMM 1: while the thread
+            // waits for a barrier (bar, parity), it issues the GEMM 2 of each
+            // chunk step whose R' is complete, in order, and returns once the
+            // barrier's phase is complete and at least `need` GEMM 2s are
+            // issued (bar = null: the barrier part holds). It polls without
+            // sleeping: a suspended thread was measured to resume up to ~1300
+            // cycles after the phase completed, on the critical path of GEMM 1.
+            // GEMM 1 of the first half of
+            // chunk step cq needs the GEMM 2 of cq - 2 issued: its completion,
+            // seen by the epilogue as s_full, then implies that r_free has
+            // passed phase cq - 2, so the epilogue's parity wait for phase
+            // cq - 1 cannot match an older phase. Bounded as mbar_wait.
+            int g2 = 0, g2_ready = 0;   // next GEMM 2; chunk steps whose GEMM 1s are issued
+            auto serve = [&](uint64_t *bar, uint32_t parity, int need) -> bool {
+                const unsigned long long t0 = global_timer_ns();
+                for (unsigned it = 1;; ++it) {
+                    if (g2 < g2_ready && mbar_test(&r_full, g2 & 1)) {
+                        gemm2(g2++);
+                        continue;
+                    }
+                    if (g2 >= need && (!bar || mbar_test(bar, parity)))
+                        return true;
+                    if ((it & 255) == 0 && global_timer_ns() - t0 > kWaitLimitNs)
+                        return false;
+                }
             };
             bool ok = mbar_wait(&w_full, 0);
             for (int q = 0; q < steps && ok; ++q) {
                 const int j = q / HPT, ch = q % HPT, c = ch >> 1, h = ch & 1, s = j % NXS;
-                if (ch == 0 && !mbar_wait(&x_full[s], (j / NXS) & 1)) {
+                const int need = h == 0 ? j * NCH + c - 1 : 0;
+                if (ch == 0 && !serve(&x_full[s], (j / NXS) & 1, need)) {
                     ok = false;
                     break;
                 }
-                if (q >= 1 && !mbar_wait(&s_free, (q - 1) & 1)) {
+                if (q >= 1 && !serve(&s_free, (q - 1) & 1, need)) {
                     ok = false;
                     break;
                 }
@@ -397,21 +421,28 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
                     const uint32_t wa = wb + (ks >> 2) * kWSlices * kWBlock + (ks & 3) * 32;
                     const uint32_t acc = ks > 0 ? 1u : 0u;
                     if (XS == 2) {
+                        // x0 [w0|w1|w2] into acc0..2 and x1 [w0|w1|w2] into acc1..3:
+                        // two N = 192 products per K step; in the first, acc3
+                        // is started by x1 w2 alone (one accumulate flag per MMA)
                         const uint32_t x1a = x0a + F * 128;
-                        umma_bf16(tmem + 64, dA + (x1a >> 4), dK + (wa >> 4), id192, acc);   // acc1..3 x1 [w0|w1|w2]
-                        umma_bf16(tmem, dA + (x0a >> 4), dK + (wa >> 4), id64, acc);         // acc0    x0 w0
-                        umma_bf16(tmem + 64, dA + (x0a >> 4), dK + ((wa + kWBlock) >> 4), id128,
-                                  1u);                                                       // acc1..2 x0 [w1|w2]
+                        umma_bf16(tmem, dA + (x0a >> 4), dK + (wa >> 4), id192, acc);        // acc0..2 x0 [w0|w1|w2]
+                        if (ks == 0) {
+                            umma_bf16(tmem + 192, dA + (x1a >> 4), dK + ((wa + 2 * kWBlock) >> 4), id64,
+                                      0u);                                                   // acc3    x1 w2
+                            umma_bf16(tmem + 64, dA + (x1a >> 4), dK + (wa >> 4), id128, 1u);  // acc1..2 x1 [w0|w1]
+                        } else {
+                            umma_bf16(tmem + 64, dA + (x1a >> 4), dK + (wa >> 4), id192, 1u);  // acc1..3 x1 [w0|w1|w2]
+                        }
                     } else {
                         umma_bf16(tmem, dA + (x0a >> 4), dK + (wa >> 4), id192, acc);        // acc0..2 x0 [w0|w1|w2]
                     }
                 }
                 umma_commit(&s_full);
-                if (h == 0 && q >= 1)  // the previous chunk step is complete
-                    ok = gemm2(j * NCH + c - 1);
+                if (h == 1 || ch == HPT - 1)  // the chunk step's last GEMM 1
+                    g2_ready = j * NCH + c + 1;
             }
-            if (ok && steps > 0)
-                ok = gemm2(n_my * NCH - 1);
+            if (ok && !serve(nullptr, 0, g2_ready))
+                ok = false;
             umma_commit(&g_done);
             // tensor memory is released only after every product has finished
             if (!mbar_wait(&g_done, 0))
@@ -428,6 +459,7 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
         const uint32_t st0 = sw128(e, 32 * sg), st1 = sw128(e, 32 * sg + 16);
         unsigned long long *lp = reinterpret_cast<unsigned long long *>(
             a.lpart + ((size_t)tr.slot * 4 + qq) * (NCH * kKC) + 8 * sg + lane);
+        const f2 c8 = pk2(1.0f / 256.0f, 1.0f / 256.0f), one2 = pk2(1.0f, 1.0f);
         int64_t ev = (int64_t)tr.tile0 * kBM + e;          // this thread's event in tile j
         const int64_t ev_step = (int64_t)tr.stride * kBM;
         bool ok = true;
@@ -443,9 +475,11 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
             // a warp whose 8 sets all lie past K (padding of the last half
             // chunk) keeps to the barriers and does no work: its rows of R'
             // feed only the G^T rows of those sets, which are never read
-            const bool idle = a.K - (ch >> 1) * kKC - h * kHS - 8 * sg <= 0;
-            // Q of this warp's 8 sets: acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8
-            float qr[8], qi[8];
+            const int nvs = a.K - (ch >> 1) * kKC - h * kHS - 8 * sg;
+            const bool idle = nvs <= 0;
+            // Q = acc0 + (acc1 + (acc2 + acc3 / 2^8) / 2^8) / 2^8 of this warp's
+            // 8 sets, as (re, im) pairs
+            f2 qv[8];
             if (!idle) {
                 uint32_t v0[16], v1[16], v2[16], v3[16];
                 tmem_ld16(tmem + lane_addr + 16 * sg, v0);
@@ -454,18 +488,13 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
                 if (XS == 2)
                     tmem_ld16(tmem + lane_addr + 192 + 16 * sg, v3);
                 tmem_ld_wait();
-                constexpr float c8 = 1.0f / 256.0f;
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    float ur = __uint_as_float(v2[2 * s]), ui = __uint_as_float(v2[2 * s + 1]);
-                    if (XS == 2) {
-                        ur = fmaf(__uint_as_float(v3[2 * s]), c8, ur);
-                        ui = fmaf(__uint_as_float(v3[2 * s + 1]), c8, ui);
-                    }
-                    ur = fmaf(ur, c8, __uint_as_float(v1[2 * s]));
-                    ui = fmaf(ui, c8, __uint_as_float(v1[2 * s + 1]));
-                    qr[s] = fmaf(ur, c8, __uint_as_float(v0[2 * s]));
-                    qi[s] = fmaf(ui, c8, __uint_as_float(v0[2 * s + 1]));
+                for (int t = 0; t < 8; ++t) {
+                    f2 u = pk2(__uint_as_float(v2[2 * t]), __uint_as_float(v2[2 * t + 1]));
+                    if (XS == 2)
+                        u = fma2(pk2(__uint_as_float(v3[2 * t]), __uint_as_float(v3[2 * t + 1])), c8, u);
+                    u = fma2(u, c8, pk2(__uint_as_float(v1[2 * t]), __uint_as_float(v1[2 * t + 1])));
+                    qv[t] = fma2(u, c8, pk2(__uint_as_float(v0[2 * t]), __uint_as_float(v0[2 * t + 1])));
                 }
             }
             tc_fence_before();
@@ -475,49 +504,56 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
             uint32_t rpk[8];
             int l[8];
             if (!idle && ev < a.n_events) {
-                float Iv[8], z[8];
-                int kx[8];
+                float zz[8];
+                int kk[8];
                 unsigned mn = 0xffffffffu;
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const float I = fmaf(qr[s], qr[s], qi[s] * qi[s]);
-                    Iv[s] = I;
+                for (int t = 0; t < 8; ++t) {
+                    float qr, qi;
+                    upk2(qv[t], qr, qi);
+                    const float I = fmaf(qr, qr, qi * qi);
                     const int bits = __float_as_int(I);
                     mn = min(mn, (unsigned)bits);
                     const float r = rcp_approx(I);
-                    rpk[s] = pack_bf16x2(qr[s] * r, qi[s] * r);
-                    // I = 2^k (1 + z), 1 + z in [sqrt(1/2), sqrt(2))
-                    const int k = (bits - 0x3F3504F3) >> 23;
-                    kx[s] = k;
-                    z[s] = __int_as_float(bits - (k << 23)) - 1.0f;
+                    float rr, ri;
+                    upk2(mul2(qv[t], pk2(r, r)), rr, ri);
+                    rpk[t] = pack_bf16x2(rr, ri);
+                    // I = 2^k (1 + z), 1 + z in [sqrt(1/2), sqrt(2)): km = k 2^23
+                    // (the arithmetic shift's low bits cleared)
+                    const int km = (bits - 0x3F3504F3) & (int)0xFF800000;
+                    zz[t] = __int_as_float(bits - km);
+                    kk[t] = km >> (23 - kFixBits);
                 }
 #pragma unroll
-                for (int s = 0; s < 8; s += 2) {
+                for (int t = 0; t < 8; t += 2) {
                     float y0, y1;
-                    upk2(log2_fixed2(pk2(z[s], z[s + 1])), y0, y1);
-                    l[s] = __float_as_int(y0) - 0x4B400000 + (kx[s] << kFixBits);
-                    l[s + 1] = __float_as_int(y1) - 0x4B400000 + (kx[s + 1] << kFixBits);
+                    upk2(log2_fixed2(sub2(pk2(zz[t], zz[t + 1]), one2)), y0, y1);
+                    l[t] = __float_as_int(y0) - 0x4B400000 + kk[t];
+                    l[t + 1] = __float_as_int(y1) - 0x4B400000 + kk[t + 1];
                 }
                 if (mn == 0u) {  // some Q = 0 (rare): record the parameter sets, if real
-                    const int nvs = a.K - (ch >> 1) * kKC - h * kHS - 8 * sg;
-                    for (int s = 0; s < 8; ++s)
-                        if (s < nvs && Iv[s] == 0.f)
-                            atomicOr(&s_kflags[ch], 1u << (8 * sg + s));
+#pragma unroll
+                    for (int t = 0; t < 8; ++t) {
+                        float qr, qi;
+                        upk2(qv[t], qr, qi);
+                        if (t < nvs && fmaf(qr, qr, qi * qi) == 0.f)
+                            atomicOr(&s_kflags[ch], 1u << (8 * sg + t));
+                    }
                 }
             } else {
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    rpk[s] = 0u;
-                    l[s] = 0;
+                for (int t = 0; t < 8; ++t) {
+                    rpk[t] = 0u;
+                    l[t] = 0;
                 }
             }
-            // fixed-point log2 sums over the warp's 32 events; lane s keeps set s
+            // fixed-point log2 sums over the warp's 32 events; lane t keeps set t
             if (!idle) {
                 int mine = 0;
 #pragma unroll
-                for (int s = 0; s < 8; ++s) {
-                    const int t = __reduce_add_sync(0xffffffffu, l[s]);
-                    mine = lane == s ? t : mine;
+                for (int t = 0; t < 8; ++t) {
+                    const int sum = __reduce_add_sync(0xffffffffu, l[t]);
+                    mine = lane == t ? sum : mine;
                 }
                 if (lane < 8)  // no return value: a fire-and-forget reduction
                     atomicAdd(lp + ch * kHS, (unsigned long long)(long long)mine);

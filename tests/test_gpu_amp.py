@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 import synth
+from grad_bound import term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -56,6 +57,8 @@ def check(pwa, wl, Vs, M_tol=1e-12, forms=None):
         assert nll_only[k] == nll[k]
         err = np.linalg.norm(g[k] - go) / np.linalg.norm(gd)
         assert err <= 1e-5, (k, err)
+        c = term_scale(wl.A_data, V)
+        assert np.all(np.abs(g[k] - go) <= 1e-5 * c), (k, np.max(np.abs(g[k] - go) / c))
     return nll, g
 
 

@@ -21,6 +21,7 @@ import pytest
 
 import oracle
 import synth
+from grad_bound import term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -94,6 +95,8 @@ def check(pwa, wl, Vs, precision, idx=None):
         assert abs(nll[k] - no) <= nll_tol(n), (k, nll[k], no, nll[k] - no)
         err = np.linalg.norm(g[k] - go) / np.linalg.norm(gd)
         assert err <= GRAD_TOL, (k, err)
+        c = term_scale(Ap, Vs[k])
+        assert np.all(np.abs(g[k] - go) <= 3e-3 * c), (k, np.max(np.abs(g[k] - go) / c))
 
 
 PRECISIONS = ["BFP16", "BFP8"]

@@ -21,6 +21,7 @@ import pytest
 
 import oracle
 import synth
+from grad_bound import term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -125,6 +126,7 @@ def test_covariant_likelihood_against_oracle(pwa, N, n_data, n_mc):
         gd = go - oracle.norm_term(Mo, V)[1]
         assert abs(nll[k] - no) <= nll_tol(n_data), (k, nll[k] - no)
         assert np.linalg.norm(g[k] - go) <= 1e-5 * np.linalg.norm(gd), k
+        assert np.all(np.abs(g[k] - go) <= 1e-5 * term_scale(Ad, V)), k
 
 
 def test_covariant_load_equals_amplitude_load(pwa):

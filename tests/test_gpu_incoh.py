@@ -17,6 +17,7 @@ import pytest
 
 import oracle
 import synth
+from grad_bound import term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -61,6 +62,8 @@ def check_sets(nll, g, wl, M_ref, Vs, table=None):
         assert abs(nll[k] - no) <= nll_tol(n), (k, nll[k], no, nll[k] - no)
         err = np.linalg.norm(g[k] - go) / np.linalg.norm(gd)
         assert err <= 1e-5, (k, err)
+        c = term_scale(wl.A_data, V, table=table is not None)
+        assert np.all(np.abs(g[k] - go) <= 1e-5 * c), (k, np.max(np.abs(g[k] - go) / c))
 
 
 def run(pwa, wl, Vs, forms):

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 import synth
+from grad_bound import term_scale
 
 pytestmark = pytest.mark.gpu
 
@@ -63,6 +64,7 @@ def test_table_form_against_oracle(pwa, N):
         gd = go - oracle.norm_term(Mo, V)[1]
         assert abs(nt[k] - no) <= nll_tol(len(wl.A_data)), (k, nt[k] - no)
         assert np.linalg.norm(gt[k] - go) <= 1e-5 * np.linalg.norm(gd)
+        assert np.all(np.abs(gt[k] - go) <= 1e-5 * term_scale(wl.A_data, V, table=True))
     # switching forms back and forth leaves the direct form unchanged
     assert np.array_equal(out["amp"][0], out["amp2"][0])
 
@@ -90,6 +92,7 @@ def test_table_form_one_million_events(pwa):
         gd = go - oracle.norm_term(Mo, V[k])[1]
         assert abs(out["table"][0][k] - no) <= 1e-3
         assert np.linalg.norm(out["table"][1][k] - go) <= 1e-5 * np.linalg.norm(gd)
+        assert np.all(np.abs(out["table"][1][k] - go) <= 1e-5 * term_scale(wl.A_data, V[k], table=True))
 
 
 def test_table_form_limits(pwa):
