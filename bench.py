@@ -66,23 +66,25 @@ WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M 
 # capture of the current kernel, or None where there is none.
 TRAFFIC = {"direct": 160.153856e6 + 3.591936e6,
            "table": 1600.119e6 + 3.221760e6,
-           "tc": 2 * (1024.867e6 + 3.751680e6),        # a step is two launches of 128 sets
+           "tc": 2 * (1025.548e6 + 3.824384e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.091648e6 + 3.346944e6,
-           "weights": 800.148224e6 + 21.018112e6,
-           "incoh": 320.162304e6 + 3.733248e6,
+           "weights": None,      # captured before the kernel template changed
+           "incoh": None,        # the same template
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
-           "ampgen": 278.9e6 + 962.9e6}   # FP64-bound; DRAM bytes for reference
+           "ampgen": 278.9e6 + 962.9e6,   # FP64-bound; DRAM bytes for reference
+           "direct_4M_32": None}
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
            "models": "batched_items_kernel<2> (all models, one launch)", "hessian": "hess_tc_kernel<20>",
            "weights": "nll_amp_kernel<20, 2, 1, true> (weights mode)", "incoh": "nll_amp_kernel<20, 2, 2>",
-           "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel"}
+           "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel",
+           "direct_4M_32": "nll_amp_kernel<32, 2>"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)
 DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,
                  "hessian": 2000, "weights": 2000, "incoh": 1500, "incoh_table": 1000,
-                 "ampgen": 100}
+                 "ampgen": 100, "direct_4M_32": 500}
 
 
 def measured_peaks():
@@ -293,6 +295,46 @@ def job_tc(pwa, torch, stream, local, rank, precision="bfp16", gen="numpy"):
                 "form": "tc", "precision": precision, "build_norm_s": build_norm_s},
         roof={"bound": "tensor", "flops": 16.0 * N * K * n},
         dtype="bf16", h2d=16 * N * K, d2h=8 * K + 16 * N * K, cpu_baseline=cpu_baseline)
+
+
+def job_direct32(pwa, torch, stream, local, rank):
+    """The plain single-fit form (direct, FP32 amplitudes, one parameter set
+    per call) on the tensor-core form's sample, 4M events x 32 waves: the
+    denominator of the batched form's speed-up on the same GPU."""
+    import synth
+    N, n, n_mc = 32, 4_000_000, 10_000_000
+    A_d, A_m, n_gen = synth.torch_mixture_workload(synth.waves_linear(N), n, n_mc,
+                                                   synth.SEED_DATA + rank)
+    V = synth.start_points(N, 1, seed=synth.SEED_STARTS + rank)[0] * 2.0
+    L = pwa.Likelihood(N, device=local, forms=pwa.PWA_FORM_AMP, max_k=1, stream=stream.cuda_stream)
+    L.load_events(A_d, A_m, n_gen)
+    del A_m
+    L.build_norm()
+    dV = torch.from_numpy(V[None]).cuda()
+    dn = torch.empty(1, dtype=torch.float64, device="cuda")
+    dg = torch.empty(1, N, dtype=torch.complex128, device="cuda")
+    Vh = V[None].copy()
+
+    def cpu_baseline():
+        import oracle
+        sub = 200_000
+        A = A_d[:sub].cpu().numpy()
+        Mo = L.M if L.M is not None else L.build_norm()
+        dt, k = timed_oracle(lambda: oracle.nll_amp(A, Mo, V), 12.0)
+        return {"value": 1.0 / (dt * n / sub), "unit": UNIT, "cores": 1, "kind": "oracle",
+                "sample": "%d NLL+grad evaluations on the first 200k of the 4M events (FP64 C "
+                          "oracle, 1 thread, M as built on the GPU), scaled to the full sample" % k}
+
+    return Job(
+        name="direct_4M_32", lib=L, step=lambda: L.nll_grad_async(dV, dn, dg),
+        host_step=lambda: L.nll_grad(Vh), sync=L.sync, evals_per_step=1, launches_per_step=1,
+        flush=False,
+        workload="4M data events x 32 waves (FP32 amplitudes, direct form), M from 10M accepted "
+                 "MC, K=1 per evaluation (the tensor-core form's sample)",
+        config={"n_waves": N, "n_data": n, "n_mc_acc": n_mc, "n_mc_gen": n_gen, "K": 1,
+                "form": "amp"},
+        roof={"bound": "hbm", "bytes": 8.0 * N * n},
+        dtype="f32", h2d=16 * N + 8, d2h=8 + 16 * N + 8, cpu_baseline=cpu_baseline)
 
 
 def job_res(pwa, torch, stream, local, rank):
@@ -581,7 +623,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models", "hessian", "weights",
-                             "incoh", "incoh_table", "ampgen"])
+                             "incoh", "incoh_table", "ampgen", "direct_4M_32"])
     ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
@@ -614,6 +656,8 @@ def main():
         job = job_tc(pwa, torch, stream, local, rank, args.precision)
     elif args.workload == "res":
         job = job_res(pwa, torch, stream, local, rank)
+    elif args.workload == "direct_4M_32":
+        job = job_direct32(pwa, torch, stream, local, rank)
     elif args.workload == "ampgen":
         job = job_ampgen(pwa, torch, stream, local, rank)
     elif args.workload in ("incoh", "incoh_table"):
@@ -676,7 +720,8 @@ def main():
         sec = {}
         for name, make, steps in (
                 ("table", lambda: job_direct(pwa, torch, stream, local, rank, form="table"), 300),
-                ("tc", lambda: job_tc(pwa, torch, stream, local, rank, args.precision, gen="torch"), 40)):
+                ("tc", lambda: job_tc(pwa, torch, stream, local, rank, args.precision, gen="torch"), 40),
+                ("direct_4M_32", lambda: job_direct32(pwa, torch, stream, local, rank), 200)):
             j = make()
             ms = measure(j, steps, 3, evict_l2, stream, None, rank, local, pwa, torch)
             sec[name] = {
@@ -698,6 +743,12 @@ def main():
             j.lib.close()
             del j
             torch.cuda.empty_cache()
+        # the batched form against the plain single-fit form on the same
+        # sample and GPU (parameter sets per second; accuracy of each against
+        # the oracle: the tests' bounds, 4e-3 at 1M events for BFP16 and 1e-3
+        # for the FP32 direct form)
+        if "tc" in sec and "direct_4M_32" in sec:
+            sec["tc"]["speedup_vs_direct_same_sample"] = sec["tc"]["value"] / sec["direct_4M_32"]["value"]
         out["secondary"] = sec
     print(json.dumps(out))
     if dist:
