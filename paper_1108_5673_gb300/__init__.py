@@ -32,6 +32,7 @@ class Likelihood:
         self.ctx = _abi.pwa_create(device, n_waves, forms, precision, max_k, stream)
         self.last_status = PWA_OK
         self.M = None
+        self._bufs = {}
 
     def load_events(self, data_amp, mc_amp, n_mc_gen):
         """[n, N] amplitudes (coherent sum, Eq. 1), or [n, n_lambda, N] for an
@@ -88,8 +89,22 @@ class Likelihood:
         return nll
 
     def nll_grad(self, V):
-        nll, g, self.last_status = self._abi.pwa_nll_grad(self.ctx, V)
-        return nll, g
+        """NLL and Wirtinger gradient for V ([K, N] or [N] complex, host):
+        (nll [K], grad [K, N]). The call goes through buffers kept per K, whose
+        addresses are computed once (taking an array's address costs about
+        1 us in Python, against a ~40 us evaluation)."""
+        V = np.asarray(V)
+        K = V.shape[0] if V.ndim == 2 else 1
+        buf = self._bufs.get(K)
+        if buf is None:
+            Vb = np.empty((K, self.n_waves), dtype=np.complex128)
+            nb = np.empty(K)
+            gb = np.empty((K, self.n_waves), dtype=np.complex128)
+            buf = self._bufs[K] = (Vb, nb, gb, Vb.ctypes.data, nb.ctypes.data, gb.ctypes.data)
+        Vb, nb, gb, aV, an, ag = buf
+        np.copyto(Vb, V.reshape(K, -1))
+        self.last_status = self._abi.pwa_nll_grad_raw(self.ctx, aV, K, an, ag)
+        return nb.copy(), gb.copy()
 
     def hessian(self, V):
         """FUMILI's approximation of the NLL Hessian over p = (Re V, Im V),

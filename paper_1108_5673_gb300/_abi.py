@@ -329,6 +329,16 @@ def pwa_nll_grad(ctx, V):
     return nll, g, rc
 
 
+def pwa_nll_grad_raw(ctx, V_addr, K, nll_addr, grad_addr):
+    """pwa_nll_grad on host addresses the caller keeps valid (the Likelihood
+    object's buffers); returns the status (PWA_OK or PWA_EDOMAIN), raises on
+    other errors."""
+    rc = (_lib or load()).pwa_nll_grad(ctx, V_addr, K, nll_addr, grad_addr)
+    if rc != PWA_OK and rc != PWA_EDOMAIN:
+        _check(ctx, rc)
+    return rc
+
+
 def pwa_nll_grad_async(ctx, d_V, K, d_nll, d_grad=None):
     """Device pointers (CUDA tensors): d_V [K, n_waves] complex128, d_nll [K]
     float64, d_grad [K, n_waves] complex128 or None."""
