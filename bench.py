@@ -70,21 +70,22 @@ TRAFFIC = {"direct": 160.153856e6 + 3.591936e6,
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.091648e6 + 3.346944e6,
-           "weights": None,      # captured before the kernel template changed
-           "incoh": None,        # the same template
+           "weights": 800.122624e6 + 20.677120e6,
+           "incoh": 320.162048e6 + 3.327744e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
            "ampgen": 278.9e6 + 962.9e6,   # FP64-bound; DRAM bytes for reference
-           "direct_4M_32": None}
+           "direct_4M_32": 1024.242e6 + 4.771840e6,
+           "cov_ampgen": 1233.902e6 + 2723.644e6}   # FP64-bound; DRAM bytes for reference
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
            "models": "batched_items_kernel<2> (all models, one launch)", "hessian": "hess_tc_kernel<20>",
            "weights": "nll_amp_kernel<20, 2, 1, true> (weights mode)", "incoh": "nll_amp_kernel<20, 2, 2>",
            "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel",
-           "direct_4M_32": "nll_amp_kernel<32, 2>"}
+           "direct_4M_32": "nll_amp_kernel<32, 2>", "cov_ampgen": "cov_amp_kernel"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)
 DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,
                  "hessian": 2000, "weights": 2000, "incoh": 1500, "incoh_table": 1000,
-                 "ampgen": 100, "direct_4M_32": 500}
+                 "ampgen": 100, "direct_4M_32": 500, "cov_ampgen": 100}
 
 
 def measured_peaks():
@@ -510,6 +511,50 @@ def job_ampgen(pwa, torch, stream, local, rank):
         note="e2e passes host kinematics in (120 MB) and takes the amplitudes back (800 MB)")
 
 
+def cov_ampgen_flops(n_waves):
+    """FP64 operations per event of the covariant generator as written, each
+    +, -, x, fma, division and square root counted as one: ~357 for the
+    four-vectors, r~, the barrier factor, the photon polarisations and the
+    spin-0 and spin-2 contractions of the four components (every metric dot
+    product counted in full, 7 operations), and ~33 per wave for the
+    Breit-Wigner and the four complex products."""
+    return 357 + 33 * n_waves
+
+
+def job_cov_ampgen(pwa, torch, stream, local, rank):
+    import synth
+    n, N = N_MC, 12
+    waves = synth.cov_waves(N)
+    p3_h, _ = synth.radiative_events(n, np.random.default_rng(synth.SEED_MC + rank))
+    p3 = torch.from_numpy(p3_h).cuda()
+    out = torch.empty(n, 4, N, dtype=torch.complex64, device="cuda")
+    L = pwa.Likelihood(N, device=local, max_k=1, stream=stream.cuda_stream)
+
+    def cpu_baseline():
+        import oracle
+        sub = 200_000
+        dt, k = timed_oracle(lambda: oracle.covariant_amplitudes(p3_h[:sub], waves), 10.0)
+        return {"value": 1.0 / (dt * n / sub), "unit": "passes/s", "cores": 1, "kind": "oracle",
+                "sample": "%d covariant amplitude evaluations of the first 200k events x 12 waves "
+                          "x 4 components (FP64 C oracle, 1 thread), scaled to 5M events" % k}
+
+    return Job(
+        name="cov_ampgen", lib=L, step=lambda: L.covariant_amplitudes(waves, p3, out),
+        host_step=lambda: L.covariant_amplitudes(waves, p3_h), sync=lambda: L.last_status,
+        evals_per_step=1, launches_per_step=1, flush=False,
+        metric="covariant amplitude passes/s (5M J/psi -> gamma K+ K- events x 12 waves x 4 "
+               "components); % FP64 peak",
+        unit="passes/s",
+        workload="covariant tensor amplitudes of J/psi -> gamma X, X -> K+ K- (spins 0 and 2) for "
+                 "5M events x 12 waves x 4 components from device-resident 3-momenta (FP64 "
+                 "arithmetic, complex64 out to a device buffer)",
+        config={"n_waves": N, "n_events": n, "components": 4,
+                "flops_per_event": cov_ampgen_flops(N)},
+        roof={"bound": "alu", "flops": float(cov_ampgen_flops(N)) * n},
+        dtype="f64", h2d=72 * n, d2h=32 * N * n, cpu_baseline=cpu_baseline,
+        note="e2e passes host 3-momenta in (360 MB) and takes the amplitudes back (1.9 GB)")
+
+
 def job_fit_extra(pwa, torch, stream, local, rank, what):
     """FUMILI Hessian of the 1M-event sample, or the projection weights of its
     5M accepted MC events (host V in; H to the host, or w into a device buffer)."""
@@ -623,7 +668,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="direct", choices=["direct", "table", "tc", "res", "models", "hessian", "weights",
-                             "incoh", "incoh_table", "ampgen", "direct_4M_32"])
+                             "incoh", "incoh_table", "ampgen", "direct_4M_32", "cov_ampgen"])
     ap.add_argument("--precision", default="bfp16", choices=["bfp16", "bfp8"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
@@ -660,6 +705,8 @@ def main():
         job = job_direct32(pwa, torch, stream, local, rank)
     elif args.workload == "ampgen":
         job = job_ampgen(pwa, torch, stream, local, rank)
+    elif args.workload == "cov_ampgen":
+        job = job_cov_ampgen(pwa, torch, stream, local, rank)
     elif args.workload in ("incoh", "incoh_table"):
         job = job_incoh(pwa, torch, stream, local, rank, "table" if args.workload == "incoh_table" else "amp")
     elif args.workload in ("hessian", "weights"):
