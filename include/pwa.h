@@ -105,7 +105,10 @@ int pwa_destroy(pwa_ctx *ctx);
  * The library copies the amplitudes into its own structure-of-arrays store
  * (one float plane per real and imaginary part of each wave, events
  * contiguous), and builds the per-event table if PWA_FORM_TABLE was
- * requested; the caller keeps ownership of its buffers. Loading again
+ * requested; the caller keeps ownership of its buffers. Device inputs (here
+ * and in every call that loads or generates from caller buffers) are read
+ * after all work already issued to the device has completed, whichever
+ * stream produced them (the call synchronises the device first). Loading again
  * replaces the sample and invalidates the normalisation matrix.
  * Errors: PWA_EINVAL (n_data < 1, n_mc_acc < 1, n_mc_gen < n_mc_acc, null
  * pointers, bad dtype), PWA_ENOMEM, PWA_ECUDA. */

@@ -193,6 +193,20 @@ bool is_device_pointer(const void *p)
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Device inputs may come from work on any stream (another library's, the
+// caller's default stream): before the library's own stream reads them, all
+// work already issued to the device completes. Used by the calls that read
+// caller-provided device buffers at load time (one-time calls).
+int device_input_ready(pwa_ctx *c)
+{
+    const cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PWA_ECUDA, "waiting for device inputs: %s", cudaGetErrorString(e));
+    }
+    return PWA_OK;
+}
+
 // [nll K | grad 2NK | status,done | V 2NK] for K <= max_k, then max_k flags
 size_t io_flags_at(int N, int max_k) { return (size_t)max_k * (1 + 4 * (size_t)N) + 1; }
 size_t io_doubles(int N, int max_k) { return io_flags_at(N, max_k) + max_k; }
@@ -232,6 +246,8 @@ int pack_rows(pwa_ctx *c, const void *src, int64_t n, int dtype, int nw, float *
         return PWA_OK;
     const size_t esz = (dtype == PWA_C64 ? 8 : 16) * (size_t)nw;
     if (is_device_pointer(src)) {
+        if (int rc = device_input_ready(c))
+            return rc;
         CK(c, launch_pack(src, dtype, n, nw, dst, pitch, c->stream));
         return PWA_OK;
     }
@@ -278,6 +294,8 @@ int load_planes(pwa_ctx *c, const void *src, int64_t n, int dtype, Planes *out)
 int load_floats(pwa_ctx *c, const double *src, int64_t n, float *dst)
 {
     if (is_device_pointer(src)) {
+        if (int rc = device_input_ready(c))
+            return rc;
         CK(c, launch_to_float(src, n, dst, c->stream));
         return PWA_OK;
     }
@@ -1309,7 +1327,10 @@ static int generate(pwa_ctx *c, const GenWave *d_waves, int max_m, const double 
 {
     const double *dk = kin;
     double *staging = nullptr;
-    if (!is_device_pointer(kin)) {
+    if (is_device_pointer(kin)) {
+        if (int rc = device_input_ready(c))
+            return rc;
+    } else {
         int rc = dev_alloc(c, (void **)&staging, (size_t)n * 3 * sizeof(double), "kinematics");
         if (rc)
             return rc;
@@ -1447,7 +1468,10 @@ static int generate_cov(pwa_ctx *c, const CovWave *d_waves, const double *p3, in
 {
     const double *dk = p3;
     double *staging = nullptr;
-    if (!is_device_pointer(p3)) {
+    if (is_device_pointer(p3)) {
+        if (int rc = device_input_ready(c))
+            return rc;
+    } else {
         int rc = dev_alloc(c, (void **)&staging, (size_t)n * 9 * sizeof(double), "momenta");
         if (rc)
             return rc;

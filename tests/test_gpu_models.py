@@ -118,3 +118,42 @@ def test_batch_errors(pwa):
         B.load_model(0, w.A_data, w.A_mc, w.n_gen)
         with pytest.raises(PwaError):       # model 1 not loaded
             B.nll_grad([synth.start_points(8, 16), synth.start_points(8, 16)])
+
+
+@pytest.mark.slow
+def test_batch_bench_configuration(pwa):
+    """The model batch as the bench runs it: 64 models (8..48 waves,
+    100k..2M events each, MC twice the data, 63.4M data events in all, the
+    device generator), 16 sets per model, one launch over work items. Three
+    models checked against the oracle on their BFP16 inputs (the one with
+    the most waves, the one with the most events, the first), two sets
+    each: NLL within the tensor-core form's tolerance, the gradient by norm
+    and per component."""
+    import torch
+    from grad_bound import term_scale
+    spec = synth.model_batch_spec()
+    K = 16
+    pick = sorted({int(np.argmax([s[0] for s in spec])), int(np.argmax([s[1] for s in spec])), 0})
+    kept = {}
+    with pwa.ModelBatch([s[0] for s in spec], K) as B:
+        for j, (nw, nd, seed) in enumerate(spec):
+            A_d, A_m, n_gen = synth.torch_mixture_workload(synth.waves_linear(nw), nd, 2 * nd, seed)
+            B.load_model(j, A_d, A_m, n_gen)
+            if j in pick:
+                kept[j] = (A_d.cpu().numpy(), A_m.cpu().numpy(), n_gen)
+            del A_d, A_m
+        torch.cuda.empty_cache()
+        Vs = [synth.start_points(s[0], K, seed=s[2] + 7) * 2.0 for s in spec]
+        nll, g = B.nll_grad(Vs)
+        assert B.last_status == pwa.PWA_OK
+    for j in pick:
+        A_d, A_m, n_gen = kept[j]
+        Ap = bfp_amplitudes(A_d, 2)
+        Mo = oracle.norm_matrix_blas(A_m, n_gen)
+        for k in (0, K - 1):
+            no, go, bad = oracle.nll_amp(Ap, Mo, Vs[j][k])
+            assert bad == 0
+            gd = go - oracle.norm_term(Mo, Vs[j][k])[1]
+            assert abs(nll[j][k] - no) <= nll_tol(len(A_d)), (j, k, nll[j][k] - no)
+            assert np.linalg.norm(g[j][k] - go) <= GRAD_TOL * np.linalg.norm(gd), (j, k)
+            assert np.all(np.abs(g[j][k] - go) <= 3e-3 * term_scale(Ap, Vs[j][k])), (j, k)
