@@ -190,10 +190,20 @@ def oracle_all_cores(A, M, V, budget_s):
 
 class Job:
     """step(): enqueue one step on `stream` (device-resident inputs);
-    host_step(): one public host call (inputs from host memory, results back)."""
+    host_step(): one public host call (inputs from host memory, results back);
+    outputs(): optional, the last step's results as a numpy array (the line
+    reports whether they are all finite)."""
 
     def __init__(self, **kw):
         self.__dict__.update(kw)
+
+
+def outputs_finite(job):
+    """Whether the last step's results are all finite (None: not checked)."""
+    f = getattr(job, "outputs", None)
+    if f is None:
+        return None
+    return bool(np.all(np.isfinite(np.asarray(f()))))
 
 
 def job_direct(pwa, torch, stream, local, rank, form="amp"):
@@ -241,6 +251,7 @@ def job_direct(pwa, torch, stream, local, rank, form="amp"):
     return Job(
         name=form if table else "direct", lib=L,
         step=lambda: L.nll_grad_async(dV, dn, dg), host_step=lambda: L.nll_grad(Vh),
+        outputs=lambda: np.concatenate([dn.cpu().numpy(), dg.cpu().numpy().view(np.float64).ravel()]),
         sync=L.sync, evals_per_step=1, launches_per_step=1, flush=True,
         workload=("1M data events x 20 waves (FP32 per-event table of 400 floats, table form), "
                   "M from 5M accepted MC, K=1 per evaluation") if table else WORKLOAD,
@@ -289,6 +300,7 @@ def job_tc(pwa, torch, stream, local, rank, precision="bfp16", gen="numpy"):
 
     return Job(
         name="tc", lib=L, step=lambda: L.nll_grad_async(dV, dn, dg), host_step=lambda: L.nll_grad(Vs),
+        outputs=lambda: np.concatenate([dn.cpu().numpy(), dg.cpu().numpy().view(np.float64).ravel()]),
         sync=L.sync, evals_per_step=K, launches_per_step=2 * 3, flush=False,
         workload="4M data events x 32 waves, K=256 parameter sets per call on the tensor cores "
                  "(%s amplitudes, 24-bit V slices), M from 10M accepted MC" % precision,
@@ -328,6 +340,7 @@ def job_direct32(pwa, torch, stream, local, rank):
 
     return Job(
         name="direct_4M_32", lib=L, step=lambda: L.nll_grad_async(dV, dn, dg),
+        outputs=lambda: np.concatenate([dn.cpu().numpy(), dg.cpu().numpy().view(np.float64).ravel()]),
         host_step=lambda: L.nll_grad(Vh), sync=L.sync, evals_per_step=1, launches_per_step=1,
         flush=False,
         workload="4M data events x 32 waves (FP32 amplitudes, direct form), M from 10M accepted "
@@ -404,8 +417,15 @@ def job_models(pwa, torch, stream, local, rank):
                           "oracle, 1 thread), scaled by waves x events to 16 sets of each of the "
                           "64 models" % (k, nw)}
 
+    last = {}
+
+    def step():
+        last["r"] = B.nll_grad(Vs)
+
     return Job(
-        name="models", lib=B, step=lambda: B.nll_grad(Vs), host_step=lambda: B.nll_grad(Vs),
+        name="models", lib=B, step=step, host_step=lambda: B.nll_grad(Vs),
+        outputs=lambda: np.concatenate([np.ravel(x) for x in last["r"][0]] +
+                                       [np.ravel(x).view(np.float64) for x in last["r"][1]]),
         sync=lambda: B.last_status, evals_per_step=64 * K, launches_per_step=3,
         flush=False,
         workload="64 trial models (n_waves 8..48, 100k..2M data events each, MC 2x data, 63.4M "
@@ -752,6 +772,7 @@ def main():
                 "d2h_bytes_per_step": job.d2h},
         "gpu_launches": job.launches_per_step * args.steps,
         "status": m["status"],
+        "outputs_finite": m["finite"],
     }
     if m["clocks"] is not None:
         out["clocks"] = m["clocks"]
@@ -781,6 +802,7 @@ def main():
                         "unit": getattr(j, "unit", UNIT), "h2d_bytes_per_step": j.h2d,
                         "d2h_bytes_per_step": j.d2h},
                 "gpu_launches": j.launches_per_step * steps, "status": ms["status"],
+                "outputs_finite": ms["finite"],
                 "config": dict(j.config, l2="flushed between timed steps" if j.flush
                                else "inputs larger than L2 (129 MB), no flush",
                                ms_per_step_back_to_back=ms["b2b_ms"])}
@@ -831,6 +853,7 @@ def measure(job, steps, warmup, evict_l2, stream, dist, rank, local, pwa, torch)
         ends[i].record(stream)
     torch.cuda.synchronize()
     status = job.sync()
+    finite = outputs_finite(job)
     total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
     # back-to-back (no flush), for reference only
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -855,7 +878,7 @@ def measure(job, steps, warmup, evict_l2, stream, dist, rank, local, pwa, torch)
         sampler.wait()
         clocks = summarise_clocks(clock_path, local)
     return {"total_ms": total_ms, "b2b_ms": b2b_ms, "e2e_s": e2e_s, "status": status,
-            "clocks": clocks}
+            "clocks": clocks, "finite": finite}
 
 
 def roofline(job, avg_s, peaks):
