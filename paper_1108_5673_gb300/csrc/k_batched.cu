@@ -47,7 +47,10 @@
 //      image the prep kernel builds.
 //  X   [stage][2 blocks of 64 events][XS F rows (x0 then x1)][128 B]: MN-major
 //      A operand of GEMM 1 (events contiguous) and K-major B operand of GEMM 2
-//      (K = events) -- the same bytes serve both products.
+//      (K = events) -- the same bytes serve both products. The data store in
+//      global memory holds every 128-event tile in exactly this byte order, so
+//      a tile arrives with one contiguous bulk copy (a 2D tensor copy of 64
+//      events x XS F rows reads XS F separate 128-byte pieces, far apart).
 //  R'  [2 blocks of 64 rows (k,re/im)][128 events][128 B]: MN-major A operand
 //      of GEMM 2, written by the epilogue (each thread stores its event's row).
 // Tensor memory (512 columns): acc0..acc3 of one half chunk (32 sets, 64
@@ -105,6 +108,7 @@ __host__ __device__ inline double round_slices(double v, int T)
 
 struct BatchArgs {
     int n_waves, F, XS, K, n_chunks;
+    const unsigned char *xg;    // the data store: n_tiles tiles of 2 XS F 128 bytes
     int64_t n_events;
     const double *V;            // [K][N] complex
     const double *M;            // [N][N] complex
@@ -268,7 +272,7 @@ struct BatchShared {
 };
 
 template <int F, int XS>
-__device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const BatchArgs &a,
+__device__ __forceinline__ void batched_body(const BatchArgs &a,
                                              const TileRange &tr, unsigned char *smem_dyn,
                                              BatchShared &sh)
 {
@@ -333,10 +337,9 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
                     flags |= FLAG_TIMEOUT;
                     break;
                 }
-                const int e0 = (tr.tile0 + j * tr.stride) * kBM;
+                const int64_t tile = tr.tile0 + (int64_t)j * tr.stride;
                 mbar_arrive_expect_tx(&x_full[s], kXBytes);
-                tma_load_2d(sX + (size_t)s * kXBytes, xmap_p, e0, 0, &x_full[s]);
-                tma_load_2d(sX + (size_t)s * kXBytes + kXBlk, xmap_p, e0 + 64, 0, &x_full[s]);
+                bulk_load(sX + (size_t)s * kXBytes, a.xg + tile * kXBytes, kXBytes, &x_full[s]);
             }
             // copies still in flight complete before the block may exit
             for (int q = (j > NXS ? j - NXS : 0); q < j; ++q)
@@ -651,7 +654,7 @@ __device__ __forceinline__ void batched_body(const CUtensorMap *xmap_p, const Ba
 // One sample, a persistent grid: CTA b takes tiles b, b + grid, ...
 template <int F, int XS>
 __global__ void __launch_bounds__(kThreads, 1)
-    batched_kernel(const __grid_constant__ CUtensorMap xmap, const BatchArgs a, const int n_tiles)
+    batched_kernel(const BatchArgs a, const int n_tiles)
 {
     extern __shared__ unsigned char smem_dyn[];
     __shared__ BatchShared sh;
@@ -662,7 +665,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tr.slot = blockIdx.x;
     tr.mv_k0 = blockIdx.x;
     tr.mv_kstride = gridDim.x;
-    batched_body<F, XS>(&xmap, a, tr, smem_dyn, sh);
+    batched_body<F, XS>(a, tr, smem_dyn, sh);
 }
 
 // Many samples (the uneven model batch) in one launch: CTA b is the work item
@@ -674,8 +677,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 // count F (the tile shape of each wave-count bucket).
 template <int XS>
 __global__ void __launch_bounds__(kThreads, 1)
-    batched_items_kernel(const BatchItem *__restrict__ items, const BatchArgs *__restrict__ models,
-                         const CUtensorMap *__restrict__ maps)
+    batched_items_kernel(const BatchItem *__restrict__ items, const BatchArgs *__restrict__ models)
 {
     extern __shared__ unsigned char smem_dyn[];
     __shared__ BatchShared sh;
@@ -688,14 +690,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     tr.slot = it.slot;
     tr.mv_k0 = it.slot == 0 ? 0 : a.K;    // the model's first item forms M V
     tr.mv_kstride = 1;
-    const CUtensorMap *m = maps + it.model;
     switch (a.F) {
-    case 16: batched_body<16, XS>(m, a, tr, smem_dyn, sh); break;
-    case 32: batched_body<32, XS>(m, a, tr, smem_dyn, sh); break;
-    case 48: batched_body<48, XS>(m, a, tr, smem_dyn, sh); break;
-    case 64: batched_body<64, XS>(m, a, tr, smem_dyn, sh); break;
-    case 80: batched_body<80, XS>(m, a, tr, smem_dyn, sh); break;
-    case 96: batched_body<96, XS>(m, a, tr, smem_dyn, sh); break;
+    case 16: batched_body<16, XS>(a, tr, smem_dyn, sh); break;
+    case 32: batched_body<32, XS>(a, tr, smem_dyn, sh); break;
+    case 48: batched_body<48, XS>(a, tr, smem_dyn, sh); break;
+    case 64: batched_body<64, XS>(a, tr, smem_dyn, sh); break;
+    case 80: batched_body<80, XS>(a, tr, smem_dyn, sh); break;
+    case 96: batched_body<96, XS>(a, tr, smem_dyn, sh); break;
     default: break;
     }
 }
@@ -792,12 +793,16 @@ __global__ void batched_items_finalize(const BatchArgs *__restrict__ models, con
 // ---- block-floating-point encoding of the data (once per load) ---------------
 // One thread per event: shared exponent E = exponent of the largest |feature|
 // (max = m 2^E, m in [1/2, 1)), slices x0 = rint(A 2^(8-E)) and, for XS = 2,
-// x1 = rint((A 2^(8-E) - x0) 256).
+// x1 = rint((A 2^(8-E) - x0) 256). Written in the tile order the kernel's
+// shared memory uses: event i sits in 64-event block i / 64 (xs F 128 bytes,
+// consecutive blocks), row r (x0 rows, then x1 rows) at 128-byte pitch with
+// the 128-byte swizzle, at byte 2 (i % 64) of its row.
 __global__ void batched_encode_kernel(const float *__restrict__ planes, int64_t pitch, int64_t n,
-                                      int rows_in, int F, int xs, __nv_bfloat16 *__restrict__ out,
+                                      int rows_in, int F, int xs, unsigned char *__restrict__ out,
                                       long long *sum_e)
 {
     long long es = 0;
+    const size_t blk_bytes = (size_t)xs * F * 128;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < pitch;
          i += (int64_t)gridDim.x * blockDim.x) {
         const bool valid = i < n;
@@ -808,6 +813,8 @@ __global__ void batched_encode_kernel(const float *__restrict__ planes, int64_t 
         int E = 0;
         if (m > 0.f)
             frexpf(m, &E);
+        unsigned char *blk = out + (size_t)(i >> 6) * blk_bytes;
+        const int byte = 2 * (int)(i & 63);
         for (int r = 0; r < F; ++r) {
             float x0 = 0.f, x1 = 0.f;
             if (valid && r < rows_in) {
@@ -815,9 +822,9 @@ __global__ void batched_encode_kernel(const float *__restrict__ planes, int64_t 
                 x0 = rintf(x);
                 x1 = rintf((x - x0) * 256.f);
             }
-            out[(int64_t)r * pitch + i] = __float2bfloat16_rn(x0);
+            *reinterpret_cast<__nv_bfloat16 *>(blk + sw128(r, byte)) = __float2bfloat16_rn(x0);
             if (xs == 2)
-                out[(int64_t)(F + r) * pitch + i] = __float2bfloat16_rn(x1);
+                *reinterpret_cast<__nv_bfloat16 *>(blk + sw128(F + r, byte)) = __float2bfloat16_rn(x1);
         }
         if (valid)
             es += E;
@@ -857,16 +864,16 @@ cudaError_t configure_xs()
 }
 
 template <int XS>
-cudaError_t launch_main(int F, int grid, uint32_t smem, cudaStream_t s, const CUtensorMap *xmap,
-                        const BatchArgs &a, int n_tiles)
+cudaError_t launch_main(int F, int grid, uint32_t smem, cudaStream_t s, const BatchArgs &a,
+                        int n_tiles)
 {
     switch (F) {
-    case 16: batched_kernel<16, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 32: batched_kernel<32, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 48: batched_kernel<48, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 64: batched_kernel<64, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 80: batched_kernel<80, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
-    case 96: batched_kernel<96, XS><<<grid, kThreads, smem, s>>>(*xmap, a, n_tiles); break;
+    case 16: batched_kernel<16, XS><<<grid, kThreads, smem, s>>>(a, n_tiles); break;
+    case 32: batched_kernel<32, XS><<<grid, kThreads, smem, s>>>(a, n_tiles); break;
+    case 48: batched_kernel<48, XS><<<grid, kThreads, smem, s>>>(a, n_tiles); break;
+    case 64: batched_kernel<64, XS><<<grid, kThreads, smem, s>>>(a, n_tiles); break;
+    case 80: batched_kernel<80, XS><<<grid, kThreads, smem, s>>>(a, n_tiles); break;
+    case 96: batched_kernel<96, XS><<<grid, kThreads, smem, s>>>(a, n_tiles); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -933,12 +940,12 @@ cudaError_t launch_batched_encode(const float *planes, int64_t pitch, int64_t n,
     const int blocks = (int)std::min<int64_t>((pitch + 255) / 256, 4096);
     batched_encode_kernel<<<blocks, 256, 0, s>>>(planes, pitch, n, 2 * n_waves,
                                                  batched_features(n_waves), xs,
-                                                 static_cast<__nv_bfloat16 *>(out), sum_e);
+                                                 static_cast<unsigned char *>(out), sum_e);
     return cudaGetLastError();
 }
 
 // K <= batched_max_k(n_waves, xs) parameter sets; scratch >= batched_scratch_bytes.
-cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, int xs,
+cudaError_t launch_batched(const void *xbf, int64_t n_events, int n_waves, int xs,
                            const long long *sum_e, const double *V, int K, const double *M,
                            void *scratch, int grid, int *status, int *done, double *nll,
                            double *grad, cudaStream_t s, int nxs)
@@ -954,6 +961,7 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
     a.XS = xs;
     a.K = K;
     a.n_chunks = nch;
+    a.xg = static_cast<const unsigned char *>(xbf);
     a.n_events = n_events;
     a.V = V;
     a.M = M;
@@ -977,8 +985,8 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
         return e;
     const int n_tiles = (int)((n_events + kBM - 1) / kBM);
     const uint32_t smem = batch_smem(F, xs, batch_hpt(K), nxs).bytes;
-    e = xs == 2 ? launch_main<2>(F, grid, smem, s, xmap, a, n_tiles)
-                : launch_main<1>(F, grid, smem, s, xmap, a, n_tiles);
+    e = xs == 2 ? launch_main<2>(F, grid, smem, s, a, n_tiles)
+                : launch_main<1>(F, grid, smem, s, a, n_tiles);
     if (e != cudaSuccess)
         return e;
     batched_finalize<<<K, 64, 0, s>>>(a, grid, done, nll, grad);
@@ -987,7 +995,7 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
 
 // ---- the uneven model batch in one launch -------------------------------------
 // Plan buffer (device, one allocation), in this order: BatchArgs[n_models],
-// CUtensorMap[n_models] (64-byte aligned), BatchItem[n_items], int
+// BatchItem[n_items], int
 // n_slots[n_models], the per-model output pointers (done, nll, grad), then
 // per model its scratch: W image, G^T partials, log partials, M V, set
 // exponents, domain flags. The log partials and domain flags of all models
@@ -995,7 +1003,7 @@ cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_wave
 namespace {
 
 struct PlanLayout {
-    size_t args, maps, items, nslots, pdone, pnll, pgrad, zero, zero_bytes, scratch, total;
+    size_t args, items, nslots, pdone, pnll, pgrad, zero, zero_bytes, scratch, total;
     std::vector<size_t> wimg, gpart, lpart, mv, T, kflags;
     std::vector<BatchItem> items_h;
     std::vector<int> slots;
@@ -1037,8 +1045,6 @@ PlanLayout plan_layout(const BatchModelDesc *m, int n_models, int xs, int K, int
     size_t o = 0;
     p.args = o;
     o = up256(o + sizeof(BatchArgs) * n_models);
-    p.maps = o;
-    o = up256(o + sizeof(CUtensorMap) * n_models);
     p.items = o;
     o = up256(o + sizeof(BatchItem) * p.items_h.size());
     p.nslots = o;
@@ -1109,6 +1115,7 @@ cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_m
         a.XS = xs;
         a.K = K;
         a.n_chunks = nch;
+        a.xg = static_cast<const unsigned char *>(m.xbf);
         a.n_events = m.n_events;
         a.V = m.V;
         a.M = m.M;
@@ -1122,7 +1129,6 @@ cudaError_t batched_plan_build(void *plan, const BatchModelDesc *models, int n_m
         a.status = m.status;
         a.nxs_req = nxs;
         memcpy(&h[p.args + i * sizeof(BatchArgs)], &a, sizeof a);
-        memcpy(&h[p.maps + i * sizeof(CUtensorMap)], &m.xmap, sizeof(CUtensorMap));
         memcpy(&h[p.nslots + i * sizeof(int)], &p.slots[i], sizeof(int));
         memcpy(&h[p.pdone + i * sizeof(void *)], &m.done, sizeof(void *));
         memcpy(&h[p.pnll + i * sizeof(void *)], &m.nll, sizeof(void *));
@@ -1155,12 +1161,11 @@ cudaError_t launch_batched_items(void *plan, const BatchModelDesc *models, int n
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     const BatchItem *items = reinterpret_cast<const BatchItem *>(d + p.items);
-    const CUtensorMap *maps = reinterpret_cast<const CUtensorMap *>(d + p.maps);
     const int n_items = (int)p.items_h.size();
     if (xs == 2)
-        batched_items_kernel<2><<<n_items, kThreads, smem, s>>>(items, args, maps);
+        batched_items_kernel<2><<<n_items, kThreads, smem, s>>>(items, args);
     else
-        batched_items_kernel<1><<<n_items, kThreads, smem, s>>>(items, args, maps);
+        batched_items_kernel<1><<<n_items, kThreads, smem, s>>>(items, args);
     if ((e = cudaGetLastError()) != cudaSuccess)
         return e;
     batched_items_finalize<<<n_models * K, 64, 0, s>>>(

@@ -40,7 +40,7 @@ struct pwa_ctx {
     float *table = nullptr;
     int64_t table_pitch = 0;
     float *tmax = nullptr;  // [N^2] max over events of |t_p|
-    void *xbf = nullptr;    // BF16 slices [2F][pitch] of the data (tensor-core form)
+    void *xbf = nullptr;    // BF16 slices of the data in 64-event blocks (tensor-core form)
     long long *xsum = nullptr;  // sum of the per-event exponents (inside xbf)
     int xs = 2;                 // BF16 slices of the amplitudes (tensor-core form)
     int n_lambda = 1;           // incoherent components per event (data planes hold L N waves)
@@ -78,7 +78,7 @@ struct pwa_ctx {
     size_t fx_bytes = 0;
     float *d_w = nullptr;       // projection weights when the caller's buffer is on the host
     int64_t w_len = 0;
-    CUtensorMap data_map, table_map, xbf_map;
+    CUtensorMap data_map, table_map;
     size_t work_bytes = 0;
     bool loaded = false, has_norm = false;
     double *M = nullptr;     // [N][N] complex
@@ -382,7 +382,7 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
             per = std::min(c->tune_tc_per, kmax);
         for (int k0 = 0; k0 < K; k0 += per) {
             const int kk = std::min(per, K - k0);
-            cudaError_t e = launch_batched(&c->xbf_map, c->n_data, N, c->xs, c->xsum, dV + (size_t)2 * N * k0,
+            cudaError_t e = launch_batched(c->xbf, c->n_data, N, c->xs, c->xsum, dV + (size_t)2 * N * k0,
                                            kk, c->M, c->d_work, c->num_sms, status, done, dnll + k0,
                                            dgrad ? dgrad + (size_t)2 * N * k0 : nullptr, c->stream,
                                            c->tune_tc_nxs);
@@ -630,23 +630,6 @@ cudaError_t encode_planes_map(CUtensorMap *map, const float *base, int64_t n, in
     cuuint32_t estr[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides,
                     box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-// BF16 planes [rows][pitch] with 128-byte swizzle, box 64 events x rows.
-cudaError_t encode_bf16_planes_map(CUtensorMap *map, const void *base, int64_t n, int64_t pitch,
-                                   int rows)
-{
-    auto fn = get_encode_fn();
-    if (!fn)
-        return cudaErrorNotSupported;
-    cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides,
-                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -1235,8 +1218,6 @@ static int finish_load(pwa_ctx *c, int rc, int64_t n_data, int64_t n_mc_acc, dou
             c->xsum = reinterpret_cast<long long *>(static_cast<char *>(c->xbf) + slice_bytes);
             cudaError_t e = launch_batched_encode(c->data.ptr, c->data.pitch, c->data.n, c->N, c->xs,
                                                   c->xbf, c->xsum, c->stream);
-            if (e == cudaSuccess)
-                e = encode_bf16_planes_map(&c->xbf_map, c->xbf, c->data.n, c->data.pitch, c->xs * F);
             if (e != cudaSuccess)
                 rc = fail(c, PWA_ECUDA, "block-floating-point store: %s", cudaGetErrorString(e));
         }
@@ -1885,7 +1866,7 @@ static std::vector<BatchModelDesc> batch_descs(pwa_batch *b, int K)
     size_t off = 0;
     for (int m = 0; m < nm; ++m) {
         const pwa_ctx *c = b->models[m];
-        d[m].xmap = c->xbf_map;
+        d[m].xbf = c->xbf;
         d[m].n_events = c->n_data;
         d[m].n_waves = c->N;
         d[m].sum_e = c->xsum;

@@ -402,8 +402,6 @@ struct Planes {
 // box_x events x box_y planes. Returns cudaSuccess or an error.
 cudaError_t encode_planes_map(CUtensorMap *map, const float *base, int64_t n, int64_t pitch,
                               int rows, int box_x, int box_y);
-cudaError_t encode_bf16_planes_map(CUtensorMap *map, const void *base, int64_t n, int64_t pitch,
-                                   int rows);
 
 // k_pack.cu
 cudaError_t launch_pack(const void *src, int dtype, int64_t n, int n_waves, float *planes,
@@ -424,14 +422,16 @@ int batched_max_k(int n_waves, int xs);   // parameter sets per launch
 size_t batched_scratch_bytes(int n_waves, int xs, int K, int grid);
 cudaError_t batched_configure();
 // Block-floating-point copy of the data planes for the tensor-core form:
-// out = [xs F][pitch] BF16 (slice x0 rows 0..F-1, slice x1 rows F..2F-1; rows
-// past 2 n_waves and events past n are zero); *sum_e (zeroed here) receives
-// the sum over events of the event exponents.
+// xs F rows of BF16 per event (slice x0 rows 0..F-1, slice x1 rows F..2F-1;
+// rows past 2 n_waves and events past n are zero) in 64-event blocks of
+// xs F 128 bytes, each laid out as the kernel's shared memory holds it (out:
+// 2 xs F pitch bytes); *sum_e (zeroed here) receives the sum over events of
+// the event exponents.
 cudaError_t launch_batched_encode(const float *planes, int64_t pitch, int64_t n, int n_waves, int xs,
                                   void *out, long long *sum_e, cudaStream_t s);
 // nxs: X pipeline stages (0: as many as shared memory takes; the autotuner
 // may ask for fewer, from 2 up to batched_max_x_stages)
-cudaError_t launch_batched(const CUtensorMap *xmap, int64_t n_events, int n_waves, int xs,
+cudaError_t launch_batched(const void *xbf, int64_t n_events, int n_waves, int xs,
                            const long long *sum_e, const double *V, int K, const double *M,
                            void *scratch, int grid, int *status, int *done, double *nll,
                            double *grad, cudaStream_t s, int nxs = 0);
@@ -442,7 +442,7 @@ int batched_max_x_stages(int n_waves, int xs, int K);
 // items_per_sm in all with equal estimated cost; one kernel takes them all
 // (one CTA per item), a prep kernel and a final kernel serve every model.
 struct BatchModelDesc {
-    CUtensorMap xmap;          // the model's BF16 slices (encode_bf16_planes_map)
+    const void *xbf;           // the model's BF16 store (launch_batched_encode)
     int64_t n_events;
     int n_waves;
     const long long *sum_e;    // the sum of its event exponents
