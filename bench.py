@@ -66,7 +66,7 @@ WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M 
 # capture of the current kernel, or None where there is none.
 TRAFFIC = {"direct": 160.153856e6 + 3.591936e6,
            "table": 1600.119e6 + 3.221760e6,
-           "tc": 2 * (1025.548e6 + 3.824384e6),        # a step is two launches of 128 sets
+           "tc": 2 * (1024.872e6 + 3.708160e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.091648e6 + 3.346944e6,
