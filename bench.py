@@ -693,6 +693,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the table and tensor-core forms in the default line")
+    ap.add_argument("--tune", action="store_true",
+                    help="run the library's autotuner on the loaded sample (no cache) before "
+                         "timing; its choice is reported in config.autotune")
     args = ap.parse_args()
     if args.steps is None:
         args.steps = DEFAULT_STEPS[args.workload] if args.impl == "gb300" else 3
@@ -743,6 +746,9 @@ def main():
         return flush.sum()
 
     peaks = measured_peaks()
+    tuned = None
+    if args.tune and hasattr(job.lib, "autotune"):
+        tuned = job.lib.autotune(None)
     m = measure(job, args.steps, args.warmup, evict_l2, stream, dist, rank, local, pwa, torch)
     total_ms_max, e2e_max = max_over_ranks(dist, [m["total_ms"], m["e2e_s"]], "cuda")
     if rank != 0:
@@ -762,6 +768,8 @@ def main():
                    "ms_per_step_back_to_back": m["b2b_ms"]})
     if getattr(job, "note", None):
         config["note"] = job.note
+    if tuned is not None:
+        config["autotune"] = tuned
     out = {
         "metric": getattr(job, "metric", METRIC), "value": value,
         "unit": getattr(job, "unit", UNIT), "n_gpus": world, "steps": args.steps,

@@ -1825,7 +1825,7 @@ struct pwa_batch {
     bool per_model = false;
     void *plan = nullptr;        // device plan of the one-launch form (for graph_k)
     size_t plan_bytes = 0;
-    int items_per_sm = 4;        // work granularity (pwa_batch_autotune picks it)
+    int items_per_sm = 16;       // work granularity (pwa_batch_autotune picks it)
     int tune_nxs = 0;            // X stages of the tensor-core kernel (0 = as many as fit)
     int num_sms = 0;
     char err[512] = {0};
@@ -2472,7 +2472,7 @@ int pwa_batch_autotune(pwa_batch *b, const char *cache_path, char *choice, int c
             return bfail(b, PWA_ECUDA, "autotune: event creation failed");
         }
         int rc = PWA_OK;
-        for (int ips : {1, 2, 4, 8}) {
+        for (int ips : {4, 8, 16, 32}) {
             for (int nxs = 2; nxs <= top && !rc; ++nxs) {
                 b->items_per_sm = ips;
                 b->tune_nxs = nxs;
