@@ -451,8 +451,9 @@ int pwa_autotune(pwa_ctx *ctx, const char *cache_path, char *choice, int choice_
 
 /* Launch-shape autotuner of a model batch (the one-launch form; Sec. 2: many
  * trial models are fitted to one data set): times the batch's evaluation for
- * max_k sets with 1, 2, 4 or 8 work items per SM and 2 up to the most X
- * pipeline stages shared memory takes, applies the fastest and records it
+ * max_k sets with 4, 8, 16 or 32 work items per SM (16 without tuning) and
+ * 2 up to the most X pipeline stages shared memory takes, applies the
+ * fastest and records it
  * in the JSON cache (cache_path as for pwa_autotune; a cached key is applied
  * without timing). The key holds the device name, SM count, number of
  * models, total waves and events, max_k and the precision. Results do not
