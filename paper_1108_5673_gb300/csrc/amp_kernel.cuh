@@ -27,15 +27,37 @@ struct AmpCfg {
     static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
     static constexpr int ROWS = 2 * N * L;
     static constexpr uint32_t STAGE_BYTES = ROWS * TE * 4;
-    // Each group owns SPG stages of the ring, so a stage's successive uses
-    // always belong to the same group: a waiter can then never be a full
-    // barrier phase behind (parity waits only tell apart adjacent phases).
+    // The ring. When two or more stages per group fit in 200 KB, each group
+    // owns SPG of them (at most four): tile j goes to group j % G and to that
+    // group's stage (j / G) % SPG, so a stage's successive uses belong to one
+    // group and a waiter is never a whole phase behind. Otherwise (one stage
+    // per group would fit), as many stages as fit are shared by the groups:
+    // tile j sits in stage j % STAGES (a third stage at 32 waves, or for two
+    // components of 20 waves, measured 8% and 21% faster than two; a fifth
+    // shared 40 KB stage at 20 waves was slower than four owned ones). A
+    // shared stage has two full barriers, for its even and its odd uses.
+    // A group waiting for use u of a stage (tile j) waits on the barrier
+    // whose previous phase was use u - 2 (tile j - 2 STAGES); with 2 STAGES a
+    // multiple of G that tile was the same group's, consumed before, so the
+    // parity wait (which only tells adjacent phases apart) cannot match an
+    // older phase; and use u + 2 cannot complete before this group releases
+    // use u (the refill for use u + 1 waits for that release).
+    static constexpr int ST_RAW = (200 * 1024) / STAGE_BYTES;
+    static constexpr int ST_CAP = ST_RAW < G ? G : (ST_RAW > 8 ? 8 : ST_RAW);
+    static constexpr int pick_stages()
+    {
+        for (int st = ST_CAP; st > G; --st)
+            if ((2 * st) % G == 0)
+                return st;
+        return G;
+    }
     static constexpr int SPG_RAW = (200 * 1024) / (STAGE_BYTES * G);
-    static constexpr int SPG = SPG_RAW < 1 ? 1 : (SPG_RAW > 4 ? 4 : SPG_RAW);
-    static constexpr int STAGES = G * SPG;
+    static constexpr bool SHARED = SPG_RAW < 2;
+    static constexpr int SPG = SHARED ? 1 : (SPG_RAW > 4 ? 4 : SPG_RAW);
+    static constexpr int STAGES = SHARED ? pick_stages() : G * SPG;
     static constexpr int THREADS = (CW + 2) * 32;      // + producer warp + helper warp
     static constexpr int NF = 2 * N + 1;               // float partials: ln-fraction, gradient
-    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 2 * STAGES * sizeof(uint64_t);
+    static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 3 * STAGES * sizeof(uint64_t);
     // dynamic shared memory must leave room for the static arrays (< 16 KB)
     static constexpr bool FITS = SMEM <= 210 * 1024;
 };
@@ -210,8 +232,10 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     constexpr int NF = C::NF;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *tiles = reinterpret_cast<float *>(smem_raw);
+    // full[s] (owned stages) or full[(u & 1) STAGES + s] (shared): use u of
+    // stage s; empty[s]: its release
     uint64_t *full = reinterpret_cast<uint64_t *>(smem_raw + (size_t)STAGES * C::STAGE_BYTES);
-    uint64_t *empty = full + STAGES;
+    uint64_t *empty = full + 2 * STAGES;
 
     __shared__ WaveCoef Vc[N];
     __shared__ double sV[2 * N];   // the helper warp's copy of V
@@ -224,12 +248,20 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // tiles of this CTA: blockIdx.x, blockIdx.x + gridDim.x, ...; tile j goes
-    // to group j % GROUPS and to that group's stage (j / GROUPS) % SPG
+    // to group j % GROUPS and to stage stage_of(j) (see AmpCfg)
     const int n_my =
         (n_tiles > (int)blockIdx.x) ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
     const uint32_t stage_tx = 2u * (uint32_t)a.n_waves * L * TE * 4u;
-    auto stage_of = [](int j) { return (j % GROUPS) * C::SPG + (j / GROUPS) % C::SPG; };
-    auto use_of = [](int j) { return (uint32_t)((j / GROUPS) / C::SPG); };
+    auto stage_of = [](int j) {
+        return C::SHARED ? j % STAGES : (j % GROUPS) * C::SPG + (j / GROUPS) % C::SPG;
+    };
+    auto use_of = [](int j) {
+        return (uint32_t)(C::SHARED ? j / STAGES : (j / GROUPS) / C::SPG);
+    };
+    auto full_of = [&](int j) {
+        return &full[(C::SHARED ? (use_of(j) & 1) * STAGES : 0) + stage_of(j)];
+    };
+    auto full_parity = [&](int j) { return C::SHARED ? (use_of(j) >> 1) & 1u : use_of(j) & 1u; };
     // tiles the producer issues (none when the timeout path is being tested)
     const int n_issue = a.stall_ns ? 0 : n_my;
     const unsigned long long wait_ns = a.stall_ns ? a.stall_ns : kWaitLimitNs;
@@ -237,15 +269,16 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
+            mbar_init(&full[STAGES + s], 1);
             mbar_init(&empty[s], GW);
         }
         fence_barrier_init();
         s_flags = 0;
         // start streaming before the prologue below (its global loads take ~1 us)
         for (int j = 0; j < n_first; ++j) {
-            mbar_arrive_expect_tx(&full[stage_of(j)], stage_tx);
+            mbar_arrive_expect_tx(full_of(j), stage_tx);
             tma_load_2d(tiles + (size_t)stage_of(j) * ROWS * TE, &map,
-                        ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[stage_of(j)]);
+                        ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, full_of(j));
         }
     }
     // Rows of padded waves (n_waves < N) are never written by TMA: zero them
@@ -277,14 +310,14 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
                     flags |= FLAG_TIMEOUT;
                     break;
                 }
-                mbar_arrive_expect_tx(&full[s], stage_tx);
+                mbar_arrive_expect_tx(full_of(j), stage_tx);
                 tma_load_2d(tiles + (size_t)s * ROWS * TE, &map,
-                            ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, &full[s]);
+                            ((int)blockIdx.x + j * (int)gridDim.x) * TE, 0, full_of(j));
             }
             // no copy may still be landing in shared memory when the CTA exits
             // (the last STAGES tiles issued are the latest use of every stage)
             for (int q = (j > STAGES ? j - STAGES : 0); q < j; ++q) {
-                if (!mbar_wait(&full[stage_of(q)], use_of(q) & 1))
+                if (!mbar_wait(full_of(q), full_parity(q)))
                     flags |= FLAG_TIMEOUT;
             }
         }
@@ -304,8 +337,7 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
         int bad = 0;
         for (int j = grp; j < n_my; j += GROUPS) {
             const int s = stage_of(j);
-            const uint32_t u = use_of(j);
-            if (!mbar_wait(&full[s], u & 1, wait_ns)) {
+            if (!mbar_wait(full_of(j), full_parity(j), wait_ns)) {
                 flags |= FLAG_TIMEOUT;
                 break;
             }
