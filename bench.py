@@ -64,17 +64,17 @@ N_WAVES, N_DATA, N_MC = 20, 1_000_000, 5_000_000
 WORKLOAD = "1M data events x 20 waves (FP32 amplitudes, direct form), M from 5M accepted MC, K=1 per evaluation"
 # DRAM bytes (read + write) per step of the timed kernel from one ncu
 # capture of the current kernel, or None where there is none.
-TRAFFIC = {"direct": 160.153856e6 + 3.591936e6,
+TRAFFIC = {"direct": 160.139776e6 + 3.347968e6,
            "table": 1600.119e6 + 3.221760e6,
            "tc": 2 * (1024.872e6 + 3.708160e6),        # a step is two launches of 128 sets
            "res": 1148.176e6 + 3.313920e6,
            "models": None,
            "hessian": 160.091648e6 + 3.346944e6,
-           "weights": 800.122624e6 + 20.677120e6,
-           "incoh": 320.162048e6 + 3.327744e6,
+           "weights": 800.125184e6 + 21.052672e6,
+           "incoh": 320.158464e6 + 3.042048e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
            "ampgen": 278.9e6 + 962.9e6,   # FP64-bound; DRAM bytes for reference
-           "direct_4M_32": 1024.242e6 + 4.771840e6,
+           "direct_4M_32": 1024.256e6 + 3.621888e6,
            "cov_ampgen": 1233.902e6 + 2723.644e6}   # FP64-bound; DRAM bytes for reference
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",
