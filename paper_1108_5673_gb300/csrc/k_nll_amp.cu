@@ -137,7 +137,9 @@ cudaError_t amp_configure()
     return e;
 }
 
-// One persistent CTA per SM; PWA_AMP_GRID overrides it (a tuning knob).
+// One persistent CTA per SM; PWA_AMP_GRID overrides it (a tuning knob, and a
+// test's way to give each CTA many tiles). It serves the TMA-fed incoherent
+// launches as well, whose scratch has the same layout.
 int amp_grid(int n_waves, int num_sms)
 {
     (void)n_waves;

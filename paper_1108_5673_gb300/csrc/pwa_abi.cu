@@ -409,7 +409,7 @@ int enqueue_eval(pwa_ctx *c, const double *dV, int K, double *dnll, double *dgra
         a.stall_ns = test_stall_ns();
         cudaError_t e = cudaSuccess;
         if (c->form == PWA_FORM_AMP && c->n_lambda > 1 && c->incoh_tma)
-            e = launch_nll_incoh_tma(&c->data_map, c->n_lambda, a, c->num_sms, c->stream);
+            e = launch_nll_incoh_tma(&c->data_map, c->n_lambda, a, amp_grid(N, c->num_sms), c->stream);
         else if (c->form == PWA_FORM_AMP && c->n_lambda > 1)
             e = launch_nll_incoh(c->data, c->n_lambda, a, c->num_sms, c->stream);
         else if (c->form == PWA_FORM_AMP)
