@@ -83,6 +83,8 @@ KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "incoh_table": "nll_table_kernel<20>", "ampgen": "amp_gen_kernel",
            "direct_4M_32": "nll_amp_kernel<32, 2>", "cov_ampgen": "cov_amp_kernel"}
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 dense FP64 (nominal)
+HBM_NOMINAL_GBS = 7900.0     # GB300 HBM3e (nominal), beside the measured copy peak
+BF16_NOMINAL_TFLOPS = 2250.0  # GB300 dense bf16 (nominal)
 DEFAULT_STEPS = {"direct": 3000, "table": 1000, "tc": 300, "res": 1000, "models": 100,
                  "hessian": 2000, "weights": 2000, "incoh": 1500, "incoh_table": 1000,
                  "ampgen": 100, "direct_4M_32": 500, "cov_ampgen": 100}
@@ -894,7 +896,8 @@ def roofline(job, avg_s, peaks):
     if job.roof["bound"] == "hbm":
         achieved = job.roof["bytes"] / avg_s / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm"], "algorithmic_bytes_per_launch": job.roof["bytes"]}
+                "frac": achieved / peaks["hbm"], "algorithmic_bytes_per_launch": job.roof["bytes"],
+                "peak_nominal": HBM_NOMINAL_GBS, "frac_nominal": achieved / HBM_NOMINAL_GBS}
         if "flops" in job.roof:   # a contraction below the machine balance: tensor use for context
             tf = job.roof["flops"] / avg_s / 1e12
             roof.update({"tensor_achieved_tflops": tf, "tensor_frac": tf / peaks["bf16"]})
@@ -908,6 +911,7 @@ def roofline(job, avg_s, peaks):
         achieved = job.roof["flops"] / avg_s / 1e12
         roof = {"bound": "tensor", "achieved": achieved, "peak": peaks["bf16"], "unit": "TFLOP/s",
                 "frac": achieved / peaks["bf16"], "algorithmic_flops_per_step": job.roof["flops"],
+                "peak_nominal": BF16_NOMINAL_TFLOPS, "frac_nominal": achieved / BF16_NOMINAL_TFLOPS,
                 "peak_note": "bf16 burst; the step time includes the small prep and final kernels"}
     roof.update({"traffic": TRAFFIC[job.name], "kernel": KERNELS[job.name],
                  "peak_kind": "nominal" if job.roof["bound"] == "alu" else peaks["kind"]})
