@@ -683,6 +683,46 @@ def job_value(world, evals_per_step, steps, total_ms_max):
     return world * evals_per_step * steps / (total_ms_max / 1e3)
 
 
+def matmul_peaks(reps=50, n=8192):
+    """Library GEMM rates on this GPU, for the roofline of a TF32 operand
+    choice: torch.matmul n^3 in TF32, BF16 and plain FP32, each timed with
+    CUDA events over `reps` back-to-back products after 5 warm-ups (2 n^3
+    flops each), with the SM clocks sampled meanwhile. Prints one JSON line."""
+    import torch
+    dev = torch.device("cuda", 0)
+    clock_path = os.path.join(tempfile.gettempdir(), "matmul_peaks_clocks.csv")
+    sampler = start_clock_sampler(clock_path)
+    out = {}
+    for name, dt, tf32 in (("tf32", torch.float32, True), ("bf16", torch.bfloat16, False),
+                           ("fp32", torch.float32, False)):
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        a = torch.randn(n, n, device=dev, dtype=dt)
+        b = torch.randn(n, n, device=dev, dtype=dt)
+        c = torch.empty(n, n, device=dev, dtype=dt)
+        for _ in range(5):
+            torch.matmul(a, b, out=c)
+        r = reps if name != "fp32" else max(reps // 5, 2)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(r):
+            torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / r
+        out[name] = {"ms_per_product": ms, "tflops": 2.0 * n ** 3 / ms / 1e9, "products": r}
+        del a, b, c
+        torch.cuda.empty_cache()
+    clocks = None
+    if sampler:
+        sampler.terminate()
+        sampler.wait()
+        clocks = summarise_clocks(clock_path, 0)
+    out["tf32_over_bf16"] = out["tf32"]["tflops"] / out["bf16"]["tflops"]
+    print(json.dumps({"matmul_peaks": out, "n": n, "clocks": clocks,
+                      "gpu": torch.cuda.get_device_name(0)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -698,7 +738,11 @@ def main():
     ap.add_argument("--tune", action="store_true",
                     help="run the library's autotuner on the loaded sample (no cache) before "
                          "timing; its choice is reported in config.autotune")
+    ap.add_argument("--matmul-peaks", action="store_true",
+                    help="time library GEMMs (TF32, BF16, FP32 8192^3) and print their rates")
     args = ap.parse_args()
+    if args.matmul_peaks:
+        return matmul_peaks()
     if args.steps is None:
         args.steps = DEFAULT_STEPS[args.workload] if args.impl == "gb300" else 3
     if args.impl == "reference":
