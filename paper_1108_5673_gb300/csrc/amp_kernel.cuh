@@ -19,10 +19,13 @@ constexpr double kLn2 = 0.69314718055994530942;
 template <int N, int G, int L = 1>
 struct AmpCfg {
     static constexpr int GROUPS = G;                   // consumer groups (tiles in turn)
-    // warps per group: 4; 3 with several components, so that the CTA keeps to
-    // eight warps and the register cap of 255 (a larger CTA is allocated as
-    // twelve warps: 168 registers, and the per-component state spilled)
-    static constexpr int GW = L > 1 ? 3 : 4;
+    // warps per group: 4; 3 with several components or from 32 waves on, so
+    // that a CTA of two groups keeps to eight warps and the register cap of
+    // 255 (a larger CTA is allocated as twelve warps: 168 registers, and the
+    // per-component or per-wave state spilled: 0.5 KB per thread at 32
+    // waves, 1.4 KB at 48; measured 16% faster at 32 waves, 42% at 40, 36%
+    // at 48, but 16% slower at 24, where four-warp groups spill 136 bytes)
+    static constexpr int GW = (L > 1 || N >= 32) ? 3 : 4;
     static constexpr int CW = GROUPS * GW;             // consumer warps
     static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
     static constexpr int ROWS = 2 * N * L;

@@ -34,11 +34,13 @@
 // low sums.
 //
 // Data movement: a persistent grid (one CTA per SM) streams tiles of 256
-// events x 2N planes from the structure-of-arrays store into a ring of
-// shared-memory stages with TMA (cp.async.bulk.tensor.2d); one producer
-// thread issues the copies; GROUPS groups of four consumer warps take tiles
-// in turn, each group cycling through its own stages of the ring. Every wait
-// is bounded (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
+// events x 2N planes (192 events from 32 waves on) from the structure-of-
+// arrays store into a ring of shared-memory stages with TMA
+// (cp.async.bulk.tensor.2d); one producer thread issues the copies; GROUPS
+// groups of four consumer warps (three from 32 waves on) take tiles in turn,
+// each group cycling through its own stages of the ring, or the groups
+// sharing the stages where one per group would fit. Every wait is bounded
+// (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
 //
 // Reductions avoid the FP64 pipe (about 1% of the FP32 rate on this part):
 // integer parts of the log sum are added exactly as integers, the rest as
@@ -77,8 +79,10 @@ cudaError_t configure_n()
     return e;
 }
 
-// Consumer groups per CTA: 2 (9 warps, up to 168 registers per thread) or
-// 3 (13 warps, 128 registers). PWA_AMP_GROUPS overrides the default.
+// Consumer groups per CTA: 2 (10 warps, up to 168 registers per thread; 8
+// warps and 255 registers from 32 waves on) or 3 (14 warps, 128 registers;
+// 11 warps and 168 registers from 32 waves on). PWA_AMP_GROUPS overrides the
+// default.
 int amp_groups()
 {
     static const int g = [] {
@@ -119,9 +123,23 @@ int pad_waves(int n)
 
 }  // namespace
 
+// Events per tile (the tensor map's box), the same for both group counts.
 int amp_box_events(int n_waves)
 {
-    return pad_waves(n_waves) > 0 ? AmpCfg<4, 2>::TE : -1;  // the same for every N and G
+    static_assert(AmpCfg<32, 2>::TE == AmpCfg<32, 3>::TE && AmpCfg<20, 2>::TE == AmpCfg<20, 3>::TE,
+                  "a tile's events do not depend on the group count");
+    switch (pad_waves(n_waves)) {
+    case 4: return AmpCfg<4, 2>::TE;
+    case 8: return AmpCfg<8, 2>::TE;
+    case 12: return AmpCfg<12, 2>::TE;
+    case 16: return AmpCfg<16, 2>::TE;
+    case 20: return AmpCfg<20, 2>::TE;
+    case 24: return AmpCfg<24, 2>::TE;
+    case 32: return AmpCfg<32, 2>::TE;
+    case 40: return AmpCfg<40, 2>::TE;
+    case 48: return AmpCfg<48, 2>::TE;
+    }
+    return -1;
 }
 
 int amp_box_rows(int n_waves) { return 2 * n_waves; }

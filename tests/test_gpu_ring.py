@@ -5,14 +5,16 @@ With one CTA per SM, the parity tests' samples give a CTA one tile or a few,
 so a stage is used once and its barriers never change phase. Here a child
 process forces a grid of three CTAs (PWA_AMP_GRID, read once per process)
 and the consumer groups per CTA (PWA_AMP_GROUPS), so that each CTA streams
-26 to 35 tiles through its ring. The cases cover the ring's shapes:
+26 to 35 tiles through its ring (256-event tiles below 32 waves, 192-event
+ones from 32 waves on and for several components). The cases cover the
+ring's shapes:
   * owned stages (two or more per consumer group; tile j to group j % G and
-    its stage (j / G) % SPG): 4, 12, 13 and 20 waves with two groups, 4 and
-    12 waves with three, incoherent 5 waves x 4 components;
+    its stage (j / G) % SPG): 4, 12, 13, 20, 24 and 32 waves with two
+    groups, 4 and 12 waves with three, incoherent 5 waves x 4 components;
   * shared stages with as many stages as groups: 48 waves with two groups,
     20 and 32 waves with three, incoherent 16 x 3 and 12 x 4;
   * shared stages with more stages than groups (a stage used by different
-    groups in turn, two full barriers per stage): 32 waves with two groups,
+    groups in turn, two full barriers per stage): 40 waves with two groups,
     incoherent 20 x 2 and 12 x 3 (three stages each).
 Each result against the FP64 oracle with the direct form's tolerances:
 |dNLL| <= 1e-3 sqrt(n / 1e6) (floor 2e-6), ||dg|| / ||g_data|| <= 1e-5, and
@@ -36,7 +38,7 @@ pytestmark = pytest.mark.gpu
 GRID = 3
 N_DATA, N_MC = 20_011, 3_000
 # (waves, components, consumer groups)
-CASES = [(4, 1, 2), (12, 1, 2), (13, 1, 2), (20, 1, 2), (32, 1, 2), (48, 1, 2),
+CASES = [(4, 1, 2), (12, 1, 2), (13, 1, 2), (20, 1, 2), (24, 1, 2), (32, 1, 2), (40, 1, 2), (48, 1, 2),
          (4, 1, 3), (12, 1, 3), (20, 1, 3), (32, 1, 3),
          (20, 2, 2), (12, 3, 2), (16, 3, 2), (5, 4, 2), (12, 4, 2)]
 HERE = os.path.dirname(os.path.abspath(__file__))
