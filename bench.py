@@ -74,7 +74,7 @@ TRAFFIC = {"direct": 160.139776e6 + 3.347968e6,
            "incoh": 320.158464e6 + 3.042048e6,
            "incoh_table": None,   # the table kernel's capture is of the coherent sample
            "ampgen": 278.9e6 + 962.9e6,   # FP64-bound; DRAM bytes for reference
-           "direct_4M_32": 1024.210e6 + 3.011584e6,
+           "direct_4M_32": None,   # kernel changed since its capture (four-warp groups, amplitudes re-read)
            "cov_ampgen": 1233.902e6 + 2723.644e6}   # FP64-bound; DRAM bytes for reference
 KERNELS = {"direct": "nll_amp_kernel<20, 2>", "table": "nll_table_kernel<20>",
            "tc": "batched_kernel<64, 2>", "res": "nll_res_tma_kernel<20, 4>",

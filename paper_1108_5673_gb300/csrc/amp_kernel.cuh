@@ -19,13 +19,14 @@ constexpr double kLn2 = 0.69314718055994530942;
 template <int N, int G, int L = 1>
 struct AmpCfg {
     static constexpr int GROUPS = G;                   // consumer groups (tiles in turn)
-    // warps per group: 4; 3 with several components or from 32 waves on, so
+    // warps per group: 4; 3 with several components or from 40 waves on, so
     // that a CTA of two groups keeps to eight warps and the register cap of
-    // 255 (a larger CTA is allocated as twelve warps: 168 registers, and the
-    // per-component or per-wave state spilled: 0.5 KB per thread at 32
-    // waves, 1.4 KB at 48; measured 16% faster at 32 waves, 42% at 40, 36%
-    // at 48, but 16% slower at 24, where four-warp groups spill 136 bytes)
-    static constexpr int GW = (L > 1 || N >= 32) ? 3 : 4;
+    // 255 (a larger CTA is allocated as twelve warps: 168 registers; the
+    // per-component state, or at 40 and 48 waves the per-wave state, does
+    // not fit). Measured on 1 GB samples: four-warp groups at 32 waves
+    // (with the re-read of the amplitudes below) 14% faster than three, and
+    // at 40 and 48 waves three-warp groups 1.7 and 1.6 times faster than four.
+    static constexpr int GW = (L > 1 || N >= 40) ? 3 : 4;
     static constexpr int CW = GROUPS * GW;             // consumer warps
     static constexpr int TE = GW * 32 * 2;             // events per tile (2 per thread)
     static constexpr int ROWS = 2 * N * L;
@@ -440,6 +441,13 @@ __global__ void __launch_bounds__(AmpCfg<N, G, L>::THREADS, 1)
                 }
             }
             if constexpr (L == 1) {
+                // from 32 waves on, the amplitudes are read again from shared
+                // memory rather than held from the pass for S (4N registers,
+                // which spilled: 0.5 KB per thread at 32 waves with four-warp
+                // groups, 1.4 KB at 48); below, holding them is faster (24
+                // waves: 3% slower with the re-read)
+                if constexpr (N >= 32)
+                    asm volatile("" ::: "memory");
                 component_grad(T, rr[0][0], rr[0][1], ri[0][0], ri[0][1]);
             } else {
 #pragma unroll 1

@@ -34,10 +34,10 @@
 // low sums.
 //
 // Data movement: a persistent grid (one CTA per SM) streams tiles of 256
-// events x 2N planes (192 events from 32 waves on) from the structure-of-
+// events x 2N planes (192 events from 40 waves on) from the structure-of-
 // arrays store into a ring of shared-memory stages with TMA
 // (cp.async.bulk.tensor.2d); one producer thread issues the copies; GROUPS
-// groups of four consumer warps (three from 32 waves on) take tiles in turn,
+// groups of four consumer warps (three from 40 waves on) take tiles in turn,
 // each group cycling through its own stages of the ring, or the groups
 // sharing the stages where one per group would fit. Every wait is bounded
 // (FLAG_TIMEOUT) so a stalled pipeline returns instead of hanging.
@@ -80,8 +80,8 @@ cudaError_t configure_n()
 }
 
 // Consumer groups per CTA: 2 (10 warps, up to 168 registers per thread; 8
-// warps and 255 registers from 32 waves on) or 3 (14 warps, 128 registers;
-// 11 warps and 168 registers from 32 waves on). PWA_AMP_GROUPS overrides the
+// warps and 255 registers from 40 waves on) or 3 (14 warps, 128 registers;
+// 11 warps and 168 registers from 40 waves on). PWA_AMP_GROUPS overrides the
 // default.
 int amp_groups()
 {
@@ -126,7 +126,7 @@ int pad_waves(int n)
 // Events per tile (the tensor map's box), the same for both group counts.
 int amp_box_events(int n_waves)
 {
-    static_assert(AmpCfg<32, 2>::TE == AmpCfg<32, 3>::TE && AmpCfg<20, 2>::TE == AmpCfg<20, 3>::TE,
+    static_assert(AmpCfg<40, 2>::TE == AmpCfg<40, 3>::TE && AmpCfg<20, 2>::TE == AmpCfg<20, 3>::TE,
                   "a tile's events do not depend on the group count");
     switch (pad_waves(n_waves)) {
     case 4: return AmpCfg<4, 2>::TE;

@@ -5,17 +5,17 @@ With one CTA per SM, the parity tests' samples give a CTA one tile or a few,
 so a stage is used once and its barriers never change phase. Here a child
 process forces a grid of three CTAs (PWA_AMP_GRID, read once per process)
 and the consumer groups per CTA (PWA_AMP_GROUPS), so that each CTA streams
-26 to 35 tiles through its ring (256-event tiles below 32 waves, 192-event
-ones from 32 waves on and for several components). The cases cover the
+26 to 35 tiles through its ring (256-event tiles below 40 waves, 192-event
+ones from 40 waves on and for several components). The cases cover the
 ring's shapes:
   * owned stages (two or more per consumer group; tile j to group j % G and
-    its stage (j / G) % SPG): 4, 12, 13, 20, 24 and 32 waves with two
-    groups, 4 and 12 waves with three, incoherent 5 waves x 4 components;
+    its stage (j / G) % SPG): 4, 12, 13, 20 and 24 waves with two groups,
+    4 and 12 waves with three, incoherent 5 waves x 4 components;
   * shared stages with as many stages as groups: 48 waves with two groups,
     20 and 32 waves with three, incoherent 16 x 3 and 12 x 4;
   * shared stages with more stages than groups (a stage used by different
-    groups in turn, two full barriers per stage): 40 waves with two groups,
-    incoherent 20 x 2 and 12 x 3 (three stages each).
+    groups in turn, two full barriers per stage): 32 and 40 waves with two
+    groups, incoherent 20 x 2 and 12 x 3 (three stages each).
 Each result against the FP64 oracle with the direct form's tolerances:
 |dNLL| <= 1e-3 sqrt(n / 1e6) (floor 2e-6), ||dg|| / ||g_data|| <= 1e-5, and
 |dg_a| <= 1e-5 c_a per component (grad_bound.py). The event counts leave a
