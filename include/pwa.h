@@ -436,7 +436,7 @@ int pwa_nll_grad_noalloc(const float *d_planes, int64_t plane_pitch, int64_t n_e
  * for the tensor-core form max_k and the precision), and applies a cached
  * choice instead of timing when the key is present. The variants: the
  * direct form's consumer groups per block (2 or 3 groups of four warps,
- * where both fit); the tensor-core form's tile parameters for max_k sets per
+ * three from 40 waves on, where both fit); the tensor-core form's tile parameters for max_k sets per
  * call, the sets per launch (multiples of 64 up to the launch's tensor- and
  * shared-memory limit) and the X pipeline stages (2 up to what shared memory
  * takes); the free-resonance kernel's blocks per SM (1 to 3). The table

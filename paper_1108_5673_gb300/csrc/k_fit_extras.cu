@@ -483,8 +483,9 @@ cudaError_t weights_tma_n(const CUtensorMap *map, const EvalArgs &a, int grid, c
 }  // namespace
 
 // Projection weights through the TMA-fed direct-form kernel (its weights
-// mode): map over the MC planes as for the data (box of 256 events x 2n
-// rows), amax over the MC sample; S by the exact product split.
+// mode): map over the MC planes as for the data (the same box: 256 events,
+// 192 from 40 waves on, x 2n rows), amax over the MC sample; S by the exact
+// product split.
 cudaError_t launch_mc_weights_tma(const CUtensorMap *map, const Planes &mc, const double *V,
                                   const float *amax, double n_gen, float *w, int *status, int grid,
                                   cudaStream_t s)

@@ -305,11 +305,12 @@ int pad_np(int n)
 }
 
 // ---- TMA-fed path: the direct-form kernel with L components per event ------
-// (amp_kernel.cuh): tiles of 256 events x 2 L n rows streamed by TMA, the
+// (amp_kernel.cuh): tiles of 192 events x 2 L n rows streamed by TMA, the
 // products split exactly against sigma (bounded over all components) and
-// their high parts summed as integers, two events per thread in FP32x2. It
-// serves N_pad * L <= 48 (a stage of 2 L N_pad x 256 floats, one per
-// consumer group, in the 200 KB ring).
+// their high parts summed as integers, two events per thread in FP32x2, two
+// groups of three consumer warps. It serves N_pad * L <= 48 (stages of
+// 2 L N_pad x 192 floats in the 200 KB ring, owned by a group where two or
+// more per group fit, shared by both groups otherwise).
 template <int N, int L>
 cudaError_t launch_tma_nl(const CUtensorMap *map, const EvalArgs &a, int grid, cudaStream_t s)
 {

@@ -7,10 +7,10 @@
 //   dNLL/dG_r  = sum w_i 2 Re(conj(S_i) V_r Y_r dBW/dG),  dBW/dG = i M BW^2,
 // with w_i = -1 / I_i for data events and 1 / N_gen for MC events.
 //
-// One persistent CTA per SM streams tiles of 256 events x (1 + 2n) rows (m,
+// One persistent CTA per SM streams tiles of 192 events x (1 + 2n) rows (m,
 // then Re/Im of Y_r for the free waves r < R and of A_a for the fixed waves)
 // from both samples, the data tiles first, into a ring of shared-memory
-// stages with TMA; two groups of four consumer warps take tiles in turn, each
+// stages with TMA; two groups of three consumer warps take tiles in turn, each
 // thread two adjacent events packed in FP32x2 registers:
 //  * BW_r per event with the exact-pair denominator of the per-event kernel
 //    (M^2, M G, (M G)^2 as float pairs, m^2 and D^2 split by FMA, a Newton
