@@ -59,6 +59,9 @@ struct AmpCfg {
     static constexpr bool SHARED = SPG_RAW < 2;
     static constexpr int SPG = SHARED ? 1 : (SPG_RAW > 4 ? 4 : SPG_RAW);
     static constexpr int STAGES = SHARED ? pick_stages() : G * SPG;
+    // the shared ring's parity argument needs 2 STAGES to be a multiple of G
+    // (and at least one stage per group)
+    static_assert(!SHARED || ((2 * STAGES) % G == 0 && STAGES >= G), "shared ring shape");
     static constexpr int THREADS = (CW + 2) * 32;      // + producer warp + helper warp
     static constexpr int NF = 2 * N + 1;               // float partials: ln-fraction, gradient
     static constexpr size_t SMEM = (size_t)STAGES * STAGE_BYTES + 3 * STAGES * sizeof(uint64_t);
